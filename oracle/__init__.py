@@ -1,0 +1,234 @@
+"""The oracle: a plain double-precision CPU implementation of the fluctuating two-species
+D2Q9 lattice Boltzmann step of arXiv:1808.05168 (Sec. II, Eqs. LB, modes-discrete, bar,
+aNI, ne-acc, MRT, noise-bin-expl, noise-bin-expl-high) and of its diagnostics (Sec. III.C
+mean pressure; Appendix structure factors).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the benchmark's CPU
+baseline are the only users; the product library never imports this package.  The C++
+source (``lb_oracle.cpp``) is compiled with ``-O2 -ffp-contract=off`` so that every
+operation rounds as written.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lb_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liblb_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liblb_oracle.so`` (host compiler only)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        c_dbl, c_int, c_i64, c_u64, c_u32, vp = (ctypes.c_double, ctypes.c_int, ctypes.c_int64,
+                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        create_args = [c_int, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_u64, c_u32,
+                       c_int, c_int, c_int]
+        lib.olb_create.argtypes = create_args
+        lib.olb_create.restype = vp
+        lib.olb_destroy.argtypes = [vp]
+        lib.olb_set_sampling.argtypes = [vp, c_i64, c_i64]
+        lib.olb_step.argtypes = [vp, c_i64]
+        lib.olb_time.argtypes = [vp]
+        lib.olb_time.restype = c_i64
+        lib.olb_set_time.argtypes = [vp, c_i64]
+        lib.olb_get_populations.argtypes = [vp, dp]
+        lib.olb_set_populations.argtypes = [vp, dp]
+        lib.olb_mass.argtypes = [vp, dp]
+        lib.olb_fields.argtypes = [vp, dp]
+        lib.olb_structure_factor.argtypes = [vp, c_int, dp]
+        lib.olb_structure_factor.restype = c_i64
+        lib.olb_mean_pressure.argtypes = [vp, dp, dp]
+        lib.olb_mean_pressure.restype = c_i64
+        lib.olb_site_noise.argtypes = [vp, c_int, c_int, c_i64, dp]
+        lib.olb_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.olb_site_normals.argtypes = [c_u64, c_u32, c_u32, c_u32, dp]
+        lib.olb_basis.argtypes = [dp, dp, dp]
+        lib.olb_dft2_power.argtypes = [dp, c_int, c_int, dp]
+        lib.olb_pressure_shift_grad.argtypes = create_args + [c_i64, dp, dp]
+        lib.olb_pressure_shift.argtypes = create_args + [c_i64]
+        lib.olb_pressure_shift.restype = c_dbl
+        _lib = lib
+        return lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+FIELDS = {"rho": 0, "c": 1, "ux": 2, "uz": 3}
+
+
+class OracleLattice:
+    """One lattice of the oracle.  Parameters follow the paper's statement of the problem
+    (Sec. II.A): Lx x Lz sites, relaxation rates (lambda_s, lambda_d, lambda_e, lambda_Q,
+    lambda_eps), thermal energy kT, coupling G and imposed gradient grad_c0."""
+
+    def __init__(self, Lx, Lz, lambda_s=1.0, lambda_d=0.8, lambda_e=None, lambda_q=1.0, lambda_eps=1.0,
+                 kT=0.0, G=0.0, grad_c0=0.0, seed=1, lattice_id=0, astar=True, wall_fixed=False,
+                 noise_loc=False):
+        self.lib = _load()
+        if lambda_e is None:
+            lambda_e = lambda_s
+        self.Lx, self.Lz = int(Lx), int(Lz)
+        self.params = dict(lambda_s=lambda_s, lambda_d=lambda_d, lambda_e=lambda_e, lambda_q=lambda_q,
+                           lambda_eps=lambda_eps, kT=kT, G=G, grad_c0=grad_c0, seed=seed,
+                           lattice_id=lattice_id, astar=astar, wall_fixed=wall_fixed, noise_loc=noise_loc)
+        self.h = self.lib.olb_create(self.Lx, self.Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G,
+                                     grad_c0, seed, lattice_id, int(astar), int(wall_fixed), int(noise_loc))
+        if not self.h:
+            raise ValueError("oracle: bad lattice size")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.olb_destroy(h)
+            self.h = None
+
+    @property
+    def n_sites(self):
+        return self.Lx * self.Lz
+
+    def set_sampling(self, discard, every):
+        self.lib.olb_set_sampling(self.h, int(discard), int(every))
+
+    def step(self, n=1):
+        self.lib.olb_step(self.h, int(n))
+
+    @property
+    def time(self):
+        return int(self.lib.olb_time(self.h))
+
+    @time.setter
+    def time(self, t):
+        self.lib.olb_set_time(self.h, int(t))
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((2, 9, self.Lz, self.Lx), np.float64)
+        self.lib.olb_get_populations(self.h, _dptr(out))
+        return out
+
+    def set_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, 9, self.Lz, self.Lx)
+        self.lib.olb_set_populations(self.h, _dptr(f))
+
+    def mass(self):
+        out = np.empty(2, np.float64)
+        self.lib.olb_mass(self.h, _dptr(out))
+        return out
+
+    def fields(self):
+        """Pre-collision fields of the next step: dict of rhoA, rhoB, ux, uz, p ([Lz, Lx])."""
+        out = np.empty((5, self.Lz, self.Lx), np.float64)
+        self.lib.olb_fields(self.h, _dptr(out))
+        return dict(rhoA=out[0], rhoB=out[1], ux=out[2], uz=out[3], p=out[4])
+
+    def structure_factor(self, field):
+        out = np.empty((self.Lz, self.Lx), np.float64)
+        n = self.lib.olb_structure_factor(self.h, FIELDS[field] if isinstance(field, str) else int(field),
+                                          _dptr(out))
+        return out, int(n)
+
+    def mean_pressure(self):
+        last = ctypes.c_double()
+        avg = ctypes.c_double()
+        n = self.lib.olb_mean_pressure(self.h, ctypes.byref(last), ctypes.byref(avg))
+        return last.value, avg.value, int(n)
+
+    def site_noise(self, x, z, step):
+        out = np.empty(18, np.float64)
+        self.lib.olb_site_noise(self.h, int(x), int(z), int(step), _dptr(out))
+        return out.reshape(2, 9)
+
+
+def philox4x32_10(ctr, key):
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.olb_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def site_normals(seed, lattice_id, site, step):
+    lib = _load()
+    out = np.empty(16, np.float64)
+    lib.olb_site_normals(int(seed), int(lattice_id), int(site), int(step), _dptr(out))
+    return out
+
+
+def basis():
+    lib = _load()
+    T = np.empty((9, 9), np.float64)
+    w = np.empty(9, np.float64)
+    N = np.empty(9, np.float64)
+    lib.olb_basis(_dptr(T), _dptr(w), _dptr(N))
+    return T, w, N
+
+
+def dft2_power(phi: np.ndarray):
+    lib = _load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    Lz, Lx = phi.shape
+    out = np.empty_like(phi)
+    lib.olb_dft2_power(_dptr(phi), int(Lx), int(Lz), _dptr(out))
+    return out
+
+
+def _lattice_args(Lx, Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G, grad_c0, seed, lattice_id,
+                  astar, wall_fixed, noise_loc):
+    if lambda_e is None:
+        lambda_e = lambda_s
+    return (int(Lx), int(Lz), float(lambda_s), float(lambda_d), float(lambda_e), float(lambda_q),
+            float(lambda_eps), float(kT), float(G), float(grad_c0), int(seed), int(lattice_id), int(astar),
+            int(wall_fixed), int(noise_loc))
+
+
+def pressure_shift(Lx, Lz, nsteps, lambda_s=1.0, lambda_d=0.8, lambda_e=None, lambda_q=1.0, lambda_eps=1.0,
+                   kT=1e-5, G=0.5, grad_c0=0.0, seed=5, lattice_id=0, astar=True, wall_fixed=False,
+                   noise_loc=False):
+    """Loss (1/n) sum_t Pbar(t) at kT minus the same at kT = 0, from the rest state."""
+    lib = _load()
+    args = _lattice_args(Lx, Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G, grad_c0, seed,
+                         lattice_id, astar, wall_fixed, noise_loc)
+    return float(lib.olb_pressure_shift(*args, int(nsteps)))
+
+
+def pressure_shift_grad(Lx, Lz, nsteps, lambda_s=1.0, lambda_d=0.8, lambda_e=None, lambda_q=1.0,
+                        lambda_eps=1.0, kT=1e-5, G=0.5, grad_c0=0.0, seed=5, lattice_id=0, astar=True,
+                        wall_fixed=False, noise_loc=False):
+    """(loss, [dL/dG, dL/dlambda_s, dL/dlambda_d]) by forward-mode dual numbers."""
+    lib = _load()
+    args = _lattice_args(Lx, Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G, grad_c0, seed,
+                         lattice_id, astar, wall_fixed, noise_loc)
+    loss = ctypes.c_double()
+    grad = np.empty(3, np.float64)
+    lib.olb_pressure_shift_grad(*args, int(nsteps), ctypes.byref(loss), _dptr(grad))
+    return loss.value, grad
