@@ -1,0 +1,167 @@
+/*
+ * lb.h -- C interface of the GB300 library for the fluctuating two-species D2Q9 lattice
+ * Boltzmann method of Belardinelli, Sbragaglia, Benzi & Ciliberto, "Lattice Boltzmann
+ * simulations of non-equilibrium fluctuations in a non-ideal binary mixture"
+ * (arXiv:1808.05168).
+ *
+ * The problem (Sec. II.A): a binary mixture A/B on an Lx x Lz D2Q9 lattice, periodic in x,
+ * between two solid walls at z = +-Lz/2 (mid-way bounce-back), with an imposed linear
+ * concentration profile c_0(z) = 1/2 + z grad_c0 (Fig. 1), reference density rho_bar = 1.
+ * One step (Eq. LB) streams both species, computes the non-ideal inter-species force
+ * (Eq. aNI, coupling G) with its a* correction (footnote to Eq. ne-acc), the gradient force
+ * (Eq. ne-acc), the barycentric velocity (Eq. bar), and relaxes every moment of Table I at its
+ * own rate (Eq. MRT) with second-order forcing and Gaussian noise whose variances obey the
+ * fluctuation-dissipation theorem (Eqs. noise-bin-expl, noise-bin-expl-high).  The
+ * diagnostics are the structure factors of Appendix A (Eqs. SF1, integral) and the mean
+ * mechanical pressure of Sec. III.C (Eq. EQUATIONofSTATE in the bulk).
+ *
+ * Conventions for every call below:
+ *  - a call returns LB_OK (0) or a negative LB_ERR_* code; nothing aborts or throws;
+ *  - host buffers are owned by the caller; sizes are element counts and are checked;
+ *  - lb_step only enqueues work on the context's stream; calls that return values to the
+ *    host synchronise that stream first;
+ *  - device memory is owned by the context and freed by lb_destroy;
+ *  - a context is used by one host thread at a time.
+ */
+#ifndef LB_GB300_H
+#define LB_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define LB_OK 0
+#define LB_ERR_BAD_PARAM (-1) /* an argument is out of its documented range            */
+#define LB_ERR_OOM (-2)       /* device memory could not be allocated                   */
+#define LB_ERR_CUDA (-3)      /* a CUDA runtime call failed                             */
+#define LB_ERR_NONFINITE (-4) /* a sampled mass or pressure is not finite               */
+#define LB_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up                     */
+#define LB_ERR_SIZE (-6)      /* a caller buffer has the wrong element count            */
+#define LB_ERR_STATE (-7)     /* the call is not valid in the context's current state   */
+
+/* ---- flags of lb_create / lb_create_batch ------------------------------------------- */
+#define LB_PREC_FP64 0x00  /* populations stored and collided in double precision        */
+#define LB_PREC_DEV32 0x01 /* float deviations from the weighted background w_l rho_bar
+                              c^S_0(z); double-precision sums for mass, pressure and the
+                              time averages                                               */
+#define LB_NO_ASTAR 0x02   /* drop the a* diffusion correction (footnote to Eq. ne-acc)   */
+#define LB_WALL_FIXED 0x04 /* wall ghost densities for the non-ideal force take the fixed
+                              wall composition c_0(+-Lz/2) instead of copying the adjacent
+                              fluid row's composition (Sec. II.A)                          */
+#define LB_NOISE_LOC 0x08  /* noise variances with the local densities ("loc", Sec. III.B)
+                              instead of the reference values ("hom")                      */
+#define LB_GRAPH 0x10      /* run lb_step through captured CUDA graphs                     */
+#define LB_PERSISTENT 0x20 /* one cooperative launch per run of steps, all lattices of the
+                              batch, with a bounded grid barrier between steps            */
+#define LB_AUTOTUNE 0x40   /* time the candidate tile shapes on the first lb_step          */
+
+/* ---- structure-factor fields and modes (Appendix A) ---------------------------------- */
+#define LB_FIELD_RHO 0 /* delta rho = rho - rho_bar                                         */
+#define LB_FIELD_C 1   /* delta c = c - c_0(z)                                              */
+#define LB_FIELD_UX 2  /* U_x of Eq. (bar)                                                  */
+#define LB_FIELD_UZ 3  /* U_z of Eq. (bar)                                                  */
+#define LB_SF_QXQZ 0   /* S(q_x, q_z): Lz x Lx doubles, [n][k] at q_z = 2 pi n / Lz,
+                          q_x = 2 pi k / Lx                                                 */
+#define LB_SF_QX 1     /* S(q_x, q_z = 0): Lx doubles                                       */
+
+/* Parameters of one lattice (Sec. II.A, Eq. MRT, Table I).  Relaxation rates lie in (0, 2):
+ * lambda_s (moments 4, 5; viscosity, Eq. vis), lambda_d (moments 1, 2; diffusion, Eq. diff),
+ * lambda_e (moment 3), lambda_q (moments 6, 7), lambda_eps (moment 8).  kT >= 0; G >= 0;
+ * grad_c0 is the imposed gradient (wall-to-wall difference / Lz) with |grad_c0| Lz < 1.
+ * seed keys the Philox4x32-10 noise stream; lattice_id is its third counter word, so two
+ * lattices with one seed and different ids draw independent noise. */
+typedef struct lb_params {
+  int32_t Lx, Lz;
+  double lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps;
+  double kT, G, grad_c0;
+  uint64_t seed;
+  uint32_t lattice_id;
+  uint32_t reserved; /* must be 0 */
+} lb_params;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Create one lattice (lattice_id 0) in the rest state f^S_l = w_l rho_bar c^S_0(z).
+ * Lx >= 1, Lz >= 2, Lx * Lz < 2^31.  *out receives the context (NULL on failure). */
+int lb_create(lb_ctx** out, int Lx, int Lz, double lambda_s, double lambda_d, double lambda_e, double lambda_q,
+              double lambda_eps, double kT, double G, double grad_c0, uint64_t seed, int flags);
+
+/* Create a batch of n >= 1 independent lattices (each may have its own size and
+ * parameters), advanced together by lb_step in one launch per step. */
+int lb_create_batch(lb_ctx** out, int n, const lb_params* params, int flags);
+
+/* Run on a caller-owned cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream);
+ * NULL selects the context's own non-blocking stream (the default after lb_create).
+ * Pending work on the previous stream is waited for first. */
+int lb_set_stream(lb_ctx* ctx, void* cuda_stream);
+
+/* Sample the diagnostics on steps t >= discard with (t - discard) % every == 0; every = 0
+ * turns sampling off (the default).  Sampling uses the pre-collision state of step t. */
+int lb_set_sampling(lb_ctx* ctx, int64_t discard, int64_t every);
+
+/* Fix the tile shape: tile_x columns per block (32, 64, 128 or 256) and rows_per_item rows
+ * per work item (>= 1; larger values are clipped to Lz).  Overrides LB_AUTOTUNE. */
+int lb_set_tile(lb_ctx* ctx, int tile_x, int rows_per_item);
+int lb_get_tile(lb_ctx* ctx, int* tile_x, int* rows_per_item);
+
+/* Advance every lattice by n >= 0 steps (asynchronous on the context's stream). */
+int lb_step(lb_ctx* ctx, int64_t n);
+
+/* Wait for the context's stream; reports a device-side error flag (LB_ERR_TIMEOUT). */
+int lb_synchronize(lb_ctx* ctx);
+
+/* Number of steps taken so far. */
+int lb_time(lb_ctx* ctx, int64_t* t);
+
+int lb_num_lattices(lb_ctx* ctx, int* n);
+int lb_lattice_shape(lb_ctx* ctx, int lattice, int* Lx, int* Lz);
+
+/* Time-averaged structure factor of one field (LB_FIELD_*) of one lattice, as the mean of
+ * |delta phi(q)|^2 over the samples, with the unitary transform (Lx Lz)^(-1/2)
+ * (Appendix A).  n_out must be Lx * Lz for LB_SF_QXQZ and Lx for LB_SF_QX.
+ * *n_samples (may be NULL) receives the sample count. */
+int lb_structure_factor(lb_ctx* ctx, int lattice, int field, int mode, double* host_out, size_t n_out,
+                        int64_t* n_samples);
+
+/* Spatial mean of the mechanical pressure (Sec. III.C) at the latest sample, and its average
+ * over all samples (compensated double-precision sum).  Either pointer may be NULL. */
+int lb_mean_pressure(lb_ctx* ctx, int lattice, double* last, double* time_avg);
+
+/* Per-species total mass sum_r sum_l f^S_l of the stored state, in double precision
+ * (exactly conserved by the method up to rounding, Sec. II.A). */
+int lb_mass(lb_ctx* ctx, int lattice, double out[2]);
+
+/* Copy the stored (post-collision) populations of one lattice as absolute values in double
+ * precision, layout [species][link][z][x] (2 * 9 * Lz * Lx values).  Links follow Fig. 1:
+ * c_0 = 0, c_1 = (1,0), c_2 = (0,1), c_3 = (-1,0), c_4 = (0,-1), c_5 = (1,1), c_6 = (-1,1),
+ * c_7 = (-1,-1), c_8 = (1,-1). */
+int lb_get_populations(lb_ctx* ctx, int lattice, double* host_out, size_t n);
+int lb_set_populations(lb_ctx* ctx, int lattice, const double* host_in, size_t n);
+
+/* Clear the structure-factor and pressure accumulators (the step count is kept). */
+int lb_reset_statistics(lb_ctx* ctx);
+
+/* Number of kernels lb_step has enqueued on the device so far (every step kernel, every
+ * diagnostics kernel, every step-counter update; kernels inside replayed graphs included). */
+int lb_kernel_launches(lb_ctx* ctx, int64_t* n);
+
+/* Bytes of device memory held by the context. */
+int lb_device_bytes(lb_ctx* ctx, size_t* bytes);
+
+const char* lb_error_string(int code);
+void lb_destroy(lb_ctx* ctx);
+
+/* Test hook for the bounded grid barrier of LB_PERSISTENT: launches a grid of `blocks`
+ * co-resident blocks that wait at a barrier expecting `expected` arrivals.  With expected >
+ * blocks the wait must give up after its spin limit and the call returns LB_ERR_TIMEOUT; with
+ * expected == blocks it returns LB_OK. */
+int lb_debug_barrier(int blocks, int expected, int spin_limit);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -58,6 +58,7 @@ def _load():
         lib.olb_time.argtypes = [vp]
         lib.olb_time.restype = c_i64
         lib.olb_set_time.argtypes = [vp, c_i64]
+        lib.olb_set_site_map.argtypes = [vp, c_int, c_int]
         lib.olb_get_populations.argtypes = [vp, dp]
         lib.olb_set_populations.argtypes = [vp, dp]
         lib.olb_mass.argtypes = [vp, dp]
@@ -129,6 +130,10 @@ class OracleLattice:
     @time.setter
     def time(self, t):
         self.lib.olb_set_time(self.h, int(t))
+
+    def set_site_map(self, x0, Lx_global):
+        """Use the noise counters of columns x0.. of a lattice Lx_global wide (window checks)."""
+        self.lib.olb_set_site_map(self.h, int(x0), int(Lx_global))
 
     def populations(self) -> np.ndarray:
         out = np.empty((2, 9, self.Lz, self.Lx), np.float64)

@@ -179,6 +179,9 @@ struct Sim {
   uint64_t seed;
   uint32_t lattice_id;
   bool astar, wall_fixed, noise_loc;
+  // Philox site counter of (x, z) is z * site_Lx + (x + site_x0) mod site_Lx: the identity
+  // map by default; a window of a wider lattice keeps that lattice's counters.
+  int site_x0 = 0, site_Lx = 0;
   double rho_bar = 1.0, c_bar0 = 0.5;  // reference values (Sec. II.A)
   std::vector<R> f;
   int64_t t = 0;
@@ -431,6 +434,12 @@ void sample(Sim<R>& S, const Pre<R>& P) {
 }
 
 template <class R>
+uint32_t site_counter(const Sim<R>& S, int x, int z) {
+  if (S.site_Lx <= 0) return (uint32_t)(z * S.Lx + x);
+  return (uint32_t)((int64_t)z * S.site_Lx + (x + S.site_x0) % S.site_Lx);
+}
+
+template <class R>
 bool is_sample_step(const Sim<R>& S) {
   return S.every > 0 && S.t >= S.discard && (S.t - S.discard) % S.every == 0;
 }
@@ -455,7 +464,7 @@ void step(Sim<R>& S) {
       const int i = z * Lx + x;
       const R Ux = P.Ux[i], Uz = P.Uz[i];
       R xi[2][9];
-      site_noise(S, P.rho[i], P.rho[n + i], (uint32_t)i, (uint32_t)S.t, xi);
+      site_noise(S, P.rho[i], P.rho[n + i], site_counter(S, x, z), (uint32_t)S.t, xi);
       for (int s = 0; s < 2; ++s) {
         R fl[9];
         for (int l = 0; l < 9; ++l) fl[l] = P.fpre[((s * 9 + l) * Lz + z) * Lx + x];
@@ -552,6 +561,12 @@ void olb_step(void* h, int64_t nsteps) {
 }
 
 int64_t olb_time(void* h) { return ((olb_sim*)h)->t; }
+
+void olb_set_site_map(void* h, int x0, int Lx_global) {
+  olb_sim* S = (olb_sim*)h;
+  S->site_x0 = x0;
+  S->site_Lx = Lx_global;
+}
 void olb_set_time(void* h, int64_t t) { ((olb_sim*)h)->t = t; }
 
 void olb_get_populations(void* h, double* out) {
@@ -614,7 +629,7 @@ void olb_site_noise(void* h, int x, int z, int64_t step_index, double* out) {
   compute_pre(*S, P);
   const int n = S->Lx * S->Lz, i = z * S->Lx + x;
   double xi[2][9];
-  site_noise(*S, P.rho[i], P.rho[n + i], (uint32_t)i, (uint32_t)step_index, xi);
+  site_noise(*S, P.rho[i], P.rho[n + i], site_counter(*S, x, z), (uint32_t)step_index, xi);
   for (int s = 0; s < 2; ++s)
     for (int a = 0; a < 9; ++a) out[s * 9 + a] = xi[s][a];
 }

@@ -1,0 +1,145 @@
+"""GB300 (sm_103a) implementation of the fluctuating two-species D2Q9 lattice Boltzmann method
+of Belardinelli, Sbragaglia, Benzi & Ciliberto (arXiv:1808.05168): the fused per-step update
+(Eq. LB with Eq. MRT, forces of Eqs. aNI and ne-acc, FDT noise of Eqs. noise-bin-expl and
+noise-bin-expl-high, mid-way bounce-back walls of Sec. II.A) and its diagnostics (structure
+factors of Appendix A, mean pressure of Sec. III.C).
+
+All arithmetic runs in the CUDA library behind ``include/lb.h``; this package only marshals
+arguments (``capi``) and offers a small object wrapper (:class:`Simulation`).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field as dc_field
+
+import numpy as np
+
+from . import capi
+from .capi import LBError
+
+__all__ = ["LatticeParams", "Simulation", "LBError", "capi"]
+
+
+@dataclass
+class LatticeParams:
+    """One lattice: size, relaxation rates (Eq. MRT, Table I), kT, coupling G (Eq. aNI),
+    imposed gradient grad_c0 (Eq. ne-acc), and the Philox key/counter words of its noise."""
+    Lx: int
+    Lz: int
+    lambda_s: float = 1.0
+    lambda_d: float = 0.8
+    lambda_e: float | None = None   # defaults to lambda_s
+    lambda_q: float = 1.0
+    lambda_eps: float = 1.0
+    kT: float = 0.0
+    G: float = 0.0
+    grad_c0: float = 0.0
+    seed: int = 1
+    lattice_id: int = 0
+
+    def to_c(self) -> capi.lb_params:
+        le = self.lambda_s if self.lambda_e is None else self.lambda_e
+        return capi.lb_params(int(self.Lx), int(self.Lz), float(self.lambda_s), float(self.lambda_d), float(le),
+                              float(self.lambda_q), float(self.lambda_eps), float(self.kT), float(self.G),
+                              float(self.grad_c0), int(self.seed), int(self.lattice_id), 0)
+
+
+FIELDS = {"rho": capi.LB_FIELD_RHO, "c": capi.LB_FIELD_C, "ux": capi.LB_FIELD_UX, "uz": capi.LB_FIELD_UZ}
+
+
+class Simulation:
+    """A batch of lattices advanced together on the GPU (a single lattice is a batch of one)."""
+
+    def __init__(self, lattices, precision: str = "fp64", astar: bool = True, wall_fixed: bool = False,
+                 noise_loc: bool = False, graph: bool = False, persistent: bool = False, autotune: bool = False):
+        if isinstance(lattices, LatticeParams):
+            lattices = [lattices]
+        self.lattices = list(lattices)
+        flags = {"fp64": capi.LB_PREC_FP64, "dev32": capi.LB_PREC_DEV32}[precision]
+        flags |= 0 if astar else capi.LB_NO_ASTAR
+        flags |= capi.LB_WALL_FIXED if wall_fixed else 0
+        flags |= capi.LB_NOISE_LOC if noise_loc else 0
+        flags |= capi.LB_GRAPH if graph else 0
+        flags |= capi.LB_PERSISTENT if persistent else 0
+        flags |= capi.LB_AUTOTUNE if autotune else 0
+        self.flags = flags
+        self.precision = precision
+        self.h = capi.lb_create_batch([p.to_c() for p in self.lattices], flags)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- control
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t handle, or None (own stream)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        capi.lb_set_stream(self.h, handle or 0)
+
+    def set_sampling(self, discard: int, every: int):
+        capi.lb_set_sampling(self.h, discard, every)
+
+    def set_tile(self, tile_x: int, rows_per_item: int):
+        capi.lb_set_tile(self.h, tile_x, rows_per_item)
+
+    def tile(self):
+        return capi.lb_get_tile(self.h)
+
+    def step(self, n: int = 1):
+        capi.lb_step(self.h, n)
+
+    def synchronize(self):
+        capi.lb_synchronize(self.h)
+
+    @property
+    def time(self) -> int:
+        return capi.lb_time(self.h)
+
+    def reset_statistics(self):
+        capi.lb_reset_statistics(self.h)
+
+    def device_bytes(self) -> int:
+        return capi.lb_device_bytes(self.h)
+
+    def kernel_launches(self) -> int:
+        return capi.lb_kernel_launches(self.h)
+
+    # ---- results
+    def shape(self, lattice: int = 0):
+        return capi.lb_lattice_shape(self.h, lattice)
+
+    def structure_factor(self, field: str = "c", lattice: int = 0, qz0_only: bool = False):
+        Lx, Lz = self.shape(lattice)
+        out = np.empty(Lx if qz0_only else (Lz, Lx), np.float64)
+        n = capi.lb_structure_factor(self.h, lattice, FIELDS.get(field, field),
+                                     capi.LB_SF_QX if qz0_only else capi.LB_SF_QXQZ, out)
+        return out, n
+
+    def mean_pressure(self, lattice: int = 0):
+        return capi.lb_mean_pressure(self.h, lattice)
+
+    def mass(self, lattice: int = 0):
+        return capi.lb_mass(self.h, lattice)
+
+    def populations(self, lattice: int = 0) -> np.ndarray:
+        Lx, Lz = self.shape(lattice)
+        out = np.empty((2, 9, Lz, Lx), np.float64)
+        capi.lb_get_populations(self.h, lattice, out)
+        return out
+
+    def set_populations(self, f: np.ndarray, lattice: int = 0):
+        Lx, Lz = self.shape(lattice)
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, 9, Lz, Lx)
+        capi.lb_set_populations(self.h, lattice, f)

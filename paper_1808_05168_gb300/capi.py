@@ -1,0 +1,237 @@
+"""ctypes binding of the C interface in ``include/lb.h`` -- argument marshalling only.
+
+Every function here has the name of the C call it wraps and raises :class:`LBError` on a
+non-zero status.  The library must have been built (``paper_1808_05168_gb300.build``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+LB_OK = 0
+LB_ERR_BAD_PARAM = -1
+LB_ERR_OOM = -2
+LB_ERR_CUDA = -3
+LB_ERR_NONFINITE = -4
+LB_ERR_TIMEOUT = -5
+LB_ERR_SIZE = -6
+LB_ERR_STATE = -7
+
+LB_PREC_FP64 = 0x00
+LB_PREC_DEV32 = 0x01
+LB_NO_ASTAR = 0x02
+LB_WALL_FIXED = 0x04
+LB_NOISE_LOC = 0x08
+LB_GRAPH = 0x10
+LB_PERSISTENT = 0x20
+LB_AUTOTUNE = 0x40
+
+LB_FIELD_RHO, LB_FIELD_C, LB_FIELD_UX, LB_FIELD_UZ = 0, 1, 2, 3
+LB_SF_QXQZ, LB_SF_QX = 0, 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblb_gb300.so")
+
+# Every symbol declared in include/lb.h.
+EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "lb_set_tile", "lb_get_tile",
+           "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
+           "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
+           "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier")
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, call: str):
+        self.code = code
+        msg = _lib.lb_error_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{call}: {msg} ({code})")
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int32), ("Lz", ctypes.c_int32), ("lambda_s", ctypes.c_double),
+                ("lambda_d", ctypes.c_double), ("lambda_e", ctypes.c_double), ("lambda_q", ctypes.c_double),
+                ("lambda_eps", ctypes.c_double), ("kT", ctypes.c_double), ("G", ctypes.c_double),
+                ("grad_c0", ctypes.c_double), ("seed", ctypes.c_uint64), ("lattice_id", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -m paper_1808_05168_gb300.build`)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i, i64, u64, d, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
+                                  ctypes.c_size_t)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "lb_create": [ctypes.POINTER(vp), i, i, d, d, d, d, d, d, d, d, u64, i],
+            "lb_create_batch": [ctypes.POINTER(vp), i, ctypes.POINTER(lb_params), i],
+            "lb_set_stream": [vp, vp],
+            "lb_set_sampling": [vp, i64, i64],
+            "lb_set_tile": [vp, i, i],
+            "lb_get_tile": [vp, ip, ip],
+            "lb_step": [vp, i64],
+            "lb_synchronize": [vp],
+            "lb_time": [vp, i64p],
+            "lb_num_lattices": [vp, ip],
+            "lb_lattice_shape": [vp, i, ip, ip],
+            "lb_structure_factor": [vp, i, i, i, dp, sz, i64p],
+            "lb_mean_pressure": [vp, i, dp, dp],
+            "lb_mass": [vp, i, dp],
+            "lb_get_populations": [vp, i, dp, sz],
+            "lb_set_populations": [vp, i, dp, sz],
+            "lb_reset_statistics": [vp],
+            "lb_device_bytes": [vp, ctypes.POINTER(sz)],
+            "lb_kernel_launches": [vp, i64p],
+            "lb_destroy": [vp],
+            "lb_debug_barrier": [i, i, i],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = None if name == "lb_destroy" else ctypes.c_int
+        lib.lb_error_string.argtypes = [ctypes.c_int]
+        lib.lb_error_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, call: str):
+    if rc != LB_OK:
+        raise LBError(rc, call)
+
+
+def _dptr(a: np.ndarray):
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 array")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def lb_create(Lx, Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G, grad_c0, seed, flags):
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.lb_create(ctypes.byref(h), int(Lx), int(Lz), float(lambda_s), float(lambda_d), float(lambda_e),
+                         float(lambda_q), float(lambda_eps), float(kT), float(G), float(grad_c0), int(seed),
+                         int(flags)), "lb_create")
+    return h
+
+
+def lb_create_batch(params, flags):
+    lib = load()
+    arr = (lb_params * len(params))(*params)
+    h = ctypes.c_void_p()
+    _check(lib.lb_create_batch(ctypes.byref(h), len(params), arr, int(flags)), "lb_create_batch")
+    return h
+
+
+def lb_set_stream(h, stream_handle):
+    _check(load().lb_set_stream(h, ctypes.c_void_p(int(stream_handle) if stream_handle else 0)), "lb_set_stream")
+
+
+def lb_set_sampling(h, discard, every):
+    _check(load().lb_set_sampling(h, int(discard), int(every)), "lb_set_sampling")
+
+
+def lb_set_tile(h, tile_x, rows_per_item):
+    _check(load().lb_set_tile(h, int(tile_x), int(rows_per_item)), "lb_set_tile")
+
+
+def lb_get_tile(h):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().lb_get_tile(h, ctypes.byref(a), ctypes.byref(b)), "lb_get_tile")
+    return a.value, b.value
+
+
+def lb_step(h, n):
+    _check(load().lb_step(h, int(n)), "lb_step")
+
+
+def lb_synchronize(h):
+    _check(load().lb_synchronize(h), "lb_synchronize")
+
+
+def lb_time(h):
+    t = ctypes.c_int64()
+    _check(load().lb_time(h, ctypes.byref(t)), "lb_time")
+    return t.value
+
+
+def lb_num_lattices(h):
+    n = ctypes.c_int()
+    _check(load().lb_num_lattices(h, ctypes.byref(n)), "lb_num_lattices")
+    return n.value
+
+
+def lb_lattice_shape(h, lattice):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().lb_lattice_shape(h, int(lattice), ctypes.byref(a), ctypes.byref(b)), "lb_lattice_shape")
+    return a.value, b.value
+
+
+def lb_structure_factor(h, lattice, field, mode, out: np.ndarray):
+    n = ctypes.c_int64()
+    _check(load().lb_structure_factor(h, int(lattice), int(field), int(mode), _dptr(out), out.size, ctypes.byref(n)),
+           "lb_structure_factor")
+    return n.value
+
+
+def lb_mean_pressure(h, lattice):
+    last, avg = ctypes.c_double(), ctypes.c_double()
+    _check(load().lb_mean_pressure(h, int(lattice), ctypes.byref(last), ctypes.byref(avg)), "lb_mean_pressure")
+    return last.value, avg.value
+
+
+def lb_mass(h, lattice):
+    out = np.empty(2, np.float64)
+    _check(load().lb_mass(h, int(lattice), _dptr(out)), "lb_mass")
+    return out
+
+
+def lb_get_populations(h, lattice, out: np.ndarray):
+    _check(load().lb_get_populations(h, int(lattice), _dptr(out), out.size), "lb_get_populations")
+
+
+def lb_set_populations(h, lattice, src: np.ndarray):
+    _check(load().lb_set_populations(h, int(lattice), _dptr(src), src.size), "lb_set_populations")
+
+
+def lb_reset_statistics(h):
+    _check(load().lb_reset_statistics(h), "lb_reset_statistics")
+
+
+def lb_device_bytes(h):
+    n = ctypes.c_size_t()
+    _check(load().lb_device_bytes(h, ctypes.byref(n)), "lb_device_bytes")
+    return n.value
+
+
+def lb_kernel_launches(h):
+    n = ctypes.c_int64()
+    _check(load().lb_kernel_launches(h, ctypes.byref(n)), "lb_kernel_launches")
+    return n.value
+
+
+def lb_error_string(code):
+    return load().lb_error_string(int(code)).decode()
+
+
+def lb_destroy(h):
+    if h:
+        load().lb_destroy(h)
+
+
+def lb_debug_barrier(blocks, expected, limit_ms):
+    return int(load().lb_debug_barrier(int(blocks), int(expected), int(limit_ms)))

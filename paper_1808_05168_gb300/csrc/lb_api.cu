@@ -1,0 +1,904 @@
+// lb_api.cu -- host runtime behind the C interface of lb.h: contexts, device memory, work
+// decomposition, step scheduling (direct launches, CUDA graphs, or one cooperative
+// persistent launch per run of steps), sampling, autotuning of the tile shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "lb_internal.cuh"
+
+using namespace lbk;
+
+namespace {
+
+const double kRhoBar = 1.0;  // reference total density (Sec. II.A)
+const double kCBar0 = 0.5;   // reference concentration c_0(z = 0) (Sec. II.A)
+const double kNorm[9] = {1.0, 1.0 / 3, 1.0 / 3, 4.0, 4.0 / 9, 1.0 / 9, 2.0 / 3, 2.0 / 3, 16.0};  // N_a, Table I
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+struct GraphKey {
+  int64_t nsteps;
+  int64_t sample_mask;  // bit k: step k of the segment samples (segments of <= 63 steps)
+  int cur;
+  int mode;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(nsteps, sample_mask, cur, mode) < std::tie(o.nsteps, o.sample_mask, o.cur, o.mode);
+  }
+};
+
+}  // namespace
+
+struct lb_ctx {
+  int n_lat = 0;
+  int flags = 0;
+  bool dev32 = false;
+  std::vector<lb_params> params;
+  std::vector<int64_t> f_off, site_off;
+  std::vector<int> row_off;
+  int64_t n_f = 0, n_sites = 0;
+  int n_rows = 0;
+  int max_lattice_sites = 0;
+
+  // tiles
+  int tile_x = 128, rows_per_item = 64;
+  bool tile_fixed = false, tuned = false;
+  std::vector<WorkItem> items;
+
+  // device memory
+  void* d_lat = nullptr;    // LatticeDev<real>[n_lat]
+  void* d_rows = nullptr;   // RowConst<real>[n_rows]
+  WorkItem* d_items = nullptr;
+  int d_items_cap = 0;
+  void* f[2] = {nullptr, nullptr};
+  void* fields = nullptr;   // 4 * n_sites reals
+  void* tmp = nullptr;      // 4 * n_sites complex
+  double* acc_sum = nullptr;
+  double* acc_comp = nullptr;
+  double* partials = nullptr;
+  int partials_cap = 0;
+  DiagStats* stats = nullptr;
+  DiagLattice* d_diag = nullptr;
+  int2* d_row_tasks = nullptr;
+  int2* d_col_tasks = nullptr;
+  int n_row_tasks = 0, n_col_tasks = 0;
+  int max_Lx = 0, max_Lz = 0;
+  int64_t* d_t = nullptr;
+  unsigned* d_barrier = nullptr;
+  int* d_err = nullptr;
+  double* d_scratch = nullptr;  // 18 * max_lattice_sites doubles (populations I/O)
+  double* d_mass = nullptr;
+  size_t bytes = 0;
+
+  std::vector<DiagLattice> diag;
+  bool diag_ready = false;
+  int cur = 0;
+  int64_t t = 0, discard = 0, every = 0, nsamples = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  int coop_grid = -1;
+  bool noise_any = false;
+  std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;  // graph, kernels in it
+  int64_t launches = 0;  // kernels enqueued by lb_step so far (graph replays included)
+};
+
+namespace {
+
+template <class T>
+int dev_alloc(lb_ctx* c, T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return LB_ERR_OOM;
+  }
+  c->bytes += bytes;
+  return LB_OK;
+}
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return LB_OK;
+  return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+}
+
+int check_params(const lb_params& p) {
+  auto rate_ok = [](double l) { return std::isfinite(l) && l > 0.0 && l < 2.0; };
+  if (p.Lx < 1 || p.Lz < 2) return LB_ERR_BAD_PARAM;
+  if ((int64_t)p.Lx * p.Lz * 18 >= (int64_t)1 << 31) return LB_ERR_BAD_PARAM;
+  if (!rate_ok(p.lambda_s) || !rate_ok(p.lambda_d) || !rate_ok(p.lambda_e) || !rate_ok(p.lambda_q) ||
+      !rate_ok(p.lambda_eps))
+    return LB_ERR_BAD_PARAM;
+  if (!std::isfinite(p.kT) || p.kT < 0.0) return LB_ERR_BAD_PARAM;
+  if (!std::isfinite(p.G) || p.G < 0.0) return LB_ERR_BAD_PARAM;
+  if (!std::isfinite(p.grad_c0) || std::fabs(p.grad_c0) * p.Lz >= 1.0) return LB_ERR_BAD_PARAM;
+  if (p.reserved != 0) return LB_ERR_BAD_PARAM;
+  return LB_OK;
+}
+
+double c0_of(const lb_params& p, double z) { return kCBar0 + z * p.grad_c0; }
+
+// Per-lattice device constants (Eqs. MRT, noise-bin-expl, noise-bin-expl-high, ne-acc).
+template <class real>
+LatticeDev<real> make_lattice(const lb_params& p, int flags, bool dev, int64_t f_off, int64_t site_off, int row_off) {
+  LatticeDev<real> L;
+  std::memset(&L, 0, sizeof(L));
+  L.Lx = p.Lx;
+  L.Lz = p.Lz;
+  L.f_off = f_off;
+  L.site_off = site_off;
+  L.row_off = row_off;
+  L.flags = 0;
+  if (!(flags & LB_NO_ASTAR)) L.flags |= DF_ASTAR;
+  if (flags & LB_WALL_FIXED) L.flags |= DF_WALL_FIXED;
+  if (flags & LB_NOISE_LOC) L.flags |= DF_NOISE_LOC;
+  if (p.kT > 0) L.flags |= DF_NOISE;
+  L.key0 = (uint32_t)(p.seed & 0xffffffffu);
+  L.key1 = (uint32_t)(p.seed >> 32);
+  L.lattice_id = p.lattice_id;
+  const double lam[9] = {1.0, p.lambda_d, p.lambda_d, p.lambda_e, p.lambda_s, p.lambda_s, p.lambda_q, p.lambda_q,
+                         p.lambda_eps};
+  for (int a = 0; a < 9; ++a) {
+    L.lam[a] = (real)lam[a];
+    L.omh[a] = (real)(1.0 - 0.5 * lam[a]);
+  }
+  L.G = (real)p.G;
+  L.g3 = (real)(p.grad_c0 / 3.0);
+  L.k9 = dev ? (real)(kRhoBar * p.grad_c0 / 9.0) : (real)0;
+  L.k36 = dev ? (real)(kRhoBar * p.grad_c0 / 36.0) : (real)0;
+  L.rho_bar_off = dev ? (real)0 : (real)kRhoBar;
+  const double rA = kRhoBar * kCBar0, rB = kRhoBar * (1.0 - kCBar0);
+  const double ld = p.lambda_d;
+  L.sig_mom = (real)std::sqrt((2.0 - ld) * ld * p.kT * rA * rB / (rA + rB));
+  L.pref_mom = (real)std::sqrt((2.0 - ld) * ld * p.kT);
+  for (int a = 3; a < 9; ++a) {
+    const double v = 3.0 * (2.0 - lam[a]) * lam[a] * kNorm[a] * p.kT;
+    L.sig[0][a] = (real)std::sqrt(v * rA);
+    L.sig[1][a] = (real)std::sqrt(v * rB);
+    L.pref[a] = (real)std::sqrt(v);
+  }
+  return L;
+}
+
+// Per-row background constants in double, with the wall ghosts of Sec. II.A.
+struct RowD {
+  double bgA, bgB, dbgA, dbgB, nbA, nbB, c0, ghost_cA, Pbg;
+};
+
+std::vector<RowD> make_rows(const lb_params& p, int flags, bool dev) {
+  const int Lz = p.Lz;
+  const bool fixed = flags & LB_WALL_FIXED;
+  const double cw_bot = c0_of(p, -0.5 * Lz), cw_top = c0_of(p, 0.5 * Lz);
+  auto bg = [&](int s, int z) -> double {  // z in -1..Lz
+    if (!dev) return 0.0;
+    double c;
+    if (z < 0) c = fixed ? cw_bot : c0_of(p, 0 + 0.5 - 0.5 * Lz);
+    else if (z >= Lz) c = fixed ? cw_top : c0_of(p, (Lz - 1) + 0.5 - 0.5 * Lz);
+    else c = c0_of(p, z + 0.5 - 0.5 * Lz);
+    return kRhoBar * (s == 0 ? c : 1.0 - c);
+  };
+  std::vector<RowD> rows(Lz);
+  for (int z = 0; z < Lz; ++z) {
+    RowD r;
+    r.c0 = c0_of(p, z + 0.5 - 0.5 * Lz);
+    r.bgA = bg(0, z);
+    r.bgB = bg(1, z);
+    r.dbgA = (bg(0, z + 1) - bg(0, z - 1)) / 6.0;
+    r.dbgB = (bg(1, z + 1) - bg(1, z - 1)) / 6.0;
+    r.nbA = 2.0 / 9.0 * (bg(0, z - 1) + bg(0, z) + bg(0, z + 1));
+    r.nbB = 2.0 / 9.0 * (bg(1, z - 1) + bg(1, z) + bg(1, z + 1));
+    r.ghost_cA = (z == 0) ? cw_bot : (z == Lz - 1 ? cw_top : 0.0);
+    r.Pbg = (r.bgA + r.bgB) / 3.0 + 0.25 * p.G * (r.bgA * r.nbB + r.bgB * r.nbA);
+    rows[z] = r;
+  }
+  return rows;
+}
+
+template <class real>
+int upload_tables(lb_ctx* c) {
+  std::vector<LatticeDev<real>> lat(c->n_lat);
+  std::vector<RowConst<real>> rows(c->n_rows);
+  c->diag.assign(c->n_lat, DiagLattice());
+  for (int i = 0; i < c->n_lat; ++i) {
+    const lb_params& p = c->params[i];
+    lat[i] = make_lattice<real>(p, c->flags, c->dev32, c->f_off[i], c->site_off[i], c->row_off[i]);
+    const std::vector<RowD> rd = make_rows(p, c->flags, c->dev32);
+    double Pbg = 0.0, mA = 0.0, mB = 0.0;
+    for (int z = 0; z < p.Lz; ++z) {
+      const RowD& r = rd[z];
+      RowConst<real> rc;
+      rc.bgA = (real)r.bgA; rc.bgB = (real)r.bgB;
+      rc.dbgA = (real)r.dbgA; rc.dbgB = (real)r.dbgB;
+      rc.nbA = (real)r.nbA; rc.nbB = (real)r.nbB;
+      rc.c0 = (real)r.c0; rc.ghost_cA = (real)r.ghost_cA;
+      rows[c->row_off[i] + z] = rc;
+      Pbg += r.Pbg;
+      mA += r.bgA;
+      mB += r.bgB;
+    }
+    DiagLattice& d = c->diag[i];
+    d.Lx = p.Lx;
+    d.Lz = p.Lz;
+    d.site_off = c->site_off[i];
+    d.P_bg_mean = Pbg / p.Lz;
+    d.mass_bg[0] = mA * p.Lx;
+    d.mass_bg[1] = mB * p.Lx;
+    d.n_sites = (double)p.Lx * p.Lz;
+  }
+  int rc = dev_alloc(c, (char**)&c->d_lat, lat.size() * sizeof(LatticeDev<real>));
+  if (rc) return rc;
+  rc = dev_alloc(c, (char**)&c->d_rows, rows.size() * sizeof(RowConst<real>));
+  if (rc) return rc;
+  if (cudaMemcpy(c->d_lat, lat.data(), lat.size() * sizeof(LatticeDev<real>), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LB_ERR_CUDA;
+  if (cudaMemcpy(c->d_rows, rows.data(), rows.size() * sizeof(RowConst<real>), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return LB_ERR_CUDA;
+  return LB_OK;
+}
+
+void drop_graphs(lb_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+}
+
+// Work items: lattices with more rows per item first (longest work first), each lattice's
+// items contiguous so that its partial sums can be reduced in a fixed order.
+int build_items(lb_ctx* c, int tile_x, int rows) {
+  std::vector<int> order(c->n_lat);
+  for (int i = 0; i < c->n_lat; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return std::min(rows, c->params[a].Lz) > std::min(rows, c->params[b].Lz);
+  });
+  std::vector<WorkItem> items;
+  std::vector<std::pair<int, int>> range(c->n_lat);
+  for (int i : order) {
+    const lb_params& p = c->params[i];
+    const int begin = (int)items.size();
+    for (int z0 = 0; z0 < p.Lz; z0 += rows)
+      for (int x0 = 0; x0 < p.Lx; x0 += tile_x) items.push_back(WorkItem{i, x0, z0, std::min(z0 + rows, p.Lz)});
+    range[i] = {begin, (int)items.size()};
+  }
+  if ((int)items.size() > c->d_items_cap) {
+    if (c->d_items) {
+      cudaFree(c->d_items);
+      c->bytes -= (size_t)c->d_items_cap * sizeof(WorkItem);
+    }
+    int rc = dev_alloc(c, &c->d_items, items.size() * sizeof(WorkItem));
+    if (rc) return rc;
+    c->d_items_cap = (int)items.size();
+  }
+  if ((int)items.size() > c->partials_cap) {
+    if (c->partials) {
+      cudaFree(c->partials);
+      c->bytes -= (size_t)c->partials_cap * 3 * sizeof(double);
+    }
+    int rc = dev_alloc(c, &c->partials, items.size() * 3 * sizeof(double));
+    if (rc) return rc;
+    c->partials_cap = (int)items.size();
+  }
+  if (cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LB_ERR_CUDA;
+  c->items = items;
+  for (int i = 0; i < c->n_lat; ++i) {
+    c->diag[i].item_begin = range[i].first;
+    c->diag[i].item_end = range[i].second;
+  }
+  if (c->d_diag &&
+      cudaMemcpy(c->d_diag, c->diag.data(), c->diag.size() * sizeof(DiagLattice), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return LB_ERR_CUDA;
+  c->tile_x = tile_x;
+  c->rows_per_item = rows;
+  c->coop_grid = -1;
+  drop_graphs(c);
+  return LB_OK;
+}
+
+int alloc_diag(lb_ctx* c) {
+  if (c->diag_ready) return LB_OK;
+  const size_t rs = c->dev32 ? sizeof(float) : sizeof(double);
+  int rc = dev_alloc(c, (char**)&c->fields, 4 * (size_t)c->n_sites * rs);
+  if (!rc) rc = dev_alloc(c, (char**)&c->tmp, 4 * (size_t)c->n_sites * 2 * rs);
+  if (!rc) rc = dev_alloc(c, &c->acc_sum, 4 * (size_t)c->n_sites * sizeof(double));
+  if (!rc) rc = dev_alloc(c, &c->acc_comp, 4 * (size_t)c->n_sites * sizeof(double));
+  if (rc) return rc;
+  std::vector<int2> rt, ct;
+  for (int i = 0; i < c->n_lat; ++i) {
+    for (int k = 0; k < 4 * c->params[i].Lz; ++k) rt.push_back(make_int2(i, k));
+    for (int k = 0; k < 4 * c->params[i].Lx; ++k) ct.push_back(make_int2(i, k));
+  }
+  rc = dev_alloc(c, &c->d_row_tasks, rt.size() * sizeof(int2));
+  if (!rc) rc = dev_alloc(c, &c->d_col_tasks, ct.size() * sizeof(int2));
+  if (rc) return rc;
+  if (cudaMemcpy(c->d_row_tasks, rt.data(), rt.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_col_tasks, ct.data(), ct.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LB_ERR_CUDA;
+  c->n_row_tasks = (int)rt.size();
+  c->n_col_tasks = (int)ct.size();
+  if (cudaMemset(c->acc_sum, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess ||
+      cudaMemset(c->acc_comp, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess)
+    return LB_ERR_CUDA;
+  c->diag_ready = true;
+  return LB_OK;
+}
+
+bool is_sample(const lb_ctx* c, int64_t t) {
+  return c->every > 0 && t >= c->discard && (t - c->discard) % c->every == 0;
+}
+
+template <class real>
+StepArgs<real> step_args(lb_ctx* c, int cur, int t_offset) {
+  StepArgs<real> a;
+  a.lat = (const LatticeDev<real>*)c->d_lat;
+  a.rows = (const RowConst<real>*)c->d_rows;
+  a.items = c->d_items;
+  a.n_items = (int)c->items.size();
+  a.src = (const real*)c->f[cur];
+  a.dst = (real*)c->f[cur ^ 1];
+  a.d_t = c->d_t;
+  a.t_offset = t_offset;
+  a.fields = (real*)c->fields;
+  a.partials = c->partials;
+  return a;
+}
+
+template <class real>
+cudaError_t enqueue_sample(lb_ctx* c) {
+  SfPlan p;
+  p.lat = c->d_diag;
+  p.row_tasks = c->d_row_tasks;
+  p.col_tasks = c->d_col_tasks;
+  p.n_row_tasks = c->n_row_tasks;
+  p.n_col_tasks = c->n_col_tasks;
+  p.max_Lx = c->max_Lx;
+  p.max_Lz = c->max_Lz;
+  cudaError_t e = launch_sf<real>(p, (const real*)c->fields, c->tmp, c->acc_sum, c->acc_comp, c->stream);
+  if (e != cudaSuccess) return e;
+  c->launches += 3;
+  return launch_finalize(c->d_diag, c->n_lat, c->partials, c->stats, c->stream);
+}
+
+// Enqueue `n` steps starting from buffer `cur`, with sampling by the bit mask.  Direct
+// launches: one step kernel per step.
+template <class real>
+cudaError_t enqueue_direct(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& sample_offsets) {
+  size_t si = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    const bool sample = si < sample_offsets.size() && sample_offsets[si] == k;
+    if (sample) ++si;
+    cudaError_t e = launch_step<real>(step_args<real>(c, cur, (int)k), c->tile_x, sample, c->noise_any, c->stream);
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+    if (sample) {
+      e = enqueue_sample<real>(c);
+      if (e != cudaSuccess) return e;
+    }
+    cur ^= 1;
+  }
+  c->launches += 1;
+  return launch_advance(c->d_t, n, c->stream);
+}
+
+// Persistent: one cooperative launch per run of steps ending with (at most) one sample step.
+template <class real>
+cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& sample_offsets) {
+  if (c->coop_grid < 0) c->coop_grid = persistent_grid<real>(c->tile_x, false, c->noise_any);
+  const int grid = std::min<int>(c->coop_grid, (int)c->items.size());
+  if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
+  int64_t k = 0;
+  size_t si = 0;
+  while (k < n) {
+    int64_t end = n;  // exclusive
+    bool sample = false;
+    if (si < sample_offsets.size()) {
+      end = sample_offsets[si] + 1;
+      sample = true;
+      ++si;
+    }
+    const int64_t len = end - k;
+    cudaError_t e = cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)len, sample, c->noise_any,
+                                     c->d_barrier, c->d_err, grid, 2000, c->stream);
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+    if (sample) {
+      e = enqueue_sample<real>(c);
+      if (e != cudaSuccess) return e;
+    }
+    if (len & 1) cur ^= 1;
+    k = end;
+  }
+  c->launches += 1;
+  return launch_advance(c->d_t, n, c->stream);
+}
+
+template <class real>
+cudaError_t enqueue(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& so, bool persistent) {
+  return persistent ? enqueue_persistent<real>(c, cur, n, so) : enqueue_direct<real>(c, cur, n, so);
+}
+
+template <class real>
+int autotune(lb_ctx* c) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int64_t, int, int, int, bool>, std::pair<int, int>> cache;
+  const auto key = std::make_tuple(c->n_lat, c->n_sites, c->max_Lx, c->max_Lz, (int)c->dev32, c->noise_any);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return build_items(c, it->second.first, it->second.second);
+  }
+  const int txs[] = {64, 128, 256};
+  const int rows[] = {8, 16, 32, 64, 128, 256, 1 << 30};
+  float best = 1e30f;
+  int bx = c->tile_x, br = c->rows_per_item;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int tx : txs) {
+    if (tx > 2 * c->max_Lx && tx > 64) continue;
+    int last = -1;
+    for (int r : rows) {
+      const int rr = std::min(r, c->max_Lz);
+      if (rr == last) continue;
+      last = rr;
+      if (build_items(c, tx, rr) != LB_OK) continue;
+      // state is untouched: every trial reads f[cur] and writes f[cur ^ 1]
+      for (int k = 0; k < 2; ++k) launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_any, c->stream);
+      cudaEventRecord(e0, c->stream);
+      const int reps = 4;
+      for (int k = 0; k < reps; ++k)
+        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_any, c->stream);
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bx = tx;
+        br = rr;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = {bx, br};
+  }
+  return build_items(c, bx, br);
+}
+
+template <class real>
+int step_impl(lb_ctx* c, int64_t n) {
+  if (c->flags & LB_AUTOTUNE && !c->tuned && !c->tile_fixed) {
+    int rc = autotune<real>(c);
+    if (rc) return rc;
+    c->tuned = true;
+  }
+  const bool persistent = c->flags & LB_PERSISTENT;
+  const bool graph = c->flags & LB_GRAPH;
+  int64_t done = 0;
+  while (done < n) {
+    // segment: up to 63 steps (graph) or everything left (direct)
+    const int64_t seg = graph ? std::min<int64_t>(n - done, 63) : (n - done);
+    std::vector<int64_t> so;
+    int64_t mask = 0;
+    for (int64_t k = 0; k < seg; ++k)
+      if (is_sample(c, c->t + done + k)) {
+        so.push_back(k);
+        if (k < 63) mask |= (int64_t)1 << k;
+      }
+    if (!so.empty() && !c->diag_ready) return LB_ERR_STATE;
+    cudaError_t e;
+    if (graph) {
+      const GraphKey key{seg, mask, c->cur, persistent ? 1 : 0};
+      auto it = c->graphs.find(key);
+      if (it == c->graphs.end()) {
+        cudaGraph_t gr;
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_err(e);
+        const int64_t before = c->launches;
+        cudaError_t ee = enqueue<real>(c, c->cur, seg, so, persistent);
+        const int64_t in_graph = c->launches - before;
+        c->launches = before;
+        e = cudaStreamEndCapture(c->stream, &gr);
+        if (ee != cudaSuccess) return cuda_err(ee);
+        if (e != cudaSuccess) return cuda_err(e);
+        cudaGraphExec_t ex;
+        e = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return cuda_err(e);
+        if (c->graphs.size() > 32) drop_graphs(c);
+        it = c->graphs.emplace(key, std::make_pair(ex, in_graph)).first;
+      }
+      e = cudaGraphLaunch(it->second.first, c->stream);
+      c->launches += it->second.second;
+    } else {
+      e = enqueue<real>(c, c->cur, seg, so, persistent);
+    }
+    if (e != cudaSuccess) return cuda_err(e);
+    c->nsamples += (int64_t)so.size();
+    if (seg & 1) c->cur ^= 1;
+    c->t += seg;
+    done += seg;
+  }
+  return LB_OK;
+}
+
+int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
+  if (!out) return LB_ERR_BAD_PARAM;
+  *out = nullptr;
+  if (n < 1 || !ps) return LB_ERR_BAD_PARAM;
+  const int known = LB_PREC_DEV32 | LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC | LB_GRAPH | LB_PERSISTENT | LB_AUTOTUNE;
+  if (flags & ~known) return LB_ERR_BAD_PARAM;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_params(ps[i]);
+    if (rc) return rc;
+  }
+  lb_ctx* c = new (std::nothrow) lb_ctx();
+  if (!c) return LB_ERR_OOM;
+  c->n_lat = n;
+  c->flags = flags;
+  c->dev32 = flags & LB_PREC_DEV32;
+  c->params.assign(ps, ps + n);
+  int64_t foff = 0, soff = 0;
+  int roff = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t sites = (int64_t)ps[i].Lx * ps[i].Lz;
+    c->f_off.push_back(foff);
+    c->site_off.push_back(soff);
+    c->row_off.push_back(roff);
+    foff += 18 * sites;
+    // keep every lattice's block 16-byte aligned
+    foff = (foff + 3) & ~(int64_t)3;
+    soff += sites;
+    roff += ps[i].Lz;
+    c->max_lattice_sites = std::max<int>(c->max_lattice_sites, (int)sites);
+    c->max_Lx = std::max(c->max_Lx, ps[i].Lx);
+    c->max_Lz = std::max(c->max_Lz, ps[i].Lz);
+    if (ps[i].kT > 0) c->noise_any = true;
+  }
+  c->n_f = foff;
+  c->n_sites = soff;
+  c->n_rows = roff;
+  const size_t rs = c->dev32 ? sizeof(float) : sizeof(double);
+  int rc = LB_OK;
+  rc = dev_alloc(c, (char**)&c->f[0], c->n_f * rs);
+  if (!rc) rc = dev_alloc(c, (char**)&c->f[1], c->n_f * rs);
+  if (!rc) rc = dev_alloc(c, &c->stats, n * sizeof(DiagStats));
+  if (!rc) rc = dev_alloc(c, &c->d_diag, n * sizeof(DiagLattice));
+  if (!rc) rc = dev_alloc(c, &c->d_t, sizeof(int64_t));
+  if (!rc) rc = dev_alloc(c, &c->d_barrier, 2 * sizeof(unsigned));
+  if (!rc) rc = dev_alloc(c, &c->d_err, sizeof(int));
+  if (!rc) rc = dev_alloc(c, &c->d_mass, 2 * sizeof(double));
+  if (!rc && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) rc = LB_ERR_CUDA;
+  c->stream = c->own_stream;
+  if (!rc) rc = c->dev32 ? upload_tables<float>(c) : upload_tables<double>(c);
+  if (!rc && (cudaMemset(c->stats, 0, n * sizeof(DiagStats)) != cudaSuccess ||
+              cudaMemset(c->d_t, 0, sizeof(int64_t)) != cudaSuccess ||
+              cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess))
+    rc = LB_ERR_CUDA;
+  if (!rc) {
+    // default tile: 128 columns; rows per item chosen so that the grid has a few waves
+    int rows = c->max_Lz;
+    const int64_t cols = [&] { int64_t s = 0; for (auto& p : c->params) s += (p.Lx + 127) / 128; return s; }();
+    while (rows > 16 && cols * ((c->max_Lz + rows - 1) / rows) < 4 * 152) rows /= 2;
+    rc = build_items(c, 128, rows);
+  }
+  if (!rc) {
+    for (int i = 0; i < n && !rc; ++i) {
+      BgParams bp{ps[i].Lx, ps[i].Lz, c->dev32 ? 1 : 0, kRhoBar, ps[i].grad_c0};
+      cudaError_t e = c->dev32 ? launch_init_rest<float>((float*)c->f[0] + c->f_off[i], bp, nullptr)
+                               : launch_init_rest<double>((double*)c->f[0] + c->f_off[i], bp, nullptr);
+      if (e != cudaSuccess) rc = cuda_err(e);
+    }
+    if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = LB_ERR_CUDA;
+  }
+  if (rc) {
+    lb_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LB_OK;
+}
+
+int sync_and_check(lb_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return LB_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LB_ERR_CUDA;
+  if (err) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return LB_ERR_TIMEOUT;
+  }
+  return LB_OK;
+}
+
+int lattice_ok(lb_ctx* c, int lattice) { return c && lattice >= 0 && lattice < c->n_lat; }
+
+int ensure_scratch(lb_ctx* c) {
+  if (c->d_scratch) return LB_OK;
+  return dev_alloc(c, &c->d_scratch, (size_t)18 * c->max_lattice_sites * sizeof(double));
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_create(lb_ctx** out, int Lx, int Lz, double lambda_s, double lambda_d, double lambda_e, double lambda_q,
+              double lambda_eps, double kT, double G, double grad_c0, uint64_t seed, int flags) {
+  lb_params p;
+  std::memset(&p, 0, sizeof(p));
+  p.Lx = Lx;
+  p.Lz = Lz;
+  p.lambda_s = lambda_s;
+  p.lambda_d = lambda_d;
+  p.lambda_e = lambda_e;
+  p.lambda_q = lambda_q;
+  p.lambda_eps = lambda_eps;
+  p.kT = kT;
+  p.G = G;
+  p.grad_c0 = grad_c0;
+  p.seed = seed;
+  p.lattice_id = 0;
+  return create_impl(out, 1, &p, flags);
+}
+
+int lb_create_batch(lb_ctx** out, int n, const lb_params* params, int flags) {
+  return create_impl(out, n, params, flags);
+}
+
+int lb_set_stream(lb_ctx* c, void* stream) {
+  if (!c) return LB_ERR_BAD_PARAM;
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->own_stream;
+  if (c->stream != s) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LB_ERR_CUDA;
+    drop_graphs(c);
+  }
+  c->stream = s;
+  return LB_OK;
+}
+
+int lb_set_sampling(lb_ctx* c, int64_t discard, int64_t every) {
+  if (!c || discard < 0 || every < 0) return LB_ERR_BAD_PARAM;
+  if (every > 0) {
+    for (auto& p : c->params)
+      if (!is_pow2(p.Lx) || !is_pow2(p.Lz) || p.Lx < 2 || p.Lx > 8192 || p.Lz > 8192) return LB_ERR_BAD_PARAM;
+    int rc = alloc_diag(c);
+    if (rc) return rc;
+    cudaError_t e = c->dev32 ? prepare_sf<float>(c->max_Lx, c->max_Lz) : prepare_sf<double>(c->max_Lx, c->max_Lz);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
+  c->discard = discard;
+  c->every = every;
+  drop_graphs(c);
+  return LB_OK;
+}
+
+int lb_set_tile(lb_ctx* c, int tile_x, int rows_per_item) {
+  if (!c) return LB_ERR_BAD_PARAM;
+  if (!(tile_x == 32 || tile_x == 64 || tile_x == 128 || tile_x == 256) || rows_per_item < 1)
+    return LB_ERR_BAD_PARAM;
+  int rc = build_items(c, tile_x, std::min(rows_per_item, c->max_Lz));
+  if (rc) return rc;
+  c->tile_fixed = true;
+  return LB_OK;
+}
+
+int lb_get_tile(lb_ctx* c, int* tile_x, int* rows_per_item) {
+  if (!c) return LB_ERR_BAD_PARAM;
+  if (tile_x) *tile_x = c->tile_x;
+  if (rows_per_item) *rows_per_item = c->rows_per_item;
+  return LB_OK;
+}
+
+int lb_step(lb_ctx* c, int64_t n) {
+  if (!c || n < 0) return LB_ERR_BAD_PARAM;
+  if (n == 0) return LB_OK;
+  return c->dev32 ? step_impl<float>(c, n) : step_impl<double>(c, n);
+}
+
+int lb_synchronize(lb_ctx* c) {
+  if (!c) return LB_ERR_BAD_PARAM;
+  return sync_and_check(c);
+}
+
+int lb_time(lb_ctx* c, int64_t* t) {
+  if (!c || !t) return LB_ERR_BAD_PARAM;
+  *t = c->t;
+  return LB_OK;
+}
+
+int lb_num_lattices(lb_ctx* c, int* n) {
+  if (!c || !n) return LB_ERR_BAD_PARAM;
+  *n = c->n_lat;
+  return LB_OK;
+}
+
+int lb_lattice_shape(lb_ctx* c, int lattice, int* Lx, int* Lz) {
+  if (!lattice_ok(c, lattice)) return LB_ERR_BAD_PARAM;
+  if (Lx) *Lx = c->params[lattice].Lx;
+  if (Lz) *Lz = c->params[lattice].Lz;
+  return LB_OK;
+}
+
+int lb_structure_factor(lb_ctx* c, int lattice, int field, int mode, double* out, size_t n_out,
+                        int64_t* n_samples) {
+  if (!lattice_ok(c, lattice) || field < 0 || field > 3 || !out || (mode != LB_SF_QXQZ && mode != LB_SF_QX))
+    return LB_ERR_BAD_PARAM;
+  const int Lx = c->params[lattice].Lx, Lz = c->params[lattice].Lz;
+  const size_t need = mode == LB_SF_QXQZ ? (size_t)Lx * Lz : (size_t)Lx;
+  if (n_out != need) return LB_ERR_SIZE;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  if (n_samples) *n_samples = c->nsamples;
+  if (!c->diag_ready || c->nsamples == 0) {
+    std::fill(out, out + need, 0.0);
+    return LB_OK;
+  }
+  const size_t off = 4 * (size_t)c->site_off[lattice] + (size_t)field * Lx * Lz;
+  std::vector<double> s(need), k(need);
+  if (cudaMemcpy(s.data(), c->acc_sum + off, need * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(k.data(), c->acc_comp + off, need * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LB_ERR_CUDA;
+  for (size_t i = 0; i < need; ++i) out[i] = (s[i] + k[i]) / (double)c->nsamples;
+  return LB_OK;
+}
+
+int lb_mean_pressure(lb_ctx* c, int lattice, double* last, double* time_avg) {
+  if (!lattice_ok(c, lattice)) return LB_ERR_BAD_PARAM;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  DiagStats st;
+  if (cudaMemcpy(&st, c->stats + lattice, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return LB_ERR_CUDA;
+  if (st.nonfinite) return LB_ERR_NONFINITE;
+  if (last) *last = st.P_last;
+  if (time_avg) *time_avg = c->nsamples ? (st.P_sum + st.P_comp) / (double)c->nsamples : 0.0;
+  return LB_OK;
+}
+
+int lb_mass(lb_ctx* c, int lattice, double out[2]) {
+  if (!lattice_ok(c, lattice) || !out) return LB_ERR_BAD_PARAM;
+  const lb_params& p = c->params[lattice];
+  BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+  cudaError_t e = c->dev32 ? launch_mass<float>((const float*)c->f[c->cur] + c->f_off[lattice], bp, c->d_mass, c->stream)
+                           : launch_mass<double>((const double*)c->f[c->cur] + c->f_off[lattice], bp, c->d_mass,
+                                                 c->stream);
+  if (e != cudaSuccess) return cuda_err(e);
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  if (cudaMemcpy(out, c->d_mass, 2 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return LB_ERR_CUDA;
+  return LB_OK;
+}
+
+int lb_get_populations(lb_ctx* c, int lattice, double* out, size_t n) {
+  if (!lattice_ok(c, lattice) || !out) return LB_ERR_BAD_PARAM;
+  const lb_params& p = c->params[lattice];
+  if (n != (size_t)18 * p.Lx * p.Lz) return LB_ERR_SIZE;
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+  cudaError_t e = c->dev32 ? launch_to_absolute<float>((const float*)c->f[c->cur] + c->f_off[lattice], bp,
+                                                       c->d_scratch, c->stream)
+                           : launch_to_absolute<double>((const double*)c->f[c->cur] + c->f_off[lattice], bp,
+                                                        c->d_scratch, c->stream);
+  if (e != cudaSuccess) return cuda_err(e);
+  rc = sync_and_check(c);
+  if (rc) return rc;
+  if (cudaMemcpy(out, c->d_scratch, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return LB_ERR_CUDA;
+  return LB_OK;
+}
+
+int lb_set_populations(lb_ctx* c, int lattice, const double* in, size_t n) {
+  if (!lattice_ok(c, lattice) || !in) return LB_ERR_BAD_PARAM;
+  const lb_params& p = c->params[lattice];
+  if (n != (size_t)18 * p.Lx * p.Lz) return LB_ERR_SIZE;
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  rc = sync_and_check(c);
+  if (rc) return rc;
+  if (cudaMemcpy(c->d_scratch, in, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return LB_ERR_CUDA;
+  BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+  cudaError_t e = c->dev32 ? launch_from_absolute<float>(c->d_scratch, bp, (float*)c->f[c->cur] + c->f_off[lattice],
+                                                         c->stream)
+                           : launch_from_absolute<double>(c->d_scratch, bp,
+                                                          (double*)c->f[c->cur] + c->f_off[lattice], c->stream);
+  if (e != cudaSuccess) return cuda_err(e);
+  return sync_and_check(c);
+}
+
+int lb_reset_statistics(lb_ctx* c) {
+  if (!c) return LB_ERR_BAD_PARAM;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  c->nsamples = 0;
+  if (cudaMemset(c->stats, 0, c->n_lat * sizeof(DiagStats)) != cudaSuccess) return LB_ERR_CUDA;
+  if (c->diag_ready) {
+    if (cudaMemset(c->acc_sum, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->acc_comp, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess)
+      return LB_ERR_CUDA;
+  }
+  return LB_OK;
+}
+
+int lb_kernel_launches(lb_ctx* c, int64_t* n) {
+  if (!c || !n) return LB_ERR_BAD_PARAM;
+  *n = c->launches;
+  return LB_OK;
+}
+
+int lb_device_bytes(lb_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LB_ERR_BAD_PARAM;
+  *bytes = c->bytes;
+  return LB_OK;
+}
+
+const char* lb_error_string(int code) {
+  switch (code) {
+    case LB_OK: return "ok";
+    case LB_ERR_BAD_PARAM: return "argument out of range";
+    case LB_ERR_OOM: return "out of device memory";
+    case LB_ERR_CUDA: return "CUDA runtime error";
+    case LB_ERR_NONFINITE: return "non-finite mass or pressure";
+    case LB_ERR_TIMEOUT: return "device-side wait timed out";
+    case LB_ERR_SIZE: return "buffer has the wrong number of elements";
+    case LB_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown error";
+  }
+}
+
+void lb_destroy(lb_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  drop_graphs(c);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  void* ptrs[] = {c->d_lat,   c->d_rows,     c->d_items,    c->f[0],      c->f[1],       c->fields,
+                  c->tmp,     c->acc_sum,    c->acc_comp,   c->partials,  c->stats,      c->d_diag,
+                  c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+int lb_debug_barrier(int blocks, int expected, int spin_limit) {
+  if (blocks < 1 || blocks > 64 || expected < 1 || spin_limit < 1 || spin_limit > 10000) return LB_ERR_BAD_PARAM;
+  int dev = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return LB_ERR_STATE;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  if (cudaMalloc(&bar, 2 * sizeof(unsigned)) != cudaSuccess) return LB_ERR_OOM;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaFree(bar);
+    return LB_ERR_OOM;
+  }
+  cudaMemset(bar, 0, 2 * sizeof(unsigned));
+  cudaMemset(err, 0, sizeof(int));
+  int rc = LB_OK;
+  cudaError_t e = launch_barrier_probe(blocks, expected, spin_limit, bar, err, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) rc = LB_ERR_CUDA;
+  int h = 0;
+  if (!rc && cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = LB_ERR_CUDA;
+  if (!rc && h) rc = LB_ERR_TIMEOUT;
+  cudaFree(bar);
+  cudaFree(err);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// lb_diag.cu -- diagnostics of the fluctuating LB method: structure factors (Appendix A,
+// Eqs. SF1 and integral, on the lattice: S(q) = |delta phi(q)|^2 with the unitary 2D
+// transform), mean mechanical pressure and per-species mass (Sec. II.A, III.C), plus the
+// utility kernels that convert between stored and absolute populations.
+//
+// Structure factors: the step kernel writes the four fields of every site on a sample step;
+// here one block per (lattice, field, row) transforms a row along x in shared memory and
+// one block per (lattice, field, q_x) transforms the column along z, squares, scales by
+// 1 / (Lx Lz) and adds the result to double-precision Neumaier (compensated) accumulators.
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+template <class real>
+struct Cplx {
+  real re, im;
+};
+
+namespace {
+
+template <class real>
+__device__ __forceinline__ void twiddle(int k, int n, real& c, real& s);
+template <>
+__device__ __forceinline__ void twiddle<float>(int k, int n, float& c, float& s) {
+  // exp(-2 pi i k / n); k / n is exact in binary for power-of-two n
+  sincospif(-2.0f * (float)k / (float)n, &s, &c);
+}
+template <>
+__device__ __forceinline__ void twiddle<double>(int k, int n, double& c, double& s) {
+  sincospi(-2.0 * (double)k / (double)n, &s, &c);
+}
+
+// In-place iterative radix-2 transform X_k = sum_j x_j exp(-2 pi i j k / n) of n = 2^logn
+// points held in bit-reversed order in shared memory; tw holds exp(-2 pi i k / n), k < n/2.
+template <class real>
+__device__ void fft_inplace(Cplx<real>* s, const Cplx<real>* tw, int n, int logn) {
+  for (int lg = 1; lg <= logn; ++lg) {
+    const int half = 1 << (lg - 1);
+    const int stride = n >> lg;  // twiddle index step for this stage
+    for (int j = threadIdx.x; j < (n >> 1); j += blockDim.x) {
+      const int pos = j & (half - 1);
+      const int i0 = ((j >> (lg - 1)) << lg) + pos, i1 = i0 + half;
+      const Cplx<real> w = tw[pos * stride];
+      const Cplx<real> b = s[i1], a = s[i0];
+      const real tr = w.re * b.re - w.im * b.im;
+      const real ti = w.re * b.im + w.im * b.re;
+      s[i0] = Cplx<real>{a.re + tr, a.im + ti};
+      s[i1] = Cplx<real>{a.re - tr, a.im - ti};
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
+
+template <class real>
+__device__ void fill_twiddles(Cplx<real>* tw, int n) {
+  for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) {
+    real c, s;
+    twiddle<real>(k, n, c, s);
+    tw[k] = Cplx<real>{c, s};
+  }
+}
+
+// Tasks: x-pass task = (lattice, field * Lz + z); z-pass task = (lattice, field * Lx + qx).
+template <class real>
+__global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const real* fields, Cplx<real>* tmp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int2 task = tasks[blockIdx.x];
+  const DiagLattice L = lat[task.x];
+  const int n = L.Lx, logn = ilog2(n);
+  Cplx<real>* s = reinterpret_cast<Cplx<real>*>(smem);
+  Cplx<real>* tw = s + n;
+  fill_twiddles<real>(tw, n);
+  const int64_t off = 4 * L.site_off + (int64_t)task.y * n;  // row of one field
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int r = (int)(__brev((unsigned)j) >> (32 - logn));
+    s[r] = Cplx<real>{fields[off + j], real(0)};
+  }
+  __syncthreads();
+  fft_inplace<real>(s, tw, n, logn);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) tmp[off + j] = s[j];
+}
+
+__device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v) {
+  const double t = sum + v;
+  if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
+  else comp += (v - t) + sum;
+  sum = t;
+}
+
+template <class real>
+__global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const Cplx<real>* tmp, double* acc_sum,
+                               double* acc_comp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int2 task = tasks[blockIdx.x];
+  const DiagLattice L = lat[task.x];
+  const int n = L.Lz, logn = ilog2(n), Lx = L.Lx;
+  const int fld = task.y / Lx, qx = task.y - fld * Lx;
+  Cplx<real>* s = reinterpret_cast<Cplx<real>*>(smem);
+  Cplx<real>* tw = s + n;
+  fill_twiddles<real>(tw, n);
+  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int r = (int)(__brev((unsigned)j) >> (32 - logn));
+    s[r] = tmp[base + (int64_t)j * Lx];
+  }
+  __syncthreads();
+  fft_inplace<real>(s, tw, n, logn);
+  const double scale = 1.0 / ((double)Lx * (double)n);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double re = (double)s[j].re, im = (double)s[j].im;
+    const int64_t o = base + (int64_t)j * Lx;
+    double sm = acc_sum[o], cp = acc_comp[o];
+    neumaier_add(sm, cp, (re * re + im * im) * scale);
+    acc_sum[o] = sm;
+    acc_comp[o] = cp;
+  }
+}
+
+__global__ void finalize_kernel(const DiagLattice* lat, int n_lat, const double* partials, DiagStats* stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_lat) return;
+  const DiagLattice L = lat[i];
+  double p = 0, ma = 0, mb = 0;
+  for (int k = L.item_begin; k < L.item_end; ++k) {
+    p += partials[3 * k];
+    ma += partials[3 * k + 1];
+    mb += partials[3 * k + 2];
+  }
+  DiagStats st = stats[i];
+  const double P = L.P_bg_mean + p / L.n_sites;
+  st.P_last = P;
+  neumaier_add(st.P_sum, st.P_comp, P);
+  st.massA_last = L.mass_bg[0] + ma;
+  st.massB_last = L.mass_bg[1] + mb;
+  if (!isfinite(P) || !isfinite(st.massA_last) || !isfinite(st.massB_last)) st.nonfinite = 1;
+  stats[i] = st;
+}
+
+// Mass of the stored state of one lattice: one block per species, fixed summation order.
+template <class real>
+__global__ void mass_kernel(const real* f, BgParams bp, double* out) {
+  const int s = blockIdx.x;
+  const int64_t LzLx = (int64_t)bp.Lx * bp.Lz;
+  const real* fs = f + (int64_t)s * 9 * LzLx;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < 9 * LzLx; k += blockDim.x) acc += (double)fs[k];
+  __shared__ double red[1024];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double bg = 0.0;
+    if (bp.dev) {
+      for (int z = 0; z < bp.Lz; ++z) {
+        const double c0 = 0.5 + (z + 0.5 - 0.5 * bp.Lz) * bp.grad_c0;
+        bg += bp.rho_bar * (s == 0 ? c0 : 1.0 - c0);
+      }
+      bg *= bp.Lx;
+    }
+    out[s] = bg + red[0];
+  }
+}
+
+__device__ __forceinline__ double weight_of(int l) { return l == 0 ? 4.0 / 9.0 : (l <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+__device__ __forceinline__ double background(const BgParams& bp, int s, int l, int z) {
+  if (!bp.dev) return 0.0;
+  const double c0 = 0.5 + (z + 0.5 - 0.5 * bp.Lz) * bp.grad_c0;
+  return weight_of(l) * bp.rho_bar * (s == 0 ? c0 : 1.0 - c0);
+}
+
+template <class real>
+__global__ void to_absolute_kernel(const real* f, BgParams bp, double* out) {
+  const int64_t LzLx = (int64_t)bp.Lx * bp.Lz, n = 18 * LzLx;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int sl = (int)(k / LzLx);
+    const int z = (int)((k - sl * LzLx) / bp.Lx);
+    out[k] = (double)f[k] + background(bp, sl / 9, sl % 9, z);
+  }
+}
+
+template <class real>
+__global__ void from_absolute_kernel(const double* in, BgParams bp, real* f) {
+  const int64_t LzLx = (int64_t)bp.Lx * bp.Lz, n = 18 * LzLx;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int sl = (int)(k / LzLx);
+    const int z = (int)((k - sl * LzLx) / bp.Lx);
+    f[k] = (real)(in[k] - background(bp, sl / 9, sl % 9, z));
+  }
+}
+
+// Rest state f^S_l = w_l rho_bar c^S_0(z) (stored as zero deviations in deviation mode).
+template <class real>
+__global__ void init_rest_kernel(real* f, BgParams bp) {
+  const int64_t LzLx = (int64_t)bp.Lx * bp.Lz, n = 18 * LzLx;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    if (bp.dev) {
+      f[k] = real(0);
+    } else {
+      const int sl = (int)(k / LzLx);
+      const int z = (int)((k - sl * LzLx) / bp.Lx);
+      const double c0 = 0.5 + (z + 0.5 - 0.5 * bp.Lz) * bp.grad_c0;
+      f[k] = (real)(weight_of(sl % 9) * bp.rho_bar * ((sl / 9) == 0 ? c0 : 1.0 - c0));
+    }
+  }
+}
+
+}  // namespace
+
+template <class real>
+size_t sf_smem_bytes(int n) {
+  return (size_t)n * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
+}
+
+template <class real>
+cudaError_t prepare_sf(int max_Lx, int max_Lz) {
+  cudaError_t e = cudaFuncSetAttribute(sf_rows_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sf_smem_bytes<real>(max_Lx));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sf_cols_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sf_smem_bytes<real>(max_Lz));
+}
+
+template <class real>
+cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
+                      cudaStream_t s) {
+  const size_t smr = sf_smem_bytes<real>(p.max_Lx), smc = sf_smem_bytes<real>(p.max_Lz);
+  sf_rows_kernel<real><<<p.n_row_tasks, 256, smr, s>>>(p.lat, p.row_tasks, fields, (Cplx<real>*)tmp);
+  sf_cols_kernel<real><<<p.n_col_tasks, 256, smc, s>>>(p.lat, p.col_tasks, (const Cplx<real>*)tmp, acc_sum,
+                                                       acc_comp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const DiagLattice* d_lat, int n_lat, const double* partials, DiagStats* stats,
+                            cudaStream_t s) {
+  finalize_kernel<<<(n_lat + 127) / 128, 128, 0, s>>>(d_lat, n_lat, partials, stats);
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_mass(const real* f, const BgParams& bp, double* out2, cudaStream_t s) {
+  mass_kernel<real><<<2, 1024, 0, s>>>(f, bp, out2);
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_to_absolute(const real* f, const BgParams& bp, double* out, cudaStream_t s) {
+  to_absolute_kernel<real><<<1024, 256, 0, s>>>(f, bp, out);
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_from_absolute(const double* in, const BgParams& bp, real* f, cudaStream_t s) {
+  from_absolute_kernel<real><<<1024, 256, 0, s>>>(in, bp, f);
+  return cudaGetLastError();
+}
+
+template <class real>
+cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s) {
+  init_rest_kernel<real><<<1024, 256, 0, s>>>(f, bp);
+  return cudaGetLastError();
+}
+
+#define LB_INST(real)                                                                                        \
+  template size_t sf_smem_bytes<real>(int);                                                                  \
+  template cudaError_t prepare_sf<real>(int, int);                                                           \
+  template cudaError_t launch_sf<real>(const SfPlan&, const real*, void*, double*, double*, cudaStream_t);   \
+  template cudaError_t launch_mass<real>(const real*, const BgParams&, double*, cudaStream_t);               \
+  template cudaError_t launch_to_absolute<real>(const real*, const BgParams&, double*, cudaStream_t);        \
+  template cudaError_t launch_from_absolute<real>(const double*, const BgParams&, real*, cudaStream_t);      \
+  template cudaError_t launch_init_rest<real>(real*, const BgParams&, cudaStream_t);
+LB_INST(float)
+LB_INST(double)
+
+}  // namespace lbk

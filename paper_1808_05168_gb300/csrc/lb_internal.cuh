@@ -1,0 +1,216 @@
+// lb_internal.cuh -- types and device helpers shared by the library's translation units.
+//
+// Populations of lattice i live at f + lat[i].f_off with layout [species][link][z][x]
+// (x contiguous, structure of arrays).  The stored value is the post-collision population
+// minus the background b^S_l(z) = w_l rho_bar c^S_0(z) in LB_PREC_DEV32 mode, and the plain
+// post-collision population in LB_PREC_FP64 mode (where the background is zero).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lb.h"
+
+namespace lbk {
+
+// D2Q9 links of Fig. 1 (c_0 = 0, c_1 = (1,0), c_2 = (0,1), c_3 = (-1,0), c_4 = (0,-1),
+// c_5 = (1,1), c_6 = (-1,1), c_7 = (-1,-1), c_8 = (1,-1)).
+#define LB_CX(l) ((l) == 1 || (l) == 5 || (l) == 8 ? 1 : ((l) == 3 || (l) == 6 || (l) == 7 ? -1 : 0))
+#define LB_CZ(l) ((l) == 2 || (l) == 5 || (l) == 6 ? 1 : ((l) == 4 || (l) == 7 || (l) == 8 ? -1 : 0))
+#define LB_OPP(l) ((l) == 0 ? 0 : ((l) <= 4 ? (((l) + 1) % 4) + 1 : (((l) - 3) % 4) + 5))
+
+// Device-level flag bits (subset of the public flags that kernels look at).
+enum : int { DF_ASTAR = 1, DF_WALL_FIXED = 2, DF_NOISE_LOC = 4, DF_NOISE = 8 };
+
+// Per-lattice constants in the working precision.
+template <class real>
+struct LatticeDev {
+  int Lx, Lz;
+  int64_t f_off;     // element offset of the population block
+  int64_t site_off;  // site offset into per-site arrays (sampled fields)
+  int row_off;       // offset into the per-row table
+  int flags;         // DF_* bits
+  uint32_t key0, key1, lattice_id, pad;
+  real lam[9];       // relaxation rate per moment (Eq. MRT)
+  real omh[9];       // 1 - lambda_a / 2 (second-order forcing)
+  real G;            // coupling (Eq. aNI)
+  real g3;           // grad_c0 / 3: gradient force density per unit rho (Eq. ne-acc)
+  real k9, k36;      // streaming shift of the background on links with c_z = -1 for
+                     // species A, per weight class (w = 1/9, 1/36); zero in FP64 mode
+  real rho_bar_off;  // rho_bar in FP64 mode, 0 in deviation mode
+  real sig_mom;      // hom noise amplitude of moments 1, 2 (Eq. noise-bin-expl)
+  real sig[2][9];    // hom noise amplitudes of moments 3..8 (Eq. noise-bin-expl-high)
+  real pref_mom;     // loc noise: sqrt((2 - l_d) l_d kT)
+  real pref[9];      // loc noise: sqrt(3 (2 - l_a) l_a N_a kT)
+};
+
+// Per-row constants of the background (zero in FP64 mode), rows 0..Lz-1.
+template <class real>
+struct RowConst {
+  real bgA, bgB;    // rho_bar c^S_0(z)
+  real dbgA, dbgB;  // background part of sum_l w_l c_lz rho^S(z + c_lz), wall ghosts included
+  real nbA, nbB;    // background part of sum_l w_l |c_l|^2 rho^S(z + c_lz), ghosts included
+  real c0;          // c_0(z)
+  real ghost_cA;    // fixed-wall ghost: c^A of the wall next to this row (0 if not a wall row)
+};
+
+// A work item: columns [x0, x0 + blockDim.x) of rows [z0, z1) of one lattice.
+struct WorkItem {
+  int lattice;
+  int x0;
+  int z0, z1;
+};
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+//   (x0, x1, x2, x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)),
+// the key advanced by the Weyl increments (W0, W1) before every round but the first.
+// ------------------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    const U4 n = {hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    c = n;
+  }
+  return c;
+}
+
+// Uniform in (0, 1) from the top 23 bits, (2 (k >> 9) + 1) 2^-24: exact in float and double.
+template <class real>
+__device__ __forceinline__ real uniform01(uint32_t k);
+template <>
+__device__ __forceinline__ float uniform01<float>(uint32_t k) {
+  return __uint2float_rn(((k >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+}
+template <>
+__device__ __forceinline__ double uniform01<double>(uint32_t k) {
+  return __uint2double_rn(((k >> 9) << 1) | 1u) * 5.9604644775390625e-8;
+}
+
+// Box-Muller: (r cos 2 pi u2, r sin 2 pi u2) with r = sqrt(-2 ln u1).
+template <class real>
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, real& n0, real& n1);
+template <>
+__device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float& n0, float& n1) {
+  const float u1 = uniform01<float>(a), u2 = uniform01<float>(b);
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  n0 = r * c;
+  n1 = r * s;
+}
+template <>
+__device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, double& n0, double& n1) {
+  const double u1 = uniform01<double>(a), u2 = uniform01<double>(b);
+  const double r = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  n0 = r * c;
+  n1 = r * s;
+}
+
+template <class real>
+__device__ __forceinline__ real rsqrt_pos(real v);
+template <>
+__device__ __forceinline__ float rsqrt_pos<float>(float v) { return sqrtf(v); }
+template <>
+__device__ __forceinline__ double rsqrt_pos<double>(double v) { return sqrt(v); }
+
+// Host-side launch helpers implemented in lb_step.cu / lb_diag.cu.
+template <class real>
+struct StepArgs {
+  const LatticeDev<real>* lat;
+  const RowConst<real>* rows;
+  const WorkItem* items;
+  int n_items;
+  const real* src;
+  real* dst;
+  const int64_t* d_t;  // device step counter; the step index is *d_t + t_offset
+  int t_offset;
+  real* fields;        // sampled fields [4][Lz][Lx] per lattice (sample steps only)
+  double* partials;    // per item: pressure deviation sum, mass deviation A, B
+};
+
+template <class real>
+cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, bool noise, cudaStream_t s);
+
+template <class real>
+cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, bool noise,
+                                   unsigned* barrier, int* err, int grid, int spin_limit, cudaStream_t s);
+
+template <class real>
+int persistent_grid(int tile_x, bool sample, bool noise);
+
+cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s);
+
+// Diagnostics (lb_diag.cu)
+struct DiagLattice {
+  int Lx, Lz;
+  int64_t site_off;    // offset in sites of this lattice in fields / spectra
+  int item_begin, item_end;
+  double P_bg_mean;    // spatial mean of the background pressure (FP64 mode: 0)
+  double mass_bg[2];   // background mass per species (FP64 mode: 0)
+  double n_sites;
+};
+
+struct DiagStats {  // per lattice, updated by the finalize kernel
+  double P_last, P_sum, P_comp;
+  double massA_last, massB_last;
+  int nonfinite;
+  int pad;
+};
+
+// Transform tasks of one sample: one block per (lattice, field * Lz + z) row and per
+// (lattice, field * Lx + q_x) column.
+struct SfPlan {
+  const DiagLattice* lat;
+  const int2* row_tasks;
+  const int2* col_tasks;
+  int n_row_tasks, n_col_tasks;
+  int max_Lx, max_Lz;
+};
+
+// What the utility kernels need to rebuild the background w_l rho_bar c^S_0(z) in double.
+struct BgParams {
+  int Lx, Lz;
+  int dev;
+  double rho_bar, grad_c0;
+};
+
+template <class real>
+size_t sf_smem_bytes(int n);
+template <class real>
+cudaError_t prepare_sf(int max_Lx, int max_Lz);
+
+template <class real>
+cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
+                      cudaStream_t s);
+
+cudaError_t launch_finalize(const DiagLattice* d_lat, int n_lat, const double* partials, DiagStats* stats,
+                            cudaStream_t s);
+
+template <class real>
+cudaError_t launch_mass(const real* f, const BgParams& bp, double* out2, cudaStream_t s);
+template <class real>
+cudaError_t launch_to_absolute(const real* f, const BgParams& bp, double* out, cudaStream_t s);
+template <class real>
+cudaError_t launch_from_absolute(const double* in, const BgParams& bp, real* f, cudaStream_t s);
+template <class real>
+cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s);
+
+cudaError_t launch_barrier_probe(int blocks, int expected, int spin_limit, unsigned* barrier, int* err,
+                                 cudaStream_t s);
+
+}  // namespace lbk

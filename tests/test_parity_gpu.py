@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C interface) with the oracle, element by element, on
+the same seeded inputs and noise stream.
+
+Tolerances: FP64 storage -- 1e-12 relative per population after up to 1000 steps; FP32
+deviation storage -- absolute error at most 1e-5 of the largest deviation from the
+background w_l rho_bar c^S_0(z); averaged diagnostics as stated per test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_05168_gb300 import LatticeParams, Simulation, capi
+
+pytestmark = pytest.mark.gpu
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1808_05168_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def background(Lx, Lz, grad_c0):
+    z = np.arange(Lz) + 0.5 - Lz / 2
+    c0 = 0.5 + z * grad_c0
+    b = np.empty((2, 9, Lz, Lx))
+    for l in range(9):
+        b[0, l] = (W[l] * c0)[:, None]
+        b[1, l] = (W[l] * (1 - c0))[:, None]
+    return b
+
+
+def oracle_of(p: LatticeParams, **flags):
+    return oracle.OracleLattice(p.Lx, p.Lz, lambda_s=p.lambda_s, lambda_d=p.lambda_d, lambda_e=p.lambda_e,
+                                lambda_q=p.lambda_q, lambda_eps=p.lambda_eps, kT=p.kT, G=p.G, grad_c0=p.grad_c0,
+                                seed=p.seed, lattice_id=p.lattice_id, **flags)
+
+
+def assert_fp64_parity(got, want, rtol=1e-12):
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    assert np.max(err) <= rtol, f"max relative error {np.max(err):.3e}"
+
+
+def assert_dev32_parity(got, want, b, tol=1e-5):
+    dev = want - b
+    scale = np.max(np.abs(dev))
+    err = np.max(np.abs(got - want))
+    assert err <= tol * scale, f"max abs error {err:.3e} vs deviation scale {scale:.3e}"
+
+
+C1 = LatticeParams(64, 32, lambda_s=1.0, lambda_d=0.8, kT=1e-5, G=0.0, grad_c0=0.5 / 32, seed=1)
+
+
+def test_fp64_ideal_mixture_1000_steps():
+    """64 x 32 ideal mixture with a wall-to-wall concentration difference of 0.5."""
+    with Simulation(C1, precision="fp64") as sim:
+        sim.step(1000)
+        got = sim.populations()
+    o = oracle_of(C1)
+    o.step(1000)
+    assert_fp64_parity(got, o.populations())
+
+
+NI = LatticeParams(100, 20, lambda_s=1.3, lambda_d=0.9, lambda_e=1.1, lambda_q=1.2, lambda_eps=1.4, kT=1e-5, G=0.5,
+                   grad_c0=0.4 / 20, seed=7)
+
+
+@pytest.mark.parametrize("tile", [(64, 7), (128, 20), (32, 3)])
+def test_fp64_nonideal_ragged_tiles(tile):
+    """Non-ideal mixture on a ragged lattice (Lx not a tile multiple, Lz not a row multiple)."""
+    with Simulation(NI, precision="fp64") as sim:
+        sim.set_tile(*tile)
+        sim.step(300)
+        got = sim.populations()
+    o = oracle_of(NI)
+    o.step(300)
+    assert_fp64_parity(got, o.populations())
+
+
+@pytest.mark.parametrize("variant", ["no_astar", "wall_fixed", "noise_loc"])
+def test_fp64_variants(variant):
+    p = LatticeParams(40, 12, lambda_s=1.2, lambda_d=1.1, kT=1e-4, G=0.6, grad_c0=0.3 / 12, seed=3)
+    kw = {"no_astar": dict(astar=False), "wall_fixed": dict(wall_fixed=True), "noise_loc": dict(noise_loc=True)}
+    with Simulation(p, precision="fp64", **kw[variant]) as sim:
+        sim.step(200)
+        got = sim.populations()
+    o = oracle_of(p, **kw[variant])
+    o.step(200)
+    assert_fp64_parity(got, o.populations())
+
+
+C2_SMALL = LatticeParams(64, 32, lambda_s=1.0, lambda_d=0.8, kT=1e-5, G=0.5, grad_c0=0.5 / 32, seed=2)
+
+
+@pytest.mark.parametrize("p", [C1, C2_SMALL], ids=["ideal", "nonideal"])
+def test_dev32_1000_steps(p):
+    """FP32 deviations from the background against the FP64 oracle after 1000 steps."""
+    with Simulation(p, precision="dev32") as sim:
+        sim.step(1000)
+        got = sim.populations()
+    o = oracle_of(p)
+    o.step(1000)
+    assert_dev32_parity(got, o.populations(), background(p.Lx, p.Lz, p.grad_c0))
+
+
+def test_batch_of_heterogeneous_lattices():
+    """Three lattices of different sizes and parameters in one launch per step; each keeps its
+    own noise stream (lattice_id is a Philox counter word)."""
+    ps = [LatticeParams(64, 16, kT=1e-5, G=0.0, grad_c0=0.01, seed=1, lattice_id=0),
+          LatticeParams(32, 8, lambda_s=1.4, kT=1e-4, G=0.5, grad_c0=0.02, seed=2, lattice_id=3),
+          LatticeParams(100, 10, lambda_d=1.2, kT=1e-5, G=0.3, grad_c0=-0.03, seed=2, lattice_id=5)]
+    for prec in ("fp64", "dev32"):
+        with Simulation(ps, precision=prec) as sim:
+            sim.step(200)
+            got = [sim.populations(i) for i in range(3)]
+        for i, p in enumerate(ps):
+            o = oracle_of(p)
+            o.step(200)
+            if prec == "fp64":
+                assert_fp64_parity(got[i], o.populations())
+            else:
+                assert_dev32_parity(got[i], o.populations(), background(p.Lx, p.Lz, p.grad_c0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_sampled_structure_factors_and_pressure(prec):
+    """Appendix A structure factors (all four fields, full q grid) and the Sec. III.C mean
+    pressure, sampled on the pre-collision state every 5 steps after 10."""
+    p = LatticeParams(32, 16, lambda_s=1.1, lambda_d=0.9, kT=1e-4, G=0.5, grad_c0=0.3 / 16, seed=4)
+    with Simulation(p, precision=prec) as sim:
+        sim.set_sampling(10, 5)
+        sim.step(101)
+        S = {f: sim.structure_factor(f) for f in ("rho", "c", "ux", "uz")}
+        Sqx = sim.structure_factor("c", qz0_only=True)
+        last, avg = sim.mean_pressure()
+    o = oracle_of(p)
+    o.set_sampling(10, 5)
+    o.step(101)
+    for f in S:
+        want, n = o.structure_factor(f)
+        got, ng = S[f]
+        assert n == ng == 19
+        if prec == "fp64":
+            np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12 * want.max())
+        else:
+            assert np.max(np.abs(got - want)) <= 2e-3 * want.mean(), f
+    np.testing.assert_array_equal(Sqx[0], S["c"][0][0])
+    olast, oavg, _ = o.mean_pressure()
+    tol = 1e-12 if prec == "fp64" else 1e-7
+    assert abs(last - olast) <= tol * abs(olast)
+    assert abs(avg - oavg) <= tol * abs(oavg)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_launch_modes_and_tiles_are_bit_identical(prec):
+    """Direct launches, CUDA graphs, the persistent cooperative launch and every tile shape
+    compute each site identically."""
+    p = LatticeParams(96, 24, kT=1e-5, G=0.5, grad_c0=0.4 / 24, seed=9)
+    results = []
+    configs = [dict(), dict(graph=True), dict(persistent=True), dict(graph=True, persistent=True)]
+    for kw in configs:
+        with Simulation(p, precision=prec, **kw) as sim:
+            sim.set_sampling(3, 7)
+            sim.step(70)
+            sim.step(33)
+            results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0]))
+    for tile in [(32, 5), (256, 24), (64, 1)]:
+        with Simulation(p, precision=prec) as sim:
+            sim.set_tile(*tile)
+            sim.set_sampling(3, 7)
+            sim.step(103)
+            results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0]))
+    for r in results[1:]:
+        np.testing.assert_array_equal(r[0], results[0][0])
+        assert r[1] == results[0][1]
+        np.testing.assert_array_equal(r[2], results[0][2])
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-13), ("dev32", 1e-9)])
+def test_mass_is_conserved(prec, rtol):
+    p = LatticeParams(64, 32, kT=1e-4, G=0.5, grad_c0=0.01, seed=5)
+    with Simulation(p, precision=prec) as sim:
+        m0 = sim.mass()
+        np.testing.assert_allclose(m0, [1024, 1024], rtol=1e-14)
+        sim.step(500)
+        np.testing.assert_allclose(sim.mass(), m0, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_set_get_round_trip(prec):
+    p = LatticeParams(33, 7, G=0.2, grad_c0=0.05)
+    f = background(33, 7, 0.05) * (1 + 0.01 * np.random.default_rng(0).standard_normal((2, 9, 7, 33)))
+    with Simulation(p, precision=prec) as sim:
+        sim.set_populations(f)
+        g = sim.populations()
+    if prec == "fp64":
+        np.testing.assert_array_equal(g, f)
+    else:
+        np.testing.assert_allclose(g, f, rtol=0, atol=1e-9)
+
+
+def test_step_from_arbitrary_state():
+    """One step from a random perturbed state (not reachable from rest) matches the oracle."""
+    p = LatticeParams(48, 10, lambda_s=0.7, lambda_d=1.6, kT=1e-3, G=0.8, grad_c0=0.02, seed=11)
+    f = background(48, 10, 0.02) * (1 + 0.05 * np.random.default_rng(1).standard_normal((2, 9, 10, 48)))
+    with Simulation(p, precision="fp64") as sim:
+        sim.set_populations(f)
+        sim.step(3)
+        got = sim.populations()
+    o = oracle_of(p)
+    o.set_populations(f)
+    o.step(3)
+    assert_fp64_parity(got, o.populations())
+
+
+def test_bounded_grid_barrier_gives_up():
+    """The grid barrier of the persistent launch waits a bounded time and reports a timeout
+    (a barrier expecting more blocks than were launched), without hanging the device."""
+    assert capi.lb_debug_barrier(2, 2, 500) == capi.LB_OK
+    assert capi.lb_debug_barrier(2, 3, 300) == capi.LB_ERR_TIMEOUT
+    assert capi.lb_debug_barrier(4, 4, 500) == capi.LB_OK
+
+
+def test_errors_on_device():
+    with Simulation(LatticeParams(30, 8), precision="fp64") as sim:
+        with pytest.raises(capi.LBError) as e:
+            sim.set_sampling(0, 1)  # Lx not a power of two
+        assert e.value.code == capi.LB_ERR_BAD_PARAM
+        with pytest.raises(capi.LBError) as e:
+            capi.lb_get_populations(sim.h, 0, np.empty(5))
+        assert e.value.code == capi.LB_ERR_SIZE
+        with pytest.raises(capi.LBError):
+            sim.populations(1)
