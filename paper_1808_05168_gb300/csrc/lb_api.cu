@@ -587,6 +587,7 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
   if (!rc && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) rc = LB_ERR_CUDA;
   c->stream = c->own_stream;
   if (!rc) rc = c->dev32 ? upload_tables<float>(c) : upload_tables<double>(c);
+  if (!rc && (c->dev32 ? prepare_step<float>(256) : prepare_step<double>(256)) != cudaSuccess) rc = LB_ERR_CUDA;
   if (!rc && (cudaMemset(c->stats, 0, n * sizeof(DiagStats)) != cudaSuccess ||
               cudaMemset(c->d_t, 0, sizeof(int64_t)) != cudaSuccess ||
               cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess))

@@ -146,6 +146,13 @@ struct StepArgs {
 template <class real>
 cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, bool noise, cudaStream_t s);
 
+// Dynamic shared memory of the step kernels for a tile width, and the one-time attribute set-up
+// that allows it (called before any launch or capture).
+template <class real>
+size_t step_smem_bytes(int tile_x);
+template <class real>
+cudaError_t prepare_step(int max_tile_x);
+
 template <class real>
 cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, bool noise,
                                    unsigned* barrier, int* err, int grid, int spin_limit, cudaStream_t s);

@@ -2,20 +2,22 @@
 // (Eq. LB with Eq. MRT), one launch per step for every lattice of a batch, or one
 // cooperative launch with a bounded grid barrier between steps.
 //
-// Work decomposition: a block of TX threads owns TX consecutive columns x of one lattice
-// and marches up rows z0..z1-1 of that lattice.  Each thread pulls the 18 populations of its
-// own site (Eq. LB, mid-way bounce-back at the walls of Sec. II.A), so every stored value
-// is read once per step from HBM with coalesced loads.  The non-ideal force (Eq. aNI) needs
-// the densities of the 8 neighbours at the same time level: each thread keeps the pulled
-// row z+1 in registers while it collides row z, and the densities of rows z-1, z, z+1 live
-// in a 4-slot shared-memory ring (one __syncthreads per row).  The two halo columns are
-// pulled by the edge threads.  The wall ghost rows follow Sec. II.A.
+// Work decomposition: a block of TX threads owns TX consecutive columns x of one lattice and
+// marches up rows z0..z1-1 of that lattice.  Each thread stages the 18 populations arriving
+// at its own site (Eq. LB; mid-way bounce-back at the walls of Sec. II.A) with per-thread
+// asynchronous copies (cp.async) into a ring of NS rows of shared memory, issued NS-2 rows
+// ahead of the row being collided, so every stored value is read once per step from HBM with
+// coalesced loads and several rows of loads are in flight per thread without holding any of
+// them in registers.  The non-ideal force (Eq. aNI) needs the densities of the 8 neighbours at
+// the same time level: the densities of rows z-1, z, z+1 live in a 4-slot shared-memory ring
+// (one __syncthreads per row); the two halo columns are staged by the edge threads.  The
+// wall ghost rows follow Sec. II.A.
 //
-// Arithmetic per site: densities and momenta from the pulled populations, forces
-// (Eqs. aNI, ne-acc, a* of its footnote), barycentric velocity (Eq. bar), moments of
-// Table I in their structured +- form, relaxation toward m^eq with second-order forcing
-// (1 - lambda_a/2) S_a, FDT noise from Philox4x32-10 (Eqs. noise-bin-expl,
-// noise-bin-expl-high), and the inverse transform f_l = w_l sum_a T_al m*_a / N_a.
+// Arithmetic per site: densities and momenta from the staged populations, forces (Eqs. aNI,
+// ne-acc, a* of its footnote), barycentric velocity (Eq. bar), moments of Table I in their
+// structured +- form, relaxation toward m^eq with second-order forcing (1 - lambda_a/2) S_a,
+// FDT noise from Philox4x32-10 (Eqs. noise-bin-expl, noise-bin-expl-high), and the inverse
+// transform f_l = w_l sum_a T_al m*_a / N_a.
 #include <cstdio>
 
 #include "lb_internal.cuh"
@@ -24,45 +26,159 @@ namespace lbk {
 
 namespace {
 
+constexpr int NS = 4;  // rows of staged populations (power of two)
+
+template <class real>
+__device__ __forceinline__ void cp_async(real* dst_smem, const real* src);
+template <>
+__device__ __forceinline__ void cp_async<float>(float* dst_smem, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <>
+__device__ __forceinline__ void cp_async<double>(double* dst_smem, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ int ring_slot(int z) { return (z + 4) & 3; }
 
-// Pull the 18 populations arriving at (x, z) (Eq. LB): link l comes from (x - c_lx, z - c_lz);
-// a link whose source row lies beyond a wall is the reflected population f*_opp(l)(x, z).
-// In deviation mode the background difference b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz
-// d_z c^S_0 is added on non-reflected links with c_lz != 0 (zero on reflected links).
+// Stage the 18 populations arriving at (x, z) (Eq. LB) into dst[k * W], k = 9 s + l: link l
+// comes from (x - c_lx, z - c_lz); a link whose source row lies beyond a wall takes the
+// reflected population f*_opp(l)(x, z).
 template <class real>
-__device__ __forceinline__ void pull_site(const real* __restrict__ f, int LzLx, int Lx, int Lz, int z, int x, int xm,
-                                          int xp, real k9, real k36, real v[18], real& dA, real& dB) {
-  const bool below = z > 0;
-  const bool above = z < Lz - 1;
+__device__ __forceinline__ void stage_column(const real* __restrict__ f, int LzLx, int Lx, int Lz, int z, int x,
+                                             real* dst, int W) {
+  const int xm = (x == 0) ? Lx - 1 : x - 1;
+  const int xp = (x + 1 == Lx) ? 0 : x + 1;
+  const bool below = z > 0, above = z < Lz - 1;
   const int r0 = z * Lx, rdn = r0 - Lx, rup = r0 + Lx;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const real* fs = f + s * 9 * LzLx;
-    const real q9 = s == 0 ? k9 : -k9, q36 = s == 0 ? k36 : -k36;
-    real* w = v + 9 * s;
-    w[0] = fs[0 * LzLx + r0 + x];
-    w[1] = fs[1 * LzLx + r0 + xm];
-    w[3] = fs[3 * LzLx + r0 + xp];
-    w[2] = below ? fs[2 * LzLx + rdn + x] - q9 : fs[4 * LzLx + r0 + x];
-    w[4] = above ? fs[4 * LzLx + rup + x] + q9 : fs[2 * LzLx + r0 + x];
-    w[5] = below ? fs[5 * LzLx + rdn + xm] - q36 : fs[7 * LzLx + r0 + x];
-    w[6] = below ? fs[6 * LzLx + rdn + xp] - q36 : fs[8 * LzLx + r0 + x];
-    w[7] = above ? fs[7 * LzLx + rup + xp] + q36 : fs[5 * LzLx + r0 + x];
-    w[8] = above ? fs[8 * LzLx + rup + xm] + q36 : fs[6 * LzLx + r0 + x];
+    real* d = dst + s * 9 * W;
+    cp_async(d + 0 * W, fs + 0 * LzLx + r0 + x);
+    cp_async(d + 1 * W, fs + 1 * LzLx + r0 + xm);
+    cp_async(d + 3 * W, fs + 3 * LzLx + r0 + xp);
+    cp_async(d + 2 * W, below ? fs + 2 * LzLx + rdn + x : fs + 4 * LzLx + r0 + x);
+    cp_async(d + 4 * W, above ? fs + 4 * LzLx + rup + x : fs + 2 * LzLx + r0 + x);
+    cp_async(d + 5 * W, below ? fs + 5 * LzLx + rdn + xm : fs + 7 * LzLx + r0 + x);
+    cp_async(d + 6 * W, below ? fs + 6 * LzLx + rdn + xp : fs + 8 * LzLx + r0 + x);
+    cp_async(d + 7 * W, above ? fs + 7 * LzLx + rup + xp : fs + 5 * LzLx + r0 + x);
+    cp_async(d + 8 * W, above ? fs + 8 * LzLx + rup + xm : fs + 6 * LzLx + r0 + x);
   }
-  dA = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-  dB = ((v[9] + v[10]) + (v[11] + v[12])) + ((v[13] + v[14]) + (v[15] + v[16])) + v[17];
 }
 
-// Density deviations only (halo columns and the row below an item's first row).
+// The 9 staged populations of species s at stage column c as deviations from the background
+// of row z: in deviation mode b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz d_z c^S_0 is added on
+// non-reflected links with c_lz != 0 (k9, k36 are zero in FP64 mode).
 template <class real>
-__device__ __forceinline__ void pull_rho(const real* __restrict__ f, int LzLx, int Lx, int Lz, int z, int x, real k9,
-                                         real k36, real& dA, real& dB) {
-  const int xm = (x == 0) ? Lx - 1 : x - 1;
-  const int xp = (x + 1 == Lx) ? 0 : x + 1;
-  real v[18];
-  pull_site(f, LzLx, Lx, Lz, z, x, xm, xp, k9, k36, v, dA, dB);
+__device__ __forceinline__ void read_species(const real* st, int W, int c, int s, bool below, bool above, real k9,
+                                             real k36, real v[9]) {
+  const real* d = st + s * 9 * W + c;
+  const real q9 = s == 0 ? k9 : -k9, q36 = s == 0 ? k36 : -k36;
+  const real b9 = below ? q9 : real(0), b36 = below ? q36 : real(0);
+  const real a9 = above ? q9 : real(0), a36 = above ? q36 : real(0);
+  v[0] = d[0];
+  v[1] = d[W];
+  v[3] = d[3 * W];
+  v[2] = d[2 * W] - b9;
+  v[4] = d[4 * W] + a9;
+  v[5] = d[5 * W] - b36;
+  v[6] = d[6 * W] - b36;
+  v[7] = d[7 * W] + a36;
+  v[8] = d[8 * W] + a36;
+}
+
+template <class real>
+__device__ __forceinline__ real sum9(const real v[9]) {
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// Moments m_1..m_8 of Table I in the structured form.
+template <class real>
+struct Mom {
+  real m1, m2, m3, m4, m5, m6, m7, m8;
+};
+
+template <class real>
+__device__ __forceinline__ Mom<real> moments(const real v[9]) {
+  const real a57 = v[5] - v[7], a68 = v[6] - v[8];
+  const real d13 = v[1] - v[3], d24 = v[2] - v[4];
+  const real s13 = v[1] + v[3], s24 = v[2] + v[4];
+  const real e = s13 + s24;
+  const real s57 = v[5] + v[7], s68 = v[6] + v[8];
+  const real dg = s57 + s68;
+  Mom<real> m;
+  m.m1 = d13 + a57 - a68;
+  m.m2 = d24 + a57 + a68;
+  m.m3 = -2 * v[0] + e + 4 * dg;
+  m.m4 = s13 - s24;
+  m.m5 = s57 - s68;
+  m.m6 = -d13 + 2 * (a57 - a68);
+  m.m7 = -d24 + 2 * (a57 + a68);
+  m.m8 = 2 * v[0] - 4 * e + 8 * dg;
+  return m;
+}
+
+// Collision of one species in moment space (Eq. MRT) with second-order forcing and noise, and
+// the inverse transform f_l = w_l sum_a T_al m*_a / N_a written to out[l * stride].
+template <class real>
+__device__ __forceinline__ void collide_store(const Mom<real>& m, real d, real rs, real Ux, real Uz, real Fx, real Fz,
+                                              real ld, real le, real ls, real lq, real leps, real od, real oe, real os,
+                                              const real xi[9], real* out, int stride) {
+  const real UxUx = Ux * Ux, UzUz = Uz * Uz;
+  const real s1 = m.m1 + ld * (rs * Ux - m.m1) + od * Fx + xi[1];
+  const real s2 = m.m2 + ld * (rs * Uz - m.m2) + od * Fz + xi[2];
+  const real s3 = m.m3 + le * (3 * rs * (UxUx + UzUz) - m.m3) + oe * (6 * (Ux * Fx + Uz * Fz)) + xi[3];
+  const real s4 = m.m4 + ls * (rs * (UxUx - UzUz) - m.m4) + os * (2 * (Ux * Fx - Uz * Fz)) + xi[4];
+  const real s5 = m.m5 + ls * (rs * Ux * Uz - m.m5) + os * (Ux * Fz + Uz * Fx) + xi[5];
+  const real s6 = m.m6 - lq * m.m6 + xi[6];
+  const real s7 = m.m7 - lq * m.m7 + xi[7];
+  const real s8 = m.m8 - leps * m.m8 + xi[8];
+  // divide by N_a = (1, 1/3, 1/3, 4, 4/9, 1/9, 2/3, 2/3, 16)
+  const real M0 = d, M1 = 3 * s1, M2 = 3 * s2, M3 = real(0.25) * s3, M4 = real(2.25) * s4, M5 = 9 * s5,
+             M6 = real(1.5) * s6, M7 = real(1.5) * s7, M8 = real(0.0625) * s8;
+  const real c9 = real(1) / 9, c36 = real(1) / 36;
+  const real base4 = M0 + M3 - 4 * M8;
+  const real base5 = M0 + 4 * M3 + 8 * M8;
+  const real p12 = M1 + M2, p1m2 = M1 - M2, q67 = 2 * (M6 + M7), q6m7 = 2 * (M6 - M7);
+  __stcs(out + 0 * stride, real(4) / 9 * (M0 - 2 * M3 + 2 * M8));
+  __stcs(out + 1 * stride, c9 * (base4 + M1 + M4 - M6));
+  __stcs(out + 2 * stride, c9 * (base4 + M2 - M4 - M7));
+  __stcs(out + 3 * stride, c9 * (base4 - M1 + M4 + M6));
+  __stcs(out + 4 * stride, c9 * (base4 - M2 - M4 + M7));
+  __stcs(out + 5 * stride, c36 * (base5 + p12 + M5 + q67));
+  __stcs(out + 6 * stride, c36 * (base5 - p1m2 - M5 - q6m7));
+  __stcs(out + 7 * stride, c36 * (base5 - p12 + M5 - q67));
+  __stcs(out + 8 * stride, c36 * (base5 + p1m2 - M5 + q6m7));
+}
+
+// Box-Muller pair of the working precision.  FP64: exact-as-libm (log, sincospi).  FP32: log
+// to full precision (its value matters near u1 -> 1), sqrt through the reciprocal square root,
+// and the angle reduced to (-pi, pi) for the fast sine/cosine: cos 2 pi u2 = -cos phi and
+// sin 2 pi u2 = -sin phi with phi = pi (2 u2 - 1); absolute error below 3e-6 on a normal.
+template <class real>
+__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, real& n0, real& n1);
+template <>
+__device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float& n0, float& n1) {
+  const float u1 = uniform01<float>(a), u2 = uniform01<float>(b);
+  const float t = -2.0f * logf(u1);
+  const float r = t * rsqrtf(t);
+  const float phi = 3.14159265358979f * (2.0f * u2 - 1.0f);
+  float s, c;
+  __sincosf(phi, &s, &c);
+  n0 = -r * c;
+  n1 = -r * s;
+}
+template <>
+__device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, double& n0, double& n1) {
+  box_muller<double>(a, b, n0, n1);
 }
 
 template <class real>
@@ -72,70 +188,45 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One collision of species S in moment space (Eq. MRT) with second-order forcing and noise;
-// v: the 9 pulled deviations; d: their sum; rs: the full density rho^S; (Fx, Fz): rho^S a^S.
-// Writes the 9 post-collision deviations back into v.
-template <class real>
-__device__ __forceinline__ void collide_species(real v[9], real d, real rs, real Ux, real Uz, real Fx, real Fz,
-                                                const real lam[9], const real omh[9], const real xi[9]) {
-  // moments of Table I in the structured form
-  const real a57 = v[5] - v[7], a68 = v[6] - v[8];
-  const real d13 = v[1] - v[3], d24 = v[2] - v[4];
-  const real e = (v[1] + v[3]) + (v[2] + v[4]);
-  const real dg = (v[5] + v[7]) + (v[6] + v[8]);
-  const real m1 = d13 + a57 - a68;
-  const real m2 = d24 + a57 + a68;
-  const real m3 = -2 * v[0] + e + 4 * dg;
-  const real m4 = (v[1] + v[3]) - (v[2] + v[4]);
-  const real m5 = (v[5] + v[7]) - (v[6] + v[8]);
-  const real m6 = -d13 + 2 * (a57 - a68);
-  const real m7 = -d24 + 2 * (a57 + a68);
-  const real m8 = 2 * v[0] - 4 * e + 8 * dg;
-  const real UxUx = Ux * Ux, UzUz = Uz * Uz;
-  // relaxation toward m^eq(rho^S, U) of Table I, forcing moments S_a, noise xi_a
-  const real s1 = m1 + lam[1] * (rs * Ux - m1) + omh[1] * Fx + xi[1];
-  const real s2 = m2 + lam[2] * (rs * Uz - m2) + omh[2] * Fz + xi[2];
-  const real s3 = m3 + lam[3] * (3 * rs * (UxUx + UzUz) - m3) + omh[3] * (6 * (Ux * Fx + Uz * Fz)) + xi[3];
-  const real s4 = m4 + lam[4] * (rs * (UxUx - UzUz) - m4) + omh[4] * (2 * (Ux * Fx - Uz * Fz)) + xi[4];
-  const real s5 = m5 + lam[5] * (rs * Ux * Uz - m5) + omh[5] * (Ux * Fz + Uz * Fx) + xi[5];
-  const real s6 = m6 - lam[6] * m6 + xi[6];
-  const real s7 = m7 - lam[7] * m7 + xi[7];
-  const real s8 = m8 - lam[8] * m8 + xi[8];
-  // divide by N_a = (1, 1/3, 1/3, 4, 4/9, 1/9, 2/3, 2/3, 16)
-  const real M0 = d, M1 = 3 * s1, M2 = 3 * s2, M3 = real(0.25) * s3, M4 = real(2.25) * s4, M5 = 9 * s5,
-             M6 = real(1.5) * s6, M7 = real(1.5) * s7, M8 = real(0.0625) * s8;
-  // f_l = w_l sum_a T_al M_a
-  const real c9 = real(1) / 9, c36 = real(1) / 36;
-  const real base4 = M0 + M3 - 4 * M8;
-  const real base5 = M0 + 4 * M3 + 8 * M8;
-  v[0] = real(4) / 9 * (M0 - 2 * M3 + 2 * M8);
-  v[1] = c9 * (base4 + M1 + M4 - M6);
-  v[3] = c9 * (base4 - M1 + M4 + M6);
-  v[2] = c9 * (base4 + M2 - M4 - M7);
-  v[4] = c9 * (base4 - M2 - M4 + M7);
-  const real p12 = M1 + M2, p1m2 = M1 - M2, q67 = 2 * (M6 + M7), q6m7 = 2 * (M6 - M7);
-  v[5] = c36 * (base5 + p12 + M5 + q67);
-  v[7] = c36 * (base5 - p12 + M5 - q67);
-  v[6] = c36 * (base5 - p1m2 - M5 - q6m7);
-  v[8] = c36 * (base5 + p1m2 - M5 + q6m7);
-}
-
 }  // namespace
 
-// Advance one work item by one step.  ring: 2 x 4 x (TX + 2) reals of shared memory.
+// Shared memory of one block: reduction scratch, the lattice's constants, the density ring
+// (2 x 4 rows) and the population stage (NS rows x 18 links), rows TX + 2 wide.
+template <class real>
+struct Smem {
+  static constexpr size_t red = 0;
+  static constexpr size_t lat = 8 * 3 * sizeof(double);
+  static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
+  __host__ __device__ static size_t stage(int tx) { return ring + (size_t)8 * (tx + 2) * sizeof(real); }
+  __host__ __device__ static size_t bytes(int tx) { return stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real); }
+};
+
+// Advance one work item by one step.
 template <class real, bool SAMPLE, bool NOISE>
-__device__ __forceinline__ void process_item(const StepArgs<real>& a, const real* __restrict__ src, real* __restrict__ dst,
-                                             int item_index, uint32_t step, real* ringA, real* ringB,
-                                             double* red) {
+__device__ __forceinline__ void process_item(const StepArgs<real>& a, const real* __restrict__ src,
+                                             real* __restrict__ dst, int item_index, uint32_t step,
+                                             unsigned char* smem) {
+  double* red = reinterpret_cast<double*>(smem + Smem<real>::red);
+  LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + Smem<real>::lat);
+  const int TX = blockDim.x, W = TX + 2;
+  real* ringA = reinterpret_cast<real*>(smem + Smem<real>::ring);
+  real* ringB = ringA + 4 * W;
+  real* stage = reinterpret_cast<real*>(smem + Smem<real>::stage(TX));
+
   const WorkItem it = a.items[item_index];
-  const LatticeDev<real>& L = a.lat[it.lattice];
+  __syncthreads();  // shared memory may still be read for the previous item
+  {
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(a.lat + it.lattice);
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(Ls);
+    for (int i = threadIdx.x; i < (int)(sizeof(LatticeDev<real>) / 4); i += TX) d32[i] = s32[i];
+  }
+  __syncthreads();
+  const LatticeDev<real>& L = *Ls;
   const int Lx = L.Lx, Lz = L.Lz, LzLx = Lx * Lz;
-  const int tid = threadIdx.x, TX = blockDim.x, W = TX + 2;
+  const int tid = threadIdx.x;
   const int nact = min(TX, Lx - it.x0);
   const bool active = tid < nact;
   const int x = it.x0 + (active ? tid : 0);
-  const int xm = (x == 0) ? Lx - 1 : x - 1;
-  const int xp = (x + 1 == Lx) ? 0 : x + 1;
   const int xl = (it.x0 == 0) ? Lx - 1 : it.x0 - 1;
   const int xr = (it.x0 + nact == Lx) ? 0 : it.x0 + nact;
   const bool do_left = tid == 0, do_right = tid == nact - 1;
@@ -144,27 +235,43 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   const real k9 = L.k9, k36 = L.k36;
   const int flags = L.flags;
   const RowConst<real>* rows = a.rows + L.row_off;
+  const int z0 = it.z0, z1 = it.z1;
 
-  __syncthreads();  // the ring may still be read for the previous item
-
-  // densities of row z (own column and halo columns) into the ring
-  auto put_rho = [&](int z, real dA, real dB) {
-    const int b = ring_slot(z) * W;
+  auto stage_row = [&](int r) {
+    if (r >= 0 && r < Lz && r <= z1) {
+      real* sb = stage + (r & (NS - 1)) * 18 * W;
+      if (active) stage_column(f, LzLx, Lx, Lz, r, x, sb + tid + 1, W);
+      if (do_left) stage_column(f, LzLx, Lx, Lz, r, xl, sb, W);
+      if (do_right) stage_column(f, LzLx, Lx, Lz, r, xr, sb + nact + 1, W);
+    }
+    cp_commit();
+  };
+  // density deviations of staged row r at stage column c (this thread staged that column)
+  auto rho_at = [&](int r, int c, real& dA, real& dB) {
+    const real* sb = stage + (r & (NS - 1)) * 18 * W;
+    real v[9];
+    read_species(sb, W, c, 0, r > 0, r < Lz - 1, k9, k36, v);
+    dA = sum9(v);
+    read_species(sb, W, c, 1, r > 0, r < Lz - 1, k9, k36, v);
+    dB = sum9(v);
+  };
+  auto put_rho = [&](int r) {
+    const int b = ring_slot(r) * W;
+    real dA, dB;
     if (active) {
+      rho_at(r, tid + 1, dA, dB);
       ringA[b + tid + 1] = dA;
       ringB[b + tid + 1] = dB;
     }
     if (do_left) {
-      real hA, hB;
-      pull_rho(f, LzLx, Lx, Lz, z, xl, k9, k36, hA, hB);
-      ringA[b] = hA;
-      ringB[b] = hB;
+      rho_at(r, 0, dA, dB);
+      ringA[b] = dA;
+      ringB[b] = dB;
     }
     if (do_right) {
-      real hA, hB;
-      pull_rho(f, LzLx, Lx, Lz, z, xr, k9, k36, hA, hB);
-      ringA[b + nact + 1] = hA;
-      ringB[b + nact + 1] = hB;
+      rho_at(r, nact + 1, dA, dB);
+      ringA[b + nact + 1] = dA;
+      ringB[b + nact + 1] = dB;
     }
   };
   // wall ghost row zg from the adjacent fluid row za (Sec. II.A)
@@ -188,141 +295,136 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     if (do_right) copy1(nact + 1);
   };
 
-  real cur[18], dA = 0, dB = 0;
-  if (active) pull_site(f, LzLx, Lx, Lz, it.z0, x, xm, xp, k9, k36, cur, dA, dB);
-  put_rho(it.z0, dA, dB);
-  if (it.z0 > 0) {
-    real pA = 0, pB = 0;
-    if (active) pull_rho(f, LzLx, Lx, Lz, it.z0 - 1, x, k9, k36, pA, pB);
-    put_rho(it.z0 - 1, pA, pB);
-  } else {
-    ghost_row(-1, 0);
-  }
+  // prologue: rows z0-1 .. z0+NS-2 in flight, rows z0-1 and z0 landed
+  for (int r = z0 - 1; r <= z0 + NS - 2; ++r) stage_row(r);
+  cp_wait<NS - 2>();
+  if (z0 > 0) put_rho(z0 - 1);
+  put_rho(z0);
+  if (z0 == 0) ghost_row(-1, 0);
 
+  const real G = L.G, g3 = L.g3;
+  const real ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
+  const real od = L.omh[1], oe = L.omh[3], os = L.omh[4];
   double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
-  const real G = L.G;
 
-  for (int z = it.z0; z < it.z1; ++z) {
-    real nxt[18], nA = 0, nB = 0;
-    if (z + 1 < Lz) {
-      if (active) pull_site(f, LzLx, Lx, Lz, z + 1, x, xm, xp, k9, k36, nxt, nA, nB);
-      put_rho(z + 1, nA, nB);
-    } else {
-      ghost_row(Lz, Lz - 1);
-    }
+  for (int z = z0; z < z1; ++z) {
+    cp_wait<NS - 3>();  // row z+1 landed
+    if (z + 1 < Lz) put_rho(z + 1);
+    else ghost_row(Lz, Lz - 1);
     __syncthreads();
+    stage_row(z + NS - 1);  // into the slot of row z-1, read by every thread before the barrier
 
     if (active) {
       const RowConst<real> rc = rows[z];
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real Aw = ringA[bc - 1], Ae = ringA[bc + 1], An = ringA[bu], Anw = ringA[bu - 1], Ane = ringA[bu + 1],
-                 As = ringA[bd], Asw = ringA[bd - 1], Ase = ringA[bd + 1];
-      const real Bw = ringB[bc - 1], Be = ringB[bc + 1], Bn = ringB[bu], Bnw = ringB[bu - 1], Bne = ringB[bu + 1],
-                 Bs = ringB[bd], Bsw = ringB[bd - 1], Bse = ringB[bd + 1];
-      const real c9 = real(1) / 9, c36 = real(1) / 36;
-      // sum_l w_l c_l rho^S(r + c_l), deviations plus the background part (Eq. aNI)
-      const real sAx = c9 * (Ae - Aw) + c36 * ((Ane - Anw) + (Ase - Asw));
-      const real sAz = c9 * (An - As) + c36 * ((Ane + Anw) - (Ase + Asw)) + rc.dbgA;
-      const real sBx = c9 * (Be - Bw) + c36 * ((Bne - Bnw) + (Bse - Bsw));
-      const real sBz = c9 * (Bn - Bs) + c36 * ((Bne + Bnw) - (Bse + Bsw)) + rc.dbgB;
-      const real rhoA = rc.bgA + dA, rhoB = rc.bgB + dB, rho = rhoA + rhoB;
-      const real inv = real(1) / rho;
-      // non-ideal force densities rho^S a^S_NI and their sum
-      const real FnAx = -G * rhoA * sBx, FnAz = -G * rhoA * sBz;
-      const real FnBx = -G * rhoB * sAx, FnBz = -G * rhoB * sAz;
-      const real FNx = FnAx + FnBx, FNz = FnAz + FnBz;
-      real FAx, FAz, FBx, FBz;
-      if (flags & DF_ASTAR) {
-        // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
-        const real cA = rhoA * inv, cB = rhoB * inv;
-        FAx = cA * FNx; FAz = cA * FNz;
-        FBx = cB * FNx; FBz = cB * FNz;
-      } else {
-        FAx = FnAx; FAz = FnAz;
-        FBx = FnBx; FBz = FnBz;
-      }
-      // gradient forcing: rho^A a^A_NE = (0, rho grad_c0 / 3) = -rho^B a^B_NE (Eq. NEcond)
-      const real ne = rho * L.g3;
-      FAz += ne;
-      FBz -= ne;
-      // barycentric velocity, Eq. (bar)
-      const real jAx = (cur[1] - cur[3]) + (cur[5] - cur[6]) + (cur[8] - cur[7]);
-      const real jAz = (cur[2] - cur[4]) + (cur[5] + cur[6]) - (cur[7] + cur[8]);
-      const real jBx = (cur[10] - cur[12]) + (cur[14] - cur[15]) + (cur[17] - cur[16]);
-      const real jBz = (cur[11] - cur[13]) + (cur[14] + cur[15]) - (cur[16] + cur[17]);
-      const real Ux = (jAx + jBx + real(0.5) * FNx) * inv;
-      const real Uz = (jAz + jBz + real(0.5) * FNz) * inv;
+      const real dA = ringA[bc], dB = ringB[bc];
+      const real* sb = stage + (z & (NS - 1)) * 18 * W;
+      const bool below = z > 0, above = z < Lz - 1;
+      real v[9];
+      read_species(sb, W, tid + 1, 0, below, above, k9, k36, v);
+      const Mom<real> mA = moments(v);
+      read_species(sb, W, tid + 1, 1, below, above, k9, k36, v);
+      const Mom<real> mB = moments(v);
 
+      const real c9 = real(1) / 9, c36 = real(1) / 36;
+      real FNx, FNz, FAx, FAz, FBx, FBz, rhoA, rhoB, inv;
+      {
+        const real Aw = ringA[bc - 1], Ae = ringA[bc + 1], An = ringA[bu], Anw = ringA[bu - 1], Ane = ringA[bu + 1],
+                   As = ringA[bd], Asw = ringA[bd - 1], Ase = ringA[bd + 1];
+        const real Bw = ringB[bc - 1], Be = ringB[bc + 1], Bn = ringB[bu], Bnw = ringB[bu - 1],
+                   Bne = ringB[bu + 1], Bs = ringB[bd], Bsw = ringB[bd - 1], Bse = ringB[bd + 1];
+        // sum_l w_l c_l rho^S(r + c_l), deviations plus the background part (Eq. aNI)
+        const real sAx = c9 * (Ae - Aw) + c36 * ((Ane - Anw) + (Ase - Asw));
+        const real sAz = c9 * (An - As) + c36 * ((Ane + Anw) - (Ase + Asw)) + rc.dbgA;
+        const real sBx = c9 * (Be - Bw) + c36 * ((Bne - Bnw) + (Bse - Bsw));
+        const real sBz = c9 * (Bn - Bs) + c36 * ((Bne + Bnw) - (Bse + Bsw)) + rc.dbgB;
+        rhoA = rc.bgA + dA;
+        rhoB = rc.bgB + dB;
+        const real rho = rhoA + rhoB;
+        inv = real(1) / rho;
+        const real FnAx = -G * rhoA * sBx, FnAz = -G * rhoA * sBz;
+        const real FnBx = -G * rhoB * sAx, FnBz = -G * rhoB * sAz;
+        FNx = FnAx + FnBx;
+        FNz = FnAz + FnBz;
+        if (flags & DF_ASTAR) {
+          // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
+          const real cA = rhoA * inv, cB = rhoB * inv;
+          FAx = cA * FNx; FAz = cA * FNz;
+          FBx = cB * FNx; FBz = cB * FNz;
+        } else {
+          FAx = FnAx; FAz = FnAz;
+          FBx = FnBx; FBz = FnBz;
+        }
+        // gradient forcing: rho^A a^A_NE = (0, rho grad_c0 / 3) = -rho^B a^B_NE (Eq. NEcond)
+        const real ne = rho * g3;
+        FAz += ne;
+        FBz -= ne;
+        if (SAMPLE) {
+          // pressure (half trace; kinetic + interaction), minus its background part
+          const real kin = (mA.m3 + mB.m3 + 2 * (dA + dB)) * (real(1) / 6);
+          const real NA = c9 * (Ae + Aw + An + As) + real(2) / 36 * (Ane + Anw + Ase + Asw);
+          const real NB = c9 * (Be + Bw + Bn + Bs) + real(2) / 36 * (Bne + Bnw + Bse + Bsw);
+          const real inter = dA * (rc.nbB + NB) + rc.bgA * NB + dB * (rc.nbA + NA) + rc.bgB * NA;
+          acc_p += (double)(kin + real(0.25) * G * inter);
+          acc_a += (double)dA;
+          acc_b += (double)dB;
+        }
+      }
+      // barycentric velocity, Eq. (bar)
+      const real Ux = (mA.m1 + mB.m1 + real(0.5) * FNx) * inv;
+      const real Uz = (mA.m2 + mB.m2 + real(0.5) * FNz) * inv;
       if (SAMPLE) {
-        real* fl = a.fields + 4 * (L.site_off) + z * Lx + x;
+        real* fl = a.fields + 4 * L.site_off + z * Lx + x;
         fl[0] = dA + dB - L.rho_bar_off;
         fl[LzLx] = (dA - rc.c0 * (dA + dB)) * inv;
         fl[2 * LzLx] = Ux;
         fl[3 * LzLx] = Uz;
-        // pressure (half trace; kinetic + interaction), minus its background part
-        const real m3A = -2 * cur[0] + (cur[1] + cur[2] + cur[3] + cur[4]) +
-                         4 * (cur[5] + cur[6] + cur[7] + cur[8]);
-        const real m3B = -2 * cur[9] + (cur[10] + cur[11] + cur[12] + cur[13]) +
-                         4 * (cur[14] + cur[15] + cur[16] + cur[17]);
-        const real kin = (m3A + m3B + 2 * (dA + dB)) * (real(1) / 6);
-        const real NA = c9 * (Ae + Aw + An + As) + real(2) / 36 * (Ane + Anw + Ase + Asw);
-        const real NB = c9 * (Be + Bw + Bn + Bs) + real(2) / 36 * (Bne + Bnw + Bse + Bsw);
-        const real inter = dA * (rc.nbB + NB) + rc.bgA * NB + dB * (rc.nbA + NA) + rc.bgB * NA;
-        acc_p += (double)(kin + real(0.25) * G * inter);
-        acc_a += (double)dA;
-        acc_b += (double)dB;
       }
 
-      real xiA[9], xiB[9];
+      real xi[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) { xiA[k] = 0; xiB[k] = 0; }
+      for (int k = 0; k < 9; ++k) xi[k] = 0;
+      real nm0 = 0, nm1 = 0;
+      const uint32_t site = (uint32_t)(z * Lx + x);
+      const bool loc = flags & DF_NOISE_LOC;
       if (NOISE) {
-        const uint32_t site = (uint32_t)(z * Lx + x);
-        real n[14];
+        real n[8];
         const U4 r0 = philox(U4{site, step, L.lattice_id, 0u}, L.key0, L.key1);
-        box_muller<real>(r0.x, r0.y, n[0], n[1]);
-        box_muller<real>(r0.z, r0.w, n[2], n[3]);
+        normal_pair<real>(r0.x, r0.y, n[0], n[1]);
+        normal_pair<real>(r0.z, r0.w, n[2], n[3]);
         const U4 r1 = philox(U4{site, step, L.lattice_id, 1u}, L.key0, L.key1);
-        box_muller<real>(r1.x, r1.y, n[4], n[5]);
-        box_muller<real>(r1.z, r1.w, n[6], n[7]);
-        const U4 r2 = philox(U4{site, step, L.lattice_id, 2u}, L.key0, L.key1);
-        box_muller<real>(r2.x, r2.y, n[8], n[9]);
-        box_muller<real>(r2.z, r2.w, n[10], n[11]);
-        const U4 r3 = philox(U4{site, step, L.lattice_id, 3u}, L.key0, L.key1);
-        box_muller<real>(r3.x, r3.y, n[12], n[13]);
-        real smom, sA[9], sB[9];
-        if (flags & DF_NOISE_LOC) {
-          smom = L.pref_mom * rsqrt_pos<real>(rhoA * rhoB * inv);
-          const real qA = rsqrt_pos<real>(rhoA), qB = rsqrt_pos<real>(rhoB);
+        normal_pair<real>(r1.x, r1.y, n[4], n[5]);
+        normal_pair<real>(r1.z, r1.w, n[6], n[7]);
+        const real smom = loc ? L.pref_mom * rsqrt_pos<real>(rhoA * rhoB * inv) : L.sig_mom;
+        const real qA = loc ? rsqrt_pos<real>(rhoA) : real(1);
+        nm0 = smom * n[0];
+        nm1 = smom * n[1];
+        xi[1] = nm0;
+        xi[2] = nm1;
 #pragma unroll
-          for (int k = 3; k < 9; ++k) { sA[k] = L.pref[k] * qA; sB[k] = L.pref[k] * qB; }
-        } else {
-          smom = L.sig_mom;
-#pragma unroll
-          for (int k = 3; k < 9; ++k) { sA[k] = L.sig[0][k]; sB[k] = L.sig[1][k]; }
-        }
-        xiA[1] = smom * n[0];
-        xiA[2] = smom * n[1];
-        xiB[1] = -xiA[1];
-        xiB[2] = -xiA[2];
-#pragma unroll
-        for (int k = 3; k < 9; ++k) {
-          xiA[k] = sA[k] * n[k - 1];
-          xiB[k] = sB[k] * n[k + 5];
-        }
+        for (int k = 3; k < 9; ++k) xi[k] = (loc ? L.pref[k] * qA : L.sig[0][k]) * n[k - 1];
       }
-      collide_species<real>(cur, dA, rhoA, Ux, Uz, FAx, FAz, L.lam, L.omh, xiA);
-      collide_species<real>(cur + 9, dB, rhoB, Ux, Uz, FBx, FBz, L.lam, L.omh, xiB);
       const int r0 = z * Lx + x;
+      collide_store<real>(mA, dA, rhoA, Ux, Uz, FAx, FAz, ld, le, ls, lq, leps, od, oe, os, xi, g + r0, LzLx);
+      if (NOISE) {
+        real n[6];
+        const U4 r2 = philox(U4{site, step, L.lattice_id, 2u}, L.key0, L.key1);
+        normal_pair<real>(r2.x, r2.y, n[0], n[1]);
+        normal_pair<real>(r2.z, r2.w, n[2], n[3]);
+        const U4 r3 = philox(U4{site, step, L.lattice_id, 3u}, L.key0, L.key1);
+        normal_pair<real>(r3.x, r3.y, n[4], n[5]);
+        const real qB = loc ? rsqrt_pos<real>(rhoB) : real(1);
+        xi[1] = -nm0;
+        xi[2] = -nm1;
 #pragma unroll
-      for (int k = 0; k < 18; ++k) g[k * LzLx + r0] = cur[k];
+        for (int k = 3; k < 9; ++k) xi[k] = (loc ? L.pref[k] * qB : L.sig[1][k]) * n[k - 3];
+      }
+      collide_store<real>(mB, dB, rhoB, Ux, Uz, FBx, FBz, ld, le, ls, lq, leps, od, oe, os, xi, g + 9 * LzLx + r0,
+                          LzLx);
     }
-#pragma unroll
-    for (int k = 0; k < 18; ++k) cur[k] = nxt[k];
-    dA = nA;
-    dB = nB;
   }
+  cp_wait<0>();  // nothing may land in shared memory after the item
 
   if (SAMPLE) {
     acc_p = warp_sum<real>(acc_p);
@@ -350,18 +452,15 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
 }
 
 template <class real>
-__host__ __device__ constexpr size_t ring_bytes(int tile_x) {
-  return (size_t)2 * 4 * (tile_x + 2) * sizeof(real) + 8 * 3 * sizeof(double) + 64;
-}
+struct MinBlocks {
+  static constexpr int value = sizeof(real) == 4 ? 2 : 1;
+};
 
 template <class real, bool SAMPLE, bool NOISE>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs<real> a) {
+__global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepArgs<real> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);
-  real* ringA = reinterpret_cast<real*>(smem + 8 * 3 * sizeof(double));
-  real* ringB = ringA + 4 * (blockDim.x + 2);
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
-  process_item<real, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, ringA, ringB, red);
+  process_item<real, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem);
 }
 
 // ---- bounded grid barrier for the persistent launch --------------------------------
@@ -405,12 +504,9 @@ __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int limi
 }
 
 template <class real, bool NOISE>
-__global__ void __launch_bounds__(256) persistent_kernel(StepArgs<real> a, int nsteps, int sample_last,
-                                                         unsigned* bar, int* err, int limit_ms) {
+__global__ void __launch_bounds__(256, MinBlocks<real>::value)
+    persistent_kernel(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);
-  real* ringA = reinterpret_cast<real*>(smem + 8 * 3 * sizeof(double));
-  real* ringB = ringA + 4 * (blockDim.x + 2);
   const int64_t t0 = *a.d_t + a.t_offset;
   for (int k = 0; k < nsteps; ++k) {
     const real* src = (k & 1) ? a.dst : a.src;
@@ -418,8 +514,8 @@ __global__ void __launch_bounds__(256) persistent_kernel(StepArgs<real> a, int n
     const uint32_t step = (uint32_t)(t0 + k);
     const bool sample = sample_last && k == nsteps - 1;
     for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) {
-      if (sample) process_item<real, true, NOISE>(a, src, dst, i, step, ringA, ringB, red);
-      else process_item<real, false, NOISE>(a, src, dst, i, step, ringA, ringB, red);
+      if (sample) process_item<real, true, NOISE>(a, src, dst, i, step, smem);
+      else process_item<real, false, NOISE>(a, src, dst, i, step, smem);
     }
     if (k + 1 < nsteps) {
       if (!grid_barrier(bar, err, gridDim.x, limit_ms)) return;
@@ -434,8 +530,26 @@ __global__ void barrier_probe_kernel(unsigned* bar, int* err, unsigned expected,
 }
 
 template <class real>
+size_t step_smem_bytes(int tile_x) {
+  return Smem<real>::bytes(tile_x);
+}
+
+template <class real>
+cudaError_t prepare_step(int max_tile_x) {
+  const int bytes = (int)Smem<real>::bytes(max_tile_x);
+  const void* fns[] = {(const void*)step_kernel<real, true, true>, (const void*)step_kernel<real, true, false>,
+                       (const void*)step_kernel<real, false, true>, (const void*)step_kernel<real, false, false>,
+                       (const void*)persistent_kernel<real, true>, (const void*)persistent_kernel<real, false>};
+  for (const void* fn : fns) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <class real>
 cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, bool noise, cudaStream_t s) {
-  const size_t smem = ring_bytes<real>(tile_x);
+  const size_t smem = Smem<real>::bytes(tile_x);
   if (a.n_items <= 0) return cudaSuccess;
   if (sample) {
     if (noise) step_kernel<real, true, true><<<a.n_items, tile_x, smem, s>>>(a);
@@ -453,7 +567,7 @@ int persistent_grid(int tile_x, bool sample, bool noise) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = ring_bytes<real>(tile_x);
+  const size_t smem = Smem<real>::bytes(tile_x);
   cudaError_t e = noise ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_kernel<real, true>, tile_x, smem)
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_kernel<real, false>, tile_x, smem);
   if (e != cudaSuccess) return 0;
@@ -463,7 +577,7 @@ int persistent_grid(int tile_x, bool sample, bool noise) {
 template <class real>
 cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, bool noise,
                                    unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
-  const size_t smem = ring_bytes<real>(tile_x);
+  const size_t smem = Smem<real>::bytes(tile_x);
   StepArgs<real> aa = a;
   int ns = nsteps, sl = sample_last ? 1 : 0;
   void* args[] = {&aa, &ns, &sl, &barrier, &err, &limit_ms};
@@ -483,13 +597,14 @@ cudaError_t launch_barrier_probe(int blocks, int expected, int limit_ms, unsigne
   return cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(blocks), dim3(32), args, 0, s);
 }
 
-template cudaError_t launch_step<float>(const StepArgs<float>&, int, bool, bool, cudaStream_t);
-template cudaError_t launch_step<double>(const StepArgs<double>&, int, bool, bool, cudaStream_t);
-template int persistent_grid<float>(int, bool, bool);
-template int persistent_grid<double>(int, bool, bool);
-template cudaError_t launch_step_persistent<float>(const StepArgs<float>&, int, int, bool, bool, unsigned*, int*, int,
-                                                   int, cudaStream_t);
-template cudaError_t launch_step_persistent<double>(const StepArgs<double>&, int, int, bool, bool, unsigned*, int*,
+#define LB_STEP_INST(real)                                                                                       \
+  template size_t step_smem_bytes<real>(int);                                                                    \
+  template cudaError_t prepare_step<real>(int);                                                                  \
+  template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, bool, cudaStream_t);                  \
+  template int persistent_grid<real>(int, bool, bool);                                                           \
+  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, bool, bool, unsigned*, int*, \
                                                     int, int, cudaStream_t);
+LB_STEP_INST(float)
+LB_STEP_INST(double)
 
 }  // namespace lbk

@@ -158,7 +158,7 @@ def test_sampled_structure_factors_and_pressure(prec):
 def test_launch_modes_and_tiles_are_bit_identical(prec):
     """Direct launches, CUDA graphs, the persistent cooperative launch and every tile shape
     compute each site identically."""
-    p = LatticeParams(96, 24, kT=1e-5, G=0.5, grad_c0=0.4 / 24, seed=9)
+    p = LatticeParams(128, 32, kT=1e-5, G=0.5, grad_c0=0.4 / 32, seed=9)
     results = []
     configs = [dict(), dict(graph=True), dict(persistent=True), dict(graph=True, persistent=True)]
     for kw in configs:
@@ -167,20 +167,26 @@ def test_launch_modes_and_tiles_are_bit_identical(prec):
             sim.step(70)
             sim.step(33)
             results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0]))
-    for tile in [(32, 5), (256, 24), (64, 1)]:
+    for tile in [(32, 5), (256, 32), (64, 1)]:
         with Simulation(p, precision=prec) as sim:
             sim.set_tile(*tile)
             sim.set_sampling(3, 7)
             sim.step(103)
             results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0]))
-    for r in results[1:]:
+    for i, r in enumerate(results[1:], start=1):
         np.testing.assert_array_equal(r[0], results[0][0])
-        assert r[1] == results[0][1]
         np.testing.assert_array_equal(r[2], results[0][2])
+        if i < len(configs):
+            assert r[1] == results[0][1]
+        else:  # another tile groups the double-precision pressure sums differently
+            np.testing.assert_allclose(r[1], results[0][1], rtol=1e-14)
 
 
-@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-13), ("dev32", 1e-9)])
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-13), ("dev32", 2e-8)])
 def test_mass_is_conserved(prec, rtol):
+    """Per-species mass (Sec. II.A).  FP64 storage conserves it to round-off; FP32 deviation
+    storage rounds every post-collision population, a random walk of about 1e-9 relative over
+    500 steps at kT = 1e-4 (the sums themselves are taken in double precision)."""
     p = LatticeParams(64, 32, kT=1e-4, G=0.5, grad_c0=0.01, seed=5)
     with Simulation(p, precision=prec) as sim:
         m0 = sim.mass()
