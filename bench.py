@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / large-lattice / e2e / CPU legs")
     ap.add_argument("--profile-small", action="store_true",
                     help="run a small single-lattice case only (for ncu captures)")
+    ap.add_argument("--profile-kT", type=float, default=1e-5, help="kT of the small case")
+    ap.add_argument("--profile-precision", default="dev32", choices=["dev32", "fp64"])
     return ap.parse_args()
 
 
@@ -326,15 +328,15 @@ def run_reference(args):
     }))
 
 
-def run_profile_small():
-    """A small case for ncu: one 4096 x 1024 FP32-deviation lattice (302 MB per state buffer, more
-    than L2), 6 steps."""
+def run_profile_small(kT, precision):
+    """A small case for ncu: one 4096 x 1024 lattice (302 MB per FP32 state buffer, more than L2),
+    6 steps."""
     import torch
 
     from paper_1808_05168_gb300 import LatticeParams, Simulation
 
-    p = LatticeParams(4096, 1024, kT=1e-5, G=0.5, grad_c0=0.5 / 1024, seed=4, lambda_e=1.0)
-    with Simulation(p, precision="dev32") as sim:
+    p = LatticeParams(4096, 1024, kT=kT, G=0.5, grad_c0=0.5 / 1024, seed=4, lambda_e=1.0)
+    with Simulation(p, precision=precision) as sim:
         sim.set_tile(128, 64)
         sim.step(6)
         sim.synchronize()
@@ -345,7 +347,7 @@ def run_profile_small():
 if __name__ == "__main__":
     a = parse()
     if a.profile_small:
-        run_profile_small()
+        run_profile_small(a.profile_kT, a.profile_precision)
     elif a.impl == "reference":
         run_reference(a)
     else:

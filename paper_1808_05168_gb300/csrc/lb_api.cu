@@ -20,7 +20,7 @@ using namespace lbk;
 namespace {
 
 const double kRhoBar = 1.0;  // reference total density (Sec. II.A)
-const double kCBar0 = 0.5;   // reference concentration c_0(z = 0) (Sec. II.A)
+constexpr double kCBar0 = 0.5;  // reference concentration c_0(z = 0) (Sec. II.A)
 const double kNorm[9] = {1.0, 1.0 / 3, 1.0 / 3, 4.0, 4.0 / 9, 1.0 / 9, 2.0 / 3, 2.0 / 3, 16.0};  // N_a, Table I
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -85,7 +85,7 @@ struct lb_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   int coop_grid = -1;
-  bool noise_any = false;
+  int noise_mode = NOISE_OFF;  // NOISE_OFF, NOISE_HOM or NOISE_LOC for the whole batch
   std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;  // graph, kernels in it
   int64_t launches = 0;  // kernels enqueued by lb_step so far (graph replays included)
 };
@@ -159,10 +159,10 @@ LatticeDev<real> make_lattice(const lb_params& p, int flags, bool dev, int64_t f
   const double ld = p.lambda_d;
   L.sig_mom = (real)std::sqrt((2.0 - ld) * ld * p.kT * rA * rB / (rA + rB));
   L.pref_mom = (real)std::sqrt((2.0 - ld) * ld * p.kT);
+  static_assert(kCBar0 == 0.5, "hom noise amplitudes assume equal reference densities");
   for (int a = 3; a < 9; ++a) {
     const double v = 3.0 * (2.0 - lam[a]) * lam[a] * kNorm[a] * p.kT;
-    L.sig[0][a] = (real)std::sqrt(v * rA);
-    L.sig[1][a] = (real)std::sqrt(v * rB);
+    L.sig[a] = (real)std::sqrt(v * rA);
     L.pref[a] = (real)std::sqrt(v);
   }
   return L;
@@ -375,7 +375,7 @@ cudaError_t enqueue_direct(lb_ctx* c, int cur, int64_t n, const std::vector<int6
   for (int64_t k = 0; k < n; ++k) {
     const bool sample = si < sample_offsets.size() && sample_offsets[si] == k;
     if (sample) ++si;
-    cudaError_t e = launch_step<real>(step_args<real>(c, cur, (int)k), c->tile_x, sample, c->noise_any, c->stream);
+    cudaError_t e = launch_step<real>(step_args<real>(c, cur, (int)k), c->tile_x, sample, c->noise_mode, c->stream);
     if (e != cudaSuccess) return e;
     c->launches += 1;
     if (sample) {
@@ -391,7 +391,7 @@ cudaError_t enqueue_direct(lb_ctx* c, int cur, int64_t n, const std::vector<int6
 // Persistent: one cooperative launch per run of steps ending with (at most) one sample step.
 template <class real>
 cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& sample_offsets) {
-  if (c->coop_grid < 0) c->coop_grid = persistent_grid<real>(c->tile_x, false, c->noise_any);
+  if (c->coop_grid < 0) c->coop_grid = persistent_grid<real>(c->tile_x, c->noise_mode);
   const int grid = std::min<int>(c->coop_grid, (int)c->items.size());
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
   int64_t k = 0;
@@ -407,7 +407,7 @@ cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<
     const int64_t len = end - k;
     cudaError_t e = cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
-    e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)len, sample, c->noise_any,
+    e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)len, sample, c->noise_mode,
                                      c->d_barrier, c->d_err, grid, 2000, c->stream);
     if (e != cudaSuccess) return e;
     c->launches += 1;
@@ -430,8 +430,8 @@ cudaError_t enqueue(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& s
 template <class real>
 int autotune(lb_ctx* c) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int64_t, int, int, int, bool>, std::pair<int, int>> cache;
-  const auto key = std::make_tuple(c->n_lat, c->n_sites, c->max_Lx, c->max_Lz, (int)c->dev32, c->noise_any);
+  static std::map<std::tuple<int, int64_t, int, int, int, int>, std::pair<int, int>> cache;
+  const auto key = std::make_tuple(c->n_lat, c->n_sites, c->max_Lx, c->max_Lz, (int)c->dev32, c->noise_mode);
   {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
@@ -453,11 +453,11 @@ int autotune(lb_ctx* c) {
       last = rr;
       if (build_items(c, tx, rr) != LB_OK) continue;
       // state is untouched: every trial reads f[cur] and writes f[cur ^ 1]
-      for (int k = 0; k < 2; ++k) launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_any, c->stream);
+      for (int k = 0; k < 2; ++k) launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->stream);
       cudaEventRecord(e0, c->stream);
       const int reps = 4;
       for (int k = 0; k < reps; ++k)
-        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_any, c->stream);
+        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->stream);
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         cudaGetLastError();
@@ -569,7 +569,7 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
     c->max_lattice_sites = std::max<int>(c->max_lattice_sites, (int)sites);
     c->max_Lx = std::max(c->max_Lx, ps[i].Lx);
     c->max_Lz = std::max(c->max_Lz, ps[i].Lz);
-    if (ps[i].kT > 0) c->noise_any = true;
+    if (ps[i].kT > 0) c->noise_mode = (flags & LB_NOISE_LOC) ? NOISE_LOC : NOISE_HOM;
   }
   c->n_f = foff;
   c->n_sites = soff;

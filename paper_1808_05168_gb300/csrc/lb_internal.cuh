@@ -22,6 +22,9 @@ namespace lbk {
 // Device-level flag bits (subset of the public flags that kernels look at).
 enum : int { DF_ASTAR = 1, DF_WALL_FIXED = 2, DF_NOISE_LOC = 4, DF_NOISE = 8 };
 
+// Noise variants of the step kernel.
+enum : int { NOISE_OFF = 0, NOISE_HOM = 1, NOISE_LOC = 2 };
+
 // Per-lattice constants in the working precision.
 template <class real>
 struct LatticeDev {
@@ -39,7 +42,8 @@ struct LatticeDev {
                      // species A, per weight class (w = 1/9, 1/36); zero in FP64 mode
   real rho_bar_off;  // rho_bar in FP64 mode, 0 in deviation mode
   real sig_mom;      // hom noise amplitude of moments 1, 2 (Eq. noise-bin-expl)
-  real sig[2][9];    // hom noise amplitudes of moments 3..8 (Eq. noise-bin-expl-high)
+  real sig[9];       // hom noise amplitudes of moments 3..8 (Eq. noise-bin-expl-high); the
+                     // reference densities of both species are rho_bar / 2 (c_bar0 = 1/2)
   real pref_mom;     // loc noise: sqrt((2 - l_d) l_d kT)
   real pref[9];      // loc noise: sqrt(3 (2 - l_a) l_a N_a kT)
 };
@@ -87,16 +91,77 @@ __device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-// Uniform in (0, 1) from the top 23 bits, (2 (k >> 9) + 1) 2^-24: exact in float and double.
+// The four Philox4x32-10 calls of one site, counters (c0, c1, c2, call) for call = 0..3, in
+// lockstep: the round keys are formed once for all four, and the products that do not yet
+// depend on the last counter word (both in round 1, M0 x in round 2, M1 x in round 3) are
+// formed once.  out[call] is bit-identical to philox({c0, c1, c2, call}, k0, k1).
+__device__ __forceinline__ void philox_site(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t k0, uint32_t k1,
+                                            U4 out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  // round 1: (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ call ^ k1, lo(M0 c0))
+  uint64_t p = (uint64_t)M0 * c0;
+  const uint32_t y3 = (uint32_t)p, t1 = (uint32_t)(p >> 32) ^ k1;
+  p = (uint64_t)M1 * c2;
+  const uint32_t y1 = (uint32_t)p, y0 = (uint32_t)(p >> 32) ^ c1 ^ k0;
+  // round 2: M0 y0 is common; M1 y2 depends on the call
+  k0 += W0;
+  k1 += W1;
+  p = (uint64_t)M0 * y0;
+  const uint32_t z3 = (uint32_t)p, z2 = (uint32_t)(p >> 32) ^ y3 ^ k1;
+  uint32_t s0[4], s1[4], s2[4], s3[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t q = (uint64_t)M1 * (t1 ^ (uint32_t)i);
+    s0[i] = (uint32_t)(q >> 32) ^ y1 ^ k0;
+    s1[i] = (uint32_t)q;
+  }
+  // round 3: M1 z2 is common; M0 s0 depends on the call
+  k0 += W0;
+  k1 += W1;
+  p = (uint64_t)M1 * z2;
+  const uint32_t r1 = (uint32_t)p, r0x = (uint32_t)(p >> 32) ^ k0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t q = (uint64_t)M0 * s0[i];
+    const uint32_t n0 = r0x ^ s1[i], n2 = (uint32_t)(q >> 32) ^ z3 ^ k1, n3 = (uint32_t)q;
+    s0[i] = n0;
+    s1[i] = r1;
+    s2[i] = n2;
+    s3[i] = n3;
+  }
+  // rounds 4..10
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    k0 += W0;
+    k1 += W1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t a = (uint64_t)M0 * s0[i], b = (uint64_t)M1 * s2[i];
+      const uint32_t n0 = (uint32_t)(b >> 32) ^ s1[i] ^ k0, n1 = (uint32_t)b;
+      const uint32_t n2 = (uint32_t)(a >> 32) ^ s3[i] ^ k1, n3 = (uint32_t)a;
+      s0[i] = n0;
+      s1[i] = n1;
+      s2[i] = n2;
+      s3[i] = n3;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = U4{s0[i], s1[i], s2[i], s3[i]};
+}
+
+// Uniform in (0, 1) from the top 23 bits, u = (2 (k >> 9) + 1) 2^-24, exact in float and double:
+// the bits form x = 1 + (k >> 9) 2^-23 in [1, 2) and u = x - (1 - 2^-24) exactly.
 template <class real>
 __device__ __forceinline__ real uniform01(uint32_t k);
 template <>
 __device__ __forceinline__ float uniform01<float>(uint32_t k) {
-  return __uint2float_rn(((k >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+  return __uint_as_float(0x3F800000u | (k >> 9)) - 0.999999940395355224609375f;
 }
 template <>
 __device__ __forceinline__ double uniform01<double>(uint32_t k) {
-  return __uint2double_rn(((k >> 9) << 1) | 1u) * 5.9604644775390625e-8;
+  return __longlong_as_double((long long)(0x3FF0000000000000ull | ((unsigned long long)(k >> 9) << 29))) -
+         0.999999940395355224609375;
 }
 
 // Box-Muller: (r cos 2 pi u2, r sin 2 pi u2) with r = sqrt(-2 ln u1).
@@ -144,7 +209,7 @@ struct StepArgs {
 };
 
 template <class real>
-cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, bool noise, cudaStream_t s);
+cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, cudaStream_t s);
 
 // Dynamic shared memory of the step kernels for a tile width, and the one-time attribute set-up
 // that allows it (called before any launch or capture).
@@ -154,11 +219,11 @@ template <class real>
 cudaError_t prepare_step(int max_tile_x);
 
 template <class real>
-cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, bool noise,
+cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, int noise,
                                    unsigned* barrier, int* err, int grid, int spin_limit, cudaStream_t s);
 
 template <class real>
-int persistent_grid(int tile_x, bool sample, bool noise);
+int persistent_grid(int tile_x, int noise);
 
 cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s);
 

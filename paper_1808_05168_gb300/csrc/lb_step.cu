@@ -202,7 +202,7 @@ struct Smem {
 };
 
 // Advance one work item by one step.
-template <class real, bool SAMPLE, bool NOISE>
+template <class real, bool SAMPLE, int NOISE>
 __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real* __restrict__ src,
                                              real* __restrict__ dst, int item_index, uint32_t step,
                                              unsigned char* smem) {
@@ -305,6 +305,12 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   const real G = L.G, g3 = L.g3;
   const real ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
   const real od = L.omh[1], oe = L.omh[3], os = L.omh[4];
+  const uint32_t key0 = L.key0, key1 = L.key1, lid = L.lattice_id;
+  // noise amplitudes: hom -- sigma of moments 1-2 and 3..8; loc -- the same without the density
+  real sg[7];
+  sg[0] = (NOISE == NOISE_LOC) ? L.pref_mom : L.sig_mom;
+#pragma unroll
+  for (int k = 3; k < 9; ++k) sg[k - 2] = (NOISE == NOISE_LOC) ? L.pref[k] : L.sig[k];
   double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
 
   for (int z = z0; z < z1; ++z) {
@@ -382,45 +388,42 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
         fl[3 * LzLx] = Uz;
       }
 
-      real xi[9];
+      real xiA[9], xiB[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) xi[k] = 0;
-      real nm0 = 0, nm1 = 0;
-      const uint32_t site = (uint32_t)(z * Lx + x);
-      const bool loc = flags & DF_NOISE_LOC;
-      if (NOISE) {
-        real n[8];
-        const U4 r0 = philox(U4{site, step, L.lattice_id, 0u}, L.key0, L.key1);
-        normal_pair<real>(r0.x, r0.y, n[0], n[1]);
-        normal_pair<real>(r0.z, r0.w, n[2], n[3]);
-        const U4 r1 = philox(U4{site, step, L.lattice_id, 1u}, L.key0, L.key1);
-        normal_pair<real>(r1.x, r1.y, n[4], n[5]);
-        normal_pair<real>(r1.z, r1.w, n[6], n[7]);
-        const real smom = loc ? L.pref_mom * rsqrt_pos<real>(rhoA * rhoB * inv) : L.sig_mom;
-        const real qA = loc ? rsqrt_pos<real>(rhoA) : real(1);
-        nm0 = smom * n[0];
-        nm1 = smom * n[1];
-        xi[1] = nm0;
-        xi[2] = nm1;
+      for (int k = 0; k < 9; ++k) {
+        xiA[k] = 0;
+        xiB[k] = 0;
+      }
+      if (NOISE != NOISE_OFF) {
+        U4 w[4];
+        philox_site((uint32_t)(z * Lx + x), step, lid, key0, key1, w);
+        real n[14];
+        normal_pair<real>(w[0].x, w[0].y, n[0], n[1]);
+        normal_pair<real>(w[0].z, w[0].w, n[2], n[3]);
+        normal_pair<real>(w[1].x, w[1].y, n[4], n[5]);
+        normal_pair<real>(w[1].z, w[1].w, n[6], n[7]);
+        normal_pair<real>(w[2].x, w[2].y, n[8], n[9]);
+        normal_pair<real>(w[2].z, w[2].w, n[10], n[11]);
+        normal_pair<real>(w[3].x, w[3].y, n[12], n[13]);
+        real smom = sg[0], qA = 1, qB = 1;
+        if (NOISE == NOISE_LOC) {
+          smom = sg[0] * rsqrt_pos<real>(rhoA * rhoB * inv);
+          qA = rsqrt_pos<real>(rhoA);
+          qB = rsqrt_pos<real>(rhoB);
+        }
+        xiA[1] = smom * n[0];
+        xiA[2] = smom * n[1];
+        xiB[1] = -xiA[1];
+        xiB[2] = -xiA[2];
 #pragma unroll
-        for (int k = 3; k < 9; ++k) xi[k] = (loc ? L.pref[k] * qA : L.sig[0][k]) * n[k - 1];
+        for (int k = 3; k < 9; ++k) {
+          xiA[k] = (sg[k - 2] * qA) * n[k - 1];
+          xiB[k] = (sg[k - 2] * qB) * n[k + 5];
+        }
       }
       const int r0 = z * Lx + x;
-      collide_store<real>(mA, dA, rhoA, Ux, Uz, FAx, FAz, ld, le, ls, lq, leps, od, oe, os, xi, g + r0, LzLx);
-      if (NOISE) {
-        real n[6];
-        const U4 r2 = philox(U4{site, step, L.lattice_id, 2u}, L.key0, L.key1);
-        normal_pair<real>(r2.x, r2.y, n[0], n[1]);
-        normal_pair<real>(r2.z, r2.w, n[2], n[3]);
-        const U4 r3 = philox(U4{site, step, L.lattice_id, 3u}, L.key0, L.key1);
-        normal_pair<real>(r3.x, r3.y, n[4], n[5]);
-        const real qB = loc ? rsqrt_pos<real>(rhoB) : real(1);
-        xi[1] = -nm0;
-        xi[2] = -nm1;
-#pragma unroll
-        for (int k = 3; k < 9; ++k) xi[k] = (loc ? L.pref[k] * qB : L.sig[1][k]) * n[k - 3];
-      }
-      collide_store<real>(mB, dB, rhoB, Ux, Uz, FBx, FBz, ld, le, ls, lq, leps, od, oe, os, xi, g + 9 * LzLx + r0,
+      collide_store<real>(mA, dA, rhoA, Ux, Uz, FAx, FAz, ld, le, ls, lq, leps, od, oe, os, xiA, g + r0, LzLx);
+      collide_store<real>(mB, dB, rhoB, Ux, Uz, FBx, FBz, ld, le, ls, lq, leps, od, oe, os, xiB, g + 9 * LzLx + r0,
                           LzLx);
     }
   }
@@ -456,7 +459,7 @@ struct MinBlocks {
   static constexpr int value = sizeof(real) == 4 ? 2 : 1;
 };
 
-template <class real, bool SAMPLE, bool NOISE>
+template <class real, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepArgs<real> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
@@ -503,7 +506,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int limi
   return ok_s != 0;
 }
 
-template <class real, bool NOISE>
+template <class real, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value)
     persistent_kernel(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -537,9 +540,11 @@ size_t step_smem_bytes(int tile_x) {
 template <class real>
 cudaError_t prepare_step(int max_tile_x) {
   const int bytes = (int)Smem<real>::bytes(max_tile_x);
-  const void* fns[] = {(const void*)step_kernel<real, true, true>, (const void*)step_kernel<real, true, false>,
-                       (const void*)step_kernel<real, false, true>, (const void*)step_kernel<real, false, false>,
-                       (const void*)persistent_kernel<real, true>, (const void*)persistent_kernel<real, false>};
+  const void* fns[] = {(const void*)step_kernel<real, true, NOISE_OFF>,  (const void*)step_kernel<real, true, NOISE_HOM>,
+                       (const void*)step_kernel<real, true, NOISE_LOC>,  (const void*)step_kernel<real, false, NOISE_OFF>,
+                       (const void*)step_kernel<real, false, NOISE_HOM>, (const void*)step_kernel<real, false, NOISE_LOC>,
+                       (const void*)persistent_kernel<real, NOISE_OFF>,  (const void*)persistent_kernel<real, NOISE_HOM>,
+                       (const void*)persistent_kernel<real, NOISE_LOC>};
   for (const void* fn : fns) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -547,42 +552,48 @@ cudaError_t prepare_step(int max_tile_x) {
   return cudaSuccess;
 }
 
+template <class real, bool SAMPLE>
+void launch_step_as(const StepArgs<real>& a, int tile_x, int noise, size_t smem, cudaStream_t s) {
+  if (noise == NOISE_HOM) step_kernel<real, SAMPLE, NOISE_HOM><<<a.n_items, tile_x, smem, s>>>(a);
+  else if (noise == NOISE_LOC) step_kernel<real, SAMPLE, NOISE_LOC><<<a.n_items, tile_x, smem, s>>>(a);
+  else step_kernel<real, SAMPLE, NOISE_OFF><<<a.n_items, tile_x, smem, s>>>(a);
+}
+
 template <class real>
-cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, bool noise, cudaStream_t s) {
+cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, cudaStream_t s) {
   const size_t smem = Smem<real>::bytes(tile_x);
   if (a.n_items <= 0) return cudaSuccess;
-  if (sample) {
-    if (noise) step_kernel<real, true, true><<<a.n_items, tile_x, smem, s>>>(a);
-    else step_kernel<real, true, false><<<a.n_items, tile_x, smem, s>>>(a);
-  } else {
-    if (noise) step_kernel<real, false, true><<<a.n_items, tile_x, smem, s>>>(a);
-    else step_kernel<real, false, false><<<a.n_items, tile_x, smem, s>>>(a);
-  }
+  if (sample) launch_step_as<real, true>(a, tile_x, noise, smem, s);
+  else launch_step_as<real, false>(a, tile_x, noise, smem, s);
   return cudaGetLastError();
 }
 
 template <class real>
-int persistent_grid(int tile_x, bool sample, bool noise) {
-  (void)sample;
+const void* persistent_fn(int noise) {
+  if (noise == NOISE_HOM) return (const void*)persistent_kernel<real, NOISE_HOM>;
+  if (noise == NOISE_LOC) return (const void*)persistent_kernel<real, NOISE_LOC>;
+  return (const void*)persistent_kernel<real, NOISE_OFF>;
+}
+
+template <class real>
+int persistent_grid(int tile_x, int noise) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = Smem<real>::bytes(tile_x);
-  cudaError_t e = noise ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_kernel<real, true>, tile_x, smem)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_kernel<real, false>, tile_x, smem);
-  if (e != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_fn<real>(noise), tile_x,
+                                                    Smem<real>::bytes(tile_x)) != cudaSuccess)
+    return 0;
   return per * sms;
 }
 
 template <class real>
-cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, bool noise,
+cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, int noise,
                                    unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
-  const size_t smem = Smem<real>::bytes(tile_x);
   StepArgs<real> aa = a;
   int ns = nsteps, sl = sample_last ? 1 : 0;
   void* args[] = {&aa, &ns, &sl, &barrier, &err, &limit_ms};
-  const void* fn = noise ? (const void*)persistent_kernel<real, true> : (const void*)persistent_kernel<real, false>;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
+  return cudaLaunchCooperativeKernel(persistent_fn<real>(noise), dim3(grid), dim3(tile_x), args,
+                                     Smem<real>::bytes(tile_x), s);
 }
 
 cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s) {
@@ -600,9 +611,9 @@ cudaError_t launch_barrier_probe(int blocks, int expected, int limit_ms, unsigne
 #define LB_STEP_INST(real)                                                                                       \
   template size_t step_smem_bytes<real>(int);                                                                    \
   template cudaError_t prepare_step<real>(int);                                                                  \
-  template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, bool, cudaStream_t);                  \
-  template int persistent_grid<real>(int, bool, bool);                                                           \
-  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, bool, bool, unsigned*, int*, \
+  template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, int, cudaStream_t);                   \
+  template int persistent_grid<real>(int, int);                                                                  \
+  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, bool, int, unsigned*, int*,   \
                                                     int, int, cudaStream_t);
 LB_STEP_INST(float)
 LB_STEP_INST(double)
