@@ -58,6 +58,8 @@ extern "C" {
 #define LB_PERSISTENT 0x20 /* one cooperative launch per run of steps, all lattices of the
                               batch, with a bounded grid barrier between steps            */
 #define LB_AUTOTUNE 0x40   /* time the candidate tile shapes on the first lb_step          */
+#define LB_NO_BULK 0x80    /* stage populations with per-thread copies even where rows are
+                              16-byte aligned (bulk copies are used by default there)     */
 
 /* ---- structure-factor fields and modes (Appendix A) ---------------------------------- */
 #define LB_FIELD_RHO 0 /* delta rho = rho - rho_bar                                         */

@@ -50,7 +50,8 @@ class Simulation:
     """A batch of lattices advanced together on the GPU (a single lattice is a batch of one)."""
 
     def __init__(self, lattices, precision: str = "fp64", astar: bool = True, wall_fixed: bool = False,
-                 noise_loc: bool = False, graph: bool = False, persistent: bool = False, autotune: bool = False):
+                 noise_loc: bool = False, graph: bool = False, persistent: bool = False, autotune: bool = False,
+                 bulk: bool = True):
         if isinstance(lattices, LatticeParams):
             lattices = [lattices]
         self.lattices = list(lattices)
@@ -61,6 +62,7 @@ class Simulation:
         flags |= capi.LB_GRAPH if graph else 0
         flags |= capi.LB_PERSISTENT if persistent else 0
         flags |= capi.LB_AUTOTUNE if autotune else 0
+        flags |= 0 if bulk else capi.LB_NO_BULK
         self.flags = flags
         self.precision = precision
         self.h = capi.lb_create_batch([p.to_c() for p in self.lattices], flags)

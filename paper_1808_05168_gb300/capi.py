@@ -29,6 +29,7 @@ LB_NOISE_LOC = 0x08
 LB_GRAPH = 0x10
 LB_PERSISTENT = 0x20
 LB_AUTOTUNE = 0x40
+LB_NO_BULK = 0x80
 
 LB_FIELD_RHO, LB_FIELD_C, LB_FIELD_UX, LB_FIELD_UZ = 0, 1, 2, 3
 LB_SF_QXQZ, LB_SF_QX = 0, 1

@@ -86,6 +86,7 @@ struct lb_ctx {
   cudaStream_t own_stream = nullptr;
   int coop_grid = -1;
   int noise_mode = NOISE_OFF;  // NOISE_OFF, NOISE_HOM or NOISE_LOC for the whole batch
+  bool bulk_ok = false;        // every lattice's rows are 16-byte aligned and bulk copies are allowed
   std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;  // graph, kernels in it
   int64_t launches = 0;  // kernels enqueued by lb_step so far (graph replays included)
 };
@@ -348,6 +349,7 @@ StepArgs<real> step_args(lb_ctx* c, int cur, int t_offset) {
   a.t_offset = t_offset;
   a.fields = (real*)c->fields;
   a.partials = c->partials;
+  a.err = c->d_err;
   return a;
 }
 
@@ -375,7 +377,7 @@ cudaError_t enqueue_direct(lb_ctx* c, int cur, int64_t n, const std::vector<int6
   for (int64_t k = 0; k < n; ++k) {
     const bool sample = si < sample_offsets.size() && sample_offsets[si] == k;
     if (sample) ++si;
-    cudaError_t e = launch_step<real>(step_args<real>(c, cur, (int)k), c->tile_x, sample, c->noise_mode, c->stream);
+    cudaError_t e = launch_step<real>(step_args<real>(c, cur, (int)k), c->tile_x, sample, c->noise_mode, c->bulk_ok, c->stream);
     if (e != cudaSuccess) return e;
     c->launches += 1;
     if (sample) {
@@ -391,7 +393,7 @@ cudaError_t enqueue_direct(lb_ctx* c, int cur, int64_t n, const std::vector<int6
 // Persistent: one cooperative launch per run of steps ending with (at most) one sample step.
 template <class real>
 cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& sample_offsets) {
-  if (c->coop_grid < 0) c->coop_grid = persistent_grid<real>(c->tile_x, c->noise_mode);
+  if (c->coop_grid < 0) c->coop_grid = persistent_grid<real>(c->tile_x, c->noise_mode, c->bulk_ok);
   const int grid = std::min<int>(c->coop_grid, (int)c->items.size());
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
   int64_t k = 0;
@@ -408,7 +410,7 @@ cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<
     cudaError_t e = cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
     e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)len, sample, c->noise_mode,
-                                     c->d_barrier, c->d_err, grid, 2000, c->stream);
+                                     c->bulk_ok, c->d_barrier, c->d_err, grid, 2000, c->stream);
     if (e != cudaSuccess) return e;
     c->launches += 1;
     if (sample) {
@@ -453,11 +455,12 @@ int autotune(lb_ctx* c) {
       last = rr;
       if (build_items(c, tx, rr) != LB_OK) continue;
       // state is untouched: every trial reads f[cur] and writes f[cur ^ 1]
-      for (int k = 0; k < 2; ++k) launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->stream);
+      for (int k = 0; k < 2; ++k)
+        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->bulk_ok, c->stream);
       cudaEventRecord(e0, c->stream);
       const int reps = 4;
       for (int k = 0; k < reps; ++k)
-        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->stream);
+        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->bulk_ok, c->stream);
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         cudaGetLastError();
@@ -542,7 +545,8 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
   if (!out) return LB_ERR_BAD_PARAM;
   *out = nullptr;
   if (n < 1 || !ps) return LB_ERR_BAD_PARAM;
-  const int known = LB_PREC_DEV32 | LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC | LB_GRAPH | LB_PERSISTENT | LB_AUTOTUNE;
+  const int known = LB_PREC_DEV32 | LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC | LB_GRAPH | LB_PERSISTENT | LB_AUTOTUNE |
+                    LB_NO_BULK;
   if (flags & ~known) return LB_ERR_BAD_PARAM;
   for (int i = 0; i < n; ++i) {
     int rc = check_params(ps[i]);
@@ -573,6 +577,12 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
   }
   c->n_f = foff;
   c->n_sites = soff;
+  {
+    const int align = c->dev32 ? 4 : 2;  // elements in 16 bytes
+    c->bulk_ok = !(flags & LB_NO_BULK);
+    for (int i = 0; i < n; ++i)
+      if (ps[i].Lx % align != 0) c->bulk_ok = false;
+  }
   c->n_rows = roff;
   const size_t rs = c->dev32 ? sizeof(float) : sizeof(double);
   int rc = LB_OK;

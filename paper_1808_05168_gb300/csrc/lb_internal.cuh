@@ -206,10 +206,13 @@ struct StepArgs {
   int t_offset;
   real* fields;        // sampled fields [4][Lz][Lx] per lattice (sample steps only)
   double* partials;    // per item: pressure deviation sum, mass deviation A, B
+  int* err;            // set to 1 by a device-side wait that gave up
 };
 
+// bulk: stage rows with bulk copies (tile_x 128 or 256, every lattice's Lx a multiple of
+// 16 bytes); otherwise per-thread copies.
 template <class real>
-cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, cudaStream_t s);
+cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, bool bulk, cudaStream_t s);
 
 // Dynamic shared memory of the step kernels for a tile width, and the one-time attribute set-up
 // that allows it (called before any launch or capture).
@@ -220,10 +223,10 @@ cudaError_t prepare_step(int max_tile_x);
 
 template <class real>
 cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, int noise,
-                                   unsigned* barrier, int* err, int grid, int spin_limit, cudaStream_t s);
+                                   bool bulk, unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s);
 
 template <class real>
-int persistent_grid(int tile_x, int noise);
+int persistent_grid(int tile_x, int noise, bool bulk);
 
 cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s);
 

@@ -3,21 +3,27 @@
 // cooperative launch with a bounded grid barrier between steps.
 //
 // Work decomposition: a block of TX threads owns TX consecutive columns x of one lattice and
-// marches up rows z0..z1-1 of that lattice.  Each thread stages the 18 populations arriving
-// at its own site (Eq. LB; mid-way bounce-back at the walls of Sec. II.A) with per-thread
-// asynchronous copies (cp.async) into a ring of NS rows of shared memory, issued NS-2 rows
-// ahead of the row being collided, so every stored value is read once per step from HBM with
-// coalesced loads and several rows of loads are in flight per thread without holding any of
-// them in registers.  The non-ideal force (Eq. aNI) needs the densities of the 8 neighbours at
-// the same time level: the densities of rows z-1, z, z+1 live in a 4-slot shared-memory ring
-// (one __syncthreads per row); the two halo columns are staged by the edge threads.  The
-// wall ghost rows follow Sec. II.A.
+// marches up rows z0..z1-1 of that lattice.  The 18 populations arriving at each site (Eq. LB;
+// mid-way bounce-back at the walls of Sec. II.A) are staged in shared memory, several rows
+// ahead of the row being collided, so that every stored value is read once per step from HBM
+// and no population is held in registers across rows.  Two staging paths compute the same
+// numbers bit for bit:
+//  - bulk (rows 16-byte aligned, TX = 128 or 256): for each of the 18 (species, link) planes
+//    one lane issues a bulk asynchronous copy of the row window [x0 - PAD, x0 + TX + PAD)
+//    (PAD = 16 bytes; wrapped periodically at the lattice's x edges) into a ring of NSI row
+//    slots, completion tracked by one mbarrier per slot; post-collision rows are written to a
+//    shared output row and stored with bulk copies;
+//  - generic (any Lx, any tile): every thread stages its own 18 values with per-thread
+//    asynchronous copies and stores with plain streaming stores.
+// The non-ideal force (Eq. aNI) needs the densities of the 8 neighbours at the same time
+// level: the densities of rows z-1, z, z+1 live in a 4-slot shared-memory ring (one barrier per
+// row); the halo columns are read by the edge threads.  The wall ghost rows follow Sec. II.A.
 //
-// Arithmetic per site: densities and momenta from the staged populations, forces (Eqs. aNI,
-// ne-acc, a* of its footnote), barycentric velocity (Eq. bar), moments of Table I in their
-// structured +- form, relaxation toward m^eq with second-order forcing (1 - lambda_a/2) S_a,
-// FDT noise from Philox4x32-10 (Eqs. noise-bin-expl, noise-bin-expl-high), and the inverse
-// transform f_l = w_l sum_a T_al m*_a / N_a.
+// Arithmetic per site: densities and momenta, forces (Eqs. aNI, ne-acc, a* of its footnote),
+// barycentric velocity (Eq. bar), moments of Table I in their structured +- form, relaxation
+// toward m^eq with second-order forcing (1 - lambda_a/2) S_a, FDT noise from Philox4x32-10
+// (Eqs. noise-bin-expl, noise-bin-expl-high), and the inverse transform
+// f_l = w_l sum_a T_al m*_a / N_a.
 #include <cstdio>
 
 #include "lb_internal.cuh"
@@ -26,19 +32,22 @@ namespace lbk {
 
 namespace {
 
-constexpr int NS = 4;  // rows of staged populations (power of two)
+constexpr int NS = 4;   // generic path: rows of staged populations (power of two)
+constexpr int NSI = 4;  // bulk path: input row slots (power of two)
+constexpr int WAIT_MS = 2000;
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// ---- per-thread asynchronous copies (generic path) ---------------------------------
 template <class real>
 __device__ __forceinline__ void cp_async(real* dst_smem, const real* src);
 template <>
 __device__ __forceinline__ void cp_async<float>(float* dst_smem, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
 }
 template <>
 __device__ __forceinline__ void cp_async<double>(double* dst_smem, const double* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -46,11 +55,50 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ---- bulk copies and mbarriers (bulk path) ------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst_smem)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src_smem, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src_smem)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ int ring_slot(int z) { return (z + 4) & 3; }
 
-// Stage the 18 populations arriving at (x, z) (Eq. LB) into dst[k * W], k = 9 s + l: link l
-// comes from (x - c_lx, z - c_lz); a link whose source row lies beyond a wall takes the
-// reflected population f*_opp(l)(x, z).
+// Generic path: stage the 18 populations arriving at (x, z) (Eq. LB) into dst[k * W],
+// k = 9 s + l: link l comes from (x - c_lx, z - c_lz); a link whose source row lies beyond a
+// wall takes the reflected population f*_opp(l)(x, z).
 template <class real>
 __device__ __forceinline__ void stage_column(const real* __restrict__ f, int LzLx, int Lx, int Lz, int z, int x,
                                              real* dst, int W) {
@@ -74,25 +122,45 @@ __device__ __forceinline__ void stage_column(const real* __restrict__ f, int LzL
   }
 }
 
-// The 9 staged populations of species s at stage column c as deviations from the background
-// of row z: in deviation mode b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz d_z c^S_0 is added on
-// non-reflected links with c_lz != 0 (k9, k36 are zero in FP64 mode).
+// The 9 populations of species s of one site as deviations from the background of its row.
+// In deviation mode the background difference b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz
+// d_z c^S_0 is added on non-reflected links with c_lz != 0 (k9, k36 are zero in FP64 mode).
 template <class real>
-__device__ __forceinline__ void read_species(const real* st, int W, int c, int s, bool below, bool above, real k9,
-                                             real k36, real v[9]) {
-  const real* d = st + s * 9 * W + c;
+__device__ __forceinline__ void deviations(real e0, real e1, real e2, real e3, real e4, real e5, real e6, real e7,
+                                           real e8, int s, bool below, bool above, real k9, real k36, real v[9]) {
   const real q9 = s == 0 ? k9 : -k9, q36 = s == 0 ? k36 : -k36;
   const real b9 = below ? q9 : real(0), b36 = below ? q36 : real(0);
   const real a9 = above ? q9 : real(0), a36 = above ? q36 : real(0);
-  v[0] = d[0];
-  v[1] = d[W];
-  v[3] = d[3 * W];
-  v[2] = d[2 * W] - b9;
-  v[4] = d[4 * W] + a9;
-  v[5] = d[5 * W] - b36;
-  v[6] = d[6 * W] - b36;
-  v[7] = d[7 * W] + a36;
-  v[8] = d[8 * W] + a36;
+  v[0] = e0;
+  v[1] = e1;
+  v[3] = e3;
+  v[2] = e2 - b9;
+  v[4] = e4 + a9;
+  v[5] = e5 - b36;
+  v[6] = e6 - b36;
+  v[7] = e7 + a36;
+  v[8] = e8 + a36;
+}
+
+// Generic path: stage column c of a slot holds the already-shifted values of that site.
+template <class real>
+__device__ __forceinline__ void read_generic(const real* st, int W, int c, int s, bool below, bool above, real k9,
+                                             real k36, real v[9]) {
+  const real* d = st + s * 9 * W + c;
+  deviations(d[0], d[W], d[2 * W], d[3 * W], d[4 * W], d[5 * W], d[6 * W], d[7 * W], d[8 * W], s, below, above, k9,
+             k36, v);
+}
+
+// Bulk path: plane k of a slot holds the source row window, so link l of the site at window
+// column j sits at column j - c_lx (at j on reflected links, whose plane holds the opposite
+// link's own row).
+template <class real, int SW>
+__device__ __forceinline__ void read_bulk(const real* st, int j, int s, bool below, bool above, real k9, real k36,
+                                          real v[9]) {
+  const real* d = st + s * 9 * SW + j;
+  const int j5 = below ? -1 : 0, j6 = below ? 1 : 0, j7 = above ? 1 : 0, j8 = above ? -1 : 0;
+  deviations(d[0], d[SW - 1], d[2 * SW], d[3 * SW + 1], d[4 * SW], d[5 * SW + j5], d[6 * SW + j6], d[7 * SW + j7],
+             d[8 * SW + j8], s, below, above, k9, k36, v);
 }
 
 template <class real>
@@ -126,21 +194,59 @@ __device__ __forceinline__ Mom<real> moments(const real v[9]) {
   return m;
 }
 
-// Collision of one species in moment space (Eq. MRT) with second-order forcing and noise, and
-// the inverse transform f_l = w_l sum_a T_al m*_a / N_a written to out[l * stride].
+// Constants of one lattice the site update needs, in registers.
 template <class real>
-__device__ __forceinline__ void collide_store(const Mom<real>& m, real d, real rs, real Ux, real Uz, real Fx, real Fz,
-                                              real ld, real le, real ls, real lq, real leps, real od, real oe, real os,
-                                              const real xi[9], real* out, int stride) {
+struct SiteK {
+  real G, g3, ld, le, ls, lq, leps, od, oe, os, rho_bar_off;
+  real sg[7];  // noise amplitudes (moments 1-2, then 3..8)
+  uint32_t key0, key1, lid;
+};
+
+template <class real, int NOISE>
+__device__ __forceinline__ SiteK<real> site_constants(const LatticeDev<real>& L) {
+  SiteK<real> K;
+  K.G = L.G;
+  K.g3 = L.g3;
+  K.ld = L.lam[1];
+  K.le = L.lam[3];
+  K.ls = L.lam[4];
+  K.lq = L.lam[6];
+  K.leps = L.lam[8];
+  K.od = L.omh[1];
+  K.oe = L.omh[3];
+  K.os = L.omh[4];
+  K.rho_bar_off = L.rho_bar_off;
+  K.sg[0] = (NOISE == NOISE_LOC) ? L.pref_mom : L.sig_mom;
+#pragma unroll
+  for (int k = 3; k < 9; ++k) K.sg[k - 2] = (NOISE == NOISE_LOC) ? L.pref[k] : L.sig[k];
+  K.key0 = L.key0;
+  K.key1 = L.key1;
+  K.lid = L.lattice_id;
+  return K;
+}
+
+// Output of one post-collision population: a streaming store to the lattice, or a store to the
+// shared output row (compile-time stride) that a bulk copy writes back.
+template <class real, bool TO_GLOBAL, int STRIDE>
+__device__ __forceinline__ void put(real* out, int stride, int l, real v) {
+  if (TO_GLOBAL) __stcs(out + l * stride, v);
+  else out[l * STRIDE] = v;
+}
+
+// Collision of one species in moment space (Eq. MRT) with second-order forcing and noise, and
+// the inverse transform f_l = w_l sum_a T_al m*_a / N_a.
+template <class real, bool TO_GLOBAL, int STRIDE>
+__device__ __forceinline__ void collide_out(const Mom<real>& m, real d, real rs, real Ux, real Uz, real Fx, real Fz,
+                                            const SiteK<real>& K, const real xi[9], real* out, int stride) {
   const real UxUx = Ux * Ux, UzUz = Uz * Uz;
-  const real s1 = m.m1 + ld * (rs * Ux - m.m1) + od * Fx + xi[1];
-  const real s2 = m.m2 + ld * (rs * Uz - m.m2) + od * Fz + xi[2];
-  const real s3 = m.m3 + le * (3 * rs * (UxUx + UzUz) - m.m3) + oe * (6 * (Ux * Fx + Uz * Fz)) + xi[3];
-  const real s4 = m.m4 + ls * (rs * (UxUx - UzUz) - m.m4) + os * (2 * (Ux * Fx - Uz * Fz)) + xi[4];
-  const real s5 = m.m5 + ls * (rs * Ux * Uz - m.m5) + os * (Ux * Fz + Uz * Fx) + xi[5];
-  const real s6 = m.m6 - lq * m.m6 + xi[6];
-  const real s7 = m.m7 - lq * m.m7 + xi[7];
-  const real s8 = m.m8 - leps * m.m8 + xi[8];
+  const real s1 = m.m1 + K.ld * (rs * Ux - m.m1) + K.od * Fx + xi[1];
+  const real s2 = m.m2 + K.ld * (rs * Uz - m.m2) + K.od * Fz + xi[2];
+  const real s3 = m.m3 + K.le * (3 * rs * (UxUx + UzUz) - m.m3) + K.oe * (6 * (Ux * Fx + Uz * Fz)) + xi[3];
+  const real s4 = m.m4 + K.ls * (rs * (UxUx - UzUz) - m.m4) + K.os * (2 * (Ux * Fx - Uz * Fz)) + xi[4];
+  const real s5 = m.m5 + K.ls * (rs * Ux * Uz - m.m5) + K.os * (Ux * Fz + Uz * Fx) + xi[5];
+  const real s6 = m.m6 - K.lq * m.m6 + xi[6];
+  const real s7 = m.m7 - K.lq * m.m7 + xi[7];
+  const real s8 = m.m8 - K.leps * m.m8 + xi[8];
   // divide by N_a = (1, 1/3, 1/3, 4, 4/9, 1/9, 2/3, 2/3, 16)
   const real M0 = d, M1 = 3 * s1, M2 = 3 * s2, M3 = real(0.25) * s3, M4 = real(2.25) * s4, M5 = 9 * s5,
              M6 = real(1.5) * s6, M7 = real(1.5) * s7, M8 = real(0.0625) * s8;
@@ -148,21 +254,21 @@ __device__ __forceinline__ void collide_store(const Mom<real>& m, real d, real r
   const real base4 = M0 + M3 - 4 * M8;
   const real base5 = M0 + 4 * M3 + 8 * M8;
   const real p12 = M1 + M2, p1m2 = M1 - M2, q67 = 2 * (M6 + M7), q6m7 = 2 * (M6 - M7);
-  __stcs(out + 0 * stride, real(4) / 9 * (M0 - 2 * M3 + 2 * M8));
-  __stcs(out + 1 * stride, c9 * (base4 + M1 + M4 - M6));
-  __stcs(out + 2 * stride, c9 * (base4 + M2 - M4 - M7));
-  __stcs(out + 3 * stride, c9 * (base4 - M1 + M4 + M6));
-  __stcs(out + 4 * stride, c9 * (base4 - M2 - M4 + M7));
-  __stcs(out + 5 * stride, c36 * (base5 + p12 + M5 + q67));
-  __stcs(out + 6 * stride, c36 * (base5 - p1m2 - M5 - q6m7));
-  __stcs(out + 7 * stride, c36 * (base5 - p12 + M5 - q67));
-  __stcs(out + 8 * stride, c36 * (base5 + p1m2 - M5 + q6m7));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 0, real(4) / 9 * (M0 - 2 * M3 + 2 * M8));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 1, c9 * (base4 + M1 + M4 - M6));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 2, c9 * (base4 + M2 - M4 - M7));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 3, c9 * (base4 - M1 + M4 + M6));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 4, c9 * (base4 - M2 - M4 + M7));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 5, c36 * (base5 + p12 + M5 + q67));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 6, c36 * (base5 - p1m2 - M5 - q6m7));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 7, c36 * (base5 - p12 + M5 - q67));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 8, c36 * (base5 + p1m2 - M5 + q6m7));
 }
 
 // Box-Muller pair of the working precision.  FP64: exact-as-libm (log, sincospi).  FP32: log
 // to full precision (its value matters near u1 -> 1), sqrt through the reciprocal square root,
 // and the angle reduced to (-pi, pi) for the fast sine/cosine: cos 2 pi u2 = -cos phi and
-// sin 2 pi u2 = -sin phi with phi = pi (2 u2 - 1); absolute error below 3e-6 on a normal.
+// sin 2 pi u2 = -sin phi with phi = 2 pi u2 - pi; absolute error below 3e-6 on a normal.
 template <class real>
 __device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, real& n0, real& n1);
 template <>
@@ -170,7 +276,7 @@ __device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float
   const float u1 = uniform01<float>(a), u2 = uniform01<float>(b);
   const float t = -2.0f * logf(u1);
   const float r = t * rsqrtf(t);
-  const float phi = 3.14159265358979f * (2.0f * u2 - 1.0f);
+  const float phi = fmaf(6.28318530717959f, u2, -3.14159265358979f);
   float s, c;
   __sincosf(phi, &s, &c);
   n0 = -r * c;
@@ -181,17 +287,145 @@ __device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, doub
   box_muller<double>(a, b, n0, n1);
 }
 
-template <class real>
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+// Everything of one site after its moments and the neighbour densities are known: forces,
+// velocity, optional sampling, noise, collision of both species and the output.
+template <class real, bool SAMPLE, int NOISE, bool TO_GLOBAL, int STRIDE>
+__device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& mA,
+                                            const Mom<real>& mB, real dA, real dB, const real* ringA,
+                                            const real* ringB, int bc, int bu, int bd, uint32_t site, uint32_t step,
+                                            real* fl, int LzLx, double& acc_p, double& acc_a, double& acc_b,
+                                            real* outA, real* outB, int ostride, int flags) {
+  const real c9 = real(1) / 9, c36 = real(1) / 36;
+  real FNx, FNz, FAx, FAz, FBx, FBz, rhoA, rhoB, inv;
+  {
+    const real Aw = ringA[bc - 1], Ae = ringA[bc + 1], An = ringA[bu], Anw = ringA[bu - 1], Ane = ringA[bu + 1],
+               As = ringA[bd], Asw = ringA[bd - 1], Ase = ringA[bd + 1];
+    const real Bw = ringB[bc - 1], Be = ringB[bc + 1], Bn = ringB[bu], Bnw = ringB[bu - 1], Bne = ringB[bu + 1],
+               Bs = ringB[bd], Bsw = ringB[bd - 1], Bse = ringB[bd + 1];
+    // sum_l w_l c_l rho^S(r + c_l), deviations plus the background part (Eq. aNI)
+    const real sAx = c9 * (Ae - Aw) + c36 * ((Ane - Anw) + (Ase - Asw));
+    const real sAz = c9 * (An - As) + c36 * ((Ane + Anw) - (Ase + Asw)) + rc.dbgA;
+    const real sBx = c9 * (Be - Bw) + c36 * ((Bne - Bnw) + (Bse - Bsw));
+    const real sBz = c9 * (Bn - Bs) + c36 * ((Bne + Bnw) - (Bse + Bsw)) + rc.dbgB;
+    rhoA = rc.bgA + dA;
+    rhoB = rc.bgB + dB;
+    const real rho = rhoA + rhoB;
+    inv = real(1) / rho;
+    const real FnAx = -K.G * rhoA * sBx, FnAz = -K.G * rhoA * sBz;
+    const real FnBx = -K.G * rhoB * sAx, FnBz = -K.G * rhoB * sAz;
+    FNx = FnAx + FnBx;
+    FNz = FnAz + FnBz;
+    if (flags & DF_ASTAR) {
+      // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
+      const real cA = rhoA * inv, cB = rhoB * inv;
+      FAx = cA * FNx;
+      FAz = cA * FNz;
+      FBx = cB * FNx;
+      FBz = cB * FNz;
+    } else {
+      FAx = FnAx;
+      FAz = FnAz;
+      FBx = FnBx;
+      FBz = FnBz;
+    }
+    // gradient forcing: rho^A a^A_NE = (0, rho grad_c0 / 3) = -rho^B a^B_NE (Eq. NEcond)
+    const real ne = rho * K.g3;
+    FAz += ne;
+    FBz -= ne;
+    if (SAMPLE) {
+      // pressure (half trace; kinetic + interaction), minus its background part
+      const real kin = (mA.m3 + mB.m3 + 2 * (dA + dB)) * (real(1) / 6);
+      const real NA = c9 * (Ae + Aw + An + As) + real(2) / 36 * (Ane + Anw + Ase + Asw);
+      const real NB = c9 * (Be + Bw + Bn + Bs) + real(2) / 36 * (Bne + Bnw + Bse + Bsw);
+      const real inter = dA * (rc.nbB + NB) + rc.bgA * NB + dB * (rc.nbA + NA) + rc.bgB * NA;
+      acc_p += (double)(kin + real(0.25) * K.G * inter);
+      acc_a += (double)dA;
+      acc_b += (double)dB;
+    }
+  }
+  // barycentric velocity, Eq. (bar)
+  const real Ux = (mA.m1 + mB.m1 + real(0.5) * FNx) * inv;
+  const real Uz = (mA.m2 + mB.m2 + real(0.5) * FNz) * inv;
+  if (SAMPLE) {
+    fl[0] = dA + dB - K.rho_bar_off;
+    fl[LzLx] = (dA - rc.c0 * (dA + dB)) * inv;
+    fl[2 * LzLx] = Ux;
+    fl[3 * LzLx] = Uz;
+  }
+  real xiA[9], xiB[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    xiA[k] = 0;
+    xiB[k] = 0;
+  }
+  if (NOISE != NOISE_OFF) {
+    U4 w[4];
+    philox_site(site, step, K.lid, K.key0, K.key1, w);
+    real n[14];
+    normal_pair<real>(w[0].x, w[0].y, n[0], n[1]);
+    normal_pair<real>(w[0].z, w[0].w, n[2], n[3]);
+    normal_pair<real>(w[1].x, w[1].y, n[4], n[5]);
+    normal_pair<real>(w[1].z, w[1].w, n[6], n[7]);
+    normal_pair<real>(w[2].x, w[2].y, n[8], n[9]);
+    normal_pair<real>(w[2].z, w[2].w, n[10], n[11]);
+    normal_pair<real>(w[3].x, w[3].y, n[12], n[13]);
+    real smom = K.sg[0], qA = 1, qB = 1;
+    if (NOISE == NOISE_LOC) {
+      smom = K.sg[0] * rsqrt_pos<real>(rhoA * rhoB * inv);
+      qA = rsqrt_pos<real>(rhoA);
+      qB = rsqrt_pos<real>(rhoB);
+    }
+    xiA[1] = smom * n[0];
+    xiA[2] = smom * n[1];
+    xiB[1] = -xiA[1];
+    xiB[2] = -xiA[2];
+#pragma unroll
+    for (int k = 3; k < 9; ++k) {
+      xiA[k] = (K.sg[k - 2] * qA) * n[k - 1];
+      xiB[k] = (K.sg[k - 2] * qB) * n[k + 5];
+    }
+  }
+  collide_out<real, TO_GLOBAL, STRIDE>(mA, dA, rhoA, Ux, Uz, FAx, FAz, K, xiA, outA, ostride);
+  collide_out<real, TO_GLOBAL, STRIDE>(mB, dB, rhoB, Ux, Uz, FBx, FBz, K, xiB, outB, ostride);
+}
+
+__device__ __forceinline__ void block_partials(double acc_p, double acc_a, double acc_b, double* red, double* out) {
+  acc_p = warp_sum(acc_p);
+  acc_a = warp_sum(acc_a);
+  acc_b = warp_sum(acc_b);
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    red[3 * wid + 0] = acc_p;
+    red[3 * wid + 1] = acc_a;
+    red[3 * wid + 2] = acc_b;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double p = 0, ma = 0, mb = 0;
+    for (int w = 0; w < nw; ++w) {
+      p += red[3 * w];
+      ma += red[3 * w + 1];
+      mb += red[3 * w + 2];
+    }
+    out[0] = p;
+    out[1] = ma;
+    out[2] = mb;
+  }
+}
+
 }  // namespace
 
-// Shared memory of one block: reduction scratch, the lattice's constants, the density ring
-// (2 x 4 rows) and the population stage (NS rows x 18 links), rows TX + 2 wide.
+// ======================================================================================
+// Shared-memory layouts.
+// ======================================================================================
+// Generic: reduction scratch, lattice constants, density ring (2 x 4 rows of TX + 2), stage
+// (NS rows x 18 links x (TX + 2)).
 template <class real>
 struct Smem {
   static constexpr size_t red = 0;
@@ -201,7 +435,25 @@ struct Smem {
   __host__ __device__ static size_t bytes(int tx) { return stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real); }
 };
 
-// Advance one work item by one step.
+// Bulk: as generic, then input slots (NSI x 18 x SW), one output row (18 x TX), NSI mbarriers
+// and an abort flag.
+template <class real, int TX>
+struct SmemBulk {
+  static constexpr int PAD = 16 / (int)sizeof(real);
+  static constexpr int SW = TX + 2 * PAD;
+  static constexpr size_t red = 0;
+  static constexpr size_t lat = 8 * 3 * sizeof(double);
+  static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
+  static constexpr size_t in = ring + ((8 * (TX + 2) * sizeof(real) + 15) / 16) * 16;
+  static constexpr size_t out = in + (size_t)NSI * 18 * SW * sizeof(real);
+  static constexpr size_t bars = out + (size_t)18 * TX * sizeof(real);
+  static constexpr size_t abort_flag = bars + NSI * sizeof(uint64_t);
+  static constexpr size_t bytes = abort_flag + 16;
+};
+
+// ======================================================================================
+// Generic path.
+// ======================================================================================
 template <class real, bool SAMPLE, int NOISE>
 __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real* __restrict__ src,
                                              real* __restrict__ dst, int item_index, uint32_t step,
@@ -246,13 +498,12 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     }
     cp_commit();
   };
-  // density deviations of staged row r at stage column c (this thread staged that column)
   auto rho_at = [&](int r, int c, real& dA, real& dB) {
     const real* sb = stage + (r & (NS - 1)) * 18 * W;
     real v[9];
-    read_species(sb, W, c, 0, r > 0, r < Lz - 1, k9, k36, v);
+    read_generic(sb, W, c, 0, r > 0, r < Lz - 1, k9, k36, v);
     dA = sum9(v);
-    read_species(sb, W, c, 1, r > 0, r < Lz - 1, k9, k36, v);
+    read_generic(sb, W, c, 1, r > 0, r < Lz - 1, k9, k36, v);
     dB = sum9(v);
   };
   auto put_rho = [&](int r) {
@@ -302,15 +553,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   put_rho(z0);
   if (z0 == 0) ghost_row(-1, 0);
 
-  const real G = L.G, g3 = L.g3;
-  const real ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
-  const real od = L.omh[1], oe = L.omh[3], os = L.omh[4];
-  const uint32_t key0 = L.key0, key1 = L.key1, lid = L.lattice_id;
-  // noise amplitudes: hom -- sigma of moments 1-2 and 3..8; loc -- the same without the density
-  real sg[7];
-  sg[0] = (NOISE == NOISE_LOC) ? L.pref_mom : L.sig_mom;
-#pragma unroll
-  for (int k = 3; k < 9; ++k) sg[k - 2] = (NOISE == NOISE_LOC) ? L.pref[k] : L.sig[k];
+  const SiteK<real> K = site_constants<real, NOISE>(L);
   double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
 
   for (int z = z0; z < z1; ++z) {
@@ -319,141 +562,243 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     else ghost_row(Lz, Lz - 1);
     __syncthreads();
     stage_row(z + NS - 1);  // into the slot of row z-1, read by every thread before the barrier
-
     if (active) {
-      const RowConst<real> rc = rows[z];
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real dA = ringA[bc], dB = ringB[bc];
       const real* sb = stage + (z & (NS - 1)) * 18 * W;
       const bool below = z > 0, above = z < Lz - 1;
       real v[9];
-      read_species(sb, W, tid + 1, 0, below, above, k9, k36, v);
+      read_generic(sb, W, tid + 1, 0, below, above, k9, k36, v);
       const Mom<real> mA = moments(v);
-      read_species(sb, W, tid + 1, 1, below, above, k9, k36, v);
+      read_generic(sb, W, tid + 1, 1, below, above, k9, k36, v);
       const Mom<real> mB = moments(v);
-
-      const real c9 = real(1) / 9, c36 = real(1) / 36;
-      real FNx, FNz, FAx, FAz, FBx, FBz, rhoA, rhoB, inv;
-      {
-        const real Aw = ringA[bc - 1], Ae = ringA[bc + 1], An = ringA[bu], Anw = ringA[bu - 1], Ane = ringA[bu + 1],
-                   As = ringA[bd], Asw = ringA[bd - 1], Ase = ringA[bd + 1];
-        const real Bw = ringB[bc - 1], Be = ringB[bc + 1], Bn = ringB[bu], Bnw = ringB[bu - 1],
-                   Bne = ringB[bu + 1], Bs = ringB[bd], Bsw = ringB[bd - 1], Bse = ringB[bd + 1];
-        // sum_l w_l c_l rho^S(r + c_l), deviations plus the background part (Eq. aNI)
-        const real sAx = c9 * (Ae - Aw) + c36 * ((Ane - Anw) + (Ase - Asw));
-        const real sAz = c9 * (An - As) + c36 * ((Ane + Anw) - (Ase + Asw)) + rc.dbgA;
-        const real sBx = c9 * (Be - Bw) + c36 * ((Bne - Bnw) + (Bse - Bsw));
-        const real sBz = c9 * (Bn - Bs) + c36 * ((Bne + Bnw) - (Bse + Bsw)) + rc.dbgB;
-        rhoA = rc.bgA + dA;
-        rhoB = rc.bgB + dB;
-        const real rho = rhoA + rhoB;
-        inv = real(1) / rho;
-        const real FnAx = -G * rhoA * sBx, FnAz = -G * rhoA * sBz;
-        const real FnBx = -G * rhoB * sAx, FnBz = -G * rhoB * sAz;
-        FNx = FnAx + FnBx;
-        FNz = FnAz + FnBz;
-        if (flags & DF_ASTAR) {
-          // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
-          const real cA = rhoA * inv, cB = rhoB * inv;
-          FAx = cA * FNx; FAz = cA * FNz;
-          FBx = cB * FNx; FBz = cB * FNz;
-        } else {
-          FAx = FnAx; FAz = FnAz;
-          FBx = FnBx; FBz = FnBz;
-        }
-        // gradient forcing: rho^A a^A_NE = (0, rho grad_c0 / 3) = -rho^B a^B_NE (Eq. NEcond)
-        const real ne = rho * g3;
-        FAz += ne;
-        FBz -= ne;
-        if (SAMPLE) {
-          // pressure (half trace; kinetic + interaction), minus its background part
-          const real kin = (mA.m3 + mB.m3 + 2 * (dA + dB)) * (real(1) / 6);
-          const real NA = c9 * (Ae + Aw + An + As) + real(2) / 36 * (Ane + Anw + Ase + Asw);
-          const real NB = c9 * (Be + Bw + Bn + Bs) + real(2) / 36 * (Bne + Bnw + Bse + Bsw);
-          const real inter = dA * (rc.nbB + NB) + rc.bgA * NB + dB * (rc.nbA + NA) + rc.bgB * NA;
-          acc_p += (double)(kin + real(0.25) * G * inter);
-          acc_a += (double)dA;
-          acc_b += (double)dB;
-        }
-      }
-      // barycentric velocity, Eq. (bar)
-      const real Ux = (mA.m1 + mB.m1 + real(0.5) * FNx) * inv;
-      const real Uz = (mA.m2 + mB.m2 + real(0.5) * FNz) * inv;
-      if (SAMPLE) {
-        real* fl = a.fields + 4 * L.site_off + z * Lx + x;
-        fl[0] = dA + dB - L.rho_bar_off;
-        fl[LzLx] = (dA - rc.c0 * (dA + dB)) * inv;
-        fl[2 * LzLx] = Ux;
-        fl[3 * LzLx] = Uz;
-      }
-
-      real xiA[9], xiB[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        xiA[k] = 0;
-        xiB[k] = 0;
-      }
-      if (NOISE != NOISE_OFF) {
-        U4 w[4];
-        philox_site((uint32_t)(z * Lx + x), step, lid, key0, key1, w);
-        real n[14];
-        normal_pair<real>(w[0].x, w[0].y, n[0], n[1]);
-        normal_pair<real>(w[0].z, w[0].w, n[2], n[3]);
-        normal_pair<real>(w[1].x, w[1].y, n[4], n[5]);
-        normal_pair<real>(w[1].z, w[1].w, n[6], n[7]);
-        normal_pair<real>(w[2].x, w[2].y, n[8], n[9]);
-        normal_pair<real>(w[2].z, w[2].w, n[10], n[11]);
-        normal_pair<real>(w[3].x, w[3].y, n[12], n[13]);
-        real smom = sg[0], qA = 1, qB = 1;
-        if (NOISE == NOISE_LOC) {
-          smom = sg[0] * rsqrt_pos<real>(rhoA * rhoB * inv);
-          qA = rsqrt_pos<real>(rhoA);
-          qB = rsqrt_pos<real>(rhoB);
-        }
-        xiA[1] = smom * n[0];
-        xiA[2] = smom * n[1];
-        xiB[1] = -xiA[1];
-        xiB[2] = -xiA[2];
-#pragma unroll
-        for (int k = 3; k < 9; ++k) {
-          xiA[k] = (sg[k - 2] * qA) * n[k - 1];
-          xiB[k] = (sg[k - 2] * qB) * n[k + 5];
-        }
-      }
       const int r0 = z * Lx + x;
-      collide_store<real>(mA, dA, rhoA, Ux, Uz, FAx, FAz, ld, le, ls, lq, leps, od, oe, os, xiA, g + r0, LzLx);
-      collide_store<real>(mB, dB, rhoB, Ux, Uz, FBx, FBz, ld, le, ls, lq, leps, od, oe, os, xiB, g + 9 * LzLx + r0,
-                          LzLx);
+      site_update<real, SAMPLE, NOISE, true, 0>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
+                                                (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
+                                                acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
     }
   }
   cp_wait<0>();  // nothing may land in shared memory after the item
-
-  if (SAMPLE) {
-    acc_p = warp_sum<real>(acc_p);
-    acc_a = warp_sum<real>(acc_a);
-    acc_b = warp_sum<real>(acc_b);
-    const int wid = tid >> 5, lane = tid & 31, nw = (TX + 31) >> 5;
-    if (lane == 0) {
-      red[3 * wid + 0] = acc_p;
-      red[3 * wid + 1] = acc_a;
-      red[3 * wid + 2] = acc_b;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double p = 0, ma = 0, mb = 0;
-      for (int w = 0; w < nw; ++w) {
-        p += red[3 * w];
-        ma += red[3 * w + 1];
-        mb += red[3 * w + 2];
-      }
-      a.partials[3 * item_index + 0] = p;
-      a.partials[3 * item_index + 1] = ma;
-      a.partials[3 * item_index + 2] = mb;
-    }
-  }
+  if (SAMPLE) block_partials(acc_p, acc_a, acc_b, red, a.partials + 3 * item_index);
 }
 
+// ======================================================================================
+// Bulk path (rows 16-byte aligned, TX = 128 or 256).
+// ======================================================================================
+template <class real, int TX>
+__device__ __forceinline__ void bulk_init(unsigned char* smem) {
+  using SM = SmemBulk<real, TX>;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSI; ++i) mbar_init(bars + i, 1);
+    *reinterpret_cast<volatile int*>(smem + SM::abort_flag) = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+}
+
+// ph: expected parity bit per input slot, carried across items by the caller.  Returns false if
+// a wait gave up (the block then stops; a.err is set).
+template <class real, int TX, bool SAMPLE, int NOISE>
+__device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const real* __restrict__ src,
+                                                  real* __restrict__ dst, int item_index, uint32_t step,
+                                                  unsigned char* smem, uint32_t& ph) {
+  using SM = SmemBulk<real, TX>;
+  constexpr int PAD = SM::PAD, SW = SM::SW, W = TX + 2;
+  double* red = reinterpret_cast<double*>(smem + SM::red);
+  LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + SM::lat);
+  real* ringA = reinterpret_cast<real*>(smem + SM::ring);
+  real* ringB = ringA + 4 * W;
+  real* instage = reinterpret_cast<real*>(smem + SM::in);
+  real* outrow = reinterpret_cast<real*>(smem + SM::out);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::abort_flag);
+
+  const WorkItem it = a.items[item_index];
+  __syncthreads();  // shared memory may still be read for the previous item
+  {
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(a.lat + it.lattice);
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(Ls);
+    for (int i = threadIdx.x; i < (int)(sizeof(LatticeDev<real>) / 4); i += TX) d32[i] = s32[i];
+  }
+  __syncthreads();
+  const LatticeDev<real>& L = *Ls;
+  const int Lx = L.Lx, Lz = L.Lz, LzLx = Lx * Lz;
+  const int tid = threadIdx.x;
+  const int x0 = it.x0;
+  const int nact = min(TX, Lx - x0);
+  const bool active = tid < nact;
+  const int x = x0 + (active ? tid : 0);
+  const bool do_left = tid == 0, do_right = tid == nact - 1;
+  const real* f = src + L.f_off;
+  real* g = dst + L.f_off;
+  const real k9 = L.k9, k36 = L.k36;
+  const int flags = L.flags;
+  const RowConst<real>* rows = a.rows + L.row_off;
+  const int z0 = it.z0, z1 = it.z1;
+  const unsigned row_bytes = 18u * (unsigned)(nact + 2 * PAD) * (unsigned)sizeof(real);
+
+  // lane k < 18 of warp 0 copies plane k of row r (its source row, reflected at the walls)
+  auto stage_row = [&](int r) {
+    if (r < 0 || r >= Lz || r > z1) return;
+    const int slot = r & (NSI - 1);
+    uint64_t* bar = bars + slot;
+    if (tid == 0) mbar_expect_tx(bar, row_bytes);
+    if (tid < 18) {
+      fence_async_smem();
+      const int s = tid / 9, l = tid - 9 * s;
+      const int cz = LB_CZ(l);
+      int sr = r - cz, p = tid;
+      if (sr < 0 || sr >= Lz) {
+        sr = r;
+        p = 9 * s + LB_OPP(l);
+      }
+      const real* rowp = f + (size_t)p * LzLx + (size_t)sr * Lx;
+      real* d = instage + (slot * 18 + tid) * SW;
+      const unsigned sz = (unsigned)sizeof(real);
+      if (x0 > 0 && x0 + nact < Lx) {
+        bulk_g2s(d, rowp + x0 - PAD, (unsigned)(nact + 2 * PAD) * sz, bar);
+      } else {
+        bulk_g2s(d, rowp + (x0 == 0 ? Lx - PAD : x0 - PAD), PAD * sz, bar);
+        if (x0 + nact < Lx) {
+          bulk_g2s(d + PAD, rowp + x0, (unsigned)(nact + PAD) * sz, bar);
+        } else {
+          bulk_g2s(d + PAD, rowp + x0, (unsigned)nact * sz, bar);
+          bulk_g2s(d + PAD + nact, rowp, PAD * sz, bar);
+        }
+      }
+    }
+  };
+  auto wait_row = [&](int r) {
+    const int slot = r & (NSI - 1);
+    const unsigned par = (ph >> slot) & 1u;
+    if (!mbar_try_wait(bars + slot, par)) {
+      const uint64_t t0 = global_ns();
+      while (!mbar_try_wait(bars + slot, par)) {
+        if (*abort_flag) break;
+        if (global_ns() - t0 > (uint64_t)WAIT_MS * 1000000ull) {
+          *abort_flag = 1;
+          atomicExch(a.err, 1);
+          break;
+        }
+      }
+    }
+    ph ^= 1u << slot;
+  };
+  auto rho_at = [&](int r, int j, real& dA, real& dB) {
+    const real* sb = instage + (r & (NSI - 1)) * 18 * SW;
+    real v[9];
+    read_bulk<real, SW>(sb, j, 0, r > 0, r < Lz - 1, k9, k36, v);
+    dA = sum9(v);
+    read_bulk<real, SW>(sb, j, 1, r > 0, r < Lz - 1, k9, k36, v);
+    dB = sum9(v);
+  };
+  auto put_rho = [&](int r) {
+    wait_row(r);
+    const int b = ring_slot(r) * W;
+    real dA, dB;
+    if (active) {
+      rho_at(r, tid + PAD, dA, dB);
+      ringA[b + tid + 1] = dA;
+      ringB[b + tid + 1] = dB;
+    }
+    if (do_left) {
+      rho_at(r, PAD - 1, dA, dB);
+      ringA[b] = dA;
+      ringB[b] = dB;
+    }
+    if (do_right) {
+      rho_at(r, nact + PAD, dA, dB);
+      ringA[b + nact + 1] = dA;
+      ringB[b + nact + 1] = dB;
+    }
+  };
+  auto ghost_row = [&](int zg, int za) {
+    const int bg = ring_slot(zg) * W, ba = ring_slot(za) * W;
+    const bool fixed = flags & DF_WALL_FIXED;
+    const real cw = rows[za].ghost_cA;
+    auto copy1 = [&](int i) {
+      const real A = ringA[ba + i], B = ringB[ba + i];
+      if (fixed) {
+        const real t = A + B;
+        ringA[bg + i] = t * cw;
+        ringB[bg + i] = t * (1 - cw);
+      } else {
+        ringA[bg + i] = A;
+        ringB[bg + i] = B;
+      }
+    };
+    if (active) copy1(tid + 1);
+    if (do_left) copy1(0);
+    if (do_right) copy1(nact + 1);
+  };
+  // lane k < 18 of warp 0 stores plane k of the output row (row zr)
+  auto store_row = [&](int zr) {
+    if (tid < 18) {
+      bulk_s2g(g + (size_t)tid * LzLx + (size_t)zr * Lx + x0, outrow + tid * TX, (unsigned)(nact * sizeof(real)));
+      bulk_commit();
+    }
+  };
+
+  // prologue: rows z0-1 .. z0+NSI-2 in flight
+  for (int r = z0 - 1; r <= z0 + NSI - 2; ++r) stage_row(r);
+  if (z0 > 0) put_rho(z0 - 1);
+  put_rho(z0);
+  if (z0 == 0) ghost_row(-1, 0);
+
+  const SiteK<real> K = site_constants<real, NOISE>(L);
+  double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
+  bool ok = true;
+
+  for (int z = z0; z < z1; ++z) {
+    if (z + 1 < Lz) put_rho(z + 1);
+    else ghost_row(Lz, Lz - 1);
+    if (tid < 18) bulk_wait_read_all();  // the previous bulk store has read the output row
+    __syncthreads();
+    if (*abort_flag) {
+      ok = false;
+      break;
+    }
+    stage_row(z + NSI - 1);  // into the slot of row z-1, read by every thread before the barrier
+    if (active) {
+      const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
+                bd = ring_slot(z - 1) * W + tid + 1;
+      const real* sb = instage + (z & (NSI - 1)) * 18 * SW;
+      const bool below = z > 0, above = z < Lz - 1;
+      real v[9];
+      read_bulk<real, SW>(sb, tid + PAD, 0, below, above, k9, k36, v);
+      const Mom<real> mA = moments(v);
+      read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
+      const Mom<real> mB = moments(v);
+      const int r0 = z * Lx + x;
+      site_update<real, SAMPLE, NOISE, false, TX>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
+                                                  (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
+                                                  acc_a, acc_b, outrow + tid, outrow + 9 * TX + tid, TX, flags);
+    }
+    fence_async_smem();  // the output row is read by the bulk store next
+    __syncthreads();
+    store_row(z);
+  }
+  if (tid < 18) bulk_wait_all();
+  if (!ok) {
+    // drain the input rows still in flight (bounded), then stop
+    if (tid == 0) {
+      for (int i = 0; i < NSI; ++i) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(bars + i, (ph >> i) & 1u) && global_ns() - t0 < 100000000ull) {
+        }
+      }
+    }
+    __syncthreads();
+    return false;
+  }
+  if (SAMPLE) block_partials(acc_p, acc_a, acc_b, red, a.partials + 3 * item_index);
+  return true;
+}
+
+// ======================================================================================
+// Kernels.
+// ======================================================================================
 template <class real>
 struct MinBlocks {
   static constexpr int value = sizeof(real) == 4 ? 2 : 1;
@@ -466,13 +811,16 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepA
   process_item<real, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem);
 }
 
-// ---- bounded grid barrier for the persistent launch --------------------------------
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+template <class real, int TX, bool SAMPLE, int NOISE>
+__global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX) step_kernel_bulk(StepArgs<real> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
+  bulk_init<real, TX>(smem);
+  uint32_t ph = 0;
+  process_item_bulk<real, TX, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem, ph);
 }
 
+// ---- bounded grid barrier for the persistent launch --------------------------------
 // bar[0]: arrivals, bar[1]: generation.  Returns false if the wait gave up after limit_ms
 // (err is then set) or another block reported an error.
 __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int limit_ms) {
@@ -526,74 +874,155 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
   }
 }
 
+template <class real, int TX, int NOISE>
+__global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX)
+    persistent_kernel_bulk(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t t0 = *a.d_t + a.t_offset;
+  bulk_init<real, TX>(smem);
+  uint32_t ph = 0;
+  for (int k = 0; k < nsteps; ++k) {
+    const real* src = (k & 1) ? a.dst : a.src;
+    real* dst = (k & 1) ? const_cast<real*>(a.src) : a.dst;
+    const uint32_t step = (uint32_t)(t0 + k);
+    const bool sample = sample_last && k == nsteps - 1;
+    for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) {
+      const bool ok = sample ? process_item_bulk<real, TX, true, NOISE>(a, src, dst, i, step, smem, ph)
+                             : process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, step, smem, ph);
+      if (!ok) return;  // the others give up at their next barrier (bounded)
+    }
+    if (k + 1 < nsteps) {
+      if (!grid_barrier(bar, err, gridDim.x, limit_ms)) return;
+    }
+  }
+}
+
 __global__ void advance_kernel(int64_t* d_t, int64_t k) { *d_t += k; }
 
 __global__ void barrier_probe_kernel(unsigned* bar, int* err, unsigned expected, int limit_ms) {
   grid_barrier(bar, err, expected, limit_ms);
 }
 
+// ======================================================================================
+// Host side.
+// ======================================================================================
 template <class real>
 size_t step_smem_bytes(int tile_x) {
   return Smem<real>::bytes(tile_x);
 }
 
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class real, int TX>
+static cudaError_t prepare_bulk() {
+  const size_t b = SmemBulk<real, TX>::bytes;
+  const void* fns[] = {(const void*)step_kernel_bulk<real, TX, true, NOISE_OFF>,
+                       (const void*)step_kernel_bulk<real, TX, true, NOISE_HOM>,
+                       (const void*)step_kernel_bulk<real, TX, true, NOISE_LOC>,
+                       (const void*)step_kernel_bulk<real, TX, false, NOISE_OFF>,
+                       (const void*)step_kernel_bulk<real, TX, false, NOISE_HOM>,
+                       (const void*)step_kernel_bulk<real, TX, false, NOISE_LOC>,
+                       (const void*)persistent_kernel_bulk<real, TX, NOISE_OFF>,
+                       (const void*)persistent_kernel_bulk<real, TX, NOISE_HOM>,
+                       (const void*)persistent_kernel_bulk<real, TX, NOISE_LOC>};
+  for (const void* fn : fns) {
+    cudaError_t e = set_smem(fn, b);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <class real>
 cudaError_t prepare_step(int max_tile_x) {
-  const int bytes = (int)Smem<real>::bytes(max_tile_x);
+  const size_t bytes = Smem<real>::bytes(max_tile_x);
   const void* fns[] = {(const void*)step_kernel<real, true, NOISE_OFF>,  (const void*)step_kernel<real, true, NOISE_HOM>,
                        (const void*)step_kernel<real, true, NOISE_LOC>,  (const void*)step_kernel<real, false, NOISE_OFF>,
                        (const void*)step_kernel<real, false, NOISE_HOM>, (const void*)step_kernel<real, false, NOISE_LOC>,
                        (const void*)persistent_kernel<real, NOISE_OFF>,  (const void*)persistent_kernel<real, NOISE_HOM>,
                        (const void*)persistent_kernel<real, NOISE_LOC>};
   for (const void* fn : fns) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = set_smem(fn, bytes);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  cudaError_t e = prepare_bulk<real, 128>();
+  if (e != cudaSuccess) return e;
+  return prepare_bulk<real, 256>();
 }
 
 template <class real, bool SAMPLE>
-void launch_step_as(const StepArgs<real>& a, int tile_x, int noise, size_t smem, cudaStream_t s) {
+static void launch_generic(const StepArgs<real>& a, int tile_x, int noise, cudaStream_t s) {
+  const size_t smem = Smem<real>::bytes(tile_x);
   if (noise == NOISE_HOM) step_kernel<real, SAMPLE, NOISE_HOM><<<a.n_items, tile_x, smem, s>>>(a);
   else if (noise == NOISE_LOC) step_kernel<real, SAMPLE, NOISE_LOC><<<a.n_items, tile_x, smem, s>>>(a);
   else step_kernel<real, SAMPLE, NOISE_OFF><<<a.n_items, tile_x, smem, s>>>(a);
 }
 
+template <class real, int TX, bool SAMPLE>
+static void launch_bulk(const StepArgs<real>& a, int noise, cudaStream_t s) {
+  const size_t smem = SmemBulk<real, TX>::bytes;
+  if (noise == NOISE_HOM) step_kernel_bulk<real, TX, SAMPLE, NOISE_HOM><<<a.n_items, TX, smem, s>>>(a);
+  else if (noise == NOISE_LOC) step_kernel_bulk<real, TX, SAMPLE, NOISE_LOC><<<a.n_items, TX, smem, s>>>(a);
+  else step_kernel_bulk<real, TX, SAMPLE, NOISE_OFF><<<a.n_items, TX, smem, s>>>(a);
+}
+
 template <class real>
-cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, cudaStream_t s) {
-  const size_t smem = Smem<real>::bytes(tile_x);
+cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, bool bulk, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
-  if (sample) launch_step_as<real, true>(a, tile_x, noise, smem, s);
-  else launch_step_as<real, false>(a, tile_x, noise, smem, s);
+  if (bulk && tile_x == 128) {
+    if (sample) launch_bulk<real, 128, true>(a, noise, s);
+    else launch_bulk<real, 128, false>(a, noise, s);
+  } else if (bulk && tile_x == 256) {
+    if (sample) launch_bulk<real, 256, true>(a, noise, s);
+    else launch_bulk<real, 256, false>(a, noise, s);
+  } else {
+    if (sample) launch_generic<real, true>(a, tile_x, noise, s);
+    else launch_generic<real, false>(a, tile_x, noise, s);
+  }
   return cudaGetLastError();
 }
 
 template <class real>
-const void* persistent_fn(int noise) {
+static const void* persistent_fn(int tile_x, int noise, bool bulk, size_t* smem) {
+  if (bulk && tile_x == 128) {
+    *smem = SmemBulk<real, 128>::bytes;
+    if (noise == NOISE_HOM) return (const void*)persistent_kernel_bulk<real, 128, NOISE_HOM>;
+    if (noise == NOISE_LOC) return (const void*)persistent_kernel_bulk<real, 128, NOISE_LOC>;
+    return (const void*)persistent_kernel_bulk<real, 128, NOISE_OFF>;
+  }
+  if (bulk && tile_x == 256) {
+    *smem = SmemBulk<real, 256>::bytes;
+    if (noise == NOISE_HOM) return (const void*)persistent_kernel_bulk<real, 256, NOISE_HOM>;
+    if (noise == NOISE_LOC) return (const void*)persistent_kernel_bulk<real, 256, NOISE_LOC>;
+    return (const void*)persistent_kernel_bulk<real, 256, NOISE_OFF>;
+  }
+  *smem = Smem<real>::bytes(tile_x);
   if (noise == NOISE_HOM) return (const void*)persistent_kernel<real, NOISE_HOM>;
   if (noise == NOISE_LOC) return (const void*)persistent_kernel<real, NOISE_LOC>;
   return (const void*)persistent_kernel<real, NOISE_OFF>;
 }
 
 template <class real>
-int persistent_grid(int tile_x, int noise) {
+int persistent_grid(int tile_x, int noise, bool bulk) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_fn<real>(noise), tile_x,
-                                                    Smem<real>::bytes(tile_x)) != cudaSuccess)
-    return 0;
+  size_t smem = 0;
+  const void* fn = persistent_fn<real>(tile_x, noise, bulk, &smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, tile_x, smem) != cudaSuccess) return 0;
   return per * sms;
 }
 
 template <class real>
 cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, int noise,
-                                   unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
+                                   bool bulk, unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
   StepArgs<real> aa = a;
   int ns = nsteps, sl = sample_last ? 1 : 0;
   void* args[] = {&aa, &ns, &sl, &barrier, &err, &limit_ms};
-  return cudaLaunchCooperativeKernel(persistent_fn<real>(noise), dim3(grid), dim3(tile_x), args,
-                                     Smem<real>::bytes(tile_x), s);
+  size_t smem = 0;
+  const void* fn = persistent_fn<real>(tile_x, noise, bulk, &smem);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
 }
 
 cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s) {
@@ -608,13 +1037,13 @@ cudaError_t launch_barrier_probe(int blocks, int expected, int limit_ms, unsigne
   return cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(blocks), dim3(32), args, 0, s);
 }
 
-#define LB_STEP_INST(real)                                                                                       \
-  template size_t step_smem_bytes<real>(int);                                                                    \
-  template cudaError_t prepare_step<real>(int);                                                                  \
-  template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, int, cudaStream_t);                   \
-  template int persistent_grid<real>(int, int);                                                                  \
-  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, bool, int, unsigned*, int*,   \
-                                                    int, int, cudaStream_t);
+#define LB_STEP_INST(real)                                                                                         \
+  template size_t step_smem_bytes<real>(int);                                                                      \
+  template cudaError_t prepare_step<real>(int);                                                                    \
+  template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, int, bool, cudaStream_t);               \
+  template int persistent_grid<real>(int, int, bool);                                                              \
+  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, bool, int, bool, unsigned*,  \
+                                                    int*, int, int, cudaStream_t);
 LB_STEP_INST(float)
 LB_STEP_INST(double)
 

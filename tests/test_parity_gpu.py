@@ -160,7 +160,8 @@ def test_launch_modes_and_tiles_are_bit_identical(prec):
     compute each site identically."""
     p = LatticeParams(128, 32, kT=1e-5, G=0.5, grad_c0=0.4 / 32, seed=9)
     results = []
-    configs = [dict(), dict(graph=True), dict(persistent=True), dict(graph=True, persistent=True)]
+    configs = [dict(), dict(graph=True), dict(persistent=True), dict(graph=True, persistent=True), dict(bulk=False),
+               dict(bulk=False, persistent=True)]
     for kw in configs:
         with Simulation(p, precision=prec, **kw) as sim:
             sim.set_sampling(3, 7)
@@ -206,6 +207,23 @@ def test_set_get_round_trip(prec):
         np.testing.assert_array_equal(g, f)
     else:
         np.testing.assert_allclose(g, f, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_multi_strip_lattice_wraps_periodically(prec):
+    """Three column strips of 128 (bulk copies with the periodic wrap at both lattice edges and
+    an interior strip), against the oracle."""
+    p = LatticeParams(384, 12, lambda_s=1.2, lambda_d=0.9, kT=1e-4, G=0.4, grad_c0=0.3 / 12, seed=21)
+    with Simulation(p, precision=prec) as sim:
+        sim.set_tile(128, 5)
+        sim.step(150)
+        got = sim.populations()
+    o = oracle_of(p)
+    o.step(150)
+    if prec == "fp64":
+        assert_fp64_parity(got, o.populations())
+    else:
+        assert_dev32_parity(got, o.populations(), background(p.Lx, p.Lz, p.grad_c0))
 
 
 def test_step_from_arbitrary_state():
