@@ -71,6 +71,7 @@ struct lb_ctx {
   int2* d_col_tasks = nullptr;
   int n_row_tasks = 0, n_col_tasks = 0;
   int max_Lx = 0, max_Lz = 0;
+  int col_strip = 1;
   int64_t* d_t = nullptr;
   unsigned* d_barrier = nullptr;
   int* d_err = nullptr;
@@ -312,10 +313,13 @@ int alloc_diag(lb_ctx* c) {
   if (!rc) rc = dev_alloc(c, &c->acc_sum, 4 * (size_t)c->n_sites * sizeof(double));
   if (!rc) rc = dev_alloc(c, &c->acc_comp, 4 * (size_t)c->n_sites * sizeof(double));
   if (rc) return rc;
+  c->col_strip = c->dev32 ? sf_column_strip<float>(c->max_Lz) : sf_column_strip<double>(c->max_Lz);
   std::vector<int2> rt, ct;
   for (int i = 0; i < c->n_lat; ++i) {
+    const int Lx = c->params[i].Lx, cq = std::min(c->col_strip, Lx);
     for (int k = 0; k < 4 * c->params[i].Lz; ++k) rt.push_back(make_int2(i, k));
-    for (int k = 0; k < 4 * c->params[i].Lx; ++k) ct.push_back(make_int2(i, k));
+    for (int fld = 0; fld < 4; ++fld)
+      for (int q = 0; q < Lx; q += cq) ct.push_back(make_int2(i, fld * Lx + q));
   }
   rc = dev_alloc(c, &c->d_row_tasks, rt.size() * sizeof(int2));
   if (!rc) rc = dev_alloc(c, &c->d_col_tasks, ct.size() * sizeof(int2));
@@ -363,6 +367,7 @@ cudaError_t enqueue_sample(lb_ctx* c) {
   p.n_col_tasks = c->n_col_tasks;
   p.max_Lx = c->max_Lx;
   p.max_Lz = c->max_Lz;
+  p.col_strip = c->col_strip;
   cudaError_t e = launch_sf<real>(p, (const real*)c->fields, c->tmp, c->acc_sum, c->acc_comp, c->stream);
   if (e != cudaSuccess) return e;
   c->launches += 3;

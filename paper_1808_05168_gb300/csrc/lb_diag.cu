@@ -89,28 +89,50 @@ __device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v
   sum = t;
 }
 
+// Column pass: one block per (lattice, field, strip of cq adjacent q_x), cq = min(CQ, Lx), so that
+// every row of the strip is read and accumulated with contiguous accesses.
 template <class real>
 __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const Cplx<real>* tmp, double* acc_sum,
-                               double* acc_comp) {
+                               double* acc_comp, int CQ) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int2 task = tasks[blockIdx.x];
   const DiagLattice L = lat[task.x];
-  const int n = L.Lz, logn = ilog2(n), Lx = L.Lx;
-  const int fld = task.y / Lx, qx = task.y - fld * Lx;
-  Cplx<real>* s = reinterpret_cast<Cplx<real>*>(smem);
-  Cplx<real>* tw = s + n;
+  const int n = L.Lz, logn = ilog2(n), Lx = L.Lx, half = n >> 1;
+  const int cq = min(CQ, Lx), lcq = ilog2(cq);
+  const int fld = task.y / Lx, qx0 = task.y - fld * Lx;
+  Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
+  Cplx<real>* s = tw + (half > 0 ? half : 1);
   fill_twiddles<real>(tw, n);
-  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx0;
+  for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
+    const int j = idx >> lcq, c = idx & (cq - 1);
     const int r = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[r] = tmp[base + (int64_t)j * Lx];
+    s[c * n + r] = tmp[base + (int64_t)j * Lx + c];
   }
   __syncthreads();
-  fft_inplace<real>(s, tw, n, logn);
+  for (int lg = 1; lg <= logn; ++lg) {
+    const int hs = 1 << (lg - 1);
+    const int stride = n >> lg;
+    for (int idx = threadIdx.x; idx < half * cq; idx += blockDim.x) {
+      const int c = idx / half, jj = idx - c * half;
+      Cplx<real>* sc = s + c * n;
+      const int pos = jj & (hs - 1);
+      const int i0 = ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
+      const Cplx<real> w = tw[pos * stride];
+      const Cplx<real> b = sc[i1], a = sc[i0];
+      const real tr = w.re * b.re - w.im * b.im;
+      const real ti = w.re * b.im + w.im * b.re;
+      sc[i0] = Cplx<real>{a.re + tr, a.im + ti};
+      sc[i1] = Cplx<real>{a.re - tr, a.im - ti};
+    }
+    __syncthreads();
+  }
   const double scale = 1.0 / ((double)Lx * (double)n);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const double re = (double)s[j].re, im = (double)s[j].im;
-    const int64_t o = base + (int64_t)j * Lx;
+  for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
+    const int j = idx >> lcq, c = idx & (cq - 1);
+    const Cplx<real> v = s[c * n + j];
+    const double re = (double)v.re, im = (double)v.im;
+    const int64_t o = base + (int64_t)j * Lx + c;
     double sm = acc_sum[o], cp = acc_comp[o];
     neumaier_add(sm, cp, (re * re + im * im) * scale);
     acc_sum[o] = sm;
@@ -217,22 +239,35 @@ size_t sf_smem_bytes(int n) {
   return (size_t)n * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
 }
 
+// Columns per column-pass block: up to 16, fewer when Lz is long (shared memory budget).
+template <class real>
+int sf_column_strip(int max_Lz) {
+  int cq = 16;
+  while (cq > 1 && ((size_t)max_Lz * cq + max_Lz / 2 + 1) * sizeof(Cplx<real>) > 160 * 1024) cq >>= 1;
+  return cq;
+}
+
+template <class real>
+size_t sf_cols_smem_bytes(int max_Lz, int cq) {
+  return ((size_t)max_Lz * cq + max_Lz / 2 + 1) * sizeof(Cplx<real>);
+}
+
 template <class real>
 cudaError_t prepare_sf(int max_Lx, int max_Lz) {
   cudaError_t e = cudaFuncSetAttribute(sf_rows_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sf_smem_bytes<real>(max_Lx));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sf_cols_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sf_smem_bytes<real>(max_Lz));
+                              (int)sf_cols_smem_bytes<real>(max_Lz, sf_column_strip<real>(max_Lz)));
 }
 
 template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
                       cudaStream_t s) {
-  const size_t smr = sf_smem_bytes<real>(p.max_Lx), smc = sf_smem_bytes<real>(p.max_Lz);
+  const size_t smr = sf_smem_bytes<real>(p.max_Lx), smc = sf_cols_smem_bytes<real>(p.max_Lz, p.col_strip);
   sf_rows_kernel<real><<<p.n_row_tasks, 256, smr, s>>>(p.lat, p.row_tasks, fields, (Cplx<real>*)tmp);
   sf_cols_kernel<real><<<p.n_col_tasks, 256, smc, s>>>(p.lat, p.col_tasks, (const Cplx<real>*)tmp, acc_sum,
-                                                       acc_comp);
+                                                       acc_comp, p.col_strip);
   return cudaGetLastError();
 }
 
@@ -269,6 +304,7 @@ cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s) {
 #define LB_INST(real)                                                                                        \
   template size_t sf_smem_bytes<real>(int);                                                                  \
   template cudaError_t prepare_sf<real>(int, int);                                                           \
+  template int sf_column_strip<real>(int);                                                                   \
   template cudaError_t launch_sf<real>(const SfPlan&, const real*, void*, double*, double*, cudaStream_t);   \
   template cudaError_t launch_mass<real>(const real*, const BgParams&, double*, cudaStream_t);               \
   template cudaError_t launch_to_absolute<real>(const real*, const BgParams&, double*, cudaStream_t);        \

@@ -255,6 +255,7 @@ struct SfPlan {
   const int2* col_tasks;
   int n_row_tasks, n_col_tasks;
   int max_Lx, max_Lz;
+  int col_strip;  // q_x columns per column-pass block
 };
 
 // What the utility kernels need to rebuild the background w_l rho_bar c^S_0(z) in double.
@@ -268,6 +269,8 @@ template <class real>
 size_t sf_smem_bytes(int n);
 template <class real>
 cudaError_t prepare_sf(int max_Lx, int max_Lz);
+template <class real>
+int sf_column_strip(int max_Lz);
 
 template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,

@@ -33,7 +33,8 @@ namespace lbk {
 namespace {
 
 constexpr int NS = 4;   // generic path: rows of staged populations (power of two)
-constexpr int NSI = 4;  // bulk path: input row slots (power of two)
+constexpr int NSI = 3;  // bulk path: input row slots
+constexpr int NSO = 2;  // bulk path: output row slots
 constexpr int WAIT_MS = 2000;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -435,8 +436,8 @@ struct Smem {
   __host__ __device__ static size_t bytes(int tx) { return stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real); }
 };
 
-// Bulk: as generic, then input slots (NSI x 18 x SW), one output row (18 x TX), NSI mbarriers
-// and an abort flag.
+// Bulk: as generic, then input slots (NSI x 18 x SW), output rows (NSO x 18 x TX), NSI
+// mbarriers and an abort flag.
 template <class real, int TX>
 struct SmemBulk {
   static constexpr int PAD = 16 / (int)sizeof(real);
@@ -446,7 +447,7 @@ struct SmemBulk {
   static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
   static constexpr size_t in = ring + ((8 * (TX + 2) * sizeof(real) + 15) / 16) * 16;
   static constexpr size_t out = in + (size_t)NSI * 18 * SW * sizeof(real);
-  static constexpr size_t bars = out + (size_t)18 * TX * sizeof(real);
+  static constexpr size_t bars = out + (size_t)NSO * 18 * TX * sizeof(real);
   static constexpr size_t abort_flag = bars + NSI * sizeof(uint64_t);
   static constexpr size_t bytes = abort_flag + 16;
 };
@@ -641,7 +642,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   // lane k < 18 of warp 0 copies plane k of row r (its source row, reflected at the walls)
   auto stage_row = [&](int r) {
     if (r < 0 || r >= Lz || r > z1) return;
-    const int slot = r & (NSI - 1);
+    const int slot = r % NSI;
     uint64_t* bar = bars + slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
     if (tid < 18) {
@@ -670,7 +671,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     }
   };
   auto wait_row = [&](int r) {
-    const int slot = r & (NSI - 1);
+    const int slot = r % NSI;
     const unsigned par = (ph >> slot) & 1u;
     if (!mbar_try_wait(bars + slot, par)) {
       const uint64_t t0 = global_ns();
@@ -686,7 +687,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     ph ^= 1u << slot;
   };
   auto rho_at = [&](int r, int j, real& dA, real& dB) {
-    const real* sb = instage + (r & (NSI - 1)) * 18 * SW;
+    const real* sb = instage + (r % NSI) * 18 * SW;
     real v[9];
     read_bulk<real, SW>(sb, j, 0, r > 0, r < Lz - 1, k9, k36, v);
     dA = sum9(v);
@@ -732,10 +733,11 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     if (do_left) copy1(0);
     if (do_right) copy1(nact + 1);
   };
-  // lane k < 18 of warp 0 stores plane k of the output row (row zr)
+  // lane k < 18 of warp 0 stores plane k of output row zr (its output slot is zr % NSO)
   auto store_row = [&](int zr) {
     if (tid < 18) {
-      bulk_s2g(g + (size_t)tid * LzLx + (size_t)zr * Lx + x0, outrow + tid * TX, (unsigned)(nact * sizeof(real)));
+      bulk_s2g(g + (size_t)tid * LzLx + (size_t)zr * Lx + x0, outrow + ((zr % NSO) * 18 + tid) * TX,
+               (unsigned)(nact * sizeof(real)));
       bulk_commit();
     }
   };
@@ -750,20 +752,28 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
   bool ok = true;
 
+  // Row z: its densities ring and the previous row's output are complete at the barrier; the
+  // previous row is then stored, the input slot of row z-1 refilled with row z+NSI-1, and row z
+  // collided into output slot z % NSO, whose previous store (row z-NSO) has been read by then.
   for (int z = z0; z < z1; ++z) {
     if (z + 1 < Lz) put_rho(z + 1);
     else ghost_row(Lz, Lz - 1);
-    if (tid < 18) bulk_wait_read_all();  // the previous bulk store has read the output row
+    if (tid < 18 && z - z0 >= NSO) {
+      // the store of row z-NSO (issued one iteration ago) has read its output slot
+      asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(NSO - 2 < 0 ? 0 : NSO - 2) : "memory");
+    }
+    fence_async_smem();  // output row z-1, written by every thread, is read by a bulk store next
     __syncthreads();
     if (*abort_flag) {
       ok = false;
       break;
     }
+    if (z > z0) store_row(z - 1);
     stage_row(z + NSI - 1);  // into the slot of row z-1, read by every thread before the barrier
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real* sb = instage + (z & (NSI - 1)) * 18 * SW;
+      const real* sb = instage + (z % NSI) * 18 * SW;
       const bool below = z > 0, above = z < Lz - 1;
       real v[9];
       read_bulk<real, SW>(sb, tid + PAD, 0, below, above, k9, k36, v);
@@ -771,13 +781,16 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
       const Mom<real> mB = moments(v);
       const int r0 = z * Lx + x;
+      real* ob = outrow + (z % NSO) * 18 * TX + tid;
       site_update<real, SAMPLE, NOISE, false, TX>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
                                                   (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
-                                                  acc_a, acc_b, outrow + tid, outrow + 9 * TX + tid, TX, flags);
+                                                  acc_a, acc_b, ob, ob + 9 * TX, TX, flags);
     }
-    fence_async_smem();  // the output row is read by the bulk store next
+  }
+  if (ok) {
+    fence_async_smem();
     __syncthreads();
-    store_row(z);
+    store_row(z1 - 1);
   }
   if (tid < 18) bulk_wait_all();
   if (!ok) {
