@@ -44,6 +44,7 @@ def parse():
                     help="run a small single-lattice case only (for ncu captures)")
     ap.add_argument("--profile-kT", type=float, default=1e-5, help="kT of the small case")
     ap.add_argument("--profile-precision", default="dev32", choices=["dev32", "fp64"])
+    ap.add_argument("--profile-generic", action="store_true", help="small case with per-thread staging")
     return ap.parse_args()
 
 
@@ -328,7 +329,7 @@ def run_reference(args):
     }))
 
 
-def run_profile_small(kT, precision):
+def run_profile_small(kT, precision, bulk=True):
     """A small case for ncu: one 4096 x 1024 lattice (302 MB per FP32 state buffer, more than L2),
     6 steps."""
     import torch
@@ -336,7 +337,7 @@ def run_profile_small(kT, precision):
     from paper_1808_05168_gb300 import LatticeParams, Simulation
 
     p = LatticeParams(4096, 1024, kT=kT, G=0.5, grad_c0=0.5 / 1024, seed=4, lambda_e=1.0)
-    with Simulation(p, precision=precision) as sim:
+    with Simulation(p, precision=precision, bulk=bulk) as sim:
         sim.set_tile(128, 64)
         sim.step(6)
         sim.synchronize()
@@ -347,7 +348,7 @@ def run_profile_small(kT, precision):
 if __name__ == "__main__":
     a = parse()
     if a.profile_small:
-        run_profile_small(a.profile_kT, a.profile_precision)
+        run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -33,8 +33,7 @@ namespace lbk {
 namespace {
 
 constexpr int NS = 4;   // generic path: rows of staged populations (power of two)
-constexpr int NSI = 3;  // bulk path: input row slots
-constexpr int NSO = 2;  // bulk path: output row slots
+constexpr int NSI = 4;  // bulk path: input row slots
 constexpr int WAIT_MS = 2000;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -436,8 +435,7 @@ struct Smem {
   __host__ __device__ static size_t bytes(int tx) { return stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real); }
 };
 
-// Bulk: as generic, then input slots (NSI x 18 x SW), output rows (NSO x 18 x TX), NSI
-// mbarriers and an abort flag.
+// Bulk: as generic, then input slots (NSI x 18 x SW), NSI mbarriers and an abort flag.
 template <class real, int TX>
 struct SmemBulk {
   static constexpr int PAD = 16 / (int)sizeof(real);
@@ -446,8 +444,7 @@ struct SmemBulk {
   static constexpr size_t lat = 8 * 3 * sizeof(double);
   static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
   static constexpr size_t in = ring + ((8 * (TX + 2) * sizeof(real) + 15) / 16) * 16;
-  static constexpr size_t out = in + (size_t)NSI * 18 * SW * sizeof(real);
-  static constexpr size_t bars = out + (size_t)NSO * 18 * TX * sizeof(real);
+  static constexpr size_t bars = in + (size_t)NSI * 18 * SW * sizeof(real);
   static constexpr size_t abort_flag = bars + NSI * sizeof(uint64_t);
   static constexpr size_t bytes = abort_flag + 16;
 };
@@ -611,7 +608,6 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   real* ringA = reinterpret_cast<real*>(smem + SM::ring);
   real* ringB = ringA + 4 * W;
   real* instage = reinterpret_cast<real*>(smem + SM::in);
-  real* outrow = reinterpret_cast<real*>(smem + SM::out);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::abort_flag);
 
@@ -646,7 +642,6 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     uint64_t* bar = bars + slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
     if (tid < 18) {
-      fence_async_smem();
       const int s = tid / 9, l = tid - 9 * s;
       const int cz = LB_CZ(l);
       int sr = r - cz, p = tid;
@@ -733,15 +728,6 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     if (do_left) copy1(0);
     if (do_right) copy1(nact + 1);
   };
-  // lane k < 18 of warp 0 stores plane k of output row zr (its output slot is zr % NSO)
-  auto store_row = [&](int zr) {
-    if (tid < 18) {
-      bulk_s2g(g + (size_t)tid * LzLx + (size_t)zr * Lx + x0, outrow + ((zr % NSO) * 18 + tid) * TX,
-               (unsigned)(nact * sizeof(real)));
-      bulk_commit();
-    }
-  };
-
   // prologue: rows z0-1 .. z0+NSI-2 in flight
   for (int r = z0 - 1; r <= z0 + NSI - 2; ++r) stage_row(r);
   if (z0 > 0) put_rho(z0 - 1);
@@ -752,23 +738,14 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
   bool ok = true;
 
-  // Row z: its densities ring and the previous row's output are complete at the barrier; the
-  // previous row is then stored, the input slot of row z-1 refilled with row z+NSI-1, and row z
-  // collided into output slot z % NSO, whose previous store (row z-NSO) has been read by then.
   for (int z = z0; z < z1; ++z) {
     if (z + 1 < Lz) put_rho(z + 1);
     else ghost_row(Lz, Lz - 1);
-    if (tid < 18 && z - z0 >= NSO) {
-      // the store of row z-NSO (issued one iteration ago) has read its output slot
-      asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(NSO - 2 < 0 ? 0 : NSO - 2) : "memory");
-    }
-    fence_async_smem();  // output row z-1, written by every thread, is read by a bulk store next
     __syncthreads();
     if (*abort_flag) {
       ok = false;
       break;
     }
-    if (z > z0) store_row(z - 1);
     stage_row(z + NSI - 1);  // into the slot of row z-1, read by every thread before the barrier
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
@@ -781,18 +758,11 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
       const Mom<real> mB = moments(v);
       const int r0 = z * Lx + x;
-      real* ob = outrow + (z % NSO) * 18 * TX + tid;
-      site_update<real, SAMPLE, NOISE, false, TX>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
-                                                  (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
-                                                  acc_a, acc_b, ob, ob + 9 * TX, TX, flags);
+      site_update<real, SAMPLE, NOISE, true, 0>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
+                                                (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
+                                                acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
     }
   }
-  if (ok) {
-    fence_async_smem();
-    __syncthreads();
-    store_row(z1 - 1);
-  }
-  if (tid < 18) bulk_wait_all();
   if (!ok) {
     // drain the input rows still in flight (bounded), then stop
     if (tid == 0) {
