@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--profile-kT", type=float, default=1e-5, help="kT of the small case")
     ap.add_argument("--profile-precision", default="dev32", choices=["dev32", "fp64"])
     ap.add_argument("--profile-generic", action="store_true", help="small case with per-thread staging")
+    ap.add_argument("--profile-tile", type=int, default=128, help="tile width of the small case")
     return ap.parse_args()
 
 
@@ -329,7 +330,7 @@ def run_reference(args):
     }))
 
 
-def run_profile_small(kT, precision, bulk=True):
+def run_profile_small(kT, precision, bulk=True, tile=128):
     """A small case for ncu: one 4096 x 1024 lattice (302 MB per FP32 state buffer, more than L2),
     6 steps."""
     import torch
@@ -338,7 +339,7 @@ def run_profile_small(kT, precision, bulk=True):
 
     p = LatticeParams(4096, 1024, kT=kT, G=0.5, grad_c0=0.5 / 1024, seed=4, lambda_e=1.0)
     with Simulation(p, precision=precision, bulk=bulk) as sim:
-        sim.set_tile(128, 64)
+        sim.set_tile(tile, 64)
         sim.step(6)
         sim.synchronize()
     torch.cuda.synchronize()
@@ -348,7 +349,7 @@ def run_profile_small(kT, precision, bulk=True):
 if __name__ == "__main__":
     a = parse()
     if a.profile_small:
-        run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic)
+        run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic, tile=a.profile_tile)
     elif a.impl == "reference":
         run_reference(a)
     else:

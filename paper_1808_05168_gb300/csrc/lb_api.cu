@@ -444,7 +444,7 @@ int autotune(lb_ctx* c) {
     auto it = cache.find(key);
     if (it != cache.end()) return build_items(c, it->second.first, it->second.second);
   }
-  const int txs[] = {64, 128, 256};
+  const int txs[] = {32, 64, 128, 256};
   const int rows[] = {8, 16, 32, 64, 128, 256, 1 << 30};
   float best = 1e30f;
   int bx = c->tile_x, br = c->rows_per_item;

@@ -1,4 +1,4 @@
-// lb_step.cu -- the fused per-step kernel of the fluctuating two-species D2Q9 MRT method
+// lb_step_impl.cuh -- the fused per-step kernel of the fluctuating two-species D2Q9 MRT method
 // (Eq. LB with Eq. MRT), one launch per step for every lattice of a batch, or one
 // cooperative launch with a bounded grid barrier between steps.
 //
@@ -8,11 +8,11 @@
 // ahead of the row being collided, so that every stored value is read once per step from HBM
 // and no population is held in registers across rows.  Two staging paths compute the same
 // numbers bit for bit:
-//  - bulk (rows 16-byte aligned, TX = 128 or 256): for each of the 18 (species, link) planes
-//    one lane issues a bulk asynchronous copy of the row window [x0 - PAD, x0 + TX + PAD)
+//  - bulk (rows 16-byte aligned, TX = 32, 64 or 128): for each of the 18 (species, link)
+//    planes one lane issues a bulk asynchronous copy of the row window [x0 - PAD, x0 + TX + PAD)
 //    (PAD = 16 bytes; wrapped periodically at the lattice's x edges) into a ring of NSI row
-//    slots, completion tracked by one mbarrier per slot; post-collision rows are written to a
-//    shared output row and stored with bulk copies;
+//    slots, completion tracked by one mbarrier per slot; a one-warp block (TX = 32) marches
+//    without waiting on other warps;
 //  - generic (any Lx, any tile): every thread stages its own 18 values with per-thread
 //    asynchronous copies and stores with plain streaming stores.
 // The non-ideal force (Eq. aNI) needs the densities of the 8 neighbours at the same time
@@ -24,6 +24,8 @@
 // toward m^eq with second-order forcing (1 - lambda_a/2) S_a, FDT noise from Philox4x32-10
 // (Eqs. noise-bin-expl, noise-bin-expl-high), and the inverse transform
 // f_l = w_l sum_a T_al m*_a / N_a.
+#pragma once
+
 #include <cstdio>
 
 #include "lb_internal.cuh"
@@ -581,7 +583,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
 }
 
 // ======================================================================================
-// Bulk path (rows 16-byte aligned, TX = 128 or 256).
+// Bulk path (rows 16-byte aligned, TX = 32, 64 or 128).
 // ======================================================================================
 template <class real, int TX>
 __device__ __forceinline__ void bulk_init(unsigned char* smem) {
@@ -635,22 +637,26 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   const int z0 = it.z0, z1 = it.z1;
   const unsigned row_bytes = 18u * (unsigned)(nact + 2 * PAD) * (unsigned)sizeof(real);
 
-  // lane k < 18 of warp 0 copies plane k of row r (its source row, reflected at the walls)
+  // plane k of row r (its source row, reflected at the walls) is copied by lane k / NW of warp
+  // k % NW, so that every warp issues about the same number of copies
+  constexpr int NW = TX / 32;
+  const int my_plane = (tid & 31) * NW + (tid >> 5);
   auto stage_row = [&](int r) {
     if (r < 0 || r >= Lz || r > z1) return;
     const int slot = r % NSI;
     uint64_t* bar = bars + slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
-    if (tid < 18) {
-      const int s = tid / 9, l = tid - 9 * s;
+    if (my_plane < 18) {
+      const int k = my_plane;
+      const int s = k / 9, l = k - 9 * s;
       const int cz = LB_CZ(l);
-      int sr = r - cz, p = tid;
+      int sr = r - cz, p = k;
       if (sr < 0 || sr >= Lz) {
         sr = r;
         p = 9 * s + LB_OPP(l);
       }
       const real* rowp = f + (size_t)p * LzLx + (size_t)sr * Lx;
-      real* d = instage + (slot * 18 + tid) * SW;
+      real* d = instage + (slot * 18 + k) * SW;
       const unsigned sz = (unsigned)sizeof(real);
       if (x0 > 0 && x0 + nact < Lx) {
         bulk_g2s(d, rowp + x0 - PAD, (unsigned)(nact + 2 * PAD) * sz, bar);
@@ -796,6 +802,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepA
 
 template <class real, int TX, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX) step_kernel_bulk(StepArgs<real> a) {
+  static_assert(TX == 32 || TX == 64 || TX == 128, "bulk tiles are 32, 64 or 128 columns");
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
   bulk_init<real, TX>(smem);
@@ -806,7 +813,7 @@ __global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX) step_ke
 // ---- bounded grid barrier for the persistent launch --------------------------------
 // bar[0]: arrivals, bar[1]: generation.  Returns false if the wait gave up after limit_ms
 // (err is then set) or another block reported an error.
-__device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int limit_ms) {
+static __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int limit_ms) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -880,12 +887,6 @@ __global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX)
   }
 }
 
-__global__ void advance_kernel(int64_t* d_t, int64_t k) { *d_t += k; }
-
-__global__ void barrier_probe_kernel(unsigned* bar, int* err, unsigned expected, int limit_ms) {
-  grid_barrier(bar, err, expected, limit_ms);
-}
-
 // ======================================================================================
 // Host side.
 // ======================================================================================
@@ -929,9 +930,10 @@ cudaError_t prepare_step(int max_tile_x) {
     cudaError_t e = set_smem(fn, bytes);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = prepare_bulk<real, 128>();
-  if (e != cudaSuccess) return e;
-  return prepare_bulk<real, 256>();
+  cudaError_t e = prepare_bulk<real, 32>();
+  if (e == cudaSuccess) e = prepare_bulk<real, 64>();
+  if (e == cudaSuccess) e = prepare_bulk<real, 128>();
+  return e;
 }
 
 template <class real, bool SAMPLE>
@@ -953,12 +955,15 @@ static void launch_bulk(const StepArgs<real>& a, int noise, cudaStream_t s) {
 template <class real>
 cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, bool bulk, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
-  if (bulk && tile_x == 128) {
+  if (bulk && tile_x == 32) {
+    if (sample) launch_bulk<real, 32, true>(a, noise, s);
+    else launch_bulk<real, 32, false>(a, noise, s);
+  } else if (bulk && tile_x == 64) {
+    if (sample) launch_bulk<real, 64, true>(a, noise, s);
+    else launch_bulk<real, 64, false>(a, noise, s);
+  } else if (bulk && tile_x == 128) {
     if (sample) launch_bulk<real, 128, true>(a, noise, s);
     else launch_bulk<real, 128, false>(a, noise, s);
-  } else if (bulk && tile_x == 256) {
-    if (sample) launch_bulk<real, 256, true>(a, noise, s);
-    else launch_bulk<real, 256, false>(a, noise, s);
   } else {
     if (sample) launch_generic<real, true>(a, tile_x, noise, s);
     else launch_generic<real, false>(a, tile_x, noise, s);
@@ -966,20 +971,19 @@ cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int no
   return cudaGetLastError();
 }
 
+template <class real, int TX>
+static const void* persistent_bulk_fn(int noise, size_t* smem) {
+  *smem = SmemBulk<real, TX>::bytes;
+  if (noise == NOISE_HOM) return (const void*)persistent_kernel_bulk<real, TX, NOISE_HOM>;
+  if (noise == NOISE_LOC) return (const void*)persistent_kernel_bulk<real, TX, NOISE_LOC>;
+  return (const void*)persistent_kernel_bulk<real, TX, NOISE_OFF>;
+}
+
 template <class real>
 static const void* persistent_fn(int tile_x, int noise, bool bulk, size_t* smem) {
-  if (bulk && tile_x == 128) {
-    *smem = SmemBulk<real, 128>::bytes;
-    if (noise == NOISE_HOM) return (const void*)persistent_kernel_bulk<real, 128, NOISE_HOM>;
-    if (noise == NOISE_LOC) return (const void*)persistent_kernel_bulk<real, 128, NOISE_LOC>;
-    return (const void*)persistent_kernel_bulk<real, 128, NOISE_OFF>;
-  }
-  if (bulk && tile_x == 256) {
-    *smem = SmemBulk<real, 256>::bytes;
-    if (noise == NOISE_HOM) return (const void*)persistent_kernel_bulk<real, 256, NOISE_HOM>;
-    if (noise == NOISE_LOC) return (const void*)persistent_kernel_bulk<real, 256, NOISE_LOC>;
-    return (const void*)persistent_kernel_bulk<real, 256, NOISE_OFF>;
-  }
+  if (bulk && tile_x == 32) return persistent_bulk_fn<real, 32>(noise, smem);
+  if (bulk && tile_x == 64) return persistent_bulk_fn<real, 64>(noise, smem);
+  if (bulk && tile_x == 128) return persistent_bulk_fn<real, 128>(noise, smem);
   *smem = Smem<real>::bytes(tile_x);
   if (noise == NOISE_HOM) return (const void*)persistent_kernel<real, NOISE_HOM>;
   if (noise == NOISE_LOC) return (const void*)persistent_kernel<real, NOISE_LOC>;
@@ -1008,6 +1012,14 @@ cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nste
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
 }
 
+#ifdef LB_STEP_COMMON_DEFS
+// Kernels and helpers that do not depend on the precision (compiled once).
+__global__ void advance_kernel(int64_t* d_t, int64_t k) { *d_t += k; }
+
+__global__ void barrier_probe_kernel(unsigned* bar, int* err, unsigned expected, int limit_ms) {
+  grid_barrier(bar, err, expected, limit_ms);
+}
+
 cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s) {
   advance_kernel<<<1, 1, 0, s>>>(d_t, k);
   return cudaGetLastError();
@@ -1020,14 +1032,6 @@ cudaError_t launch_barrier_probe(int blocks, int expected, int limit_ms, unsigne
   return cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(blocks), dim3(32), args, 0, s);
 }
 
-#define LB_STEP_INST(real)                                                                                         \
-  template size_t step_smem_bytes<real>(int);                                                                      \
-  template cudaError_t prepare_step<real>(int);                                                                    \
-  template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, int, bool, cudaStream_t);               \
-  template int persistent_grid<real>(int, int, bool);                                                              \
-  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, bool, int, bool, unsigned*,  \
-                                                    int*, int, int, cudaStream_t);
-LB_STEP_INST(float)
-LB_STEP_INST(double)
+#endif
 
 }  // namespace lbk
