@@ -20,7 +20,7 @@
  *  - the a* correction of the footnote to Eq. (ne-acc) is on unless disabled;
  *  - hom noise uses rho^A_ref = rho_bar c_bar0, rho^B_ref = rho_bar (1 - c_bar0);
  *  - the noise stream: Philox4x32-10, key = (seed_lo, seed_hi), counter = (site, step,
- *    lattice_id, call), u = (2 (k >> 9) + 1) 2^-24, Box-Muller pairs;
+ *    lattice_id, call), u = (2 (k mod 2^23) + 1) 2^-24, Box-Muller pairs;
  *  - walls: mid-way bounce-back; the wall-ghost densities for the non-ideal force copy
  *    the adjacent fluid row (Sec. II.A), or take a fixed wall composition if asked;
  *  - diagnostics are taken on the pre-collision state after streaming.
@@ -142,8 +142,8 @@ void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t 
   for (int i = 0; i < 4; ++i) out[i] = x[i];
 }
 
-// Uniform in (0,1) from the top 23 bits: (2 (k >> 9) + 1) 2^-24, exact in float and double.
-double uniform_of(uint32_t k) { return (double)(2u * (k >> 9) + 1u) * std::ldexp(1.0, -24); }
+// Uniform in (0,1) from the low 23 bits: (2 (k mod 2^23) + 1) 2^-24, exact in float and double.
+double uniform_of(uint32_t k) { return (double)(2u * (k & 0x7FFFFFu) + 1u) * std::ldexp(1.0, -24); }
 
 // Sixteen standard normals for one site and step: Box-Muller on the pairs (u_{2i}, u_{2i+1})
 // of four Philox calls (call = 0..3): n_{2i} = r cos(2 pi u_{2i+1}), n_{2i+1} = r sin(...),

@@ -150,17 +150,18 @@ __device__ __forceinline__ void philox_site(uint32_t c0, uint32_t c1, uint32_t c
   for (int i = 0; i < 4; ++i) out[i] = U4{s0[i], s1[i], s2[i], s3[i]};
 }
 
-// Uniform in (0, 1) from the top 23 bits, u = (2 (k >> 9) + 1) 2^-24, exact in float and double:
-// the bits form x = 1 + (k >> 9) 2^-23 in [1, 2) and u = x - (1 - 2^-24) exactly.
+// Uniform in (0, 1) from the low 23 bits, u = (2 (k mod 2^23) + 1) 2^-24, exact in float and
+// double: the bits form x = 1 + (k mod 2^23) 2^-23 in [1, 2) and u = x - (1 - 2^-24) exactly.
+__device__ __forceinline__ float unit_interval_bits(uint32_t k) { return __uint_as_float(0x3F800000u | (k & 0x7FFFFFu)); }
 template <class real>
 __device__ __forceinline__ real uniform01(uint32_t k);
 template <>
 __device__ __forceinline__ float uniform01<float>(uint32_t k) {
-  return __uint_as_float(0x3F800000u | (k >> 9)) - 0.999999940395355224609375f;
+  return unit_interval_bits(k) - 0.999999940395355224609375f;
 }
 template <>
 __device__ __forceinline__ double uniform01<double>(uint32_t k) {
-  return __longlong_as_double((long long)(0x3FF0000000000000ull | ((unsigned long long)(k >> 9) << 29))) -
+  return __longlong_as_double((long long)(0x3FF0000000000000ull | ((unsigned long long)(k & 0x7FFFFFu) << 29))) -
          0.999999940395355224609375;
 }
 

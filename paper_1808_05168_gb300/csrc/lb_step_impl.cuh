@@ -35,7 +35,13 @@ namespace lbk {
 namespace {
 
 constexpr int NS = 4;   // generic path: rows of staged populations (power of two)
-constexpr int NSI = 4;  // bulk path: input row slots
+#ifndef LB_BULK_NSI
+#define LB_BULK_NSI 4
+#endif
+#ifndef LB_BULK_BLOCKS_F32
+#define LB_BULK_BLOCKS_F32 5  // resident 128-column blocks per SM the float bulk kernels target
+#endif
+constexpr int NSI = LB_BULK_NSI;  // bulk path: input row slots
 constexpr int WAIT_MS = 2000;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -275,10 +281,11 @@ template <class real>
 __device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, real& n0, real& n1);
 template <>
 __device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float& n0, float& n1) {
-  const float u1 = uniform01<float>(a), u2 = uniform01<float>(b);
+  const float u1 = uniform01<float>(a);
   const float t = -2.0f * logf(u1);
   const float r = t * rsqrtf(t);
-  const float phi = fmaf(6.28318530717959f, u2, -3.14159265358979f);
+  // phi = 2 pi u2 - pi = 2 pi x2 - 3 pi + 2 pi 2^-24 with x2 = u2 + 1 - 2^-24 built from the bits
+  const float phi = fmaf(6.28318530717959f, unit_interval_bits(b), -9.42477758729298f);
   float s, c;
   __sincosf(phi, &s, &c);
   n0 = -r * c;
@@ -800,8 +807,13 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepA
   process_item<real, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem);
 }
 
+template <class real>
+struct BulkBlocks {  // 128-thread blocks per SM the bulk kernels are compiled for
+  static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 : 2;
+};
+
 template <class real, int TX, bool SAMPLE, int NOISE>
-__global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX) step_kernel_bulk(StepArgs<real> a) {
+__global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX) step_kernel_bulk(StepArgs<real> a) {
   static_assert(TX == 32 || TX == 64 || TX == 128, "bulk tiles are 32, 64 or 128 columns");
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
@@ -865,7 +877,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
 }
 
 template <class real, int TX, int NOISE>
-__global__ void __launch_bounds__(TX, MinBlocks<real>::value * 256 / TX)
+__global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX)
     persistent_kernel_bulk(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
