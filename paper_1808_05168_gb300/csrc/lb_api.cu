@@ -319,7 +319,7 @@ int alloc_diag(lb_ctx* c) {
     const int Lx = c->params[i].Lx, cq = std::min(c->col_strip, Lx);
     for (int k = 0; k < 4 * c->params[i].Lz; ++k) rt.push_back(make_int2(i, k));
     for (int fld = 0; fld < 4; ++fld)
-      for (int q = 0; q < Lx; q += cq) ct.push_back(make_int2(i, fld * Lx + q));
+      for (int q = 0; q <= Lx / 2; q += cq) ct.push_back(make_int2(i, fld * Lx + q));  // S(-q) = S(q)
   }
   rc = dev_alloc(c, &c->d_row_tasks, rt.size() * sizeof(int2));
   if (!rc) rc = dev_alloc(c, &c->d_col_tasks, ct.size() * sizeof(int2));
@@ -765,12 +765,22 @@ int lb_structure_factor(lb_ctx* c, int lattice, int field, int mode, double* out
     std::fill(out, out + need, 0.0);
     return LB_OK;
   }
-  const size_t off = 4 * (size_t)c->site_off[lattice] + (size_t)field * Lx * Lz;
-  std::vector<double> s(need), k(need);
-  if (cudaMemcpy(s.data(), c->acc_sum + off, need * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(k.data(), c->acc_comp + off, need * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+  const size_t full = (size_t)Lx * Lz;
+  const size_t off = 4 * (size_t)c->site_off[lattice] + (size_t)field * full;
+  std::vector<double> s(full), k(full);
+  if (cudaMemcpy(s.data(), c->acc_sum + off, full * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(k.data(), c->acc_comp + off, full * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LB_ERR_CUDA;
-  for (size_t i = 0; i < need; ++i) out[i] = (s[i] + k[i]) / (double)c->nsamples;
+  // accumulated: q_x = 0 .. Lx/2 (Kahan sums: total = sum - comp); the rest by S(q) = S(-q)
+  const double inv = 1.0 / (double)c->nsamples;
+  const int rows_out = mode == LB_SF_QXQZ ? Lz : 1;
+  for (int n = 0; n < rows_out; ++n)
+    for (int q = 0; q < Lx; ++q) {
+      const int nn = q <= Lx / 2 ? n : (Lz - n) % Lz;
+      const int qq = q <= Lx / 2 ? q : Lx - q;
+      const size_t src = (size_t)nn * Lx + qq;
+      out[(size_t)n * Lx + q] = (s[src] - k[src]) * inv;
+    }
   return LB_OK;
 }
 

@@ -82,6 +82,14 @@ __global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const 
   for (int j = threadIdx.x; j < n; j += blockDim.x) tmp[off + j] = s[j];
 }
 
+// Kahan summation of non-negative terms: the estimate of the total is sum - comp.
+__device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
+  const double y = v - comp;
+  const double t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
 __device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v) {
   const double t = sum + v;
   if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
@@ -90,7 +98,10 @@ __device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v
 }
 
 // Column pass: one block per (lattice, field, strip of cq adjacent q_x), cq = min(CQ, Lx), so that
-// every row of the strip is read and accumulated with contiguous accesses.
+// every row of the strip is read and accumulated with contiguous accesses.  The fields are
+// real, so S(-q) = S(q): strips cover q_x = 0 .. Lx/2 only and the rest is filled by symmetry
+// when the spectrum is read out.  The power is formed in the working precision and added to a
+// double-precision Kahan sum.
 template <class real>
 __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const Cplx<real>* tmp, double* acc_sum,
                                double* acc_comp, int CQ) {
@@ -127,14 +138,13 @@ __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const 
     }
     __syncthreads();
   }
-  const double scale = 1.0 / ((double)Lx * (double)n);
+  const real scale = real(1) / ((real)Lx * (real)n);
   for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
     const int j = idx >> lcq, c = idx & (cq - 1);
     const Cplx<real> v = s[c * n + j];
-    const double re = (double)v.re, im = (double)v.im;
     const int64_t o = base + (int64_t)j * Lx + c;
     double sm = acc_sum[o], cp = acc_comp[o];
-    neumaier_add(sm, cp, (re * re + im * im) * scale);
+    kahan_add(sm, cp, (double)((v.re * v.re + v.im * v.im) * scale));
     acc_sum[o] = sm;
     acc_comp[o] = cp;
   }

@@ -132,22 +132,41 @@ __device__ __forceinline__ void stage_column(const real* __restrict__ f, int LzL
 
 // The 9 populations of species s of one site as deviations from the background of its row.
 // In deviation mode the background difference b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz
-// d_z c^S_0 is added on non-reflected links with c_lz != 0 (k9, k36 are zero in FP64 mode).
+// d_z c^S_0 belongs on every non-reflected link with c_lz != 0 (k9, k36: its size on the
+// 1/9- and 1/36-weight links of species A; zero in FP64 mode).  In interior rows these shifts
+// sum to zero and change no moment but m_2 (see interior_m2_shift), so they are applied to the
+// moments there; in the two wall rows, where the reflected links carry none, per link.
 template <class real>
 __device__ __forceinline__ void deviations(real e0, real e1, real e2, real e3, real e4, real e5, real e6, real e7,
                                            real e8, int s, bool below, bool above, real k9, real k36, real v[9]) {
-  const real q9 = s == 0 ? k9 : -k9, q36 = s == 0 ? k36 : -k36;
-  const real b9 = below ? q9 : real(0), b36 = below ? q36 : real(0);
-  const real a9 = above ? q9 : real(0), a36 = above ? q36 : real(0);
   v[0] = e0;
   v[1] = e1;
   v[3] = e3;
-  v[2] = e2 - b9;
-  v[4] = e4 + a9;
-  v[5] = e5 - b36;
-  v[6] = e6 - b36;
-  v[7] = e7 + a36;
-  v[8] = e8 + a36;
+  v[2] = e2;
+  v[4] = e4;
+  v[5] = e5;
+  v[6] = e6;
+  v[7] = e7;
+  v[8] = e8;
+  if (!(below && above)) {
+    const real q9 = s == 0 ? k9 : -k9, q36 = s == 0 ? k36 : -k36;
+    const real b9 = below ? q9 : real(0), b36 = below ? q36 : real(0);
+    const real a9 = above ? q9 : real(0), a36 = above ? q36 : real(0);
+    v[2] = e2 - b9;
+    v[4] = e4 + a9;
+    v[5] = e5 - b36;
+    v[6] = e6 - b36;
+    v[7] = e7 + a36;
+    v[8] = e8 + a36;
+  }
+}
+
+// Interior rows: the shifts (-q9 on link 2, +q9 on 4, -q36 on 5 and 6, +q36 on 7 and 8; q = k for
+// species A, -k for B) have zero sum and zero moments except m_2 = -2 q9 - 4 q36.
+template <class real>
+__device__ __forceinline__ real interior_m2_shift(int s, real k9, real k36) {
+  const real q = 2 * k9 + 4 * k36;
+  return s == 0 ? -q : q;
 }
 
 // Generic path: stage column c of a slot holds the already-shifted values of that site.
@@ -576,9 +595,13 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
       const bool below = z > 0, above = z < Lz - 1;
       real v[9];
       read_generic(sb, W, tid + 1, 0, below, above, k9, k36, v);
-      const Mom<real> mA = moments(v);
+      Mom<real> mA = moments(v);
       read_generic(sb, W, tid + 1, 1, below, above, k9, k36, v);
-      const Mom<real> mB = moments(v);
+      Mom<real> mB = moments(v);
+      if (below && above) {
+        mA.m2 += interior_m2_shift(0, k9, k36);
+        mB.m2 += interior_m2_shift(1, k9, k36);
+      }
       const int r0 = z * Lx + x;
       site_update<real, SAMPLE, NOISE, true, 0>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
                                                 (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
@@ -767,9 +790,13 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       const bool below = z > 0, above = z < Lz - 1;
       real v[9];
       read_bulk<real, SW>(sb, tid + PAD, 0, below, above, k9, k36, v);
-      const Mom<real> mA = moments(v);
+      Mom<real> mA = moments(v);
       read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
-      const Mom<real> mB = moments(v);
+      Mom<real> mB = moments(v);
+      if (below && above) {
+        mA.m2 += interior_m2_shift(0, k9, k36);
+        mB.m2 += interior_m2_shift(1, k9, k36);
+      }
       const int r0 = z * Lx + x;
       site_update<real, SAMPLE, NOISE, true, 0>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
                                                 (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
