@@ -144,6 +144,15 @@ int lb_mass(lb_ctx* ctx, int lattice, double out[2]);
 int lb_get_populations(lb_ctx* ctx, int lattice, double* host_out, size_t n);
 int lb_set_populations(lb_ctx* ctx, int lattice, const double* host_in, size_t n);
 
+/* Power spectrum of one snapshot of a real field (Appendix A, Eqs. SF1 and integral on the
+ * lattice): out[n * Lx + k] = |sum_{x,z} phi[z * Lx + x] exp(-2 pi i (k x / Lx + n z / Lz))|^2
+ * / (Lx Lz).  field and out are device pointers to Lx * Lz doubles (x fastest; out may not
+ * alias field); Lx and Lz are powers of two in 2..8192.  Host pointers or other sizes return
+ * LB_ERR_BAD_PARAM.  Stream-ordered on `stream` (NULL: legacy default stream), which also
+ * orders a device scratch of Lx * Lz * 16 bytes allocated and freed with cudaMallocAsync /
+ * cudaFreeAsync; returns before the result is ready. */
+int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* stream);
+
 /* Clear the structure-factor and pressure accumulators (the step count is kept). */
 int lb_reset_statistics(lb_ctx* ctx);
 

@@ -40,7 +40,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "lb_set_tile", "lb_get_tile",
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
            "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
-           "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier")
+           "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
+           "lb_power_spectrum")
 
 
 class LBError(RuntimeError):
@@ -99,6 +100,7 @@ def load():
             "lb_kernel_launches": [vp, i64p],
             "lb_destroy": [vp],
             "lb_debug_barrier": [i, i, i],
+            "lb_power_spectrum": [vp, i, i, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -232,6 +234,12 @@ def lb_error_string(code):
 def lb_destroy(h):
     if h:
         load().lb_destroy(h)
+
+
+def lb_power_spectrum(field_ptr, Lx, Lz, out_ptr, stream_handle=0):
+    """field_ptr, out_ptr: device addresses (e.g. torch tensor .data_ptr()) of Lx * Lz doubles."""
+    _check(load().lb_power_spectrum(ctypes.c_void_p(int(field_ptr)), int(Lx), int(Lz), ctypes.c_void_p(int(out_ptr)),
+                                    ctypes.c_void_p(int(stream_handle) if stream_handle else 0)), "lb_power_spectrum")
 
 
 def lb_debug_barrier(blocks, expected, limit_ms):

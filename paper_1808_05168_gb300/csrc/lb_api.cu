@@ -900,6 +900,52 @@ void lb_destroy(lb_ctx* c) {
   delete c;
 }
 
+namespace {
+bool device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int prepare_power_spectrum_once() {
+  static std::mutex mu;
+  static bool done = false;
+  std::lock_guard<std::mutex> g(mu);
+  if (!done) {
+    if (prepare_power_spectrum() != cudaSuccess) return LB_ERR_CUDA;
+    done = true;
+  }
+  return LB_OK;
+}
+
+int power_spectrum_args_ok(const double* field, int Lx, int Lz, const double* out) {
+  if (!field || !out || !is_pow2(Lx) || !is_pow2(Lz) || Lx < 2 || Lz < 2 || Lx > 8192 || Lz > 8192)
+    return LB_ERR_BAD_PARAM;
+  if (!device_pointer(field) || !device_pointer(out)) return LB_ERR_BAD_PARAM;
+  return LB_OK;
+}
+}  // namespace
+
+int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* stream) {
+  int rc = power_spectrum_args_ok(field, Lx, Lz, out);
+  if (rc) return rc;
+  rc = prepare_power_spectrum_once();
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* tmp = nullptr;
+  if (cudaMallocAsync(&tmp, (size_t)Lx * Lz * 2 * sizeof(double), s) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ERR_OOM;
+  }
+  cudaError_t e = launch_power_spectrum(field, Lx, Lz, out, tmp, s);
+  cudaError_t f = cudaFreeAsync(tmp, s);
+  if (e != cudaSuccess || f != cudaSuccess) return LB_ERR_CUDA;
+  return LB_OK;
+}
+
 int lb_debug_barrier(int blocks, int expected, int spin_limit) {
   if (blocks < 1 || blocks > 64 || expected < 1 || spin_limit < 1 || spin_limit > 10000) return LB_ERR_BAD_PARAM;
   int dev = 0, coop = 0;

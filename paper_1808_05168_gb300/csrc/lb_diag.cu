@@ -150,6 +150,58 @@ __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const 
   }
 }
 
+// ---- power spectrum of one real field (one snapshot, written out, nothing accumulated) -----
+// Row pass: block z transforms row z of phi along x into tmp.
+__global__ void ps_rows_kernel(const double* __restrict__ phi, int Lx, int Lz, Cplx<double>* __restrict__ tmp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int z = blockIdx.x, n = Lx, logn = ilog2(n);
+  Cplx<double>* s = reinterpret_cast<Cplx<double>*>(smem);
+  Cplx<double>* tw = s + n;
+  fill_twiddles<double>(tw, n);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int r = (int)(__brev((unsigned)j) >> (32 - logn));
+    s[r] = Cplx<double>{phi[(int64_t)z * Lx + j], 0.0};
+  }
+  __syncthreads();
+  fft_inplace<double>(s, tw, n, logn);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) tmp[(int64_t)z * Lx + j] = s[j];
+}
+
+// Column pass: block b transforms columns [b cq, (b + 1) cq) along z and writes |X|^2 / (Lx Lz).
+__global__ void ps_cols_kernel(const Cplx<double>* __restrict__ tmp, int Lx, int Lz, int cq, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = Lz, logn = ilog2(n), half = n >> 1, lcq = ilog2(cq), q0 = blockIdx.x * cq;
+  Cplx<double>* tw = reinterpret_cast<Cplx<double>*>(smem);
+  Cplx<double>* s = tw + half;
+  fill_twiddles<double>(tw, n);
+  for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
+    const int j = idx >> lcq, c = idx & (cq - 1);
+    const int r = (int)(__brev((unsigned)j) >> (32 - logn));
+    s[c * n + r] = tmp[(int64_t)j * Lx + q0 + c];
+  }
+  __syncthreads();
+  for (int lg = 1; lg <= logn; ++lg) {
+    const int hs = 1 << (lg - 1), stride = n >> lg;
+    for (int idx = threadIdx.x; idx < half * cq; idx += blockDim.x) {
+      const int c = idx / half, jj = idx - c * half;
+      Cplx<double>* sc = s + c * n;
+      const int pos = jj & (hs - 1);
+      const int i0 = ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
+      const Cplx<double> w = tw[pos * stride], b = sc[i1], a = sc[i0];
+      const double tr = w.re * b.re - w.im * b.im, ti = w.re * b.im + w.im * b.re;
+      sc[i0] = Cplx<double>{a.re + tr, a.im + ti};
+      sc[i1] = Cplx<double>{a.re - tr, a.im - ti};
+    }
+    __syncthreads();
+  }
+  const double scale = 1.0 / ((double)Lx * (double)n);
+  for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
+    const int j = idx >> lcq, c = idx & (cq - 1);
+    const Cplx<double> v = s[c * n + j];
+    out[(int64_t)j * Lx + q0 + c] = (v.re * v.re + v.im * v.im) * scale;
+  }
+}
+
 __global__ void finalize_kernel(const DiagLattice* lat, int n_lat, const double* partials, DiagStats* stats) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_lat) return;
@@ -308,6 +360,28 @@ cudaError_t launch_from_absolute(const double* in, const BgParams& bp, real* f, 
 template <class real>
 cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s) {
   init_rest_kernel<real><<<1024, 256, 0, s>>>(f, bp);
+  return cudaGetLastError();
+}
+
+// Columns per block of the one-snapshot column pass (shared memory at most 160 KB).
+static int ps_column_strip(int Lx, int Lz) {
+  int cq = 16;
+  while (cq > 1 && ((size_t)Lz * cq + Lz / 2) * sizeof(Cplx<double>) > 160 * 1024) cq >>= 1;
+  return cq < Lx ? cq : Lx;
+}
+
+cudaError_t prepare_power_spectrum() {
+  cudaError_t e = cudaFuncSetAttribute(ps_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((8192 + 4096) * sizeof(Cplx<double>)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(ps_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+}
+
+cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* out, void* tmp, cudaStream_t s) {
+  const int cq = ps_column_strip(Lx, Lz);
+  ps_rows_kernel<<<Lz, 256, (size_t)(Lx + Lx / 2) * sizeof(Cplx<double>), s>>>(field, Lx, Lz, (Cplx<double>*)tmp);
+  ps_cols_kernel<<<Lx / cq, 256, ((size_t)Lz * cq + Lz / 2) * sizeof(Cplx<double>), s>>>(
+      (const Cplx<double>*)tmp, Lx, Lz, cq, out);
   return cudaGetLastError();
 }
 

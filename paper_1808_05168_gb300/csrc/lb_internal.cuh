@@ -289,6 +289,11 @@ cudaError_t launch_from_absolute(const double* in, const BgParams& bp, real* f, 
 template <class real>
 cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s);
 
+// Power spectrum of one real double-precision field (Lx, Lz powers of two, 2..8192), with a
+// caller-provided scratch of Lx * Lz complex doubles; prepare once before use.
+cudaError_t prepare_power_spectrum();
+cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* out, void* tmp, cudaStream_t s);
+
 cudaError_t launch_barrier_probe(int blocks, int expected, int spin_limit, unsigned* barrier, int* err,
                                  cudaStream_t s);
 
