@@ -153,6 +153,22 @@ int lb_set_populations(lb_ctx* ctx, int lattice, const double* host_in, size_t n
  * cudaFreeAsync; returns before the result is ready. */
 int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* stream);
 
+/* lb_power_spectrum for callers that must not allocate device memory (the paper has no
+ * counterpart; this is a deployment aid).  Some callers cannot call cudaMalloc, cudaFree or any
+ * allocating routine where they need a spectrum: code running while another owner captures a
+ * CUDA graph, processes whose device memory is owned by another framework's pool, or loops that
+ * must never wait on an allocator.  Same arguments, result and stream ordering as
+ * lb_power_spectrum, with Lx * Lz <= LB_NOALLOC_MAX_POINTS (larger sizes return LB_ERR_SIZE);
+ * the intermediate transform lives in a fixed 4 MiB array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  The first call on a device
+ * (with that device current) looks up the array's device address and sets the kernels'
+ * attributes, so make that first call before any stream capture.  Every call shares the one
+ * array: calls whose work overlaps on the GPU (different streams, or different host threads)
+ * race on it and give wrong results; the array needs no clearing, since each call overwrites
+ * what it reads. */
+#define LB_NOALLOC_MAX_POINTS (1 << 18)
+int lb_power_spectrum_noalloc(const double* field, int Lx, int Lz, double* out, void* stream);
+
 /* Clear the structure-factor and pressure accumulators (the step count is kept). */
 int lb_reset_statistics(lb_ctx* ctx);
 

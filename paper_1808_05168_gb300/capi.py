@@ -41,7 +41,8 @@ EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
            "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
-           "lb_power_spectrum")
+           "lb_power_spectrum", "lb_power_spectrum_noalloc")
+LB_NOALLOC_MAX_POINTS = 1 << 18
 
 
 class LBError(RuntimeError):
@@ -101,6 +102,7 @@ def load():
             "lb_destroy": [vp],
             "lb_debug_barrier": [i, i, i],
             "lb_power_spectrum": [vp, i, i, vp, vp],
+            "lb_power_spectrum_noalloc": [vp, i, i, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -240,6 +242,14 @@ def lb_power_spectrum(field_ptr, Lx, Lz, out_ptr, stream_handle=0):
     """field_ptr, out_ptr: device addresses (e.g. torch tensor .data_ptr()) of Lx * Lz doubles."""
     _check(load().lb_power_spectrum(ctypes.c_void_p(int(field_ptr)), int(Lx), int(Lz), ctypes.c_void_p(int(out_ptr)),
                                     ctypes.c_void_p(int(stream_handle) if stream_handle else 0)), "lb_power_spectrum")
+
+
+def lb_power_spectrum_noalloc(field_ptr, Lx, Lz, out_ptr, stream_handle=0):
+    """As lb_power_spectrum, without any device allocation (Lx * Lz <= LB_NOALLOC_MAX_POINTS)."""
+    _check(load().lb_power_spectrum_noalloc(ctypes.c_void_p(int(field_ptr)), int(Lx), int(Lz),
+                                            ctypes.c_void_p(int(out_ptr)),
+                                            ctypes.c_void_p(int(stream_handle) if stream_handle else 0)),
+           "lb_power_spectrum_noalloc")
 
 
 def lb_debug_barrier(blocks, expected, limit_ms):
