@@ -112,7 +112,7 @@ def kernel_traffic(kind):
     try:
         with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1808_05168_gb300", "csrc", "lb_step.cu"), "rb").read()
+        src = open(os.path.join(ROOT, "paper_1808_05168_gb300", "csrc", "lb_step_impl.cuh"), "rb").read()
         if d.get("lb_step_cu_sha256") != hashlib.sha256(src).hexdigest():
             return None
         e = d.get(kind)

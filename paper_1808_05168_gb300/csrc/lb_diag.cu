@@ -62,24 +62,48 @@ __device__ void fill_twiddles(Cplx<real>* tw, int n) {
   }
 }
 
-// Tasks: x-pass task = (lattice, field * Lz + z); z-pass task = (lattice, field * Lx + qx).
+// Row pass: one block per (lattice, field, group of R = rows_per_block(Lx, Lz) consecutive rows
+// z0 ..), so that short rows share one twiddle table and every thread has butterflies to do.
+// Task = (lattice, field * Lz + z0).
+__host__ __device__ __forceinline__ int rows_per_block(int Lx, int Lz) {
+  int r = 2048 / Lx;
+  if (r < 1) r = 1;
+  return r < Lz ? r : Lz;
+}
+
 template <class real>
 __global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const real* fields, Cplx<real>* tmp) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int2 task = tasks[blockIdx.x];
   const DiagLattice L = lat[task.x];
-  const int n = L.Lx, logn = ilog2(n);
-  Cplx<real>* s = reinterpret_cast<Cplx<real>*>(smem);
-  Cplx<real>* tw = s + n;
+  const int n = L.Lx, logn = ilog2(n), half = n >> 1;
+  const int R = rows_per_block(L.Lx, L.Lz), lr = ilog2(R);
+  Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
+  Cplx<real>* s = tw + (half > 0 ? half : 1);
   fill_twiddles<real>(tw, n);
-  const int64_t off = 4 * L.site_off + (int64_t)task.y * n;  // row of one field
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int r = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[r] = Cplx<real>{fields[off + j], real(0)};
+  const int64_t off = 4 * L.site_off + (int64_t)task.y * n;  // first row of the group
+  for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) {
+    const int r = idx >> logn, j = idx & (n - 1);
+    const int b = (int)(__brev((unsigned)j) >> (32 - logn));
+    s[r * n + b] = Cplx<real>{fields[off + idx], real(0)};
   }
   __syncthreads();
-  fft_inplace<real>(s, tw, n, logn);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) tmp[off + j] = s[j];
+  for (int lg = 1; lg <= logn; ++lg) {
+    const int hs = 1 << (lg - 1), stride = n >> lg;
+    for (int idx = threadIdx.x; idx < R * half; idx += blockDim.x) {
+      const int r = idx >> (logn - 1), jj = idx & (half - 1);
+      Cplx<real>* sr = s + r * n;
+      const int pos = jj & (hs - 1);
+      const int i0 = ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
+      const Cplx<real> w = tw[pos * stride], b = sr[i1], a = sr[i0];
+      const real tr = w.re * b.re - w.im * b.im, ti = w.re * b.im + w.im * b.re;
+      sr[i0] = Cplx<real>{a.re + tr, a.im + ti};
+      sr[i1] = Cplx<real>{a.re - tr, a.im - ti};
+    }
+    __syncthreads();
+  }
+  (void)lr;
+  for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) tmp[off + idx] = s[idx];
 }
 
 // Kahan summation of non-negative terms: the estimate of the total is sum - comp.
@@ -297,8 +321,9 @@ __global__ void init_rest_kernel(real* f, BgParams bp) {
 }  // namespace
 
 template <class real>
-size_t sf_smem_bytes(int n) {
-  return (size_t)n * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
+size_t sf_smem_bytes(int n) {  // row pass: the larger of one row and 2048 points, plus twiddles
+  const int pts = n > 2048 ? n : 2048;
+  return (size_t)pts * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
 }
 
 // Columns per column-pass block: up to 16, fewer when Lz is long (shared memory budget).

@@ -248,8 +248,8 @@ struct DiagStats {  // per lattice, updated by the finalize kernel
   int pad;
 };
 
-// Transform tasks of one sample: one block per (lattice, field * Lz + z) row and per
-// (lattice, field * Lx + q_x) column.
+// Transform tasks of one sample: one block per (lattice, field * Lz + z0) group of rows (see
+// rows_per_block in lb_diag.cu) and per (lattice, field * Lx + q_x0) strip of columns.
 struct SfPlan {
   const DiagLattice* lat;
   const int2* row_tasks;
