@@ -169,6 +169,20 @@ int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* st
 #define LB_NOALLOC_MAX_POINTS (1 << 18)
 int lb_power_spectrum_noalloc(const double* field, int Lx, int Lz, double* out, void* stream);
 
+/* Gradient of the time-averaged mean-pressure shift on a fixed noise stream,
+ *   L = (1/T) sum_{t<T} Pbar(t)|_{kT} - (1/T) sum_{t<T} Pbar(t)|_{kT=0},
+ * both runs from the rest state with the context's parameters (Pbar(t): spatial mean of the
+ * mechanical pressure of Sec. III.C on the pre-collision state of step t; the kT = 0 run is the
+ * noiseless companion of Eqs. EQP/NEQP), with respect to (G, lambda_s, lambda_d); lambda_e,
+ * lambda_q, lambda_eps and kT are held fixed.  grad[0..2] = dL/dG, dL/dlambda_s, dL/dlambda_d
+ * by a hand-written reverse sweep of the step that recomputes the forward states from
+ * checkpoints taken every ckpt_every steps (1 <= ckpt_every <= steps); grad may be NULL to get
+ * the loss alone.  The context's own state, step count and statistics are not touched.
+ * Requires a single-lattice context with the default options (a* on, copy-rule wall ghosts,
+ * hom noise; LB_ERR_STATE otherwise).  Device memory: about (steps/ckpt_every + ckpt_every + 5)
+ * states, allocated for the call and freed before it returns.  Synchronous. */
+int lb_pressure_shift_gradient(lb_ctx* ctx, int64_t steps, int64_t ckpt_every, double grad[3], double* loss);
+
 /* Clear the structure-factor and pressure accumulators (the step count is kept). */
 int lb_reset_statistics(lb_ctx* ctx);
 

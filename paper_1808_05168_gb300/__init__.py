@@ -135,6 +135,11 @@ class Simulation:
     def mass(self, lattice: int = 0):
         return capi.lb_mass(self.h, lattice)
 
+    def pressure_shift_gradient(self, steps: int, ckpt_every: int = 100, want_grad: bool = True):
+        """(L, [dL/dG, dL/dlambda_s, dL/dlambda_d]) of the time-averaged mean-pressure shift from
+        the rest state over `steps` steps (reverse sweep with checkpoints every `ckpt_every`)."""
+        return capi.lb_pressure_shift_gradient(self.h, steps, min(ckpt_every, steps), want_grad)
+
     def populations(self, lattice: int = 0) -> np.ndarray:
         Lx, Lz = self.shape(lattice)
         out = np.empty((2, 9, Lz, Lx), np.float64)

@@ -41,7 +41,7 @@ EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
            "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
-           "lb_power_spectrum", "lb_power_spectrum_noalloc")
+           "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient")
 LB_NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -103,6 +103,7 @@ def load():
             "lb_debug_barrier": [i, i, i],
             "lb_power_spectrum": [vp, i, i, vp, vp],
             "lb_power_spectrum_noalloc": [vp, i, i, vp, vp],
+            "lb_pressure_shift_gradient": [vp, i64, i64, dp, dp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -250,6 +251,15 @@ def lb_power_spectrum_noalloc(field_ptr, Lx, Lz, out_ptr, stream_handle=0):
                                             ctypes.c_void_p(int(out_ptr)),
                                             ctypes.c_void_p(int(stream_handle) if stream_handle else 0)),
            "lb_power_spectrum_noalloc")
+
+
+def lb_pressure_shift_gradient(h, steps, ckpt_every, want_grad=True):
+    """(loss, grad[3] or None): see include/lb.h."""
+    loss = ctypes.c_double()
+    grad = np.zeros(3, np.float64)
+    _check(load().lb_pressure_shift_gradient(h, int(steps), int(ckpt_every), _dptr(grad) if want_grad else None,
+                                             ctypes.byref(loss)), "lb_pressure_shift_gradient")
+    return loss.value, (grad if want_grad else None)
 
 
 def lb_debug_barrier(blocks, expected, limit_ms):

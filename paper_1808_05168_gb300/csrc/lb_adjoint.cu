@@ -1,0 +1,437 @@
+// lb_adjoint.cu -- reverse-mode (adjoint) sweep of the fluctuating LB step for the gradient of
+// the time-averaged mean-pressure shift
+//     L = (1/T) sum_{t<T} Pbar(t) |_{kT}  -  (1/T) sum_{t<T} Pbar(t) |_{kT = 0}
+// with respect to (G, lambda_s, lambda_d), on a fixed noise stream, both runs from the rest
+// state.  Pbar(t) is the spatial mean of the mechanical pressure (Sec. III.C) of the
+// pre-collision state of step t.
+//
+// One step k maps the stored state f*_{k-1} to f*_k (Eq. LB with Eq. MRT).  Its adjoint maps
+// fbar*_k (the loss's sensitivity to f*_k) to fbar*_{k-1} and adds the step's share of the
+// parameter gradient, in three kernels:
+//   1. densities: rho^S of the pre-collision state at every site (needed by the neighbours);
+//   2. local: at every site, the forward quantities are recomputed and the transposed Jacobian
+//      of the site update is applied to fbar*_k(r) (plus the pressure term of the loss); this
+//      gives the sensitivity to the 18 pulled populations through the site's own moments and
+//      densities, the sensitivity to the two neighbour sums sum_l w_l c_l rho^S(r + c_l) of
+//      Eq. (aNI), and the parameter contributions;
+//   3. gather/push: each site collects what its neighbours' forces and pressures owe to its
+//      densities (wall ghosts copy the adjacent row, Sec. II.A), adds it to every pulled
+//      population of the species, and pushes the result back along the streaming map (the
+//      transpose of the pull with mid-way bounce-back is a one-to-one scatter).
+// The forward states are recomputed segment by segment from checkpoints (every C steps) into a
+// ring of C states, so memory is O(T/C + C) states.
+//
+// Supported: one lattice, the a* correction on, wall ghosts copying the adjacent row, hom noise
+// (the default configuration); both precisions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+namespace {
+
+// v_l = sum_a T_al m_a (the transpose of the moment transform), Table I.
+template <class real>
+__device__ __forceinline__ void transpose_moments(const real m[9], real v[9]) {
+  const real b4 = m[0] + m[3] - 4 * m[8], b5 = m[0] + 4 * m[3] + 8 * m[8];
+  v[0] = m[0] - 2 * m[3] + 2 * m[8];
+  v[1] = b4 + m[1] + m[4] - m[6];
+  v[2] = b4 + m[2] - m[4] - m[7];
+  v[3] = b4 - m[1] + m[4] + m[6];
+  v[4] = b4 - m[2] - m[4] + m[7];
+  v[5] = b5 + m[1] + m[2] + m[5] + 2 * m[6] + 2 * m[7];
+  v[6] = b5 - m[1] + m[2] - m[5] - 2 * m[6] + 2 * m[7];
+  v[7] = b5 - m[1] - m[2] + m[5] - 2 * m[6] - 2 * m[7];
+  v[8] = b5 + m[1] - m[2] - m[5] + 2 * m[6] - 2 * m[7];
+}
+
+// m_a = sum_l T_al v_l, Table I (all nine moments).
+template <class real>
+__device__ __forceinline__ void all_moments(const real v[9], real m[9]) {
+  const real a57 = v[5] - v[7], a68 = v[6] - v[8], d13 = v[1] - v[3], d24 = v[2] - v[4];
+  const real s13 = v[1] + v[3], s24 = v[2] + v[4], s57 = v[5] + v[7], s68 = v[6] + v[8];
+  const real e = s13 + s24, dg = s57 + s68;
+  m[0] = v[0] + e + dg;
+  m[1] = d13 + a57 - a68;
+  m[2] = d24 + a57 + a68;
+  m[3] = -2 * v[0] + e + 4 * dg;
+  m[4] = s13 - s24;
+  m[5] = s57 - s68;
+  m[6] = -d13 + 2 * (a57 - a68);
+  m[7] = -d24 + 2 * (a57 + a68);
+  m[8] = 2 * v[0] - 4 * e + 8 * dg;
+}
+
+__constant__ int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kCZ[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__constant__ int kOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+// Deviations of the 18 populations pulled at (x, z) (Eq. LB; reflected at the walls; the
+// background streaming shift on non-reflected links), as in the forward kernel.
+template <class real>
+__device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int Lz, int x, int z, real k9, real k36,
+                                       real v[18]) {
+  const int LzLx = Lx * Lz;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+      const int zs = z - kCZ[l];
+      const int xs = (x - kCX[l] + Lx) % Lx;
+      real val;
+      if (zs >= 0 && zs < Lz) {
+        val = f[(s * 9 + l) * LzLx + zs * Lx + xs];
+        const real q = (l == 0 || l == 1 || l == 3) ? real(0) : ((l <= 4) ? k9 : k36);
+        const real sh = kCZ[l] > 0 ? -q : (kCZ[l] < 0 ? q : real(0));
+        val += s == 0 ? sh : -sh;
+      } else {
+        val = f[(s * 9 + kOPP[l]) * LzLx + z * Lx + x];
+      }
+      v[s * 9 + l] = val;
+    }
+}
+
+// Absolute pre-collision densities of every site.
+template <class real>
+__global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real>* lat, const RowConst<real>* rows,
+                               real* __restrict__ rho) {
+  const LatticeDev<real> L = lat[0];
+  const int N = L.Lx * L.Lz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int x = i % L.Lx, z = i / L.Lx;
+  real v[18];
+  pull18(f, L.Lx, L.Lz, x, z, L.k9, L.k36, v);
+  real a = 0, b = 0;
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    a += v[l];
+    b += v[9 + l];
+  }
+  rho[i] = rows[z].bgA + a;
+  rho[N + i] = rows[z].bgB + b;
+}
+
+// Density of species s at (x, z) with the copy-rule wall ghosts.
+template <class real>
+__device__ __forceinline__ real rho_at(const real* rho, int Lx, int Lz, int s, int x, int z) {
+  x = (x + Lx) % Lx;
+  z = z < 0 ? 0 : (z >= Lz ? Lz - 1 : z);
+  return rho[s * Lx * Lz + z * Lx + x];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// d sigma / d lambda for sigma^2 = K (2 - lambda) lambda.
+template <class real>
+__device__ __forceinline__ real dsigma(real sigma, real lam) {
+  return sigma * (1 - lam) / ((2 - lam) * lam);
+}
+
+template <class real>
+__device__ __forceinline__ void normals14(uint32_t site, uint32_t step, const LatticeDev<real>& L, real n[14]);
+template <>
+__device__ __forceinline__ void normals14<double>(uint32_t site, uint32_t step, const LatticeDev<double>& L,
+                                                  double n[14]) {
+  U4 w[4];
+  philox_site(site, step, L.lattice_id, L.key0, L.key1, w);
+  box_muller<double>(w[0].x, w[0].y, n[0], n[1]);
+  box_muller<double>(w[0].z, w[0].w, n[2], n[3]);
+  box_muller<double>(w[1].x, w[1].y, n[4], n[5]);
+  box_muller<double>(w[1].z, w[1].w, n[6], n[7]);
+  box_muller<double>(w[2].x, w[2].y, n[8], n[9]);
+  box_muller<double>(w[2].z, w[2].w, n[10], n[11]);
+  box_muller<double>(w[3].x, w[3].y, n[12], n[13]);
+}
+template <>
+__device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, const LatticeDev<float>& L, float n[14]) {
+  U4 w[4];
+  philox_site(site, step, L.lattice_id, L.key0, L.key1, w);
+  const uint32_t k[16] = {w[0].x, w[0].y, w[0].z, w[0].w, w[1].x, w[1].y, w[1].z, w[1].w,
+                          w[2].x, w[2].y, w[2].z, w[2].w, w[3].x, w[3].y, w[3].z, w[3].w};
+#pragma unroll
+  for (int p = 0; p < 7; ++p) {
+    // same formulas as the forward FP32 kernel
+    const float u1 = uniform01<float>(k[2 * p]);
+    const float t = -2.0f * logf(u1);
+    const float r = t * rsqrtf(t);
+    const float phi = fmaf(6.28318530717959f, __uint_as_float(0x3F800000u | (k[2 * p + 1] & 0x7FFFFFu)),
+                           -9.42477758729298f);
+    float sn, cs;
+    __sincosf(phi, &sn, &cs);
+    n[2 * p] = -r * cs;
+    n[2 * p + 1] = -r * sn;
+  }
+}
+
+// The local part of the transposed step at every site (see the file comment).  alpha: weight of
+// the site's pressure in the loss.  Outputs: fl[18][N] (local sensitivity of the pulled
+// populations), sb[4][N] (sensitivity of sum_l w_l c_l rho^A, rho^B (r + c_l): x, z for A then
+// B), and per block the three parameter partials (G, lambda_s, lambda_d).
+template <class real, bool NOISE>
+__global__ void adj_local_kernel(const real* __restrict__ f, const real* __restrict__ fbar,
+                                 const LatticeDev<real>* lat, const RowConst<real>* rows,
+                                 const real* __restrict__ rho, uint32_t step, real alpha, real* __restrict__ fl,
+                                 real* __restrict__ sb, double* __restrict__ partials) {
+  const LatticeDev<real> L = lat[0];
+  const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double gG = 0, gS = 0, gD = 0;
+  if (i < N) {
+    const int x = i % Lx, z = i / Lx;
+    const RowConst<real> rc = rows[z];
+    real v[18];
+    pull18(f, Lx, Lz, x, z, L.k9, L.k36, v);
+    real mA[9], mB[9];
+    all_moments(v, mA);
+    all_moments(v + 9, mB);
+    const real rA = rho[i], rB = rho[N + i];
+    const real rho_t = rA + rB, inv = real(1) / rho_t;
+    // neighbour sums (Eq. aNI) and the pressure's neighbour sums, copy-rule ghosts
+    real sAx = 0, sAz = 0, sBx = 0, sBz = 0, NA = 0, NB = 0;
+    for (int l = 1; l < 9; ++l) {
+      const real w = l <= 4 ? real(1) / 9 : real(1) / 36;
+      const real c2 = (real)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
+      const real a = rho_at(rho, Lx, Lz, 0, x + kCX[l], z + kCZ[l]);
+      const real b = rho_at(rho, Lx, Lz, 1, x + kCX[l], z + kCZ[l]);
+      sAx += w * kCX[l] * a;
+      sAz += w * kCZ[l] * a;
+      sBx += w * kCX[l] * b;
+      sBz += w * kCZ[l] * b;
+      NA += w * c2 * a;
+      NB += w * c2 * b;
+    }
+    const real G = L.G;
+    const real FNx = -G * (rA * sBx + rB * sAx), FNz = -G * (rA * sBz + rB * sAz);
+    const real cA = rA * inv, cB = rB * inv;
+    const real ne = rho_t * L.g3;
+    const real FA[2] = {cA * FNx, cA * FNz + ne};
+    const real FB[2] = {cB * FNx, cB * FNz - ne};
+    const real Px = mA[1] + mB[1] + real(0.5) * FNx, Pz = mA[2] + mB[2] + real(0.5) * FNz;
+    const real Ux = Px * inv, Uz = Pz * inv;
+    const real ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
+    const real lam[9] = {real(1), ld, ld, le, ls, ls, lq, lq, leps};
+
+    real n[14];
+    if (NOISE) normals14<real>((uint32_t)i, step, L, n);
+
+    // adjoints accumulated over both species
+    real Ubx = 0, Ubz = 0, FNbx = 0, FNbz = 0, rhob_t = 0, invb = 0;
+    real rhob[2] = {0, 0};
+    real mb[2][9];
+    real lamb_d = 0, lamb_s = 0;
+    real sbarA[9], sbarB[9];
+    for (int s = 0; s < 2; ++s) {
+      const real* m = s == 0 ? mA : mB;
+      const real rs = s == 0 ? rA : rB;
+      const real* F = s == 0 ? FA : FB;
+      real g[9];
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const real w = l == 0 ? real(4) / 9 : (l <= 4 ? real(1) / 9 : real(1) / 36);
+        g[l] = w * fbar[(s * 9 + l) * N + i];
+      }
+      real sbar[9];
+      all_moments(g, sbar);  // sbar_a = (1/N_a) sum_l T_al w_l fbar_l, before the 1/N_a
+      const real invN[9] = {1, 3, 3, real(0.25), real(2.25), 9, real(1.5), real(1.5), real(0.0625)};
+#pragma unroll
+      for (int a = 0; a < 9; ++a) sbar[a] *= invN[a];
+      for (int a = 0; a < 9; ++a) (s == 0 ? sbarA : sbarB)[a] = sbar[a];
+      // s_0 = rho^S
+      rhob[s] += sbar[0];
+      // equilibrium moments and forcing sources
+      const real UxUx = Ux * Ux, UzUz = Uz * Uz;
+      const real meq[6] = {0, rs * Ux, rs * Uz, 3 * rs * (UxUx + UzUz), rs * (UxUx - UzUz), rs * Ux * Uz};
+      const real src[6] = {0, F[0], F[1], 6 * (Ux * F[0] + Uz * F[1]), 2 * (Ux * F[0] - Uz * F[1]),
+                           Ux * F[1] + Uz * F[0]};
+      real mbar[9];
+      mbar[0] = 0;
+      real meqb[6], srcb[6];
+      for (int a = 1; a < 9; ++a) mbar[a] = (1 - lam[a]) * sbar[a];
+      for (int a = 1; a < 6; ++a) {
+        meqb[a] = lam[a] * sbar[a];
+        srcb[a] = (1 - real(0.5) * lam[a]) * sbar[a];
+        const real dl = sbar[a] * (meq[a] - m[a] - real(0.5) * src[a]);
+        if (a <= 2) lamb_d += dl;
+        else if (a >= 4) lamb_s += dl;
+      }
+      // meq -> rho^S, U
+      rhob[s] += meqb[1] * Ux + meqb[2] * Uz + 3 * meqb[3] * (UxUx + UzUz) + meqb[4] * (UxUx - UzUz) +
+                 meqb[5] * Ux * Uz;
+      Ubx += meqb[1] * rs + 6 * meqb[3] * rs * Ux + 2 * meqb[4] * rs * Ux + meqb[5] * rs * Uz;
+      Ubz += meqb[2] * rs + 6 * meqb[3] * rs * Uz - 2 * meqb[4] * rs * Uz + meqb[5] * rs * Ux;
+      // sources -> F^S, U
+      const real Fbx = srcb[1] + 6 * srcb[3] * Ux + 2 * srcb[4] * Ux + srcb[5] * Uz;
+      const real Fbz = srcb[2] + 6 * srcb[3] * Uz - 2 * srcb[4] * Uz + srcb[5] * Ux;
+      Ubx += 6 * srcb[3] * F[0] + 2 * srcb[4] * F[0] + srcb[5] * F[1];
+      Ubz += 6 * srcb[3] * F[1] - 2 * srcb[4] * F[1] + srcb[5] * F[0];
+      // F^S = (rho^S / rho) F_N +- (0, rho g3)
+      const real cS = s == 0 ? cA : cB;
+      FNbx += cS * Fbx;
+      FNbz += cS * Fbz;
+      const real cSb = Fbx * FNx + Fbz * FNz;
+      rhob[s] += cSb * inv;
+      invb += cSb * rs;
+      rhob_t += (s == 0 ? 1 : -1) * L.g3 * Fbz;
+      for (int a = 0; a < 9; ++a) mb[s][a] = mbar[a];
+    }
+    // U = (j^A + j^B + F_N / 2) / rho
+    const real Pbx = Ubx * inv, Pbz = Ubz * inv;
+    invb += Ubx * Px + Ubz * Pz;
+    mb[0][1] += Pbx;
+    mb[0][2] += Pbz;
+    mb[1][1] += Pbx;
+    mb[1][2] += Pbz;
+    FNbx += real(0.5) * Pbx;
+    FNbz += real(0.5) * Pbz;
+    // F_N = -G (rho^A s^B + rho^B s^A)
+    gG += (double)(-(FNbx * (rA * sBx + rB * sAx) + FNbz * (rA * sBz + rB * sAz)));
+    rhob[0] += -G * (FNbx * sBx + FNbz * sBz);
+    rhob[1] += -G * (FNbx * sAx + FNbz * sAz);
+    sb[0 * N + i] = -G * rB * FNbx;  // sensitivity of s^A (x, z)
+    sb[1 * N + i] = -G * rB * FNbz;
+    sb[2 * N + i] = -G * rA * FNbx;  // sensitivity of s^B (x, z)
+    sb[3 * N + i] = -G * rA * FNbz;
+    // the loss's pressure at this site: (1/2) sum |c|^2 f + (G/4) [rho^A N^B + rho^B N^A]
+    rhob[0] += alpha * real(0.25) * G * NB;
+    rhob[1] += alpha * real(0.25) * G * NA;
+    gG += (double)(alpha * real(0.25) * (rA * NB + rB * NA));
+    // inv = 1 / rho, rho = rho^A + rho^B
+    rhob_t += -invb * inv * inv;
+    rhob[0] += rhob_t;
+    rhob[1] += rhob_t;
+    // noise amplitudes depend on lambda_d (moments 1, 2) and lambda_s (moments 4, 5)
+    if (NOISE) {
+      const real dsm = dsigma(L.sig_mom, ld);
+      lamb_d += dsm * (n[0] * (sbarA[1] - sbarB[1]) + n[1] * (sbarA[2] - sbarB[2]));
+      const real d4 = dsigma(L.sig[4], ls), d5 = dsigma(L.sig[5], ls);
+      lamb_s += d4 * (sbarA[4] * n[3] + sbarB[4] * n[9]) + d5 * (sbarA[5] * n[4] + sbarB[5] * n[10]);
+    }
+    gS += (double)lamb_s;
+    gD += (double)lamb_d;
+    // back to the pulled populations: moments (transposed), density (every link), kinetic pressure
+    for (int s = 0; s < 2; ++s) {
+      real o[9];
+      mb[s][0] = rhob[s];
+      transpose_moments(mb[s], o);
+#pragma unroll
+      for (int l = 0; l < 9; ++l) {
+        const real c2 = (real)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
+        fl[(s * 9 + l) * N + i] = o[l] + alpha * real(0.5) * c2;
+      }
+    }
+  }
+  // block partials of the parameter gradient
+  __shared__ double red[3][32];
+  gG = warp_sum(gG);
+  gS = warp_sum(gS);
+  gD = warp_sum(gD);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = gG;
+    red[1][wid] = gS;
+    red[2][wid] = gD;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c += red[2][w];
+    }
+    partials[3 * blockIdx.x + 0] = a;
+    partials[3 * blockIdx.x + 1] = b;
+    partials[3 * blockIdx.x + 2] = c;
+  }
+}
+
+// Gather the neighbour-owed density sensitivities and push along the transposed streaming map.
+template <class real>
+__global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const real* __restrict__ rho,
+                                       const real* __restrict__ fl, const real* __restrict__ sb, real alpha,
+                                       real* __restrict__ fbar_prev) {
+  const LatticeDev<real> L = lat[0];
+  const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int x = i % Lx, z = i / Lx;
+  const real q = alpha * real(0.25) * L.G;
+  real rbA = 0, rbB = 0;
+  auto add_from = [&](int xs, int zs, int l) {
+    const int j = zs * Lx + ((xs + Lx) % Lx);
+    const real w = l <= 4 ? real(1) / 9 : real(1) / 36;
+    const real c2 = (real)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
+    rbA += w * (kCX[l] * sb[0 * N + j] + kCZ[l] * sb[1 * N + j]) + w * c2 * q * rho[N + j];
+    rbB += w * (kCX[l] * sb[2 * N + j] + kCZ[l] * sb[3 * N + j]) + w * c2 * q * rho[j];
+  };
+  for (int l = 1; l < 9; ++l) {
+    const int zs = z - kCZ[l];
+    if (zs >= 0 && zs < Lz) add_from(x - kCX[l], zs, l);
+    // the wall ghost next to this row copies this row's density
+    if ((z == 0 && kCZ[l] == -1) || (z == Lz - 1 && kCZ[l] == 1)) add_from(x - kCX[l], z, l);
+  }
+  const int LzLx = N;
+  for (int s = 0; s < 2; ++s) {
+    const real rb = s == 0 ? rbA : rbB;
+    for (int l = 0; l < 9; ++l) {
+      const real val = fl[(s * 9 + l) * N + i] + rb;
+      const int zs = z - kCZ[l];
+      if (zs >= 0 && zs < Lz) {
+        const int xs = (x - kCX[l] + Lx) % Lx;
+        fbar_prev[(s * 9 + l) * LzLx + zs * Lx + xs] = val;
+      } else {
+        fbar_prev[(s * 9 + kOPP[l]) * LzLx + z * Lx + x] = val;
+      }
+    }
+  }
+}
+
+__global__ void adj_sum_partials(const double* partials, int n, double sign, double* grad) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0, b = 0, c = 0;
+  for (int k = 0; k < n; ++k) {
+    a += partials[3 * k];
+    b += partials[3 * k + 1];
+    c += partials[3 * k + 2];
+  }
+  grad[0] += sign * a;
+  grad[1] += sign * b;
+  grad[2] += sign * c;
+}
+
+}  // namespace
+
+template <class real>
+cudaError_t launch_adjoint_step(const real* f_prev, const real* fbar, real* fbar_prev, const LatticeDev<real>* lat,
+                                const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
+                                double sign, real* rho, real* fl, real* sb, double* partials, double* grad,
+                                cudaStream_t s) {
+  const int B = 128, nb = (n_sites + B - 1) / B;
+  adj_rho_kernel<real><<<nb, B, 0, s>>>(f_prev, lat, rows, rho);
+  if (noise)
+    adj_local_kernel<real, true><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, (real)alpha, fl, sb, partials);
+  else
+    adj_local_kernel<real, false><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, (real)alpha, fl, sb, partials);
+  adj_gather_push_kernel<real><<<nb, B, 0, s>>>(lat, rho, fl, sb, (real)alpha, fbar_prev);
+  adj_sum_partials<<<1, 32, 0, s>>>(partials, nb, sign, grad);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint_step<float>(const float*, const float*, float*, const LatticeDev<float>*,
+                                                const RowConst<float>*, int, uint32_t, bool, double, double, float*,
+                                                float*, float*, double*, double*, cudaStream_t);
+template cudaError_t launch_adjoint_step<double>(const double*, const double*, double*, const LatticeDev<double>*,
+                                                 const RowConst<double>*, int, uint32_t, bool, double, double, double*,
+                                                 double*, double*, double*, double*, cudaStream_t);
+
+}  // namespace lbk

@@ -655,7 +655,136 @@ int ensure_scratch(lb_ctx* c) {
 
 }  // namespace
 
+namespace {
+
+// ---- adjoint sweep for the gradient of the mean-pressure shift -----------------------------
+template <class real>
+int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* loss) {
+  const lb_params& p = c->params[0];
+  const int N = p.Lx * p.Lz;
+  const size_t S = (size_t)18 * N;  // reals per state (lattice 0 starts at offset 0)
+  const int64_t nck = (T + C - 1) / C;
+  const bool want_grad = grad != nullptr;
+  cudaStream_t st = c->stream;
+  std::vector<void*> owned;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    owned.push_back(q);
+    return q;
+  };
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* q : owned) cudaFree(q);
+  };
+  real* ck = (real*)alloc(nck * S * sizeof(real));
+  real* ring = want_grad ? (real*)alloc(C * S * sizeof(real)) : nullptr;
+  real* cur = (real*)alloc(2 * S * sizeof(real));
+  real* fb = want_grad ? (real*)alloc(2 * S * sizeof(real)) : nullptr;
+  real* fields = (real*)alloc(4 * (size_t)N * sizeof(real));
+  real* rho = want_grad ? (real*)alloc(2 * (size_t)N * sizeof(real)) : nullptr;
+  real* fl = want_grad ? (real*)alloc(S * sizeof(real)) : nullptr;
+  real* sb = want_grad ? (real*)alloc(4 * (size_t)N * sizeof(real)) : nullptr;
+  const int nb = (N + 127) / 128;
+  double* partials = (double*)alloc((size_t)3 * std::max<int>(nb, (int)c->items.size()) * sizeof(double));
+  double* d_grad = (double*)alloc(3 * sizeof(double));
+  DiagStats* stats = (DiagStats*)alloc(sizeof(DiagStats));
+  int64_t* zero_t = (int64_t*)alloc(sizeof(int64_t));
+  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb)) || !cur || !fields || !partials || !d_grad || !stats ||
+      !zero_t) {
+    release();
+    return LB_ERR_OOM;
+  }
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  ok(cudaMemsetAsync(zero_t, 0, sizeof(int64_t), st));
+  ok(cudaMemsetAsync(d_grad, 0, 3 * sizeof(double), st));
+  auto args = [&](const real* src, real* dst, int64_t k) {
+    StepArgs<real> a = step_args<real>(c, 0, 0);
+    a.src = src;
+    a.dst = dst;
+    a.d_t = zero_t;
+    a.t_offset = (int)k;
+    a.fields = fields;
+    a.partials = partials;
+    return a;
+  };
+  const BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+  double L[2] = {0.0, 0.0};
+  for (int run = 0; run < 2 && e == cudaSuccess; ++run) {
+    const int noise = run == 0 ? c->noise_mode : NOISE_OFF;
+    // forward from rest: checkpoints f*_{c-1} before every C-th step, pressure of every step
+    ok(launch_init_rest<real>(cur, bp, st));
+    ok(cudaMemsetAsync(stats, 0, sizeof(DiagStats), st));
+    for (int64_t k = 0; k < T && e == cudaSuccess; ++k) {
+      real* src = cur + (k & 1) * S;
+      real* dst = cur + ((k + 1) & 1) * S;
+      if (k % C == 0) ok(cudaMemcpyAsync(ck + (k / C) * S, src, S * sizeof(real), cudaMemcpyDeviceToDevice, st));
+      ok(launch_step<real>(args(src, dst, k), c->tile_x, true, noise, c->bulk_ok, st));
+      ok(launch_finalize(c->d_diag, 1, partials, stats, st));
+    }
+    DiagStats hs;
+    ok(cudaMemcpyAsync(&hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    ok(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) break;
+    if (hs.nonfinite) {
+      release();
+      return LB_ERR_NONFINITE;
+    }
+    L[run] = (hs.P_sum + hs.P_comp) / (double)T;
+    if (!want_grad) continue;
+    // reverse sweep, one checkpoint segment at a time
+    const double sign = run == 0 ? 1.0 : -1.0;
+    const double alpha = sign / ((double)T * (double)N);
+    int fcur = 0;
+    ok(cudaMemsetAsync(fb, 0, S * sizeof(real), st));
+    for (int64_t seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
+      const int64_t c0 = seg * C, len = std::min<int64_t>(C, T - c0);
+      ok(cudaMemcpyAsync(ring, ck + seg * S, S * sizeof(real), cudaMemcpyDeviceToDevice, st));
+      for (int64_t i = 1; i < len; ++i)
+        ok(launch_step<real>(args(ring + (i - 1) * S, ring + i * S, c0 + i - 1), c->tile_x, false, noise, c->bulk_ok,
+                             st));
+      for (int64_t k = c0 + len - 1; k >= c0 && e == cudaSuccess; --k) {
+        ok(launch_adjoint_step<real>(ring + (k - c0) * S, fb + fcur * S, fb + (1 - fcur) * S,
+                                     (const LatticeDev<real>*)c->d_lat, (const RowConst<real>*)c->d_rows, N,
+                                     (uint32_t)k, noise != NOISE_OFF, alpha, sign, rho, fl, sb, partials, d_grad, st));
+        fcur = 1 - fcur;
+      }
+    }
+  }
+  if (e == cudaSuccess && want_grad) {
+    ok(cudaMemcpyAsync(grad, d_grad, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ok(cudaStreamSynchronize(st));
+  }
+  release();
+  if (e != cudaSuccess) return cuda_err(e);
+  if (loss) *loss = L[0] - L[1];
+  int err = 0;
+  if (cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && err) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return LB_ERR_TIMEOUT;
+  }
+  return LB_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int lb_pressure_shift_gradient(lb_ctx* c, int64_t steps, int64_t ckpt_every, double grad[3], double* loss) {
+  if (!c || steps < 1 || ckpt_every < 1 || ckpt_every > steps) return LB_ERR_BAD_PARAM;
+  if (c->n_lat != 1 || (c->flags & (LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC))) return LB_ERR_STATE;
+  if (steps >= ((int64_t)1 << 31)) return LB_ERR_BAD_PARAM;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  return c->dev32 ? pressure_shift_impl<float>(c, steps, ckpt_every, grad, loss)
+                  : pressure_shift_impl<double>(c, steps, ckpt_every, grad, loss);
+}
 
 int lb_create(lb_ctx** out, int Lx, int Lz, double lambda_s, double lambda_d, double lambda_e, double lambda_q,
               double lambda_eps, double kT, double G, double grad_c0, uint64_t seed, int flags) {

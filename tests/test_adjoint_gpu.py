@@ -1,0 +1,87 @@
+"""Gradient of the time-averaged mean-pressure shift (reverse sweep with checkpoints) against the
+oracle's forward-mode dual-number gradient and against central differences of the library's own
+loss on the same noise stream."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_05168_gb300 import LatticeParams, Simulation, capi, workloads
+
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(Lx=16, Lz=8, kT=1e-3, G=0.5, grad_c0=0.05, lambda_s=1.2, lambda_d=0.9, lambda_e=1.0, seed=5)
+
+
+def gpu_grad(p, steps, ckpt, precision="fp64", want_grad=True):
+    with Simulation(p, precision=precision) as sim:
+        return sim.pressure_shift_gradient(steps, ckpt, want_grad)
+
+
+@pytest.mark.parametrize("prec,gtol,ltol", [("fp64", 1e-8, 1e-10), ("dev32", 3e-3, 1e-4)])
+def test_adjoint_matches_oracle_dual_numbers(prec, gtol, ltol):
+    p = LatticeParams(**SMALL)
+    steps = 40
+    loss, g = gpu_grad(p, steps, 7, prec)  # 6 segments, the last one shorter
+    o_loss, o_g = oracle.pressure_shift_grad(p.Lx, p.Lz, steps, lambda_s=p.lambda_s, lambda_d=p.lambda_d,
+                                             lambda_e=p.lambda_e, kT=p.kT, G=p.G, grad_c0=p.grad_c0, seed=p.seed)
+    assert abs(loss - o_loss) <= ltol * abs(o_loss), (loss, o_loss)
+    np.testing.assert_allclose(g, o_g, rtol=0, atol=gtol * np.max(np.abs(o_g)))
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    p = LatticeParams(**SMALL)
+    _, g1 = gpu_grad(p, 30, 1)
+    _, g2 = gpu_grad(p, 30, 30)
+    _, g3 = gpu_grad(p, 30, 4)
+    np.testing.assert_allclose(g1, g2, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(g1, g3, rtol=1e-13, atol=0)
+
+
+def test_noiseless_shift_is_zero():
+    p = LatticeParams(**dict(SMALL, kT=0.0))
+    loss, g = gpu_grad(p, 20, 5)
+    assert loss == 0.0
+    assert np.all(g == 0.0)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-5), ("dev32", 5e-2)])
+def test_adjoint_matches_central_differences_full_size(prec, rtol):
+    """256 x 128, G = 0.5, wall-to-wall difference 0.5, kT = 1e-5, 2000 steps, checkpoints every
+    100 steps; central differences with step 1e-4 on the same noise."""
+    (p,) = workloads.c5()
+    steps, h = 2000, 1e-4
+    loss, g = gpu_grad(p, steps, 100, prec)
+    fd = []
+    for key in ("G", "lambda_s", "lambda_d"):
+        up = LatticeParams(**{**p.__dict__, key: getattr(p, key) + h})
+        dn = LatticeParams(**{**p.__dict__, key: getattr(p, key) - h})
+        lu, _ = gpu_grad(up, steps, 100, prec, want_grad=False)
+        ld, _ = gpu_grad(dn, steps, 100, prec, want_grad=False)
+        fd.append((lu - ld) / (2 * h))
+    fd = np.array(fd)
+    assert np.all(np.isfinite(g)) and abs(loss) > 0
+    np.testing.assert_allclose(g, fd, rtol=0, atol=rtol * np.max(np.abs(fd)))
+
+
+def test_autograd_function():
+    import torch
+    from paper_1808_05168_gb300.autograd import MeanPressureShift
+    p = LatticeParams(**SMALL)
+    G = torch.tensor(p.G, dtype=torch.float64, requires_grad=True)
+    ls = torch.tensor(p.lambda_s, dtype=torch.float64, requires_grad=True)
+    ld = torch.tensor(p.lambda_d, dtype=torch.float64, requires_grad=True)
+    L = MeanPressureShift.apply(G, ls, ld, p, 25, 5)
+    (2.0 * L).backward()
+    loss, g = gpu_grad(p, 25, 5)
+    assert float(L) == loss
+    np.testing.assert_array_equal([G.grad.item(), ls.grad.item(), ld.grad.item()], 2.0 * g)
+
+
+def test_unsupported_configurations_are_refused():
+    with Simulation([LatticeParams(8, 4), LatticeParams(8, 4, lattice_id=1)]) as sim:
+        with pytest.raises(capi.LBError) as e:
+            sim.pressure_shift_gradient(10, 5)
+        assert e.value.code == capi.LB_ERR_STATE
+    with Simulation(LatticeParams(8, 4, kT=1e-4), noise_loc=True) as sim:
+        with pytest.raises(capi.LBError):
+            sim.pressure_shift_gradient(10, 5)
