@@ -738,7 +738,8 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
     }
     L[run] = (hs.P_sum + hs.P_comp) / (double)T;
     if (!want_grad) continue;
-    // reverse sweep, one checkpoint segment at a time
+    // reverse sweep, one checkpoint segment at a time; the run's sign (+ noisy, - noiseless)
+    // enters through the loss weight alpha, to which the whole sweep is linear
     const double sign = run == 0 ? 1.0 : -1.0;
     const double alpha = sign / ((double)T * (double)N);
     int fcur = 0;
@@ -752,7 +753,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
       for (int64_t k = c0 + len - 1; k >= c0 && e == cudaSuccess; --k) {
         ok(launch_adjoint_step<real>(ring + (k - c0) * S, fb + fcur * S, fb + (1 - fcur) * S,
                                      (const LatticeDev<real>*)c->d_lat, (const RowConst<real>*)c->d_rows, N,
-                                     (uint32_t)k, noise != NOISE_OFF, alpha, sign, rho, fl, sb, partials, d_grad, st));
+                                     (uint32_t)k, noise != NOISE_OFF, alpha, 1.0, rho, fl, sb, partials, d_grad, st));
         fcur = 1 - fcur;
       }
     }

@@ -73,7 +73,7 @@ def test_autograd_function():
     L = MeanPressureShift.apply(G, ls, ld, p, 25, 5)
     (2.0 * L).backward()
     loss, g = gpu_grad(p, 25, 5)
-    assert float(L) == loss
+    assert float(L.detach()) == loss
     np.testing.assert_array_equal([G.grad.item(), ls.grad.item(), ld.grad.item()], 2.0 * g)
 
 
