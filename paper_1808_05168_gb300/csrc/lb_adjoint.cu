@@ -74,8 +74,8 @@ __constant__ int kOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 // Deviations of the 18 populations pulled at (x, z) (Eq. LB; reflected at the walls; the
 // background streaming shift on non-reflected links), as in the forward kernel.
 template <class real>
-__device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int Lz, int x, int z, real k9, real k36,
-                                       real v[18]) {
+__device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int Lz, int x, int z, double k9, double k36,
+                                       double v[18]) {
   const int LzLx = Lx * Lz;
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -83,14 +83,14 @@ __device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int L
     for (int l = 0; l < 9; ++l) {
       const int zs = z - kCZ[l];
       const int xs = (x - kCX[l] + Lx) % Lx;
-      real val;
+      double val;
       if (zs >= 0 && zs < Lz) {
-        val = f[(s * 9 + l) * LzLx + zs * Lx + xs];
-        const real q = (l == 0 || l == 1 || l == 3) ? real(0) : ((l <= 4) ? k9 : k36);
-        const real sh = kCZ[l] > 0 ? -q : (kCZ[l] < 0 ? q : real(0));
+        val = (double)f[(s * 9 + l) * LzLx + zs * Lx + xs];
+        const double q = (l == 0 || l == 1 || l == 3) ? 0.0 : ((l <= 4) ? k9 : k36);
+        const double sh = kCZ[l] > 0 ? -q : (kCZ[l] < 0 ? q : 0.0);
         val += s == 0 ? sh : -sh;
       } else {
-        val = f[(s * 9 + kOPP[l]) * LzLx + z * Lx + x];
+        val = (double)f[(s * 9 + kOPP[l]) * LzLx + z * Lx + x];
       }
       v[s * 9 + l] = val;
     }
@@ -99,27 +99,26 @@ __device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int L
 // Absolute pre-collision densities of every site.
 template <class real>
 __global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real>* lat, const RowConst<real>* rows,
-                               real* __restrict__ rho) {
+                               double* __restrict__ rho) {
   const LatticeDev<real> L = lat[0];
   const int N = L.Lx * L.Lz;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int x = i % L.Lx, z = i / L.Lx;
-  real v[18];
-  pull18(f, L.Lx, L.Lz, x, z, L.k9, L.k36, v);
-  real a = 0, b = 0;
+  double v[18];
+  pull18(f, L.Lx, L.Lz, x, z, (double)L.k9, (double)L.k36, v);
+  double a = 0, b = 0;
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     a += v[l];
     b += v[9 + l];
   }
-  rho[i] = rows[z].bgA + a;
-  rho[N + i] = rows[z].bgB + b;
+  rho[i] = (double)rows[z].bgA + a;
+  rho[N + i] = (double)rows[z].bgB + b;
 }
 
 // Density of species s at (x, z) with the copy-rule wall ghosts.
-template <class real>
-__device__ __forceinline__ real rho_at(const real* rho, int Lx, int Lz, int s, int x, int z) {
+__device__ __forceinline__ double rho_at(const double* rho, int Lx, int Lz, int s, int x, int z) {
   x = (x + Lx) % Lx;
   z = z < 0 ? 0 : (z >= Lz ? Lz - 1 : z);
   return rho[s * Lx * Lz + z * Lx + x];
@@ -177,32 +176,34 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
 // the site's pressure in the loss.  Outputs: fl[18][N] (local sensitivity of the pulled
 // populations), sb[4][N] (sensitivity of sum_l w_l c_l rho^A, rho^B (r + c_l): x, z for A then
 // B), and per block the three parameter partials (G, lambda_s, lambda_d).
+// The state may be single precision (FP32 deviations); the transposed step is evaluated in double
+// precision throughout, since the loss is a small difference of two runs' pressures.
 template <class real, bool NOISE>
-__global__ void adj_local_kernel(const real* __restrict__ f, const real* __restrict__ fbar,
+__global__ void adj_local_kernel(const real* __restrict__ f, const double* __restrict__ fbar,
                                  const LatticeDev<real>* lat, const RowConst<real>* rows,
-                                 const real* __restrict__ rho, uint32_t step, real alpha, real* __restrict__ fl,
-                                 real* __restrict__ sb, double* __restrict__ partials) {
-  const LatticeDev<real> L = lat[0];
+                                 const double* __restrict__ rho, uint32_t step, double alpha, double* __restrict__ fl,
+                                 double* __restrict__ sb, double* __restrict__ partials) {
+  using real_s = real;
+  const LatticeDev<real_s> L = lat[0];
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double gG = 0, gS = 0, gD = 0;
   if (i < N) {
     const int x = i % Lx, z = i / Lx;
-    const RowConst<real> rc = rows[z];
-    real v[18];
-    pull18(f, Lx, Lz, x, z, L.k9, L.k36, v);
-    real mA[9], mB[9];
+    double v[18];
+    pull18(f, Lx, Lz, x, z, (double)L.k9, (double)L.k36, v);
+    double mA[9], mB[9];
     all_moments(v, mA);
     all_moments(v + 9, mB);
-    const real rA = rho[i], rB = rho[N + i];
-    const real rho_t = rA + rB, inv = real(1) / rho_t;
+    const double rA = rho[i], rB = rho[N + i];
+    const double rho_t = rA + rB, inv = double(1) / rho_t;
     // neighbour sums (Eq. aNI) and the pressure's neighbour sums, copy-rule ghosts
-    real sAx = 0, sAz = 0, sBx = 0, sBz = 0, NA = 0, NB = 0;
+    double sAx = 0, sAz = 0, sBx = 0, sBz = 0, NA = 0, NB = 0;
     for (int l = 1; l < 9; ++l) {
-      const real w = l <= 4 ? real(1) / 9 : real(1) / 36;
-      const real c2 = (real)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
-      const real a = rho_at(rho, Lx, Lz, 0, x + kCX[l], z + kCZ[l]);
-      const real b = rho_at(rho, Lx, Lz, 1, x + kCX[l], z + kCZ[l]);
+      const double w = l <= 4 ? double(1) / 9 : double(1) / 36;
+      const double c2 = (double)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
+      const double a = rho_at(rho, Lx, Lz, 0, x + kCX[l], z + kCZ[l]);
+      const double b = rho_at(rho, Lx, Lz, 1, x + kCX[l], z + kCZ[l]);
       sAx += w * kCX[l] * a;
       sAz += w * kCZ[l] * a;
       sBx += w * kCX[l] * b;
@@ -210,57 +211,62 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const real* __restr
       NA += w * c2 * a;
       NB += w * c2 * b;
     }
-    const real G = L.G;
-    const real FNx = -G * (rA * sBx + rB * sAx), FNz = -G * (rA * sBz + rB * sAz);
-    const real cA = rA * inv, cB = rB * inv;
-    const real ne = rho_t * L.g3;
-    const real FA[2] = {cA * FNx, cA * FNz + ne};
-    const real FB[2] = {cB * FNx, cB * FNz - ne};
-    const real Px = mA[1] + mB[1] + real(0.5) * FNx, Pz = mA[2] + mB[2] + real(0.5) * FNz;
-    const real Ux = Px * inv, Uz = Pz * inv;
-    const real ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
-    const real lam[9] = {real(1), ld, ld, le, ls, ls, lq, lq, leps};
+    const double G = L.G;
+    const double FNx = -G * (rA * sBx + rB * sAx), FNz = -G * (rA * sBz + rB * sAz);
+    const double cA = rA * inv, cB = rB * inv;
+    const double ne = rho_t * L.g3;
+    const double FA[2] = {cA * FNx, cA * FNz + ne};
+    const double FB[2] = {cB * FNx, cB * FNz - ne};
+    const double Px = mA[1] + mB[1] + double(0.5) * FNx, Pz = mA[2] + mB[2] + double(0.5) * FNz;
+    const double Ux = Px * inv, Uz = Pz * inv;
+    const double ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
+    const double lam[9] = {double(1), ld, ld, le, ls, ls, lq, lq, leps};
 
-    real n[14];
-    if (NOISE) normals14<real>((uint32_t)i, step, L, n);
+    double n[14];
+    if (NOISE) {
+      real_s nn[14];
+      normals14<real_s>((uint32_t)i, step, L, nn);
+#pragma unroll
+      for (int q = 0; q < 14; ++q) n[q] = (double)nn[q];
+    }
 
     // adjoints accumulated over both species
-    real Ubx = 0, Ubz = 0, FNbx = 0, FNbz = 0, rhob_t = 0, invb = 0;
-    real rhob[2] = {0, 0};
-    real mb[2][9];
-    real lamb_d = 0, lamb_s = 0;
-    real sbarA[9], sbarB[9];
+    double Ubx = 0, Ubz = 0, FNbx = 0, FNbz = 0, rhob_t = 0, invb = 0;
+    double rhob[2] = {0, 0};
+    double mb[2][9];
+    double lamb_d = 0, lamb_s = 0;
+    double sbarA[9], sbarB[9];
     for (int s = 0; s < 2; ++s) {
-      const real* m = s == 0 ? mA : mB;
-      const real rs = s == 0 ? rA : rB;
-      const real* F = s == 0 ? FA : FB;
-      real g[9];
+      const double* m = s == 0 ? mA : mB;
+      const double rs = s == 0 ? rA : rB;
+      const double* F = s == 0 ? FA : FB;
+      double g[9];
 #pragma unroll
       for (int l = 0; l < 9; ++l) {
-        const real w = l == 0 ? real(4) / 9 : (l <= 4 ? real(1) / 9 : real(1) / 36);
+        const double w = l == 0 ? double(4) / 9 : (l <= 4 ? double(1) / 9 : double(1) / 36);
         g[l] = w * fbar[(s * 9 + l) * N + i];
       }
-      real sbar[9];
+      double sbar[9];
       all_moments(g, sbar);  // sbar_a = (1/N_a) sum_l T_al w_l fbar_l, before the 1/N_a
-      const real invN[9] = {1, 3, 3, real(0.25), real(2.25), 9, real(1.5), real(1.5), real(0.0625)};
+      const double invN[9] = {1, 3, 3, double(0.25), double(2.25), 9, double(1.5), double(1.5), double(0.0625)};
 #pragma unroll
       for (int a = 0; a < 9; ++a) sbar[a] *= invN[a];
       for (int a = 0; a < 9; ++a) (s == 0 ? sbarA : sbarB)[a] = sbar[a];
       // s_0 = rho^S
       rhob[s] += sbar[0];
       // equilibrium moments and forcing sources
-      const real UxUx = Ux * Ux, UzUz = Uz * Uz;
-      const real meq[6] = {0, rs * Ux, rs * Uz, 3 * rs * (UxUx + UzUz), rs * (UxUx - UzUz), rs * Ux * Uz};
-      const real src[6] = {0, F[0], F[1], 6 * (Ux * F[0] + Uz * F[1]), 2 * (Ux * F[0] - Uz * F[1]),
+      const double UxUx = Ux * Ux, UzUz = Uz * Uz;
+      const double meq[6] = {0, rs * Ux, rs * Uz, 3 * rs * (UxUx + UzUz), rs * (UxUx - UzUz), rs * Ux * Uz};
+      const double src[6] = {0, F[0], F[1], 6 * (Ux * F[0] + Uz * F[1]), 2 * (Ux * F[0] - Uz * F[1]),
                            Ux * F[1] + Uz * F[0]};
-      real mbar[9];
+      double mbar[9];
       mbar[0] = 0;
-      real meqb[6], srcb[6];
+      double meqb[6], srcb[6];
       for (int a = 1; a < 9; ++a) mbar[a] = (1 - lam[a]) * sbar[a];
       for (int a = 1; a < 6; ++a) {
         meqb[a] = lam[a] * sbar[a];
-        srcb[a] = (1 - real(0.5) * lam[a]) * sbar[a];
-        const real dl = sbar[a] * (meq[a] - m[a] - real(0.5) * src[a]);
+        srcb[a] = (1 - double(0.5) * lam[a]) * sbar[a];
+        const double dl = sbar[a] * (meq[a] - m[a] - double(0.5) * src[a]);
         if (a <= 2) lamb_d += dl;
         else if (a >= 4) lamb_s += dl;
       }
@@ -270,29 +276,29 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const real* __restr
       Ubx += meqb[1] * rs + 6 * meqb[3] * rs * Ux + 2 * meqb[4] * rs * Ux + meqb[5] * rs * Uz;
       Ubz += meqb[2] * rs + 6 * meqb[3] * rs * Uz - 2 * meqb[4] * rs * Uz + meqb[5] * rs * Ux;
       // sources -> F^S, U
-      const real Fbx = srcb[1] + 6 * srcb[3] * Ux + 2 * srcb[4] * Ux + srcb[5] * Uz;
-      const real Fbz = srcb[2] + 6 * srcb[3] * Uz - 2 * srcb[4] * Uz + srcb[5] * Ux;
+      const double Fbx = srcb[1] + 6 * srcb[3] * Ux + 2 * srcb[4] * Ux + srcb[5] * Uz;
+      const double Fbz = srcb[2] + 6 * srcb[3] * Uz - 2 * srcb[4] * Uz + srcb[5] * Ux;
       Ubx += 6 * srcb[3] * F[0] + 2 * srcb[4] * F[0] + srcb[5] * F[1];
       Ubz += 6 * srcb[3] * F[1] - 2 * srcb[4] * F[1] + srcb[5] * F[0];
       // F^S = (rho^S / rho) F_N +- (0, rho g3)
-      const real cS = s == 0 ? cA : cB;
+      const double cS = s == 0 ? cA : cB;
       FNbx += cS * Fbx;
       FNbz += cS * Fbz;
-      const real cSb = Fbx * FNx + Fbz * FNz;
+      const double cSb = Fbx * FNx + Fbz * FNz;
       rhob[s] += cSb * inv;
       invb += cSb * rs;
       rhob_t += (s == 0 ? 1 : -1) * L.g3 * Fbz;
       for (int a = 0; a < 9; ++a) mb[s][a] = mbar[a];
     }
     // U = (j^A + j^B + F_N / 2) / rho
-    const real Pbx = Ubx * inv, Pbz = Ubz * inv;
+    const double Pbx = Ubx * inv, Pbz = Ubz * inv;
     invb += Ubx * Px + Ubz * Pz;
     mb[0][1] += Pbx;
     mb[0][2] += Pbz;
     mb[1][1] += Pbx;
     mb[1][2] += Pbz;
-    FNbx += real(0.5) * Pbx;
-    FNbz += real(0.5) * Pbz;
+    FNbx += double(0.5) * Pbx;
+    FNbz += double(0.5) * Pbz;
     // F_N = -G (rho^A s^B + rho^B s^A)
     gG += (double)(-(FNbx * (rA * sBx + rB * sAx) + FNbz * (rA * sBz + rB * sAz)));
     rhob[0] += -G * (FNbx * sBx + FNbz * sBz);
@@ -302,31 +308,31 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const real* __restr
     sb[2 * N + i] = -G * rA * FNbx;  // sensitivity of s^B (x, z)
     sb[3 * N + i] = -G * rA * FNbz;
     // the loss's pressure at this site: (1/2) sum |c|^2 f + (G/4) [rho^A N^B + rho^B N^A]
-    rhob[0] += alpha * real(0.25) * G * NB;
-    rhob[1] += alpha * real(0.25) * G * NA;
-    gG += (double)(alpha * real(0.25) * (rA * NB + rB * NA));
+    rhob[0] += alpha * double(0.25) * G * NB;
+    rhob[1] += alpha * double(0.25) * G * NA;
+    gG += (double)(alpha * double(0.25) * (rA * NB + rB * NA));
     // inv = 1 / rho, rho = rho^A + rho^B
     rhob_t += -invb * inv * inv;
     rhob[0] += rhob_t;
     rhob[1] += rhob_t;
     // noise amplitudes depend on lambda_d (moments 1, 2) and lambda_s (moments 4, 5)
     if (NOISE) {
-      const real dsm = dsigma(L.sig_mom, ld);
+      const double dsm = dsigma<double>((double)L.sig_mom, ld);
       lamb_d += dsm * (n[0] * (sbarA[1] - sbarB[1]) + n[1] * (sbarA[2] - sbarB[2]));
-      const real d4 = dsigma(L.sig[4], ls), d5 = dsigma(L.sig[5], ls);
+      const double d4 = dsigma<double>((double)L.sig[4], ls), d5 = dsigma<double>((double)L.sig[5], ls);
       lamb_s += d4 * (sbarA[4] * n[3] + sbarB[4] * n[9]) + d5 * (sbarA[5] * n[4] + sbarB[5] * n[10]);
     }
     gS += (double)lamb_s;
     gD += (double)lamb_d;
     // back to the pulled populations: moments (transposed), density (every link), kinetic pressure
     for (int s = 0; s < 2; ++s) {
-      real o[9];
+      double o[9];
       mb[s][0] = rhob[s];
       transpose_moments(mb[s], o);
 #pragma unroll
       for (int l = 0; l < 9; ++l) {
-        const real c2 = (real)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
-        fl[(s * 9 + l) * N + i] = o[l] + alpha * real(0.5) * c2;
+        const double c2 = (double)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
+        fl[(s * 9 + l) * N + i] = o[l] + alpha * double(0.5) * c2;
       }
     }
   }
@@ -357,20 +363,20 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const real* __restr
 
 // Gather the neighbour-owed density sensitivities and push along the transposed streaming map.
 template <class real>
-__global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const real* __restrict__ rho,
-                                       const real* __restrict__ fl, const real* __restrict__ sb, real alpha,
-                                       real* __restrict__ fbar_prev) {
+__global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const double* __restrict__ rho,
+                                       const double* __restrict__ fl, const double* __restrict__ sb, double alpha,
+                                       double* __restrict__ fbar_prev) {
   const LatticeDev<real> L = lat[0];
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int x = i % Lx, z = i / Lx;
-  const real q = alpha * real(0.25) * L.G;
-  real rbA = 0, rbB = 0;
+  const double q = alpha * 0.25 * (double)L.G;
+  double rbA = 0, rbB = 0;
   auto add_from = [&](int xs, int zs, int l) {
     const int j = zs * Lx + ((xs + Lx) % Lx);
-    const real w = l <= 4 ? real(1) / 9 : real(1) / 36;
-    const real c2 = (real)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
+    const double w = l <= 4 ? 1.0 / 9 : 1.0 / 36;
+    const double c2 = (double)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
     rbA += w * (kCX[l] * sb[0 * N + j] + kCZ[l] * sb[1 * N + j]) + w * c2 * q * rho[N + j];
     rbB += w * (kCX[l] * sb[2 * N + j] + kCZ[l] * sb[3 * N + j]) + w * c2 * q * rho[j];
   };
@@ -382,9 +388,9 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const real* 
   }
   const int LzLx = N;
   for (int s = 0; s < 2; ++s) {
-    const real rb = s == 0 ? rbA : rbB;
+    const double rb = s == 0 ? rbA : rbB;
     for (int l = 0; l < 9; ++l) {
-      const real val = fl[(s * 9 + l) * N + i] + rb;
+      const double val = fl[(s * 9 + l) * N + i] + rb;
       const int zs = z - kCZ[l];
       if (zs >= 0 && zs < Lz) {
         const int xs = (x - kCX[l] + Lx) % Lx;
@@ -412,24 +418,24 @@ __global__ void adj_sum_partials(const double* partials, int n, double sign, dou
 }  // namespace
 
 template <class real>
-cudaError_t launch_adjoint_step(const real* f_prev, const real* fbar, real* fbar_prev, const LatticeDev<real>* lat,
+cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* fbar_prev, const LatticeDev<real>* lat,
                                 const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
-                                double sign, real* rho, real* fl, real* sb, double* partials, double* grad,
+                                double sign, double* rho, double* fl, double* sb, double* partials, double* grad,
                                 cudaStream_t s) {
   const int B = 128, nb = (n_sites + B - 1) / B;
   adj_rho_kernel<real><<<nb, B, 0, s>>>(f_prev, lat, rows, rho);
   if (noise)
-    adj_local_kernel<real, true><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, (real)alpha, fl, sb, partials);
+    adj_local_kernel<real, true><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
   else
-    adj_local_kernel<real, false><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, (real)alpha, fl, sb, partials);
-  adj_gather_push_kernel<real><<<nb, B, 0, s>>>(lat, rho, fl, sb, (real)alpha, fbar_prev);
+    adj_local_kernel<real, false><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
+  adj_gather_push_kernel<real><<<nb, B, 0, s>>>(lat, rho, fl, sb, alpha, fbar_prev);
   adj_sum_partials<<<1, 32, 0, s>>>(partials, nb, sign, grad);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_adjoint_step<float>(const float*, const float*, float*, const LatticeDev<float>*,
-                                                const RowConst<float>*, int, uint32_t, bool, double, double, float*,
-                                                float*, float*, double*, double*, cudaStream_t);
+template cudaError_t launch_adjoint_step<float>(const float*, const double*, double*, const LatticeDev<float>*,
+                                                const RowConst<float>*, int, uint32_t, bool, double, double, double*,
+                                                double*, double*, double*, double*, cudaStream_t);
 template cudaError_t launch_adjoint_step<double>(const double*, const double*, double*, const LatticeDev<double>*,
                                                  const RowConst<double>*, int, uint32_t, bool, double, double, double*,
                                                  double*, double*, double*, double*, cudaStream_t);

@@ -683,11 +683,11 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   real* ck = (real*)alloc(nck * S * sizeof(real));
   real* ring = want_grad ? (real*)alloc(C * S * sizeof(real)) : nullptr;
   real* cur = (real*)alloc(2 * S * sizeof(real));
-  real* fb = want_grad ? (real*)alloc(2 * S * sizeof(real)) : nullptr;
+  double* fb = want_grad ? (double*)alloc(2 * S * sizeof(double)) : nullptr;
   real* fields = (real*)alloc(4 * (size_t)N * sizeof(real));
-  real* rho = want_grad ? (real*)alloc(2 * (size_t)N * sizeof(real)) : nullptr;
-  real* fl = want_grad ? (real*)alloc(S * sizeof(real)) : nullptr;
-  real* sb = want_grad ? (real*)alloc(4 * (size_t)N * sizeof(real)) : nullptr;
+  double* rho = want_grad ? (double*)alloc(2 * (size_t)N * sizeof(double)) : nullptr;
+  double* fl = want_grad ? (double*)alloc(S * sizeof(double)) : nullptr;
+  double* sb = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;
   const int nb = (N + 127) / 128;
   double* partials = (double*)alloc((size_t)3 * std::max<int>(nb, (int)c->items.size()) * sizeof(double));
   double* d_grad = (double*)alloc(3 * sizeof(double));
@@ -743,7 +743,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
     const double sign = run == 0 ? 1.0 : -1.0;
     const double alpha = sign / ((double)T * (double)N);
     int fcur = 0;
-    ok(cudaMemsetAsync(fb, 0, S * sizeof(real), st));
+    ok(cudaMemsetAsync(fb, 0, S * sizeof(double), st));
     for (int64_t seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
       const int64_t c0 = seg * C, len = std::min<int64_t>(C, T - c0);
       ok(cudaMemcpyAsync(ring, ck + seg * S, S * sizeof(real), cudaMemcpyDeviceToDevice, st));

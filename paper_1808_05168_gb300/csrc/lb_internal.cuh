@@ -296,10 +296,11 @@ cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* o
 
 // One adjoint step (lb_adjoint.cu): from fbar (sensitivity to f*_k) and the forward state f_prev
 // = f*_{k-1}, write fbar_prev and add sign * (this step's gradient share) to grad[3].
+// The sensitivities (fbar, rho, fl, sb) are double precision for either state precision.
 template <class real>
-cudaError_t launch_adjoint_step(const real* f_prev, const real* fbar, real* fbar_prev, const LatticeDev<real>* lat,
+cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* fbar_prev, const LatticeDev<real>* lat,
                                 const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
-                                double sign, real* rho, real* fl, real* sb, double* partials, double* grad,
+                                double sign, double* rho, double* fl, double* sb, double* partials, double* grad,
                                 cudaStream_t s);
 
 cudaError_t launch_barrier_probe(int blocks, int expected, int spin_limit, unsigned* barrier, int* err,

@@ -38,18 +38,20 @@ def test_checkpoint_interval_does_not_change_the_gradient():
 
 
 def test_noiseless_shift_is_zero():
+    """At kT = 0 both runs coincide: the loss vanishes and so does its gradient, up to the rounding
+    of the two runs' sums (each run's dPbar/dG alone is about rho^A rho^B / 3 = 1/12)."""
     p = LatticeParams(**dict(SMALL, kT=0.0))
     loss, g = gpu_grad(p, 20, 5)
     assert loss == 0.0
-    assert np.all(g == 0.0)
+    assert np.max(np.abs(g)) < 1e-13
 
 
-@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-5), ("dev32", 5e-2)])
-def test_adjoint_matches_central_differences_full_size(prec, rtol):
+def test_adjoint_matches_central_differences_full_size():
     """256 x 128, G = 0.5, wall-to-wall difference 0.5, kT = 1e-5, 2000 steps, checkpoints every
-    100 steps; central differences with step 1e-4 on the same noise."""
+    100 steps; central differences with step 1e-4 on the same noise (FP64 storage: the FP32
+    loss is not resolved to the 1e-10 that a step of 1e-4 needs)."""
     (p,) = workloads.c5()
-    steps, h = 2000, 1e-4
+    steps, h, rtol, prec = 2000, 1e-4, 1e-5, "fp64"
     loss, g = gpu_grad(p, steps, 100, prec)
     fd = []
     for key in ("G", "lambda_s", "lambda_d"):
@@ -61,6 +63,16 @@ def test_adjoint_matches_central_differences_full_size(prec, rtol):
     fd = np.array(fd)
     assert np.all(np.isfinite(g)) and abs(loss) > 0
     np.testing.assert_allclose(g, fd, rtol=0, atol=rtol * np.max(np.abs(fd)))
+
+
+def test_fp32_gradient_follows_fp64_full_size():
+    """The FP32-deviation run's gradient (its own trajectory, transposed in double precision)
+    against the FP64 run's, on the 256 x 128, 2000-step configuration."""
+    (p,) = workloads.c5()
+    l64, g64 = gpu_grad(p, 2000, 100, "fp64")
+    l32, g32 = gpu_grad(p, 2000, 100, "dev32")
+    assert abs(l32 - l64) <= 5e-3 * abs(l64), (l32, l64)
+    np.testing.assert_allclose(g32, g64, rtol=0, atol=2e-2 * np.max(np.abs(g64)))
 
 
 def test_autograd_function():
