@@ -202,7 +202,7 @@ def run_ours(args):
                    "l2": "state 9.6 GB >> 129 MB L2; no flush needed", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": kernel_traffic("dev32_c3"),
-                     "kernel": "lb::step_kernel<float,false,true>", "peak_source": f"hbm_gbs ({peak_kind})",
+                     "kernel": "step_kernel_bulk<float,128,plain,hom noise> (or the tile the autotuner picked)", "peak_source": f"hbm_gbs ({peak_kind})",
                      "kernel_ms": step_kernel_ms, "bytes_per_launch": BYTES_PER_SITE["dev32"] * sites},
         "clocks": clk,
         "gpu_launches": launches,
