@@ -1,0 +1,73 @@
+"""The CUDA path against the paper's closed forms and scaling statements, on seed ensembles
+(statistical tolerances, stated per test).  Set-up of Sec. III: Lx = 4 L, L = 32, kT = 1e-4,
+lambda_s = lambda_d = 1 (D = nu = 1/6 by Eqs. diff and vis), FP32 deviation storage."""
+import numpy as np
+import pytest
+
+from paper_1808_05168_gb300 import LatticeParams, protocols
+
+pytestmark = pytest.mark.gpu
+
+KT = 1e-4
+RATES = dict(lambda_s=1.0, lambda_d=1.0, lambda_e=1.0)
+
+
+def test_equilibrium_spectra_are_flat_fdt_values():
+    """Sec. III.A, Eqs. (VELOCITY_EQ), (CONCENTRATION_EQ): S_U = kT/rho_bar and
+    S_c = 3 (kT/rho_bar) c_bar (1 - c_bar) = 0.75 kT, flat along q = (q, 0) and (0, q); the density
+    spectrum of an ideal gas with sound speed^2 1/3 is 3 kT rho_bar (derived)."""
+    base = LatticeParams(128, 32, kT=KT, G=0.0, grad_c0=0.0, **RATES)
+    sp = protocols.ensemble_spectra(base, range(100, 132), steps=22000, discard=2000, every=10)
+    for f, w in [("ux", KT), ("uz", KT), ("c", 0.75 * KT), ("rho", 3 * KT)]:
+        S = sp[f][0].copy()
+        S[0, 0] = np.nan
+        assert abs(np.nanmean(S) / w - 1) < 0.01, f
+        along_x = np.nanmean(S, axis=0)[1:] / w
+        along_z = np.nanmean(S, axis=1)[1:] / w
+        assert np.max(np.abs(along_x - 1)) < 0.02, (f, along_x)
+        assert np.max(np.abs(along_z - 1)) < 0.02, (f, along_z)
+
+
+def test_nonequilibrium_spectra():
+    """Sec. III.B: with grad c_0 = 0.01 the velocity spectra keep their equilibrium value, while
+    S_c(q, 0) = 0.75 kT [1 + phi S_NE(q L)] with phi of Eq. (prefactor) grows at small q and
+    approaches the unbounded law S_NE = (qL)^-4 at large qL without fit parameters (below it at
+    small qL, the effect of confinement)."""
+    base = LatticeParams(128, 32, kT=KT, G=0.0, grad_c0=0.01, **RATES)
+    sp = protocols.ensemble_spectra(base, range(200, 264), steps=42000, discard=2000, every=10,
+                                    fields=("c", "ux", "uz"))
+    for f in ("ux", "uz"):
+        S = sp[f][0][:, 1:]
+        assert abs(S.mean() / KT - 1) < 0.01, f
+    D = nu = (1 / 1.0 - 0.5) / 3
+    phi = (1 / 3) * 32 ** 4 * 0.01 ** 2 / (0.5 * 0.5 * (nu + D) * D)
+    enh = sp["c"][0][0] / (0.75 * KT) - 1
+    err = sp["c"][1][0] / (0.75 * KT)
+    qt = 2 * np.pi * np.arange(128) / 128 * 32
+    bulk = phi * qt[1:] ** -4.0
+    ratio = enh[1:12] / bulk[:11]
+    assert enh[1] > 3.0                                  # strong enhancement at qL ~ 1.6
+    assert np.all(np.diff(enh[1:12]) < 0)                # decreasing in q
+    assert np.all(np.diff(ratio[2:10]) > -0.05)          # approaching the bulk law
+    k = np.arange(9, 12)                                  # qL = 14.1 .. 17.3
+    mean_ratio = enh[k].sum() / (phi * qt[k] ** -4.0).sum()
+    sigma = np.sqrt((err[k] ** 2).sum()) / (phi * qt[k] ** -4.0).sum()
+    assert abs(mean_ratio - 1) < 0.15 + 3 * sigma, (mean_ratio, sigma)
+
+
+def test_nonequilibrium_pressure_protocol():
+    """Sec. III.C, Eqs. (EQP), (NEQP): the NE pressure vanishes for an ideal mixture (G = 0), is
+    present for G = 0.3, and depends on the gradient and size only through the wall-to-wall
+    difference in 2D (P_NE ~ (grad c_0)^2 L^2): L = 32 and L = 64 agree at fixed difference."""
+    b32 = LatticeParams(128, 32, G=0.3, **RATES)
+    b64 = LatticeParams(256, 64, G=0.3, **RATES)
+    ideal = protocols.ne_pressure(LatticeParams(128, 32, G=0.0, **RATES), KT, 0.32 / 32, range(1000, 1512),
+                                  steps=40000, discard=4000)
+    assert abs(ideal["P_ne"]) < 3 * ideal["stderr"], ideal
+    r32 = protocols.ne_pressure(b32, KT, 0.32 / 32, range(1000, 1512), steps=40000, discard=4000)
+    assert r32["P_ne"] > 5 * r32["stderr"], r32
+    r64 = protocols.ne_pressure(b64, KT, 0.32 / 64, range(1000, 1256), steps=60000, discard=10000)
+    assert r64["P_ne"] > 5 * r64["stderr"], r64
+    assert abs(r64["P_ne"] - r32["P_ne"]) < 3 * np.hypot(r32["stderr"], r64["stderr"]), (r32, r64)
+    # the equilibrium thermal shift dP_eq is present and G-dependent only weakly
+    assert ideal["dP_eq"] > 0 and r32["dP_eq"] > 0
