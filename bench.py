@@ -140,8 +140,10 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    from paper_1808_05168_gb300.ensemble import seeds_for_rank
+
     P = LB_STEPS_PER_STEP
-    lattices = workloads.c3(seed0=1000 + 64 * rank)
+    lattices = workloads.c3(seed0=seeds_for_rank(rank, 64).start)
     sites = workloads.sites(lattices)
     stream = torch.cuda.Stream()
     sim = Simulation(lattices, precision="dev32", graph=True, autotune=True)
