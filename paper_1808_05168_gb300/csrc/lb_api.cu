@@ -148,10 +148,13 @@ LatticeDev<real> make_lattice(const lb_params& p, int flags, bool dev, int64_t f
   L.lattice_id = p.lattice_id;
   const double lam[9] = {1.0, p.lambda_d, p.lambda_d, p.lambda_e, p.lambda_s, p.lambda_s, p.lambda_q, p.lambda_q,
                          p.lambda_eps};
+  bool unit = true;
   for (int a = 0; a < 9; ++a) {
     L.lam[a] = (real)lam[a];
     L.omh[a] = (real)(1.0 - 0.5 * lam[a]);
+    if (a >= 3 && lam[a] != 1.0) unit = false;
   }
+  if (unit) L.flags |= DF_UNIT;
   L.G = (real)p.G;
   L.g3 = (real)(p.grad_c0 / 3.0);
   L.k9 = dev ? (real)(kRhoBar * p.grad_c0 / 9.0) : (real)0;
@@ -166,6 +169,19 @@ LatticeDev<real> make_lattice(const lb_params& p, int flags, bool dev, int64_t f
     const double v = 3.0 * (2.0 - lam[a]) * lam[a] * kNorm[a] * p.kT;
     L.sig[a] = (real)std::sqrt(v * rA);
     L.pref[a] = (real)std::sqrt(v);
+  }
+  // folded coefficients (see LatticeDev::kA): constant factors of m^eq_3 (3), S_3 (6), S_4 (2)
+  const bool loc = flags & LB_NOISE_LOC;
+  for (int a = 0; a < 9; ++a) {
+    const double invN = 1.0 / kNorm[a];
+    const double qf = a == 3 ? 3.0 : 1.0, sf = a == 3 ? 6.0 : (a == 4 ? 2.0 : 1.0);
+    L.kA[a] = (real)((1.0 - lam[a]) * invN);
+    L.kB[a] = (real)(a >= 1 && a <= 5 ? lam[a] * qf * invN : 0.0);
+    L.kC[a] = (real)(a >= 1 && a <= 5 ? (1.0 - 0.5 * lam[a]) * sf * invN : 0.0);
+    double sig = 0.0;
+    if (a == 1 || a == 2) sig = loc ? std::sqrt((2.0 - ld) * ld * p.kT) : std::sqrt((2.0 - ld) * ld * p.kT * rA * rB / (rA + rB));
+    else if (a >= 3) sig = std::sqrt(3.0 * (2.0 - lam[a]) * lam[a] * kNorm[a] * p.kT * (loc ? 1.0 : rA));
+    L.kN[a] = (real)(sig * invN);
   }
   return L;
 }

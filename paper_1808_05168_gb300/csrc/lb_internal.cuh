@@ -20,7 +20,8 @@ namespace lbk {
 #define LB_OPP(l) ((l) == 0 ? 0 : ((l) <= 4 ? (((l) + 1) % 4) + 1 : (((l) - 3) % 4) + 5))
 
 // Device-level flag bits (subset of the public flags that kernels look at).
-enum : int { DF_ASTAR = 1, DF_WALL_FIXED = 2, DF_NOISE_LOC = 4, DF_NOISE = 8 };
+// DF_UNIT: the rates of moments 3..8 are all exactly 1 (the step kernels then skip those moments).
+enum : int { DF_ASTAR = 1, DF_WALL_FIXED = 2, DF_NOISE_LOC = 4, DF_NOISE = 8, DF_UNIT = 16 };
 
 // Noise variants of the step kernel.
 enum : int { NOISE_OFF = 0, NOISE_HOM = 1, NOISE_LOC = 2 };
@@ -46,6 +47,11 @@ struct LatticeDev {
                      // reference densities of both species are rho_bar / 2 (c_bar0 = 1/2)
   real pref_mom;     // loc noise: sqrt((2 - l_d) l_d kT)
   real pref[9];      // loc noise: sqrt(3 (2 - l_a) l_a N_a kT)
+  // Eq. MRT divided by N_a, as used by the step kernels: m*_a / N_a = kA[a] m_a + kB[a] q_a +
+  // kC[a] s_a + kN[a] n_a, with q_a, s_a the equilibrium and forcing moments without their
+  // constant factors (q_3 = rho |U|^2, s_3 = U.F, s_4 = U_x F_x - U_z F_z) and n_a a standard
+  // normal (kN: hom amplitudes; for loc, times sqrt of the local density)
+  real kA[9], kB[9], kC[9], kN[9];
 };
 
 // Per-row constants of the background (zero in FP64 mode), rows 0..Lz-1.
@@ -188,11 +194,11 @@ __device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, doubl
 }
 
 template <class real>
-__device__ __forceinline__ real rsqrt_pos(real v);
+__device__ __forceinline__ real sqrt_pos(real v);
 template <>
-__device__ __forceinline__ float rsqrt_pos<float>(float v) { return sqrtf(v); }
+__device__ __forceinline__ float sqrt_pos<float>(float v) { return sqrtf(v); }
 template <>
-__device__ __forceinline__ double rsqrt_pos<double>(double v) { return sqrt(v); }
+__device__ __forceinline__ double sqrt_pos<double>(double v) { return sqrt(v); }
 
 // Host-side launch helpers implemented in lb_step.cu / lb_diag.cu.
 template <class real>

@@ -221,11 +221,11 @@ __device__ __forceinline__ Mom<real> moments(const real v[9]) {
   return m;
 }
 
-// Constants of one lattice the site update needs, in registers.
+// Constants of one lattice the site update needs, in registers (unused ones are never loaded).
 template <class real>
 struct SiteK {
-  real G, g3, ld, le, ls, lq, leps, od, oe, os, rho_bar_off;
-  real sg[7];  // noise amplitudes (moments 1-2, then 3..8)
+  real G, g3, rho_bar_off;
+  real kA[9], kB[9], kC[9], kN[9];  // folded collision coefficients, as in LatticeDev
   uint32_t key0, key1, lid;
 };
 
@@ -234,23 +234,25 @@ __device__ __forceinline__ SiteK<real> site_constants(const LatticeDev<real>& L)
   SiteK<real> K;
   K.G = L.G;
   K.g3 = L.g3;
-  K.ld = L.lam[1];
-  K.le = L.lam[3];
-  K.ls = L.lam[4];
-  K.lq = L.lam[6];
-  K.leps = L.lam[8];
-  K.od = L.omh[1];
-  K.oe = L.omh[3];
-  K.os = L.omh[4];
   K.rho_bar_off = L.rho_bar_off;
-  K.sg[0] = (NOISE == NOISE_LOC) ? L.pref_mom : L.sig_mom;
 #pragma unroll
-  for (int k = 3; k < 9; ++k) K.sg[k - 2] = (NOISE == NOISE_LOC) ? L.pref[k] : L.sig[k];
+  for (int a = 0; a < 9; ++a) {
+    K.kA[a] = L.kA[a];
+    K.kB[a] = L.kB[a];
+    K.kC[a] = L.kC[a];
+    K.kN[a] = L.kN[a];
+  }
   K.key0 = L.key0;
   K.key1 = L.key1;
   K.lid = L.lattice_id;
   return K;
 }
+
+// Compile-time flag for the two variants of the site update.
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
 
 // Output of one post-collision population: a streaming store to the lattice, or a store to the
 // shared output row (compile-time stride) that a bulk copy writes back.
@@ -261,22 +263,50 @@ __device__ __forceinline__ void put(real* out, int stride, int l, real v) {
 }
 
 // Collision of one species in moment space (Eq. MRT) with second-order forcing and noise, and
-// the inverse transform f_l = w_l sum_a T_al m*_a / N_a.
-template <class real, bool TO_GLOBAL, int STRIDE>
+// the inverse transform f_l = w_l sum_a T_al m*_a / N_a.  Relaxation, forcing and noise factors
+// and 1/N_a are folded into the per-lattice coefficients kA..kN; moments 1-2 share theirs (both
+// relax at l_d), as do 6-7 (l_Q).  UNIT: the rates of moments 3..8 are 1, so their pre-collision
+// values drop out (kA = 0) and are never formed.  nz[1..8]: the standard normals of this
+// species' moments; cm, cq: their amplitude factors for moments 1-2 and 3-8 (sign and local
+// density; +-1 and 1 for hom noise).
+template <class real, int NOISE, bool UNIT, bool TO_GLOBAL, int STRIDE>
 __device__ __forceinline__ void collide_out(const Mom<real>& m, real d, real rs, real Ux, real Uz, real Fx, real Fz,
-                                            const SiteK<real>& K, const real xi[9], real* out, int stride) {
-  const real UxUx = Ux * Ux, UzUz = Uz * Uz;
-  const real s1 = m.m1 + K.ld * (rs * Ux - m.m1) + K.od * Fx + xi[1];
-  const real s2 = m.m2 + K.ld * (rs * Uz - m.m2) + K.od * Fz + xi[2];
-  const real s3 = m.m3 + K.le * (3 * rs * (UxUx + UzUz) - m.m3) + K.oe * (6 * (Ux * Fx + Uz * Fz)) + xi[3];
-  const real s4 = m.m4 + K.ls * (rs * (UxUx - UzUz) - m.m4) + K.os * (2 * (Ux * Fx - Uz * Fz)) + xi[4];
-  const real s5 = m.m5 + K.ls * (rs * Ux * Uz - m.m5) + K.os * (Ux * Fz + Uz * Fx) + xi[5];
-  const real s6 = m.m6 - K.lq * m.m6 + xi[6];
-  const real s7 = m.m7 - K.lq * m.m7 + xi[7];
-  const real s8 = m.m8 - K.leps * m.m8 + xi[8];
-  // divide by N_a = (1, 1/3, 1/3, 4, 4/9, 1/9, 2/3, 2/3, 16)
-  const real M0 = d, M1 = 3 * s1, M2 = 3 * s2, M3 = real(0.25) * s3, M4 = real(2.25) * s4, M5 = 9 * s5,
-             M6 = real(1.5) * s6, M7 = real(1.5) * s7, M8 = real(0.0625) * s8;
+                                            const SiteK<real>& K, const real nz[9], real cm, real cq, real* out,
+                                            int stride) {
+  const real UxUx = Ux * Ux, UzUz = Uz * Uz, UxUz = Ux * Uz;
+  const real r1 = K.kB[1] * rs;
+  real M1 = K.kA[1] * m.m1 + r1 * Ux + K.kC[1] * Fx;
+  real M2 = K.kA[1] * m.m2 + r1 * Uz + K.kC[1] * Fz;
+  real M3 = (K.kB[3] * rs) * (UxUx + UzUz) + K.kC[3] * (Ux * Fx + Uz * Fz);
+  real M4 = (K.kB[4] * rs) * (UxUx - UzUz) + K.kC[4] * (Ux * Fx - Uz * Fz);
+  real M5 = (K.kB[5] * rs) * UxUz + K.kC[5] * (Ux * Fz + Uz * Fx);
+  real M6 = 0, M7 = 0, M8 = 0;
+  if (!UNIT) {
+    M3 += K.kA[3] * m.m3;
+    M4 += K.kA[4] * m.m4;
+    M5 += K.kA[5] * m.m5;
+    M6 = K.kA[6] * m.m6;
+    M7 = K.kA[6] * m.m7;
+    M8 = K.kA[8] * m.m8;
+  }
+  if (NOISE != NOISE_OFF) {
+    const real a1 = K.kN[1] * cm, a6 = K.kN[6] * cq, a8 = K.kN[8] * cq;
+    M1 += a1 * nz[1];
+    M2 += a1 * nz[2];
+    M3 += (K.kN[3] * cq) * nz[3];
+    M4 += (K.kN[4] * cq) * nz[4];
+    M5 += (K.kN[5] * cq) * nz[5];
+    if (UNIT) {
+      M6 = a6 * nz[6];
+      M7 = a6 * nz[7];
+      M8 = a8 * nz[8];
+    } else {
+      M6 += a6 * nz[6];
+      M7 += a6 * nz[7];
+      M8 += a8 * nz[8];
+    }
+  }
+  const real M0 = d;
   const real c9 = real(1) / 9, c36 = real(1) / 36;
   const real base4 = M0 + M3 - 4 * M8;
   const real base5 = M0 + 4 * M3 + 8 * M8;
@@ -323,7 +353,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Everything of one site after its moments and the neighbour densities are known: forces,
 // velocity, optional sampling, noise, collision of both species and the output.
-template <class real, bool SAMPLE, int NOISE, bool TO_GLOBAL, int STRIDE>
+template <class real, bool SAMPLE, int NOISE, bool UNIT, bool TO_GLOBAL, int STRIDE>
 __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& mA,
                                             const Mom<real>& mB, real dA, real dB, const real* ringA,
                                             const real* ringB, int bc, int bu, int bd, uint32_t site, uint32_t step,
@@ -386,12 +416,13 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
     fl[2 * LzLx] = Ux;
     fl[3 * LzLx] = Uz;
   }
-  real xiA[9], xiB[9];
+  real nA[9], nB[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    xiA[k] = 0;
-    xiB[k] = 0;
+    nA[k] = 0;
+    nB[k] = 0;
   }
+  real cmA = 1, cmB = -1, cqA = 1, cqB = 1;  // momentum noise is equal and opposite in A and B
   if (NOISE != NOISE_OFF) {
     U4 w[4];
     philox_site(site, step, K.lid, K.key0, K.key1, w);
@@ -403,24 +434,22 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
     normal_pair<real>(w[2].x, w[2].y, n[8], n[9]);
     normal_pair<real>(w[2].z, w[2].w, n[10], n[11]);
     normal_pair<real>(w[3].x, w[3].y, n[12], n[13]);
-    real smom = K.sg[0], qA = 1, qB = 1;
     if (NOISE == NOISE_LOC) {
-      smom = K.sg[0] * rsqrt_pos<real>(rhoA * rhoB * inv);
-      qA = rsqrt_pos<real>(rhoA);
-      qB = rsqrt_pos<real>(rhoB);
+      cmA = sqrt_pos<real>(rhoA * rhoB * inv);
+      cmB = -cmA;
+      cqA = sqrt_pos<real>(rhoA);
+      cqB = sqrt_pos<real>(rhoB);
     }
-    xiA[1] = smom * n[0];
-    xiA[2] = smom * n[1];
-    xiB[1] = -xiA[1];
-    xiB[2] = -xiA[2];
+    nA[1] = nB[1] = n[0];
+    nA[2] = nB[2] = n[1];
 #pragma unroll
     for (int k = 3; k < 9; ++k) {
-      xiA[k] = (K.sg[k - 2] * qA) * n[k - 1];
-      xiB[k] = (K.sg[k - 2] * qB) * n[k + 5];
+      nA[k] = n[k - 1];
+      nB[k] = n[k + 5];
     }
   }
-  collide_out<real, TO_GLOBAL, STRIDE>(mA, dA, rhoA, Ux, Uz, FAx, FAz, K, xiA, outA, ostride);
-  collide_out<real, TO_GLOBAL, STRIDE>(mB, dB, rhoB, Ux, Uz, FBx, FBz, K, xiB, outB, ostride);
+  collide_out<real, NOISE, UNIT, TO_GLOBAL, STRIDE>(mA, dA, rhoA, Ux, Uz, FAx, FAz, K, nA, cmA, cqA, outA, ostride);
+  collide_out<real, NOISE, UNIT, TO_GLOBAL, STRIDE>(mB, dB, rhoB, Ux, Uz, FBx, FBz, K, nB, cmB, cqB, outB, ostride);
 }
 
 __device__ __forceinline__ void block_partials(double acc_p, double acc_a, double acc_b, double* red, double* out) {
@@ -593,19 +622,24 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
                 bd = ring_slot(z - 1) * W + tid + 1;
       const real* sb = stage + (z & (NS - 1)) * 18 * W;
       const bool below = z > 0, above = z < Lz - 1;
-      real v[9];
-      read_generic(sb, W, tid + 1, 0, below, above, k9, k36, v);
-      Mom<real> mA = moments(v);
-      read_generic(sb, W, tid + 1, 1, below, above, k9, k36, v);
-      Mom<real> mB = moments(v);
-      if (below && above) {
-        mA.m2 += interior_m2_shift(0, k9, k36);
-        mB.m2 += interior_m2_shift(1, k9, k36);
-      }
       const int r0 = z * Lx + x;
-      site_update<real, SAMPLE, NOISE, true, 0>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
-                                                (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
-                                                acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
+      // both variants are inlined; the branch is uniform over the block (one lattice per item)
+      auto site = [&](auto unit) {
+        real v[9];
+        read_generic(sb, W, tid + 1, 0, below, above, k9, k36, v);
+        Mom<real> mA = moments(v);
+        read_generic(sb, W, tid + 1, 1, below, above, k9, k36, v);
+        Mom<real> mB = moments(v);
+        if (below && above) {
+          mA.m2 += interior_m2_shift(0, k9, k36);
+          mB.m2 += interior_m2_shift(1, k9, k36);
+        }
+        site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
+            K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd, (uint32_t)r0, step,
+            a.fields + 4 * L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
+      };
+      if (flags & DF_UNIT) site(BoolC<true>());
+      else site(BoolC<false>());
     }
   }
   cp_wait<0>();  // nothing may land in shared memory after the item
@@ -788,19 +822,24 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
                 bd = ring_slot(z - 1) * W + tid + 1;
       const real* sb = instage + (z % NSI) * 18 * SW;
       const bool below = z > 0, above = z < Lz - 1;
-      real v[9];
-      read_bulk<real, SW>(sb, tid + PAD, 0, below, above, k9, k36, v);
-      Mom<real> mA = moments(v);
-      read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
-      Mom<real> mB = moments(v);
-      if (below && above) {
-        mA.m2 += interior_m2_shift(0, k9, k36);
-        mB.m2 += interior_m2_shift(1, k9, k36);
-      }
       const int r0 = z * Lx + x;
-      site_update<real, SAMPLE, NOISE, true, 0>(K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd,
-                                                (uint32_t)r0, step, a.fields + 4 * L.site_off + r0, LzLx, acc_p,
-                                                acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
+      // both variants are inlined; the branch is uniform over the block (one lattice per item)
+      auto site = [&](auto unit) {
+        real v[9];
+        read_bulk<real, SW>(sb, tid + PAD, 0, below, above, k9, k36, v);
+        Mom<real> mA = moments(v);
+        read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
+        Mom<real> mB = moments(v);
+        if (below && above) {
+          mA.m2 += interior_m2_shift(0, k9, k36);
+          mB.m2 += interior_m2_shift(1, k9, k36);
+        }
+        site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
+            K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd, (uint32_t)r0, step,
+            a.fields + 4 * L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
+      };
+      if (flags & DF_UNIT) site(BoolC<true>());
+      else site(BoolC<false>());
     }
   }
   if (!ok) {
