@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--profile-precision", default="dev32", choices=["dev32", "fp64"])
     ap.add_argument("--profile-generic", action="store_true", help="small case with per-thread staging")
     ap.add_argument("--profile-tile", type=int, default=128, help="tile width of the small case")
+    ap.add_argument("--profile-rows", type=int, default=64, help="rows per block of the small case")
     ap.add_argument("--profile-ensemble", type=int, default=0,
                     help="run the ensemble with this many seeds for 6 steps (for ncu captures)")
     return ap.parse_args()
@@ -334,7 +335,7 @@ def run_reference(args):
     }))
 
 
-def run_profile_small(kT, precision, bulk=True, tile=128):
+def run_profile_small(kT, precision, bulk=True, tile=128, rows=64):
     """A small case for ncu: one 4096 x 1024 lattice (302 MB per FP32 state buffer, more than L2),
     6 steps."""
     import torch
@@ -343,7 +344,7 @@ def run_profile_small(kT, precision, bulk=True, tile=128):
 
     p = LatticeParams(4096, 1024, kT=kT, G=0.5, grad_c0=0.5 / 1024, seed=4, lambda_e=1.0)
     with Simulation(p, precision=precision, bulk=bulk) as sim:
-        sim.set_tile(tile, 64)
+        sim.set_tile(tile, rows)
         sim.step(6)
         sim.synchronize()
     torch.cuda.synchronize()
@@ -370,7 +371,8 @@ if __name__ == "__main__":
     if a.profile_ensemble:
         run_profile_ensemble(a.profile_ensemble)
     elif a.profile_small:
-        run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic, tile=a.profile_tile)
+        run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic, tile=a.profile_tile,
+                          rows=a.profile_rows)
     elif a.impl == "reference":
         run_reference(a)
     else:

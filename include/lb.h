@@ -66,6 +66,8 @@ extern "C" {
 #define LB_FIELD_C 1   /* delta c = c - c_0(z)                                              */
 #define LB_FIELD_UX 2  /* U_x of Eq. (bar)                                                  */
 #define LB_FIELD_UZ 3  /* U_z of Eq. (bar)                                                  */
+#define LB_FIELD_P 4   /* mechanical pressure, half the trace of the pressure tensor (profiles
+                          only: lb_profile)                                                 */
 #define LB_SF_QXQZ 0   /* S(q_x, q_z): Lz x Lx doubles, [n][k] at q_z = 2 pi n / Lz,
                           q_x = 2 pi k / Lx                                                 */
 #define LB_SF_QX 1     /* S(q_x, q_z = 0): Lx doubles                                       */
@@ -128,6 +130,14 @@ int lb_lattice_shape(lb_ctx* ctx, int lattice, int* Lx, int* Lz);
  * *n_samples (may be NULL) receives the sample count. */
 int lb_structure_factor(lb_ctx* ctx, int lattice, int field, int mode, double* host_out, size_t n_out,
                         int64_t* n_samples);
+
+/* z-profile of one field of one lattice (Sec. III.C, the average total pressure and density
+ * profiles): for rows j = 0..Lz-1 (height z_j = j + 1/2 - Lz/2), the average over the samples of
+ * the row mean (1/Lx) sum_x phi(x, z_j) of the absolute field phi = rho, c, U_x, U_z (LB_FIELD_RHO,
+ * LB_FIELD_C, LB_FIELD_UX, LB_FIELD_UZ) or the mechanical pressure P (LB_FIELD_P), all taken on
+ * the pre-collision state of the sample steps.  host_out: caller-owned, n_out == Lz doubles, else
+ * LB_ERR_SIZE.  Zeros before the first sample; *n_samples (may be NULL) receives the count. */
+int lb_profile(lb_ctx* ctx, int lattice, int field, double* host_out, size_t n_out, int64_t* n_samples);
 
 /* Spatial mean of the mechanical pressure (Sec. III.C) at the latest sample, and its average
  * over all samples (compensated double-precision sum).  Either pointer may be NULL. */
@@ -201,6 +211,14 @@ void lb_destroy(lb_ctx* ctx);
  * blocks the wait must give up after its spin limit and the call returns LB_ERR_TIMEOUT; with
  * expected == blocks it returns LB_OK. */
 int lb_debug_barrier(int blocks, int expected, int spin_limit);
+
+/* Test hook for the Gaussian noise of the step kernels (Sec. II.B): the Box-Muller normals that
+ * the kernels of precision `precision` (LB_PREC_FP64 or LB_PREC_DEV32) form from Philox word
+ * pairs.  host_words: 2 n_pairs words (a_0, b_0, a_1, b_1, ...), u1 from a_i sets the radius
+ * sqrt(-2 ln u1) and u2 from b_i the angle 2 pi u2, with u = (2 (k mod 2^23) + 1) 2^-24;
+ * host_out: 2 n_pairs doubles, the pair (r cos 2 pi u2, r sin 2 pi u2) of each.  Both buffers are
+ * caller-owned host memory; 0 <= n_pairs <= 2^24, else LB_ERR_BAD_PARAM.  Synchronous. */
+int lb_debug_box_muller(int precision, const uint32_t* host_words, int64_t n_pairs, double* host_out);
 
 #ifdef __cplusplus
 }

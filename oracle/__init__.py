@@ -65,11 +65,14 @@ def _load():
         lib.olb_fields.argtypes = [vp, dp]
         lib.olb_structure_factor.argtypes = [vp, c_int, dp]
         lib.olb_structure_factor.restype = c_i64
+        lib.olb_profile.argtypes = [vp, c_int, dp]
+        lib.olb_profile.restype = c_i64
         lib.olb_mean_pressure.argtypes = [vp, dp, dp]
         lib.olb_mean_pressure.restype = c_i64
         lib.olb_site_noise.argtypes = [vp, c_int, c_int, c_i64, dp]
         lib.olb_philox4x32_10.argtypes = [u32p, u32p, u32p]
         lib.olb_site_normals.argtypes = [c_u64, c_u32, c_u32, c_u32, dp]
+        lib.olb_box_muller.argtypes = [u32p, c_i64, dp]
         lib.olb_basis.argtypes = [dp, dp, dp]
         lib.olb_dft2_power.argtypes = [dp, c_int, c_int, dp]
         lib.olb_pressure_shift_grad.argtypes = create_args + [c_i64, dp, dp]
@@ -85,6 +88,7 @@ def _dptr(a: np.ndarray):
 
 
 FIELDS = {"rho": 0, "c": 1, "ux": 2, "uz": 3}
+PROFILE_FIELDS = {"rho": 0, "c": 1, "ux": 2, "uz": 3, "p": 4}
 
 
 class OracleLattice:
@@ -161,6 +165,14 @@ class OracleLattice:
                                           _dptr(out))
         return out, int(n)
 
+    def profile(self, field):
+        """Time average over the samples of the row means of rho, c, Ux, Uz or P (Sec. III.C
+        profiles), rows 0..Lz-1, and the sample count."""
+        out = np.empty(self.Lz, np.float64)
+        k = PROFILE_FIELDS[field] if isinstance(field, str) else int(field)
+        n = self.lib.olb_profile(self.h, k, _dptr(out))
+        return out, int(n)
+
     def mean_pressure(self):
         last = ctypes.c_double()
         avg = ctypes.c_double()
@@ -186,6 +198,17 @@ def site_normals(seed, lattice_id, site, step):
     lib = _load()
     out = np.empty(16, np.float64)
     lib.olb_site_normals(int(seed), int(lattice_id), int(site), int(step), _dptr(out))
+    return out
+
+
+def box_muller(words) -> np.ndarray:
+    """Box-Muller normals in FP64 of the word pairs (words[2i], words[2i+1]), in that order."""
+    lib = _load()
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(-1))
+    if w.size % 2:
+        raise ValueError("words must hold pairs")
+    out = np.empty(w.size, np.float64)
+    lib.olb_box_muller(w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), w.size // 2, _dptr(out))
     return out
 
 

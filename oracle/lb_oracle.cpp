@@ -145,22 +145,26 @@ void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t 
 // Uniform in (0,1) from the low 23 bits: (2 (k mod 2^23) + 1) 2^-24, exact in float and double.
 double uniform_of(uint32_t k) { return (double)(2u * (k & 0x7FFFFFu) + 1u) * std::ldexp(1.0, -24); }
 
-// Sixteen standard normals for one site and step: Box-Muller on the pairs (u_{2i}, u_{2i+1})
-// of four Philox calls (call = 0..3): n_{2i} = r cos(2 pi u_{2i+1}), n_{2i+1} = r sin(...),
-// r = sqrt(-2 ln u_{2i}).
+// Box-Muller (Sec. II.B draws Gaussian noise; the pairing is the textbook polar form): from the
+// words (a, b), u1 = uniform_of(a), u2 = uniform_of(b), r = sqrt(-2 ln u1) and the two standard
+// normals n0 = r cos(2 pi u2), n1 = r sin(2 pi u2).
+void box_muller(uint32_t a, uint32_t b, double out[2]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double u1 = uniform_of(a), u2 = uniform_of(b);
+  const double r = std::sqrt(-2.0 * std::log(u1));
+  out[0] = r * std::cos(two_pi * u2);
+  out[1] = r * std::sin(two_pi * u2);
+}
+
+// Sixteen standard normals for one site and step: Box-Muller on the word pairs (k_{2i}, k_{2i+1})
+// of four Philox calls (call = 0..3).
 void site_normals(uint64_t seed, uint32_t lattice_id, uint32_t site, uint32_t step, double n[16]) {
   const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
-  const double two_pi = 6.283185307179586476925286766559;
   for (uint32_t call = 0; call < 4; ++call) {
     const uint32_t ctr[4] = {site, step, lattice_id, call};
     uint32_t k[4];
     philox4x32_10(ctr, key, k);
-    for (int pair = 0; pair < 2; ++pair) {
-      const double u1 = uniform_of(k[2 * pair]), u2 = uniform_of(k[2 * pair + 1]);
-      const double r = std::sqrt(-2.0 * std::log(u1));
-      n[4 * call + 2 * pair] = r * std::cos(two_pi * u2);
-      n[4 * call + 2 * pair + 1] = r * std::sin(two_pi * u2);
-    }
+    for (int pair = 0; pair < 2; ++pair) box_muller(k[2 * pair], k[2 * pair + 1], n + 4 * call + 2 * pair);
   }
 }
 
@@ -189,6 +193,8 @@ struct Sim {
   int64_t discard = 0, every = 0, nsamples = 0;
   std::vector<double> S_acc;  // [4][Lz][Lx]: fields rho, c, Ux, Uz
   double P_sum = 0.0, P_last = 0.0;
+  // z-profiles (Sec. III.C): sums over samples of the row means of rho, c, Ux, Uz and P
+  std::vector<double> prof_acc;  // [5][Lz]
   // loss accumulation for the gradient reference: sum over steps of the mean pressure
   bool accumulate_loss = false;
   R loss_sum = R(0.0);
@@ -207,6 +213,7 @@ struct Sim {
             f[idx(s, l, z, x)] = R(B.w[l] * rho_bar * cs);
           }
     S_acc.assign((size_t)4 * Lz * Lx, 0.0);
+    prof_acc.assign((size_t)5 * Lz, 0.0);
   }
 };
 
@@ -428,6 +435,20 @@ void sample(Sim<R>& S, const Pre<R>& P) {
   double mean = 0.0;
   for (int i = 0; i < n; ++i) mean += value_of(p[i]);
   mean /= (double)n;
+  // row means of the absolute fields rho, c, Ux, Uz and of the pressure, one row at a time
+  for (int z = 0; z < Lz; ++z) {
+    double row[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int x = 0; x < Lx; ++x) {
+      const int i = z * Lx + x;
+      const double rA = value_of(P.rho[i]), rB = value_of(P.rho[n + i]);
+      row[0] += rA + rB;
+      row[1] += rA / (rA + rB);
+      row[2] += value_of(P.Ux[i]);
+      row[3] += value_of(P.Uz[i]);
+      row[4] += value_of(p[i]);
+    }
+    for (int k = 0; k < 5; ++k) S.prof_acc[(size_t)k * Lz + z] += row[k] / (double)Lx;
+  }
   S.P_last = mean;
   S.P_sum += mean;
   S.nsamples += 1;
@@ -614,6 +635,14 @@ int64_t olb_structure_factor(void* h, int field, double* out) {
   return S->nsamples;
 }
 
+// Time-averaged row means of field k (0 rho, 1 c, 2 Ux, 3 Uz, 4 P) at rows 0..Lz-1.
+int64_t olb_profile(void* h, int field, double* out) {
+  olb_sim* S = (olb_sim*)h;
+  for (int z = 0; z < S->Lz; ++z)
+    out[z] = S->nsamples ? S->prof_acc[(size_t)field * S->Lz + z] / (double)S->nsamples : 0.0;
+  return S->nsamples;
+}
+
 int64_t olb_mean_pressure(void* h, double* last, double* avg) {
   olb_sim* S = (olb_sim*)h;
   *last = S->P_last;
@@ -640,6 +669,11 @@ void olb_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 
 void olb_site_normals(uint64_t seed, uint32_t lattice_id, uint32_t site, uint32_t step_index, double* out) {
   site_normals(seed, lattice_id, site, step_index, out);
+}
+
+// words: 2 n_pairs values (a_0, b_0, a_1, b_1, ...); out: 2 n_pairs normals in the same order.
+void olb_box_muller(const uint32_t* words, int64_t n_pairs, double* out) {
+  for (int64_t i = 0; i < n_pairs; ++i) box_muller(words[2 * i], words[2 * i + 1], out + 2 * i);
 }
 
 void olb_basis(double* T, double* w, double* N) {

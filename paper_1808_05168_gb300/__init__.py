@@ -43,7 +43,8 @@ class LatticeParams:
                               float(self.grad_c0), int(self.seed), int(self.lattice_id), 0)
 
 
-FIELDS = {"rho": capi.LB_FIELD_RHO, "c": capi.LB_FIELD_C, "ux": capi.LB_FIELD_UX, "uz": capi.LB_FIELD_UZ}
+FIELDS = {"rho": capi.LB_FIELD_RHO, "c": capi.LB_FIELD_C, "ux": capi.LB_FIELD_UX, "uz": capi.LB_FIELD_UZ,
+          "p": capi.LB_FIELD_P}
 
 
 class Simulation:
@@ -127,6 +128,12 @@ class Simulation:
         out = np.empty(Lx if qz0_only else (Lz, Lx), np.float64)
         n = capi.lb_structure_factor(self.h, lattice, FIELDS.get(field, field),
                                      capi.LB_SF_QX if qz0_only else capi.LB_SF_QXQZ, out)
+        return out, n
+
+    def profile(self, field: str = "p", lattice: int = 0):
+        """Time-averaged z-profile (row means over x) of rho, c, ux, uz or p, and the sample count."""
+        out = np.empty(self.shape(lattice)[1], np.float64)
+        n = capi.lb_profile(self.h, lattice, FIELDS.get(field, field), out)
         return out, n
 
     def mean_pressure(self, lattice: int = 0):

@@ -31,7 +31,7 @@ LB_PERSISTENT = 0x20
 LB_AUTOTUNE = 0x40
 LB_NO_BULK = 0x80
 
-LB_FIELD_RHO, LB_FIELD_C, LB_FIELD_UX, LB_FIELD_UZ = 0, 1, 2, 3
+LB_FIELD_RHO, LB_FIELD_C, LB_FIELD_UX, LB_FIELD_UZ, LB_FIELD_P = 0, 1, 2, 3, 4
 LB_SF_QXQZ, LB_SF_QX = 0, 1
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblb_gb300.so")
@@ -39,8 +39,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 # Every symbol declared in include/lb.h.
 EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "lb_set_tile", "lb_get_tile",
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
-           "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
+           "lb_profile", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
+           "lb_debug_box_muller",
            "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient")
 LB_NOALLOC_MAX_POINTS = 1 << 18
 
@@ -93,6 +94,7 @@ def load():
             "lb_lattice_shape": [vp, i, ip, ip],
             "lb_structure_factor": [vp, i, i, i, dp, sz, i64p],
             "lb_mean_pressure": [vp, i, dp, dp],
+            "lb_profile": [vp, i, i, dp, sz, i64p],
             "lb_mass": [vp, i, dp],
             "lb_get_populations": [vp, i, dp, sz],
             "lb_set_populations": [vp, i, dp, sz],
@@ -101,6 +103,7 @@ def load():
             "lb_kernel_launches": [vp, i64p],
             "lb_destroy": [vp],
             "lb_debug_barrier": [i, i, i],
+            "lb_debug_box_muller": [i, ctypes.POINTER(ctypes.c_uint32), i64, dp],
             "lb_power_spectrum": [vp, i, i, vp, vp],
             "lb_power_spectrum_noalloc": [vp, i, i, vp, vp],
             "lb_pressure_shift_gradient": [vp, i64, i64, dp, dp],
@@ -194,6 +197,12 @@ def lb_structure_factor(h, lattice, field, mode, out: np.ndarray):
     return n.value
 
 
+def lb_profile(h, lattice, field, out: np.ndarray):
+    n = ctypes.c_int64()
+    _check(load().lb_profile(h, int(lattice), int(field), _dptr(out), out.size, ctypes.byref(n)), "lb_profile")
+    return n.value
+
+
 def lb_mean_pressure(h, lattice):
     last, avg = ctypes.c_double(), ctypes.c_double()
     _check(load().lb_mean_pressure(h, int(lattice), ctypes.byref(last), ctypes.byref(avg)), "lb_mean_pressure")
@@ -264,3 +273,14 @@ def lb_pressure_shift_gradient(h, steps, ckpt_every, want_grad=True):
 
 def lb_debug_barrier(blocks, expected, limit_ms):
     return int(load().lb_debug_barrier(int(blocks), int(expected), int(limit_ms)))
+
+
+def lb_debug_box_muller(precision, words):
+    """Normals (2 per word pair) that the step kernels of `precision` form; see include/lb.h."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(-1))
+    if w.size % 2:
+        raise ValueError("words must hold pairs")
+    out = np.empty(w.size, np.float64)
+    _check(load().lb_debug_box_muller(int(precision), w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                      w.size // 2, _dptr(out)), "lb_debug_box_muller")
+    return out

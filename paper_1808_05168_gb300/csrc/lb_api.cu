@@ -60,6 +60,10 @@ struct lb_ctx {
   int d_items_cap = 0;
   void* f[2] = {nullptr, nullptr};
   void* fields = nullptr;   // 4 * n_sites reals
+  void* pfield = nullptr;   // n_sites reals: sampled pressure
+  double* prof_sum = nullptr;   // 5 * n_rows: z-profiles
+  double* prof_comp = nullptr;
+  int* d_row_lat = nullptr;     // n_rows: lattice of each global row
   void* tmp = nullptr;      // 4 * n_sites complex
   double* acc_sum = nullptr;
   double* acc_comp = nullptr;
@@ -246,6 +250,7 @@ int upload_tables(lb_ctx* c) {
     d.Lx = p.Lx;
     d.Lz = p.Lz;
     d.site_off = c->site_off[i];
+    d.row_off = c->row_off[i];
     d.P_bg_mean = Pbg / p.Lz;
     d.mass_bg[0] = mA * p.Lx;
     d.mass_bg[1] = mB * p.Lx;
@@ -325,6 +330,10 @@ int alloc_diag(lb_ctx* c) {
   if (c->diag_ready) return LB_OK;
   const size_t rs = c->dev32 ? sizeof(float) : sizeof(double);
   int rc = dev_alloc(c, (char**)&c->fields, 4 * (size_t)c->n_sites * rs);
+  if (!rc) rc = dev_alloc(c, (char**)&c->pfield, (size_t)c->n_sites * rs);
+  if (!rc) rc = dev_alloc(c, &c->prof_sum, 5 * (size_t)c->n_rows * sizeof(double));
+  if (!rc) rc = dev_alloc(c, &c->prof_comp, 5 * (size_t)c->n_rows * sizeof(double));
+  if (!rc) rc = dev_alloc(c, &c->d_row_lat, (size_t)c->n_rows * sizeof(int));
   if (!rc) rc = dev_alloc(c, (char**)&c->tmp, 4 * (size_t)c->n_sites * 2 * rs);
   if (!rc) rc = dev_alloc(c, &c->acc_sum, 4 * (size_t)c->n_sites * sizeof(double));
   if (!rc) rc = dev_alloc(c, &c->acc_comp, 4 * (size_t)c->n_sites * sizeof(double));
@@ -348,6 +357,13 @@ int alloc_diag(lb_ctx* c) {
     return LB_ERR_CUDA;
   c->n_row_tasks = (int)rt.size();
   c->n_col_tasks = (int)ct.size();
+  std::vector<int> row_lat(c->n_rows);
+  for (int i = 0; i < c->n_lat; ++i)
+    for (int z = 0; z < c->params[i].Lz; ++z) row_lat[c->row_off[i] + z] = i;
+  if (cudaMemcpy(c->d_row_lat, row_lat.data(), row_lat.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->prof_sum, 0, 5 * (size_t)c->n_rows * sizeof(double)) != cudaSuccess ||
+      cudaMemset(c->prof_comp, 0, 5 * (size_t)c->n_rows * sizeof(double)) != cudaSuccess)
+    return LB_ERR_CUDA;
   if (cudaMemset(c->acc_sum, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess ||
       cudaMemset(c->acc_comp, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess)
     return LB_ERR_CUDA;
@@ -371,6 +387,7 @@ StepArgs<real> step_args(lb_ctx* c, int cur, int t_offset) {
   a.d_t = c->d_t;
   a.t_offset = t_offset;
   a.fields = (real*)c->fields;
+  a.pfield = (real*)c->pfield;
   a.partials = c->partials;
   a.err = c->d_err;
   return a;
@@ -389,7 +406,10 @@ cudaError_t enqueue_sample(lb_ctx* c) {
   p.col_strip = c->col_strip;
   cudaError_t e = launch_sf<real>(p, (const real*)c->fields, c->tmp, c->acc_sum, c->acc_comp, c->stream);
   if (e != cudaSuccess) return e;
-  c->launches += 3;
+  e = launch_profiles<real>(c->d_diag, c->d_row_lat, c->n_rows, (const real*)c->fields, (const real*)c->pfield,
+                            c->prof_sum, c->prof_comp, c->stream);
+  if (e != cudaSuccess) return e;
+  c->launches += 4;
   return launch_finalize(c->d_diag, c->n_lat, c->partials, c->stats, c->stream);
 }
 
@@ -701,6 +721,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   real* cur = (real*)alloc(2 * S * sizeof(real));
   double* fb = want_grad ? (double*)alloc(2 * S * sizeof(double)) : nullptr;
   real* fields = (real*)alloc(4 * (size_t)N * sizeof(real));
+  real* pfield = (real*)alloc((size_t)N * sizeof(real));
   double* rho = want_grad ? (double*)alloc(2 * (size_t)N * sizeof(double)) : nullptr;
   double* fl = want_grad ? (double*)alloc(S * sizeof(double)) : nullptr;
   double* sb = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;
@@ -709,7 +730,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   double* d_grad = (double*)alloc(3 * sizeof(double));
   DiagStats* stats = (DiagStats*)alloc(sizeof(DiagStats));
   int64_t* zero_t = (int64_t*)alloc(sizeof(int64_t));
-  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb)) || !cur || !fields || !partials || !d_grad || !stats ||
+  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb)) || !cur || !fields || !pfield || !partials || !d_grad || !stats ||
       !zero_t) {
     release();
     return LB_ERR_OOM;
@@ -727,6 +748,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
     a.d_t = zero_t;
     a.t_offset = (int)k;
     a.fields = fields;
+    a.pfield = pfield;
     a.partials = partials;
     return a;
   };
@@ -933,6 +955,36 @@ int lb_structure_factor(lb_ctx* c, int lattice, int field, int mode, double* out
   return LB_OK;
 }
 
+int lb_profile(lb_ctx* c, int lattice, int field, double* out, size_t n_out, int64_t* n_samples) {
+  if (!lattice_ok(c, lattice) || field < 0 || field > LB_FIELD_P || !out) return LB_ERR_BAD_PARAM;
+  const lb_params& p = c->params[lattice];
+  if (n_out != (size_t)p.Lz) return LB_ERR_SIZE;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  if (n_samples) *n_samples = c->nsamples;
+  if (!c->diag_ready || c->nsamples == 0) {
+    std::fill(out, out + p.Lz, 0.0);
+    return LB_OK;
+  }
+  const size_t off = (size_t)field * c->n_rows + c->row_off[lattice];
+  std::vector<double> s(p.Lz), k(p.Lz);
+  if (cudaMemcpy(s.data(), c->prof_sum + off, p.Lz * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(k.data(), c->prof_comp + off, p.Lz * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LB_ERR_CUDA;
+  // the accumulated row means are of deviations: add rho_bar, c_0(z) or the row's background
+  // pressure (zero in FP64 mode) back
+  const std::vector<RowD> rd = make_rows(p, c->flags, c->dev32);
+  const double inv = 1.0 / (double)c->nsamples;
+  for (int z = 0; z < p.Lz; ++z) {
+    double v = (s[z] + k[z]) * inv;
+    if (field == LB_FIELD_RHO) v += kRhoBar;
+    else if (field == LB_FIELD_C) v += rd[z].c0;
+    else if (field == LB_FIELD_P) v += rd[z].Pbg;
+    out[z] = v;
+  }
+  return LB_OK;
+}
+
 int lb_mean_pressure(lb_ctx* c, int lattice, double* last, double* time_avg) {
   if (!lattice_ok(c, lattice)) return LB_ERR_BAD_PARAM;
   int rc = sync_and_check(c);
@@ -1003,7 +1055,9 @@ int lb_reset_statistics(lb_ctx* c) {
   if (cudaMemset(c->stats, 0, c->n_lat * sizeof(DiagStats)) != cudaSuccess) return LB_ERR_CUDA;
   if (c->diag_ready) {
     if (cudaMemset(c->acc_sum, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess ||
-        cudaMemset(c->acc_comp, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess)
+        cudaMemset(c->acc_comp, 0, 4 * (size_t)c->n_sites * sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->prof_sum, 0, 5 * (size_t)c->n_rows * sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->prof_comp, 0, 5 * (size_t)c->n_rows * sizeof(double)) != cudaSuccess)
       return LB_ERR_CUDA;
   }
   return LB_OK;
@@ -1043,7 +1097,8 @@ void lb_destroy(lb_ctx* c) {
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   void* ptrs[] = {c->d_lat,   c->d_rows,     c->d_items,    c->f[0],      c->f[1],       c->fields,
                   c->tmp,     c->acc_sum,    c->acc_comp,   c->partials,  c->stats,      c->d_diag,
-                  c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass};
+                  c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass,
+                  c->pfield, c->prof_sum, c->prof_comp, c->d_row_lat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -1119,6 +1174,32 @@ int lb_debug_barrier(int blocks, int expected, int spin_limit) {
   if (!rc && h) rc = LB_ERR_TIMEOUT;
   cudaFree(bar);
   cudaFree(err);
+  return rc;
+}
+
+int lb_debug_box_muller(int precision, const uint32_t* host_words, int64_t n_pairs, double* host_out) {
+  if ((precision != LB_PREC_FP64 && precision != LB_PREC_DEV32) || n_pairs < 0 || n_pairs > (int64_t(1) << 24))
+    return LB_ERR_BAD_PARAM;
+  if (n_pairs == 0) return LB_OK;
+  if (!host_words || !host_out) return LB_ERR_BAD_PARAM;
+  uint32_t* dw = nullptr;
+  double* dout = nullptr;
+  if (cudaMalloc(&dw, (size_t)n_pairs * 2 * sizeof(uint32_t)) != cudaSuccess) return LB_ERR_OOM;
+  if (cudaMalloc(&dout, (size_t)n_pairs * 2 * sizeof(double)) != cudaSuccess) {
+    cudaFree(dw);
+    return LB_ERR_OOM;
+  }
+  int rc = LB_OK;
+  if (cudaMemcpy(dw, host_words, (size_t)n_pairs * 2 * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = LB_ERR_CUDA;
+  if (!rc) {
+    cudaError_t e = precision == LB_PREC_FP64 ? launch_debug_normals<double>(dw, n_pairs, dout, nullptr)
+                                              : launch_debug_normals<float>(dw, n_pairs, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, dout, (size_t)n_pairs * 2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = LB_ERR_CUDA;
+  }
+  cudaFree(dw);
+  cudaFree(dout);
   return rc;
 }
 

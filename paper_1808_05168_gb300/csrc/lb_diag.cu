@@ -410,6 +410,48 @@ cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* o
   return cudaGetLastError();
 }
 
+// z-profiles (Sec. III.C): warp r of the grid sums global row r over x in a fixed order
+// (lane-strided partial sums, then a butterfly) for the four sampled fields and the pressure, and
+// adds the row means to the compensated per-row sums [5][n_rows].
+template <class real>
+__global__ void profile_kernel(const DiagLattice* __restrict__ lat, const int* __restrict__ row_lat, int n_rows,
+                               const real* __restrict__ fields, const real* __restrict__ pfield,
+                               double* __restrict__ prof_sum, double* __restrict__ prof_comp) {
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rows) return;  // whole warps
+  const DiagLattice& L = lat[row_lat[r]];
+  const int Lx = L.Lx, z = r - L.row_off;
+  const int64_t LzLx = (int64_t)Lx * L.Lz;
+  const real* f0 = fields + 4 * L.site_off + (int64_t)z * Lx;
+  const real* p0 = pfield + L.site_off + (int64_t)z * Lx;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int x = lane; x < Lx; x += 32) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += (double)f0[k * LzLx + x];
+    acc[4] += (double)p0[x];
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (lane == 0) {
+    const double inv = 1.0 / (double)Lx;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) neumaier_add(prof_sum[(int64_t)k * n_rows + r], prof_comp[(int64_t)k * n_rows + r],
+                                             acc[k] * inv);
+  }
+}
+
+template <class real>
+cudaError_t launch_profiles(const DiagLattice* lat, const int* row_lat, int n_rows, const real* fields,
+                            const real* pfield, double* prof_sum, double* prof_comp, cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  const int64_t blocks = ((int64_t)n_rows * 32 + 255) / 256;
+  profile_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(lat, row_lat, n_rows, fields, pfield, prof_sum, prof_comp);
+  return cudaGetLastError();
+}
+
 #define LB_INST(real)                                                                                        \
   template size_t sf_smem_bytes<real>(int);                                                                  \
   template cudaError_t prepare_sf<real>(int, int);                                                           \
@@ -418,7 +460,9 @@ cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* o
   template cudaError_t launch_mass<real>(const real*, const BgParams&, double*, cudaStream_t);               \
   template cudaError_t launch_to_absolute<real>(const real*, const BgParams&, double*, cudaStream_t);        \
   template cudaError_t launch_from_absolute<real>(const double*, const BgParams&, real*, cudaStream_t);      \
-  template cudaError_t launch_init_rest<real>(real*, const BgParams&, cudaStream_t);
+  template cudaError_t launch_init_rest<real>(real*, const BgParams&, cudaStream_t);                         \
+  template cudaError_t launch_profiles<real>(const DiagLattice*, const int*, int, const real*, const real*,    \
+                                             double*, double*, cudaStream_t);
 LB_INST(float)
 LB_INST(double)
 

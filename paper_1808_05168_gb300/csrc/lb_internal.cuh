@@ -212,6 +212,8 @@ struct StepArgs {
   const int64_t* d_t;  // device step counter; the step index is *d_t + t_offset
   int t_offset;
   real* fields;        // sampled fields [4][Lz][Lx] per lattice (sample steps only)
+  real* pfield;        // sampled pressure [Lz][Lx] per lattice, minus the row background in
+                       // deviation mode (sample steps only)
   double* partials;    // per item: pressure deviation sum, mass deviation A, B
   int* err;            // set to 1 by a device-side wait that gave up
 };
@@ -241,6 +243,7 @@ cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s);
 struct DiagLattice {
   int Lx, Lz;
   int64_t site_off;    // offset in sites of this lattice in fields / spectra
+  int row_off;         // offset of row 0 in the per-row tables (profiles)
   int item_begin, item_end;
   double P_bg_mean;    // spatial mean of the background pressure (FP64 mode: 0)
   double mass_bg[2];   // background mass per species (FP64 mode: 0)
@@ -283,6 +286,13 @@ template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
                       cudaStream_t s);
 
+// z-profiles (Sec. III.C): adds the row means of delta rho, delta c, Ux, Uz and the pressure
+// (deviation) of the sampled fields to per-row compensated sums [5][n_rows]; row_lat[r] is the
+// lattice of global row r.
+template <class real>
+cudaError_t launch_profiles(const DiagLattice* lat, const int* row_lat, int n_rows, const real* fields,
+                            const real* pfield, double* prof_sum, double* prof_comp, cudaStream_t s);
+
 cudaError_t launch_finalize(const DiagLattice* d_lat, int n_lat, const double* partials, DiagStats* stats,
                             cudaStream_t s);
 
@@ -308,6 +318,9 @@ cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* 
                                 const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
                                 double sign, double* rho, double* fl, double* sb, double* partials, double* grad,
                                 cudaStream_t s);
+
+template <class real>
+cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double* out, cudaStream_t s);
 
 cudaError_t launch_barrier_probe(int blocks, int expected, int spin_limit, unsigned* barrier, int* err,
                                  cudaStream_t s);

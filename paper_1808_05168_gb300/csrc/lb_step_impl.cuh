@@ -306,37 +306,66 @@ __device__ __forceinline__ void collide_out(const Mom<real>& m, real d, real rs,
       M8 += a8 * nz[8];
     }
   }
+  // links of opposite velocity pair up as f = u + v and f_opp = u - v (u: the even moments,
+  // v: the odd ones)
   const real M0 = d;
   const real c9 = real(1) / 9, c36 = real(1) / 36;
   const real base4 = M0 + M3 - 4 * M8;
   const real base5 = M0 + 4 * M3 + 8 * M8;
-  const real p12 = M1 + M2, p1m2 = M1 - M2, q67 = 2 * (M6 + M7), q6m7 = 2 * (M6 - M7);
+  const real u13 = c9 * (base4 + M4), v13 = c9 * (M1 - M6);
+  const real u24 = c9 * (base4 - M4), v24 = c9 * (M2 - M7);
+  const real u57 = c36 * (base5 + M5), v57 = c36 * ((M1 + M2) + 2 * (M6 + M7));
+  const real u68 = c36 * (base5 - M5), v68 = c36 * ((M1 - M2) + 2 * (M6 - M7));
   put<real, TO_GLOBAL, STRIDE>(out, stride, 0, real(4) / 9 * (M0 - 2 * M3 + 2 * M8));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 1, c9 * (base4 + M1 + M4 - M6));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 2, c9 * (base4 + M2 - M4 - M7));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 3, c9 * (base4 - M1 + M4 + M6));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 4, c9 * (base4 - M2 - M4 + M7));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 5, c36 * (base5 + p12 + M5 + q67));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 6, c36 * (base5 - p1m2 - M5 - q6m7));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 7, c36 * (base5 - p12 + M5 - q67));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 8, c36 * (base5 + p1m2 - M5 + q6m7));
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 1, u13 + v13);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 2, u24 + v24);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 3, u13 - v13);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 4, u24 - v24);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 5, u57 + v57);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 6, u68 - v68);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 7, u57 - v57);
+  put<real, TO_GLOBAL, STRIDE>(out, stride, 8, u68 + v68);
 }
 
-// Box-Muller pair of the working precision.  FP64: exact-as-libm (log, sincospi).  FP32: log
-// to full precision (its value matters near u1 -> 1), sqrt through the reciprocal square root,
-// and the angle reduced to (-pi, pi) for the fast sine/cosine: cos 2 pi u2 = -cos phi and
-// sin 2 pi u2 = -sin phi with phi = 2 pi u2 - pi; absolute error below 3e-6 on a normal.
+// Box-Muller pair of the working precision.  FP64: exact-as-libm (log, sincospi).  FP32:
+// t = -2 ln u1 from the hardware base-2 logarithm, whose absolute error (~2^-22) the square root
+// would magnify where t is small; there (v = 1 - u1 < 2^-6, v exact) the series
+// -ln(1 - v) = v + v^2/2 + v^3/3 + ... is used instead (next term below 1e-6 of t).  The radius
+// is t / sqrt(t) through the reciprocal square root, and the angle is reduced to (-pi, pi) for
+// the fast sine/cosine: cos 2 pi u2 = -cos phi and sin 2 pi u2 = -sin phi with
+// phi = 2 pi u2 - pi.  Absolute error below 3e-6 on a normal.
+// The hardware approximations in their flush-to-zero forms: their arguments here are never
+// subnormal (u1 >= 2^-24, t > 2^-24, phi a multiple of 2^-44), so the results are those of the
+// plain forms without their subnormal handling.
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void sincos_ftz(float x, float& s, float& c) {
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
+}
+
 template <class real>
 __device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, real& n0, real& n1);
 template <>
 __device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float& n0, float& n1) {
   const float u1 = uniform01<float>(a);
-  const float t = -2.0f * logf(u1);
-  const float r = t * rsqrtf(t);
+  const float v = 1.0f - u1;
+  const float t_log = -1.38629436111989061f * lg2_ftz(u1);
+  const float t_ser = v * fmaf(v, fmaf(v, 0.666666666666666667f, 1.0f), 2.0f);
+  const float t = v < 0.015625f ? t_ser : t_log;
+  const float r = t * rsqrt_ftz(t);
   // phi = 2 pi u2 - pi = 2 pi x2 - 3 pi + 2 pi 2^-24 with x2 = u2 + 1 - 2^-24 built from the bits
   const float phi = fmaf(6.28318530717959f, unit_interval_bits(b), -9.42477758729298f);
   float s, c;
-  __sincosf(phi, &s, &c);
+  sincos_ftz(phi, s, c);
   n0 = -r * c;
   n1 = -r * s;
 }
@@ -357,8 +386,8 @@ template <class real, bool SAMPLE, int NOISE, bool UNIT, bool TO_GLOBAL, int STR
 __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& mA,
                                             const Mom<real>& mB, real dA, real dB, const real* ringA,
                                             const real* ringB, int bc, int bu, int bd, uint32_t site, uint32_t step,
-                                            real* fl, int LzLx, double& acc_p, double& acc_a, double& acc_b,
-                                            real* outA, real* outB, int ostride, int flags) {
+                                            real* fl, real* pl, int LzLx, double& acc_p, double& acc_a,
+                                            double& acc_b, real* outA, real* outB, int ostride, int flags) {
   const real c9 = real(1) / 9, c36 = real(1) / 36;
   real FNx, FNz, FAx, FAz, FBx, FBz, rhoA, rhoB, inv;
   {
@@ -402,7 +431,9 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
       const real NA = c9 * (Ae + Aw + An + As) + real(2) / 36 * (Ane + Anw + Ase + Asw);
       const real NB = c9 * (Be + Bw + Bn + Bs) + real(2) / 36 * (Bne + Bnw + Bse + Bsw);
       const real inter = dA * (rc.nbB + NB) + rc.bgA * NB + dB * (rc.nbA + NA) + rc.bgB * NA;
-      acc_p += (double)(kin + real(0.25) * K.G * inter);
+      const real psite = kin + real(0.25) * K.G * inter;
+      pl[0] = psite;
+      acc_p += (double)psite;
       acc_a += (double)dA;
       acc_b += (double)dB;
     }
@@ -636,7 +667,8 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
         }
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
             K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd, (uint32_t)r0, step,
-            a.fields + 4 * L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
+            a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
+            g + 9 * LzLx + r0, LzLx, flags);
       };
       if (flags & DF_UNIT) site(BoolC<true>());
       else site(BoolC<false>());
@@ -836,7 +868,8 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
         }
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
             K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd, (uint32_t)r0, step,
-            a.fields + 4 * L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0, g + 9 * LzLx + r0, LzLx, flags);
+            a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
+            g + 9 * LzLx + r0, LzLx, flags);
       };
       if (flags & DF_UNIT) site(BoolC<true>());
       else site(BoolC<false>());
@@ -1088,6 +1121,25 @@ cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nste
   size_t smem = 0;
   const void* fn = persistent_fn<real>(tile_x, noise, bulk, &smem);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
+}
+
+// The normals of the step kernels for given Philox word pairs (test hook).
+template <class real>
+__global__ void debug_normals_kernel(const uint32_t* __restrict__ words, int64_t n_pairs, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pairs) return;
+  real n0, n1;
+  normal_pair<real>(words[2 * i], words[2 * i + 1], n0, n1);
+  out[2 * i] = (double)n0;
+  out[2 * i + 1] = (double)n1;
+}
+
+template <class real>
+cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double* out, cudaStream_t s) {
+  if (n_pairs <= 0) return cudaSuccess;
+  const int64_t blocks = (n_pairs + 255) / 256;
+  debug_normals_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(words, n_pairs, out);
+  return cudaGetLastError();
 }
 
 #ifdef LB_STEP_COMMON_DEFS

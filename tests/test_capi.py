@@ -62,6 +62,10 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lb_synchronize(None) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_mass(None, 0, None) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_debug_barrier(0, 1, 10) == capi.LB_ERR_BAD_PARAM
+    assert lib.lb_profile(None, 0, capi.LB_FIELD_P, None, 0, None) == capi.LB_ERR_BAD_PARAM
+    assert lib.lb_debug_box_muller(7, None, 1, None) == capi.LB_ERR_BAD_PARAM
+    assert lib.lb_debug_box_muller(capi.LB_PREC_DEV32, None, -1, None) == capi.LB_ERR_BAD_PARAM
+    assert lib.lb_debug_box_muller(capi.LB_PREC_DEV32, None, 1, None) == capi.LB_ERR_BAD_PARAM
     lib.lb_destroy(None)
 
 

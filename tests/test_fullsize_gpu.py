@@ -78,3 +78,47 @@ def test_large_lattice_column_windows(prec):
             dev = np.max(np.abs(o.populations() - b))
             err = np.max(np.abs(got - want))
             assert err <= 1e-5 * dev, (x, err, dev)
+
+
+@pytest.fixture(scope="module")
+def c2_oracle():
+    (p,) = workloads.c2()
+    o = oracle_of(p)
+    o.set_sampling(40, 10)
+    o.step(60)
+    return p, o
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_c2_spectra_pressure_and_profiles(prec, c2_oracle):
+    """The 512 x 256 lattice (G = 0.5, wall-to-wall difference 0.5, kT = 1e-5) with the
+    diagnostics of Appendix A and Sec. III.C on two sample steps: every field's S(q_x, q_z) over
+    the whole q grid, the mean pressure and the z-profiles, against the oracle."""
+    p, o = c2_oracle
+    with Simulation(p, precision=prec, graph=True) as sim:
+        sim.set_sampling(40, 10)
+        sim.step(60)
+        S = {f: sim.structure_factor(f) for f in ("rho", "c", "ux", "uz")}
+        last, avg = sim.mean_pressure()
+        prof = {f: sim.profile(f) for f in ("rho", "c", "ux", "uz", "p")}
+    for f, (got, n) in S.items():
+        want, no = o.structure_factor(f)
+        assert n == no == 2
+        if prec == "fp64":
+            np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12 * want.max())
+        else:
+            # absolute part: the noise-dominated modes; relative part: the q_x = 0 modes, which
+            # carry the deterministic density and concentration profiles (FP32 row sums)
+            assert np.all(np.abs(got - want) <= 2e-3 * want.mean() + 1e-5 * np.abs(want)), f
+    olast, oavg, _ = o.mean_pressure()
+    tol = 1e-12 if prec == "fp64" else 1e-7
+    assert abs(last - olast) <= tol * abs(olast) and abs(avg - oavg) <= tol * abs(oavg)
+    z = np.arange(p.Lz) + 0.5 - p.Lz / 2
+    bg = {"rho": 1.0, "c": 0.5 + z * p.grad_c0, "ux": 0.0, "uz": 0.0}
+    for f, (got, n) in prof.items():
+        want, _ = o.profile(f)
+        if prec == "fp64":
+            np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+        else:
+            b = bg.get(f, want.mean())
+            assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - b)) + 1e-12, f

@@ -50,6 +50,28 @@ def test_normals_are_standard():
     assert not np.allclose(oracle.site_normals(7, 3, 5, 11), oracle.site_normals(8, 3, 5, 11))
 
 
+def test_box_muller_word_roles_and_stream_wiring():
+    """Box-Muller pairs (Sec. II.B noise): the first word of a pair sets the radius
+    sqrt(-2 ln u1), the second the angle 2 pi u2, u = (2 (k mod 2^23) + 1) 2^-24 from the low 23
+    bits; the site's sixteen normals are the pairs of its four Philox calls, counter (site, step,
+    lattice, call) and key (seed low, seed high)."""
+    # closed forms at the ends of the grid; the high bits are ignored
+    n = oracle.box_muller([0xFF800000, 0x00000000, 0x007FFFFF, 0x003FFFFF])
+    r0 = np.sqrt(48 * np.log(2.0))  # u1 = 2^-24
+    r1 = np.sqrt(-2 * np.log1p(-2.0 ** -24))  # u1 = 1 - 2^-24
+    ang0 = 2 * np.pi * 2.0 ** -24
+    ang1 = 2 * np.pi * (0.5 - 2.0 ** -24)  # u2 = (2 (2^22 - 1) + 1) 2^-24
+    np.testing.assert_allclose(n[:2], [r0 * np.cos(ang0), r0 * np.sin(ang0)], rtol=1e-14)
+    np.testing.assert_allclose(n[2:], [r1 * np.cos(ang1), r1 * np.sin(ang1)], rtol=1e-9)
+    assert n[3] > 0 and n[2] < 0
+    # wiring of the site stream onto the Philox words
+    seed, lid, site, step = (5 << 32) | 123, 9, 77, 4
+    words = []
+    for call in range(4):
+        words += oracle.philox4x32_10([site, step, lid, call], [seed & 0xFFFFFFFF, seed >> 32])
+    np.testing.assert_array_equal(oracle.site_normals(seed, lid, site, step), oracle.box_muller(words))
+
+
 # ---------------------------------------------------------------- moment basis
 def test_basis_is_weighted_orthogonal_with_golden_norms():
     """Table I basis: sum_l w_l T_al T_bl = N_a delta_ab (Eq. modes-discrete), N_a by hand."""
@@ -256,6 +278,37 @@ def test_noiseless_pressure_is_flat_and_follows_eos():
     o0 = oracle.OracleLattice(4, 16, lambda_s=1.0, lambda_d=0.8, G=0, kT=0, grad_c0=0.01)
     o0.step(500)
     assert np.ptp(o0.fields()["p"]) < 1e-14
+
+
+def test_profiles_are_time_averaged_row_means():
+    """Sec. III.C profiles: with G = 0 and no noise the steady rows carry c_0(z), rho_bar, zero
+    velocity and the ideal pressure rho_bar / 3 at every height; with noise and G > 0 the row
+    means still sum to the conserved mass and their z-average is the mean pressure."""
+    o = oracle.OracleLattice(4, 16, lambda_s=1.0, lambda_d=0.8, G=0, kT=0, grad_c0=0.01)
+    o.step(4000)
+    o.set_sampling(4000, 2)
+    o.step(9)
+    z = np.arange(16) + 0.5 - 8
+    prof = {f: o.profile(f) for f in ("rho", "c", "ux", "uz", "p")}
+    assert all(n == 5 for _, n in prof.values())
+    np.testing.assert_allclose(prof["c"][0], 0.5 + 0.01 * z, rtol=0, atol=1e-13)
+    # (the total mass carries ~1e-12 of accumulated round-off after 4000 steps)
+    np.testing.assert_allclose(prof["rho"][0], 1.0, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(prof["p"][0], 1 / 3, rtol=0, atol=1e-11)
+    assert np.ptp(prof["rho"][0]) < 1e-14 and np.ptp(prof["p"][0]) < 1e-14
+    assert np.max(np.abs(prof["ux"][0])) < 1e-15 and np.max(np.abs(prof["uz"][0])) < 1e-15
+
+    o = oracle.OracleLattice(8, 12, G=0.5, kT=1e-4, grad_c0=0.02, seed=3)
+    o.set_sampling(10, 3)
+    o.step(40)
+    rho, n = o.profile("rho")
+    assert n == 10
+    assert abs(rho.sum() - 12.0) < 1e-13  # sum_z (1/Lx) sum_x rho = total mass / Lx
+    p, _ = o.profile("p")
+    _, p_avg, _ = o.mean_pressure()
+    assert abs(p.mean() - p_avg) < 1e-14
+    c, _ = o.profile("c")
+    assert np.all(np.diff(c) > 0)  # the imposed gradient orders the rows
 
 
 # ---------------------------------------------------------------- Fourier transform

@@ -155,6 +155,39 @@ def test_sampled_structure_factors_and_pressure(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_profiles_of_a_batch(prec):
+    """Sec. III.C z-profiles of rho, c, U and the pressure (time averages of row means on the
+    sampled pre-collision state) for each lattice of a heterogeneous batch, against the oracle.
+    FP32 deviations: the row means of the deviations from the background agree to 1e-5 of the
+    largest such deviation (plus 1e-12 absolute), the bar of the populations."""
+    ps = [LatticeParams(32, 16, kT=1e-4, G=0.5, grad_c0=0.3 / 16, seed=4, lattice_id=0),
+          LatticeParams(64, 8, kT=2e-4, G=0.3, grad_c0=-0.2 / 8, seed=4, lattice_id=1)]
+    with Simulation(ps, precision=prec) as sim:
+        sim.set_sampling(10, 4)
+        sim.step(83)
+        got = [{f: sim.profile(f, lattice=i) for f in ("rho", "c", "ux", "uz", "p")} for i in range(2)]
+    for i, p in enumerate(ps):
+        o = oracle_of(p)
+        o.set_sampling(10, 4)
+        o.step(83)
+        z = np.arange(p.Lz) + 0.5 - p.Lz / 2
+        bg = {"rho": 1.0, "c": 0.5 + z * p.grad_c0, "ux": 0.0, "uz": 0.0, "p": None}
+        for f, (g, n) in got[i].items():
+            want, no = o.profile(f)
+            assert n == no == 19
+            if prec == "fp64":
+                np.testing.assert_allclose(g, want, rtol=1e-12, atol=1e-15)
+            else:
+                b = bg[f] if bg[f] is not None else want.mean()
+                scale = np.max(np.abs(want - b))
+                assert np.max(np.abs(g - want)) <= 1e-5 * scale + 1e-12, (i, f, np.max(np.abs(g - want)), scale)
+    with Simulation(ps, precision=prec) as sim:
+        assert np.all(sim.profile("p", lattice=1)[0] == 0) and sim.profile("p", lattice=1)[1] == 0
+        with pytest.raises(capi.LBError):
+            capi.lb_profile(sim.h, 0, capi.LB_FIELD_P, np.empty(15))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
 def test_launch_modes_and_tiles_are_bit_identical(prec):
     """Direct launches, CUDA graphs, the persistent cooperative launch and every tile shape
     compute each site identically."""
@@ -167,16 +200,19 @@ def test_launch_modes_and_tiles_are_bit_identical(prec):
             sim.set_sampling(3, 7)
             sim.step(70)
             sim.step(33)
-            results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0]))
+            results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0],
+                            sim.profile("p")[0]))
     for tile in [(32, 5), (256, 32), (64, 1)]:
         with Simulation(p, precision=prec) as sim:
             sim.set_tile(*tile)
             sim.set_sampling(3, 7)
             sim.step(103)
-            results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0]))
+            results.append((sim.populations(), sim.mean_pressure(), sim.structure_factor("c")[0],
+                            sim.profile("p")[0]))
     for i, r in enumerate(results[1:], start=1):
         np.testing.assert_array_equal(r[0], results[0][0])
         np.testing.assert_array_equal(r[2], results[0][2])
+        np.testing.assert_array_equal(r[3], results[0][3])
         if i < len(configs):
             assert r[1] == results[0][1]
         else:  # another tile groups the double-precision pressure sums differently
@@ -258,3 +294,25 @@ def test_errors_on_device():
         assert e.value.code == capi.LB_ERR_SIZE
         with pytest.raises(capi.LBError):
             sim.populations(1)
+
+
+def test_box_muller_normals_of_both_precisions():
+    """The normals the step kernels draw, against the oracle's FP64 Box-Muller: random word
+    pairs, every u1 of the band below 1 where the FP32 radius switches to its series, and the
+    smallest u1 (the largest radii).  FP64 agrees to rounding; FP32 within 3e-6 absolute."""
+    rng = np.random.default_rng(11)
+    m = 1 << 18
+    a = np.concatenate([rng.integers(0, 1 << 32, m, dtype=np.uint64),
+                        np.arange((1 << 23) - (1 << 18), 1 << 23, dtype=np.uint64),  # v = 1 - u1 < 2^-5
+                        np.arange(0, 1 << 14, dtype=np.uint64)])                       # u1 < 2^-9
+    b = rng.integers(0, 1 << 32, a.size, dtype=np.uint64)
+    words = np.empty(2 * a.size, np.uint32)
+    words[0::2] = a.astype(np.uint32)
+    words[1::2] = b.astype(np.uint32)
+    want = oracle.box_muller(words)
+    got64 = capi.lb_debug_box_muller(capi.LB_PREC_FP64, words)
+    got32 = capi.lb_debug_box_muller(capi.LB_PREC_DEV32, words)
+    assert np.max(np.abs(got64 - want)) < 1e-13
+    err = np.abs(got32 - want)
+    assert np.max(err) < 3e-6, (np.max(err), int(np.argmax(err)))
+    assert capi.lb_debug_box_muller(capi.LB_PREC_DEV32, np.zeros(0, np.uint32)).size == 0
