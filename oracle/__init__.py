@@ -65,6 +65,11 @@ def _load():
         lib.olb_fields.argtypes = [vp, dp]
         lib.olb_structure_factor.argtypes = [vp, c_int, dp]
         lib.olb_structure_factor.restype = c_i64
+        lib.olb_set_correlations.argtypes = [vp, c_int, c_int, ctypes.POINTER(c_int)]
+        lib.olb_correlation.argtypes = [vp, c_int, dp]
+        lib.olb_correlation.restype = c_i64
+        lib.olb_mode_correlation.argtypes = [vp, c_int, c_int, dp]
+        lib.olb_mode_correlation.restype = c_i64
         lib.olb_profile.argtypes = [vp, c_int, dp]
         lib.olb_profile.restype = c_i64
         lib.olb_mean_pressure.argtypes = [vp, dp, dp]
@@ -172,6 +177,29 @@ class OracleLattice:
         k = PROFILE_FIELDS[field] if isinstance(field, str) else int(field)
         n = self.lib.olb_profile(self.h, k, _dptr(out))
         return out, int(n)
+
+    def set_correlations(self, fields, modes=()):
+        """Accumulate, from the next sample on, the equal-x real-space correlation of each field in
+        `fields` and its mode correlations C(q_x, z, z') for the q_x mode indices `modes`."""
+        mask = 0
+        for f in fields:
+            mask |= 1 << (FIELDS[f] if isinstance(f, str) else int(f))
+        m = (ctypes.c_int * max(1, len(modes)))(*[int(k) for k in modes])
+        self.modes = list(modes)
+        self.lib.olb_set_correlations(self.h, mask, len(modes), m)
+
+    def correlation(self, field):
+        """<dphi(x, z) dphi(x, z')> averaged over x and the samples: (Lz, Lz) array, sample count."""
+        out = np.empty((self.Lz, self.Lz), np.float64)
+        n = self.lib.olb_correlation(self.h, FIELDS[field] if isinstance(field, str) else int(field), _dptr(out))
+        return out, int(n)
+
+    def mode_correlation(self, field, mode_index):
+        """C(q_x, z, z') = <dphi(q_x, z)^* dphi(q_x, z')> for the mode_index-th requested mode."""
+        out = np.empty((self.Lz, self.Lz, 2), np.float64)
+        n = self.lib.olb_mode_correlation(self.h, FIELDS[field] if isinstance(field, str) else int(field),
+                                          int(mode_index), _dptr(out))
+        return out[..., 0] + 1j * out[..., 1], int(n)
 
     def mean_pressure(self):
         last = ctypes.c_double()

@@ -195,6 +195,13 @@ struct Sim {
   double P_sum = 0.0, P_last = 0.0;
   // z-profiles (Sec. III.C): sums over samples of the row means of rho, c, Ux, Uz and P
   std::vector<double> prof_acc;  // [5][Lz]
+  // two-point correlations of the fields in corr_mask (bit f for field f): the equal-x real-space
+  // correlation (1/Lx) sum_x dphi(x, z) dphi(x, z') (Sec. III.A-B) and, for the q_x mode
+  // indices in corr_modes, C(q_x, z, z') = dphi(q_x, z)^* dphi(q_x, z') (Appendix A)
+  int corr_mask = 0;
+  std::vector<int> corr_modes;
+  std::vector<double> R_acc;  // [4][Lz][Lz]
+  std::vector<double> C_acc;  // [4][modes][Lz][Lz][re, im]
   // loss accumulation for the gradient reference: sum over steps of the mean pressure
   bool accumulate_loss = false;
   R loss_sum = R(0.0);
@@ -411,22 +418,69 @@ void dft2_power(const double* phi, int Lx, int Lz, double* out) {
 
 // One sample of the diagnostics on the pre-collision state: structure factors of
 // delta rho = rho - rho_bar, delta c = c - c_0(z), U_x, U_z, and the mean pressure.
+// The sampled field f (0 delta rho, 1 delta c, 2 Ux, 3 Uz) of Appendix A at every site.
+template <class R>
+void sampled_field(const Sim<R>& S, const Pre<R>& P, int fld, std::vector<double>& field) {
+  const int Lx = S.Lx, Lz = S.Lz, n = Lx * Lz;
+  field.assign((size_t)n, 0.0);
+  for (int z = 0; z < Lz; ++z)
+    for (int x = 0; x < Lx; ++x) {
+      const int i = z * Lx + x;
+      const double rA = value_of(P.rho[i]), rB = value_of(P.rho[n + i]);
+      if (fld == 0) field[i] = rA + rB - S.rho_bar;
+      else if (fld == 1) field[i] = rA / (rA + rB) - S.c0(z);
+      else if (fld == 2) field[i] = value_of(P.Ux[i]);
+      else field[i] = value_of(P.Uz[i]);
+    }
+}
+
+// Two-point correlations of one sample, written out from their definitions: the real-space
+// product averaged over x, and the products of the partial transforms
+// dphi(q_x, z) = Lx^(-1/2) sum_x dphi(x, z) exp(-i q_x x) of Eq. (SF1).
+template <class R>
+void correlate(Sim<R>& S, const Pre<R>& P) {
+  const int Lx = S.Lx, Lz = S.Lz;
+  const size_t LL = (size_t)Lz * Lz, nm = S.corr_modes.size();
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> field, re((size_t)Lz), im((size_t)Lz);
+  for (int fld = 0; fld < 4; ++fld) {
+    if (!(S.corr_mask & (1 << fld))) continue;
+    sampled_field(S, P, fld, field);
+    for (int z = 0; z < Lz; ++z)
+      for (int zp = 0; zp < Lz; ++zp) {
+        double acc = 0.0;
+        for (int x = 0; x < Lx; ++x) acc += field[(size_t)z * Lx + x] * field[(size_t)zp * Lx + x];
+        S.R_acc[fld * LL + (size_t)z * Lz + zp] += acc / (double)Lx;
+      }
+    for (size_t m = 0; m < nm; ++m) {
+      const int k = S.corr_modes[m];
+      for (int z = 0; z < Lz; ++z) {
+        double a = 0.0, b = 0.0;
+        for (int x = 0; x < Lx; ++x) {
+          const double ang = two_pi * (double)(((int64_t)k * x) % Lx) / (double)Lx;
+          a += field[(size_t)z * Lx + x] * std::cos(ang);
+          b -= field[(size_t)z * Lx + x] * std::sin(ang);
+        }
+        re[z] = a / std::sqrt((double)Lx);
+        im[z] = b / std::sqrt((double)Lx);
+      }
+      double* C = S.C_acc.data() + ((size_t)fld * nm + m) * LL * 2;
+      for (int z = 0; z < Lz; ++z)
+        for (int zp = 0; zp < Lz; ++zp) {
+          // conj(X_z) X_z'
+          C[2 * ((size_t)z * Lz + zp)] += re[z] * re[zp] + im[z] * im[zp];
+          C[2 * ((size_t)z * Lz + zp) + 1] += re[z] * im[zp] - im[z] * re[zp];
+        }
+    }
+  }
+}
+
 template <class R>
 void sample(Sim<R>& S, const Pre<R>& P) {
   const int Lx = S.Lx, Lz = S.Lz, n = Lx * Lz;
-  std::vector<double> field((size_t)n), power((size_t)n);
+  std::vector<double> field, power((size_t)n);
   for (int fld = 0; fld < 4; ++fld) {
-    for (int z = 0; z < Lz; ++z)
-      for (int x = 0; x < Lx; ++x) {
-        const int i = z * Lx + x;
-        const double rA = value_of(P.rho[i]), rB = value_of(P.rho[n + i]);
-        double v;
-        if (fld == 0) v = rA + rB - S.rho_bar;
-        else if (fld == 1) v = rA / (rA + rB) - S.c0(z);
-        else if (fld == 2) v = value_of(P.Ux[i]);
-        else v = value_of(P.Uz[i]);
-        field[i] = v;
-      }
+    sampled_field(S, P, fld, field);
     dft2_power(field.data(), Lx, Lz, power.data());
     for (int i = 0; i < n; ++i) S.S_acc[(size_t)fld * n + i] += power[i];
   }
@@ -449,6 +503,7 @@ void sample(Sim<R>& S, const Pre<R>& P) {
     }
     for (int k = 0; k < 5; ++k) S.prof_acc[(size_t)k * Lz + z] += row[k] / (double)Lx;
   }
+  if (S.corr_mask) correlate(S, P);
   S.P_last = mean;
   S.P_sum += mean;
   S.nsamples += 1;
@@ -632,6 +687,32 @@ int64_t olb_structure_factor(void* h, int field, double* out) {
   const size_t n = (size_t)S->Lx * S->Lz;
   for (size_t i = 0; i < n; ++i)
     out[i] = S->nsamples ? S->S_acc[(size_t)field * n + i] / (double)S->nsamples : 0.0;
+  return S->nsamples;
+}
+
+// Correlations from the next sample on: field mask (bit f for field f), q_x mode indices.
+void olb_set_correlations(void* h, int mask, int n_modes, const int* modes) {
+  olb_sim* S = (olb_sim*)h;
+  S->corr_mask = mask & 15;
+  S->corr_modes.assign(modes, modes + n_modes);
+  const size_t LL = (size_t)S->Lz * S->Lz;
+  S->R_acc.assign(4 * LL, 0.0);
+  S->C_acc.assign(4 * (size_t)n_modes * LL * 2, 0.0);
+}
+
+// Averages over the samples: R (Lz x Lz) of a field; C of a field and mode (Lz x Lz complex).
+int64_t olb_correlation(void* h, int field, double* out) {
+  olb_sim* S = (olb_sim*)h;
+  const size_t LL = (size_t)S->Lz * S->Lz;
+  for (size_t i = 0; i < LL; ++i) out[i] = S->nsamples ? S->R_acc[field * LL + i] / (double)S->nsamples : 0.0;
+  return S->nsamples;
+}
+
+int64_t olb_mode_correlation(void* h, int field, int mode_index, double* out) {
+  olb_sim* S = (olb_sim*)h;
+  const size_t LL = (size_t)S->Lz * S->Lz, nm = S->corr_modes.size();
+  const double* C = S->C_acc.data() + ((size_t)field * nm + mode_index) * LL * 2;
+  for (size_t i = 0; i < 2 * LL; ++i) out[i] = S->nsamples ? C[i] / (double)S->nsamples : 0.0;
   return S->nsamples;
 }
 

@@ -130,94 +130,123 @@ __device__ __forceinline__ void stage_column(const real* __restrict__ f, int LzL
   }
 }
 
-// The 9 populations of species s of one site as deviations from the background of its row.
+// ---- (A, B) pairs ------------------------------------------------------------------
+// The two species go through identical arithmetic, so every per-species quantity of a site is
+// carried as a pair (lane x: species A, lane y: species B).  FP32: the packed two-lane
+// instructions of sm_100 and later, one instruction for both species; FP64: two scalar
+// operations.
+template <class real>
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
+};
+template <class real>
+using Pr = typename PairOf<real>::type;
+
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pr(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 pr(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double2 pr(double a) { return make_double2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+// The 9 populations of both species of one site as deviations from the background of its row.
 // In deviation mode the background difference b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz
 // d_z c^S_0 belongs on every non-reflected link with c_lz != 0 (k9, k36: its size on the
-// 1/9- and 1/36-weight links of species A; zero in FP64 mode).  In interior rows these shifts
-// sum to zero and change no moment but m_2 (see interior_m2_shift), so they are applied to the
-// moments there; in the two wall rows, where the reflected links carry none, per link.
+// 1/9- and 1/36-weight links of species A, the opposite for B; zero in FP64 mode).  In interior
+// rows these shifts sum to zero and change no moment but m_2 (see interior_m2_shift), so they are
+// applied to the moments there; in the two wall rows, where the reflected links carry none, per
+// link.
 template <class real>
-__device__ __forceinline__ void deviations(real e0, real e1, real e2, real e3, real e4, real e5, real e6, real e7,
-                                           real e8, int s, bool below, bool above, real k9, real k36, real v[9]) {
-  v[0] = e0;
-  v[1] = e1;
-  v[3] = e3;
-  v[2] = e2;
-  v[4] = e4;
-  v[5] = e5;
-  v[6] = e6;
-  v[7] = e7;
-  v[8] = e8;
+__device__ __forceinline__ void deviations(Pr<real> v[9], bool below, bool above, real k9, real k36) {
   if (!(below && above)) {
-    const real q9 = s == 0 ? k9 : -k9, q36 = s == 0 ? k36 : -k36;
-    const real b9 = below ? q9 : real(0), b36 = below ? q36 : real(0);
-    const real a9 = above ? q9 : real(0), a36 = above ? q36 : real(0);
-    v[2] = e2 - b9;
-    v[4] = e4 + a9;
-    v[5] = e5 - b36;
-    v[6] = e6 - b36;
-    v[7] = e7 + a36;
-    v[8] = e8 + a36;
+    const Pr<real> q9 = pr(k9, -k9), q36 = pr(k36, -k36), z = pr(real(0));
+    const Pr<real> b9 = below ? q9 : z, b36 = below ? q36 : z;
+    const Pr<real> a9 = above ? q9 : z, a36 = above ? q36 : z;
+    v[2] = sub2(v[2], b9);
+    v[4] = add2(v[4], a9);
+    v[5] = sub2(v[5], b36);
+    v[6] = sub2(v[6], b36);
+    v[7] = add2(v[7], a36);
+    v[8] = add2(v[8], a36);
   }
 }
 
 // Interior rows: the shifts (-q9 on link 2, +q9 on 4, -q36 on 5 and 6, +q36 on 7 and 8; q = k for
 // species A, -k for B) have zero sum and zero moments except m_2 = -2 q9 - 4 q36.
 template <class real>
-__device__ __forceinline__ real interior_m2_shift(int s, real k9, real k36) {
+__device__ __forceinline__ Pr<real> interior_m2_shift(real k9, real k36) {
   const real q = 2 * k9 + 4 * k36;
-  return s == 0 ? -q : q;
+  return pr(-q, q);
 }
 
 // Generic path: stage column c of a slot holds the already-shifted values of that site.
 template <class real>
-__device__ __forceinline__ void read_generic(const real* st, int W, int c, int s, bool below, bool above, real k9,
-                                             real k36, real v[9]) {
-  const real* d = st + s * 9 * W + c;
-  deviations(d[0], d[W], d[2 * W], d[3 * W], d[4 * W], d[5 * W], d[6 * W], d[7 * W], d[8 * W], s, below, above, k9,
-             k36, v);
+__device__ __forceinline__ void read_generic(const real* st, int W, int c, bool below, bool above, real k9, real k36,
+                                             Pr<real> v[9]) {
+  const real* d = st + c;
+#pragma unroll
+  for (int l = 0; l < 9; ++l) v[l] = pr(d[l * W], d[(9 + l) * W]);
+  deviations(v, below, above, k9, k36);
 }
 
 // Bulk path: plane k of a slot holds the source row window, so link l of the site at window
 // column j sits at column j - c_lx (at j on reflected links, whose plane holds the opposite
 // link's own row).
 template <class real, int SW>
-__device__ __forceinline__ void read_bulk(const real* st, int j, int s, bool below, bool above, real k9, real k36,
-                                          real v[9]) {
-  const real* d = st + s * 9 * SW + j;
+__device__ __forceinline__ void read_bulk(const real* st, int j, bool below, bool above, real k9, real k36,
+                                          Pr<real> v[9]) {
+  const real* a = st + j;
+  const real* b = st + 9 * SW + j;
   const int j5 = below ? -1 : 0, j6 = below ? 1 : 0, j7 = above ? 1 : 0, j8 = above ? -1 : 0;
-  deviations(d[0], d[SW - 1], d[2 * SW], d[3 * SW + 1], d[4 * SW], d[5 * SW + j5], d[6 * SW + j6], d[7 * SW + j7],
-             d[8 * SW + j8], s, below, above, k9, k36, v);
+  const int o[9] = {0, SW - 1, 2 * SW, 3 * SW + 1, 4 * SW, 5 * SW + j5, 6 * SW + j6, 7 * SW + j7, 8 * SW + j8};
+#pragma unroll
+  for (int l = 0; l < 9; ++l) v[l] = pr(a[o[l]], b[o[l]]);
+  deviations(v, below, above, k9, k36);
 }
 
 template <class real>
-__device__ __forceinline__ real sum9(const real v[9]) {
-  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+__device__ __forceinline__ Pr<real> sum9(const Pr<real> v[9]) {
+  return add2(add2(add2(add2(v[0], v[1]), add2(v[2], v[3])), add2(add2(v[4], v[5]), add2(v[6], v[7]))), v[8]);
 }
 
-// Moments m_1..m_8 of Table I in the structured form.
+// Moments m_1..m_8 of Table I of both species, in the structured form.
 template <class real>
 struct Mom {
-  real m1, m2, m3, m4, m5, m6, m7, m8;
+  Pr<real> m1, m2, m3, m4, m5, m6, m7, m8;
 };
 
 template <class real>
-__device__ __forceinline__ Mom<real> moments(const real v[9]) {
-  const real a57 = v[5] - v[7], a68 = v[6] - v[8];
-  const real d13 = v[1] - v[3], d24 = v[2] - v[4];
-  const real s13 = v[1] + v[3], s24 = v[2] + v[4];
-  const real e = s13 + s24;
-  const real s57 = v[5] + v[7], s68 = v[6] + v[8];
-  const real dg = s57 + s68;
+__device__ __forceinline__ Mom<real> moments(const Pr<real> v[9]) {
+  const Pr<real> a57 = sub2(v[5], v[7]), a68 = sub2(v[6], v[8]);
+  const Pr<real> d13 = sub2(v[1], v[3]), d24 = sub2(v[2], v[4]);
+  const Pr<real> s13 = add2(v[1], v[3]), s24 = add2(v[2], v[4]);
+  const Pr<real> e = add2(s13, s24);
+  const Pr<real> s57 = add2(v[5], v[7]), s68 = add2(v[6], v[8]);
+  const Pr<real> dg = add2(s57, s68);
+  const Pr<real> am = sub2(a57, a68), ap = add2(a57, a68);
   Mom<real> m;
-  m.m1 = d13 + a57 - a68;
-  m.m2 = d24 + a57 + a68;
-  m.m3 = -2 * v[0] + e + 4 * dg;
-  m.m4 = s13 - s24;
-  m.m5 = s57 - s68;
-  m.m6 = -d13 + 2 * (a57 - a68);
-  m.m7 = -d24 + 2 * (a57 + a68);
-  m.m8 = 2 * v[0] - 4 * e + 8 * dg;
+  m.m1 = add2(d13, am);
+  m.m2 = add2(d24, ap);
+  m.m3 = fma2(pr(real(-2)), v[0], fma2(pr(real(4)), dg, e));
+  m.m4 = sub2(s13, s24);
+  m.m5 = sub2(s57, s68);
+  m.m6 = sub2(add2(am, am), d13);
+  m.m7 = sub2(add2(ap, ap), d24);
+  m.m8 = fma2(pr(real(2)), v[0], fma2(pr(real(-4)), e, mul2(pr(real(8)), dg)));
   return m;
 }
 
@@ -262,78 +291,72 @@ __device__ __forceinline__ void put(real* out, int stride, int l, real v) {
   else out[l * STRIDE] = v;
 }
 
-// Collision of one species in moment space (Eq. MRT) with second-order forcing and noise, and
+// Collision of both species in moment space (Eq. MRT) with second-order forcing and noise, and
 // the inverse transform f_l = w_l sum_a T_al m*_a / N_a.  Relaxation, forcing and noise factors
 // and 1/N_a are folded into the per-lattice coefficients kA..kN; moments 1-2 share theirs (both
-// relax at l_d), as do 6-7 (l_Q).  UNIT: the rates of moments 3..8 are 1, so their pre-collision
-// values drop out (kA = 0) and are never formed.  nz[1..8]: the standard normals of this
-// species' moments; cm, cq: their amplitude factors for moments 1-2 and 3-8 (sign and local
-// density; +-1 and 1 for hom noise).
+// relax at l_d), as do 6-7 (l_Q).  UNIT: the rates of moments 3..8 are 1, so their
+// pre-collision values drop out (kA = 0) and are never formed.  nz[1..8]: the standard normals
+// of the moments (pairs); cm, cq: their amplitude factors for moments 1-2 and 3-8 (sign and
+// local density; (1, -1) and (1, 1) for hom noise).
 template <class real, int NOISE, bool UNIT, bool TO_GLOBAL, int STRIDE>
-__device__ __forceinline__ void collide_out(const Mom<real>& m, real d, real rs, real Ux, real Uz, real Fx, real Fz,
-                                            const SiteK<real>& K, const real nz[9], real cm, real cq, real* out,
-                                            int stride) {
-  const real UxUx = Ux * Ux, UzUz = Uz * Uz, UxUz = Ux * Uz;
-  const real r1 = K.kB[1] * rs;
-  real M1 = K.kA[1] * m.m1 + r1 * Ux + K.kC[1] * Fx;
-  real M2 = K.kA[1] * m.m2 + r1 * Uz + K.kC[1] * Fz;
-  real M3 = (K.kB[3] * rs) * (UxUx + UzUz) + K.kC[3] * (Ux * Fx + Uz * Fz);
-  real M4 = (K.kB[4] * rs) * (UxUx - UzUz) + K.kC[4] * (Ux * Fx - Uz * Fz);
-  real M5 = (K.kB[5] * rs) * UxUz + K.kC[5] * (Ux * Fz + Uz * Fx);
-  real M6 = 0, M7 = 0, M8 = 0;
+__device__ __forceinline__ void collide_out(const Mom<real>& m, Pr<real> d, Pr<real> rs, real Ux, real Uz,
+                                            Pr<real> Fx, Pr<real> Fz, const SiteK<real>& K, const Pr<real> nz[9],
+                                            Pr<real> cm, Pr<real> cq, real* outA, real* outB, int stride) {
+  using P = Pr<real>;
+  const P U_x = pr(Ux), U_z = pr(Uz);
+  const real UxUx = Ux * Ux, UzUz = Uz * Uz;
+  const P r1 = mul2(pr(K.kB[1]), rs);
+  P M1 = fma2(pr(K.kC[1]), Fx, fma2(r1, U_x, mul2(pr(K.kA[1]), m.m1)));
+  P M2 = fma2(pr(K.kC[1]), Fz, fma2(r1, U_z, mul2(pr(K.kA[1]), m.m2)));
+  const P uxF = mul2(U_x, Fx), uzF = mul2(U_z, Fz);
+  P M3 = fma2(mul2(pr(K.kB[3]), rs), pr(UxUx + UzUz), mul2(pr(K.kC[3]), add2(uxF, uzF)));
+  P M4 = fma2(mul2(pr(K.kB[4]), rs), pr(UxUx - UzUz), mul2(pr(K.kC[4]), sub2(uxF, uzF)));
+  P M5 = fma2(mul2(pr(K.kB[5]), rs), pr(Ux * Uz), mul2(pr(K.kC[5]), fma2(U_x, Fz, mul2(U_z, Fx))));
+  P M6 = pr(real(0)), M7 = pr(real(0)), M8 = pr(real(0));
   if (!UNIT) {
-    M3 += K.kA[3] * m.m3;
-    M4 += K.kA[4] * m.m4;
-    M5 += K.kA[5] * m.m5;
-    M6 = K.kA[6] * m.m6;
-    M7 = K.kA[6] * m.m7;
-    M8 = K.kA[8] * m.m8;
+    M3 = fma2(pr(K.kA[3]), m.m3, M3);
+    M4 = fma2(pr(K.kA[4]), m.m4, M4);
+    M5 = fma2(pr(K.kA[5]), m.m5, M5);
+    M6 = mul2(pr(K.kA[6]), m.m6);
+    M7 = mul2(pr(K.kA[6]), m.m7);
+    M8 = mul2(pr(K.kA[8]), m.m8);
   }
   if (NOISE != NOISE_OFF) {
-    const real a1 = K.kN[1] * cm, a6 = K.kN[6] * cq, a8 = K.kN[8] * cq;
-    M1 += a1 * nz[1];
-    M2 += a1 * nz[2];
-    M3 += (K.kN[3] * cq) * nz[3];
-    M4 += (K.kN[4] * cq) * nz[4];
-    M5 += (K.kN[5] * cq) * nz[5];
+    const P a1 = mul2(pr(K.kN[1]), cm), a6 = mul2(pr(K.kN[6]), cq), a8 = mul2(pr(K.kN[8]), cq);
+    M1 = fma2(a1, nz[1], M1);
+    M2 = fma2(a1, nz[2], M2);
+    M3 = fma2(mul2(pr(K.kN[3]), cq), nz[3], M3);
+    M4 = fma2(mul2(pr(K.kN[4]), cq), nz[4], M4);
+    M5 = fma2(mul2(pr(K.kN[5]), cq), nz[5], M5);
     if (UNIT) {
-      M6 = a6 * nz[6];
-      M7 = a6 * nz[7];
-      M8 = a8 * nz[8];
+      M6 = mul2(a6, nz[6]);
+      M7 = mul2(a6, nz[7]);
+      M8 = mul2(a8, nz[8]);
     } else {
-      M6 += a6 * nz[6];
-      M7 += a6 * nz[7];
-      M8 += a8 * nz[8];
+      M6 = fma2(a6, nz[6], M6);
+      M7 = fma2(a6, nz[7], M7);
+      M8 = fma2(a8, nz[8], M8);
     }
   }
   // links of opposite velocity pair up as f = u + v and f_opp = u - v (u: the even moments,
   // v: the odd ones)
-  const real M0 = d;
-  const real c9 = real(1) / 9, c36 = real(1) / 36;
-  const real base4 = M0 + M3 - 4 * M8;
-  const real base5 = M0 + 4 * M3 + 8 * M8;
-  const real u13 = c9 * (base4 + M4), v13 = c9 * (M1 - M6);
-  const real u24 = c9 * (base4 - M4), v24 = c9 * (M2 - M7);
-  const real u57 = c36 * (base5 + M5), v57 = c36 * ((M1 + M2) + 2 * (M6 + M7));
-  const real u68 = c36 * (base5 - M5), v68 = c36 * ((M1 - M2) + 2 * (M6 - M7));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 0, real(4) / 9 * (M0 - 2 * M3 + 2 * M8));
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 1, u13 + v13);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 2, u24 + v24);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 3, u13 - v13);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 4, u24 - v24);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 5, u57 + v57);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 6, u68 - v68);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 7, u57 - v57);
-  put<real, TO_GLOBAL, STRIDE>(out, stride, 8, u68 + v68);
+  const P c9 = pr(real(1) / 9), c36 = pr(real(1) / 36);
+  const P base4 = fma2(pr(real(-4)), M8, add2(d, M3));
+  const P base5 = fma2(pr(real(8)), M8, fma2(pr(real(4)), M3, d));
+  const P u13 = mul2(c9, add2(base4, M4)), v13 = mul2(c9, sub2(M1, M6));
+  const P u24 = mul2(c9, sub2(base4, M4)), v24 = mul2(c9, sub2(M2, M7));
+  const P u57 = mul2(c36, add2(base5, M5)), v57 = mul2(c36, fma2(pr(real(2)), add2(M6, M7), add2(M1, M2)));
+  const P u68 = mul2(c36, sub2(base5, M5)), v68 = mul2(c36, fma2(pr(real(2)), sub2(M6, M7), sub2(M1, M2)));
+  const P f0 = mul2(pr(real(4) / 9), fma2(pr(real(2)), M8, fma2(pr(real(-2)), M3, d)));
+  const P f[9] = {f0,             add2(u13, v13), add2(u24, v24), sub2(u13, v13), sub2(u24, v24),
+                  add2(u57, v57), sub2(u68, v68), sub2(u57, v57), add2(u68, v68)};
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    put<real, TO_GLOBAL, STRIDE>(outA, stride, l, f[l].x);
+    put<real, TO_GLOBAL, STRIDE>(outB, stride, l, f[l].y);
+  }
 }
 
-// Box-Muller pair of the working precision.  FP64: exact-as-libm (log, sincospi).  FP32:
-// t = -2 ln u1 from the hardware base-2 logarithm, whose absolute error (~2^-22) the square root
-// would magnify where t is small; there (v = 1 - u1 < 2^-6, v exact) the series
-// -ln(1 - v) = v + v^2/2 + v^3/3 + ... is used instead (next term below 1e-6 of t).  The radius
-// is t / sqrt(t) through the reciprocal square root, and the angle is reduced to (-pi, pi) for
-// the fast sine/cosine: cos 2 pi u2 = -cos phi and sin 2 pi u2 = -sin phi with
-// phi = 2 pi u2 - pi.  Absolute error below 3e-6 on a normal.
 // The hardware approximations in their flush-to-zero forms: their arguments here are never
 // subnormal (u1 >= 2^-24, t > 2^-24, phi a multiple of 2^-44), so the results are those of the
 // plain forms without their subnormal handling.
@@ -380,107 +403,89 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Everything of one site after its moments and the neighbour densities are known: forces,
-// velocity, optional sampling, noise, collision of both species and the output.
+// Everything of one site after its moments are known and the densities of its row and the two
+// neighbouring rows sit in the ring: forces, velocity, optional sampling, noise, collision of
+// both species and the output.
 template <class real, bool SAMPLE, int NOISE, bool UNIT, bool TO_GLOBAL, int STRIDE>
-__device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& mA,
-                                            const Mom<real>& mB, real dA, real dB, const real* ringA,
-                                            const real* ringB, int bc, int bu, int bd, uint32_t site, uint32_t step,
-                                            real* fl, real* pl, int LzLx, double& acc_p, double& acc_a,
-                                            double& acc_b, real* outA, real* outB, int ostride, int flags) {
-  const real c9 = real(1) / 9, c36 = real(1) / 36;
-  real FNx, FNz, FAx, FAz, FBx, FBz, rhoA, rhoB, inv;
-  {
-    const real Aw = ringA[bc - 1], Ae = ringA[bc + 1], An = ringA[bu], Anw = ringA[bu - 1], Ane = ringA[bu + 1],
-               As = ringA[bd], Asw = ringA[bd - 1], Ase = ringA[bd + 1];
-    const real Bw = ringB[bc - 1], Be = ringB[bc + 1], Bn = ringB[bu], Bnw = ringB[bu - 1], Bne = ringB[bu + 1],
-               Bs = ringB[bd], Bsw = ringB[bd - 1], Bse = ringB[bd + 1];
-    // sum_l w_l c_l rho^S(r + c_l), deviations plus the background part (Eq. aNI)
-    const real sAx = c9 * (Ae - Aw) + c36 * ((Ane - Anw) + (Ase - Asw));
-    const real sAz = c9 * (An - As) + c36 * ((Ane + Anw) - (Ase + Asw)) + rc.dbgA;
-    const real sBx = c9 * (Be - Bw) + c36 * ((Bne - Bnw) + (Bse - Bsw));
-    const real sBz = c9 * (Bn - Bs) + c36 * ((Bne + Bnw) - (Bse + Bsw)) + rc.dbgB;
-    rhoA = rc.bgA + dA;
-    rhoB = rc.bgB + dB;
-    const real rho = rhoA + rhoB;
-    inv = real(1) / rho;
-    const real FnAx = -K.G * rhoA * sBx, FnAz = -K.G * rhoA * sBz;
-    const real FnBx = -K.G * rhoB * sAx, FnBz = -K.G * rhoB * sAz;
-    FNx = FnAx + FnBx;
-    FNz = FnAz + FnBz;
-    if (flags & DF_ASTAR) {
-      // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
-      const real cA = rhoA * inv, cB = rhoB * inv;
-      FAx = cA * FNx;
-      FAz = cA * FNz;
-      FBx = cB * FNx;
-      FBz = cB * FNz;
-    } else {
-      FAx = FnAx;
-      FAz = FnAz;
-      FBx = FnBx;
-      FBz = FnBz;
-    }
-    // gradient forcing: rho^A a^A_NE = (0, rho grad_c0 / 3) = -rho^B a^B_NE (Eq. NEcond)
-    const real ne = rho * K.g3;
-    FAz += ne;
-    FBz -= ne;
-    if (SAMPLE) {
-      // pressure (half trace; kinetic + interaction), minus its background part
-      const real kin = (mA.m3 + mB.m3 + 2 * (dA + dB)) * (real(1) / 6);
-      const real NA = c9 * (Ae + Aw + An + As) + real(2) / 36 * (Ane + Anw + Ase + Asw);
-      const real NB = c9 * (Be + Bw + Bn + Bs) + real(2) / 36 * (Bne + Bnw + Bse + Bsw);
-      const real inter = dA * (rc.nbB + NB) + rc.bgA * NB + dB * (rc.nbA + NA) + rc.bgB * NA;
-      const real psite = kin + real(0.25) * K.G * inter;
-      pl[0] = psite;
-      acc_p += (double)psite;
-      acc_a += (double)dA;
-      acc_b += (double)dB;
-    }
+__device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& m,
+                                            const Pr<real>* ring, int bc, int bu, int bd, uint32_t site,
+                                            uint32_t step, real* fl, real* pl, int LzLx, double& acc_p,
+                                            double& acc_a, double& acc_b, real* outA, real* outB, int ostride,
+                                            int flags) {
+  using P = Pr<real>;
+  const P c9 = pr(real(1) / 9), c36 = pr(real(1) / 36);
+  const P d = ring[bc];
+  const P w = ring[bc - 1], e = ring[bc + 1], n = ring[bu], nw = ring[bu - 1], ne = ring[bu + 1], s = ring[bd],
+          sw = ring[bd - 1], se = ring[bd + 1];
+  // sum_l w_l c_l rho^S(r + c_l) of both species, deviations plus the background part (Eq. aNI)
+  const P sx = fma2(c9, sub2(e, w), mul2(c36, add2(sub2(ne, nw), sub2(se, sw))));
+  const P sz = add2(fma2(c9, sub2(n, s), mul2(c36, sub2(add2(ne, nw), add2(se, sw)))), pr(rc.dbgA, rc.dbgB));
+  const P rs = add2(pr(rc.bgA, rc.bgB), d);  // (rho^A, rho^B)
+  const real rho = rs.x + rs.y;
+  const real inv = real(1) / rho;
+  // non-ideal forces: F^A = -G rho^A sum(rho^B), F^B = -G rho^B sum(rho^A)
+  const real gA = -K.G * rs.x, gB = -K.G * rs.y;
+  const real FnAx = gA * sx.y, FnAz = gA * sz.y, FnBx = gB * sx.x, FnBz = gB * sz.x;
+  const real FNx = FnAx + FnBx, FNz = FnAz + FnBz;
+  P Fx, Fz;
+  if (flags & DF_ASTAR) {
+    // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
+    const P cs = mul2(rs, pr(inv));
+    Fx = mul2(cs, pr(FNx));
+    Fz = mul2(cs, pr(FNz));
+  } else {
+    Fx = pr(FnAx, FnBx);
+    Fz = pr(FnAz, FnBz);
+  }
+  // gradient forcing: rho^A a^A_NE = (0, rho grad_c0 / 3) = -rho^B a^B_NE (Eq. NEcond)
+  Fz = fma2(pr(rho), pr(K.g3, -K.g3), Fz);
+  if (SAMPLE) {
+    // pressure (half trace; kinetic + interaction), minus its background part
+    const real kin = (m.m3.x + m.m3.y + 2 * (d.x + d.y)) * (real(1) / 6);
+    const P N = fma2(c9, add2(add2(e, w), add2(n, s)), mul2(pr(real(2) / 36), add2(add2(ne, nw), add2(se, sw))));
+    const real inter = d.x * (rc.nbB + N.y) + rc.bgA * N.y + d.y * (rc.nbA + N.x) + rc.bgB * N.x;
+    const real psite = kin + real(0.25) * K.G * inter;
+    pl[0] = psite;
+    acc_p += (double)psite;
+    acc_a += (double)d.x;
+    acc_b += (double)d.y;
   }
   // barycentric velocity, Eq. (bar)
-  const real Ux = (mA.m1 + mB.m1 + real(0.5) * FNx) * inv;
-  const real Uz = (mA.m2 + mB.m2 + real(0.5) * FNz) * inv;
+  const real Ux = (m.m1.x + m.m1.y + real(0.5) * FNx) * inv;
+  const real Uz = (m.m2.x + m.m2.y + real(0.5) * FNz) * inv;
   if (SAMPLE) {
-    fl[0] = dA + dB - K.rho_bar_off;
-    fl[LzLx] = (dA - rc.c0 * (dA + dB)) * inv;
+    fl[0] = d.x + d.y - K.rho_bar_off;
+    fl[LzLx] = (d.x - rc.c0 * (d.x + d.y)) * inv;
     fl[2 * LzLx] = Ux;
     fl[3 * LzLx] = Uz;
   }
-  real nA[9], nB[9];
+  P nz[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    nA[k] = 0;
-    nB[k] = 0;
-  }
-  real cmA = 1, cmB = -1, cqA = 1, cqB = 1;  // momentum noise is equal and opposite in A and B
+  for (int k = 0; k < 9; ++k) nz[k] = pr(real(0));
+  P cm = pr(real(1), real(-1)), cq = pr(real(1));  // momentum noise is equal and opposite in A and B
   if (NOISE != NOISE_OFF) {
-    U4 w[4];
-    philox_site(site, step, K.lid, K.key0, K.key1, w);
-    real n[14];
-    normal_pair<real>(w[0].x, w[0].y, n[0], n[1]);
-    normal_pair<real>(w[0].z, w[0].w, n[2], n[3]);
-    normal_pair<real>(w[1].x, w[1].y, n[4], n[5]);
-    normal_pair<real>(w[1].z, w[1].w, n[6], n[7]);
-    normal_pair<real>(w[2].x, w[2].y, n[8], n[9]);
-    normal_pair<real>(w[2].z, w[2].w, n[10], n[11]);
-    normal_pair<real>(w[3].x, w[3].y, n[12], n[13]);
+    U4 w4[4];
+    philox_site(site, step, K.lid, K.key0, K.key1, w4);
+    real g[14];
+    normal_pair<real>(w4[0].x, w4[0].y, g[0], g[1]);
+    normal_pair<real>(w4[0].z, w4[0].w, g[2], g[3]);
+    normal_pair<real>(w4[1].x, w4[1].y, g[4], g[5]);
+    normal_pair<real>(w4[1].z, w4[1].w, g[6], g[7]);
+    normal_pair<real>(w4[2].x, w4[2].y, g[8], g[9]);
+    normal_pair<real>(w4[2].z, w4[2].w, g[10], g[11]);
+    normal_pair<real>(w4[3].x, w4[3].y, g[12], g[13]);
     if (NOISE == NOISE_LOC) {
-      cmA = sqrt_pos<real>(rhoA * rhoB * inv);
-      cmB = -cmA;
-      cqA = sqrt_pos<real>(rhoA);
-      cqB = sqrt_pos<real>(rhoB);
+      const real sm = sqrt_pos<real>(rs.x * rs.y * inv);
+      cm = pr(sm, -sm);
+      cq = pr(sqrt_pos<real>(rs.x), sqrt_pos<real>(rs.y));
     }
-    nA[1] = nB[1] = n[0];
-    nA[2] = nB[2] = n[1];
+    // normals 0-1: momentum (one draw for both species); 2-7: moments 3..8 of A; 8-13: of B
+    nz[1] = pr(g[0]);
+    nz[2] = pr(g[1]);
 #pragma unroll
-    for (int k = 3; k < 9; ++k) {
-      nA[k] = n[k - 1];
-      nB[k] = n[k + 5];
-    }
+    for (int k = 3; k < 9; ++k) nz[k] = pr(g[k - 1], g[k + 5]);
   }
-  collide_out<real, NOISE, UNIT, TO_GLOBAL, STRIDE>(mA, dA, rhoA, Ux, Uz, FAx, FAz, K, nA, cmA, cqA, outA, ostride);
-  collide_out<real, NOISE, UNIT, TO_GLOBAL, STRIDE>(mB, dB, rhoB, Ux, Uz, FBx, FBz, K, nB, cmB, cqB, outB, ostride);
+  collide_out<real, NOISE, UNIT, TO_GLOBAL, STRIDE>(m, d, rs, Ux, Uz, Fx, Fz, K, nz, cm, cq, outA, outB, ostride);
 }
 
 __device__ __forceinline__ void block_partials(double acc_p, double acc_a, double acc_b, double* red, double* out) {
@@ -547,8 +552,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   double* red = reinterpret_cast<double*>(smem + Smem<real>::red);
   LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + Smem<real>::lat);
   const int TX = blockDim.x, W = TX + 2;
-  real* ringA = reinterpret_cast<real*>(smem + Smem<real>::ring);
-  real* ringB = ringA + 4 * W;
+  Pr<real>* ring = reinterpret_cast<Pr<real>*>(smem + Smem<real>::ring);
   real* stage = reinterpret_cast<real*>(smem + Smem<real>::stage(TX));
 
   const WorkItem it = a.items[item_index];
@@ -584,32 +588,17 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     }
     cp_commit();
   };
-  auto rho_at = [&](int r, int c, real& dA, real& dB) {
+  auto rho_at = [&](int r, int c) {
     const real* sb = stage + (r & (NS - 1)) * 18 * W;
-    real v[9];
-    read_generic(sb, W, c, 0, r > 0, r < Lz - 1, k9, k36, v);
-    dA = sum9(v);
-    read_generic(sb, W, c, 1, r > 0, r < Lz - 1, k9, k36, v);
-    dB = sum9(v);
+    Pr<real> v[9];
+    read_generic(sb, W, c, r > 0, r < Lz - 1, k9, k36, v);
+    return sum9<real>(v);
   };
   auto put_rho = [&](int r) {
     const int b = ring_slot(r) * W;
-    real dA, dB;
-    if (active) {
-      rho_at(r, tid + 1, dA, dB);
-      ringA[b + tid + 1] = dA;
-      ringB[b + tid + 1] = dB;
-    }
-    if (do_left) {
-      rho_at(r, 0, dA, dB);
-      ringA[b] = dA;
-      ringB[b] = dB;
-    }
-    if (do_right) {
-      rho_at(r, nact + 1, dA, dB);
-      ringA[b + nact + 1] = dA;
-      ringB[b + nact + 1] = dB;
-    }
+    if (active) ring[b + tid + 1] = rho_at(r, tid + 1);
+    if (do_left) ring[b] = rho_at(r, 0);
+    if (do_right) ring[b + nact + 1] = rho_at(r, nact + 1);
   };
   // wall ghost row zg from the adjacent fluid row za (Sec. II.A)
   auto ghost_row = [&](int zg, int za) {
@@ -617,14 +606,12 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     const bool fixed = flags & DF_WALL_FIXED;
     const real cw = rows[za].ghost_cA;
     auto copy1 = [&](int i) {
-      const real A = ringA[ba + i], B = ringB[ba + i];
+      const Pr<real> a = ring[ba + i];
       if (fixed) {
-        const real t = A + B;
-        ringA[bg + i] = t * cw;
-        ringB[bg + i] = t * (1 - cw);
+        const real t = a.x + a.y;
+        ring[bg + i] = pr(t * cw, t * (1 - cw));
       } else {
-        ringA[bg + i] = A;
-        ringB[bg + i] = B;
+        ring[bg + i] = a;
       }
     };
     if (active) copy1(tid + 1);
@@ -656,17 +643,12 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
       const int r0 = z * Lx + x;
       // both variants are inlined; the branch is uniform over the block (one lattice per item)
       auto site = [&](auto unit) {
-        real v[9];
-        read_generic(sb, W, tid + 1, 0, below, above, k9, k36, v);
-        Mom<real> mA = moments(v);
-        read_generic(sb, W, tid + 1, 1, below, above, k9, k36, v);
-        Mom<real> mB = moments(v);
-        if (below && above) {
-          mA.m2 += interior_m2_shift(0, k9, k36);
-          mB.m2 += interior_m2_shift(1, k9, k36);
-        }
+        Pr<real> v[9];
+        read_generic(sb, W, tid + 1, below, above, k9, k36, v);
+        Mom<real> m = moments<real>(v);
+        if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
-            K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd, (uint32_t)r0, step,
+            K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags);
       };
@@ -703,8 +685,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   constexpr int PAD = SM::PAD, SW = SM::SW, W = TX + 2;
   double* red = reinterpret_cast<double*>(smem + SM::red);
   LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + SM::lat);
-  real* ringA = reinterpret_cast<real*>(smem + SM::ring);
-  real* ringB = ringA + 4 * W;
+  Pr<real>* ring = reinterpret_cast<Pr<real>*>(smem + SM::ring);
   real* instage = reinterpret_cast<real*>(smem + SM::in);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::abort_flag);
@@ -783,47 +764,30 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     }
     ph ^= 1u << slot;
   };
-  auto rho_at = [&](int r, int j, real& dA, real& dB) {
+  auto rho_at = [&](int r, int j) {
     const real* sb = instage + (r % NSI) * 18 * SW;
-    real v[9];
-    read_bulk<real, SW>(sb, j, 0, r > 0, r < Lz - 1, k9, k36, v);
-    dA = sum9(v);
-    read_bulk<real, SW>(sb, j, 1, r > 0, r < Lz - 1, k9, k36, v);
-    dB = sum9(v);
+    Pr<real> v[9];
+    read_bulk<real, SW>(sb, j, r > 0, r < Lz - 1, k9, k36, v);
+    return sum9<real>(v);
   };
   auto put_rho = [&](int r) {
     wait_row(r);
     const int b = ring_slot(r) * W;
-    real dA, dB;
-    if (active) {
-      rho_at(r, tid + PAD, dA, dB);
-      ringA[b + tid + 1] = dA;
-      ringB[b + tid + 1] = dB;
-    }
-    if (do_left) {
-      rho_at(r, PAD - 1, dA, dB);
-      ringA[b] = dA;
-      ringB[b] = dB;
-    }
-    if (do_right) {
-      rho_at(r, nact + PAD, dA, dB);
-      ringA[b + nact + 1] = dA;
-      ringB[b + nact + 1] = dB;
-    }
+    if (active) ring[b + tid + 1] = rho_at(r, tid + PAD);
+    if (do_left) ring[b] = rho_at(r, PAD - 1);
+    if (do_right) ring[b + nact + 1] = rho_at(r, nact + PAD);
   };
   auto ghost_row = [&](int zg, int za) {
     const int bg = ring_slot(zg) * W, ba = ring_slot(za) * W;
     const bool fixed = flags & DF_WALL_FIXED;
     const real cw = rows[za].ghost_cA;
     auto copy1 = [&](int i) {
-      const real A = ringA[ba + i], B = ringB[ba + i];
+      const Pr<real> a = ring[ba + i];
       if (fixed) {
-        const real t = A + B;
-        ringA[bg + i] = t * cw;
-        ringB[bg + i] = t * (1 - cw);
+        const real t = a.x + a.y;
+        ring[bg + i] = pr(t * cw, t * (1 - cw));
       } else {
-        ringA[bg + i] = A;
-        ringB[bg + i] = B;
+        ring[bg + i] = a;
       }
     };
     if (active) copy1(tid + 1);
@@ -857,17 +821,12 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       const int r0 = z * Lx + x;
       // both variants are inlined; the branch is uniform over the block (one lattice per item)
       auto site = [&](auto unit) {
-        real v[9];
-        read_bulk<real, SW>(sb, tid + PAD, 0, below, above, k9, k36, v);
-        Mom<real> mA = moments(v);
-        read_bulk<real, SW>(sb, tid + PAD, 1, below, above, k9, k36, v);
-        Mom<real> mB = moments(v);
-        if (below && above) {
-          mA.m2 += interior_m2_shift(0, k9, k36);
-          mB.m2 += interior_m2_shift(1, k9, k36);
-        }
+        Pr<real> v[9];
+        read_bulk<real, SW>(sb, tid + PAD, below, above, k9, k36, v);
+        Mom<real> m = moments<real>(v);
+        if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
-            K, rows[z], mA, mB, ringA[bc], ringB[bc], ringA, ringB, bc, bu, bd, (uint32_t)r0, step,
+            K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags);
       };

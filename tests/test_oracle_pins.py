@@ -311,6 +311,44 @@ def test_profiles_are_time_averaged_row_means():
     assert np.all(np.diff(c) > 0)  # the imposed gradient orders the rows
 
 
+def test_correlations_obey_parseval_and_appendix_a():
+    """Appendix A: the mode correlations C(q_x, z, z') = <dphi(q_x, z)^* dphi(q_x, z')> give the
+    structure factor by the transform in z, S(q_x, q_z) = (1/Lz) sum_{z,z'} e^{i q_z (z - z')}
+    C(q_x, z, z') (against the separately computed 2D power), and summed over every q_x they give
+    the real-space correlation <dphi(x, z) dphi(x, z')>_x (Parseval); that one is symmetric with
+    the field's mean square on its diagonal."""
+    Lx, Lz = 8, 6
+    o = oracle.OracleLattice(Lx, Lz, kT=1e-4, G=0.3, grad_c0=0.02, seed=3)
+    o.set_sampling(2, 3)
+    o.set_correlations(["rho", "c", "ux", "uz"], modes=range(Lx))
+    o.step(12)
+    z = np.arange(Lz)
+    for f in ("rho", "c", "ux", "uz"):
+        R, n = o.correlation(f)
+        assert n == 4
+        C = [o.mode_correlation(f, k)[0] for k in range(Lx)]
+        np.testing.assert_allclose(sum(C).real / Lx, R, rtol=0, atol=1e-12 * np.abs(R).max())
+        assert np.abs(sum(C).imag).max() < 1e-12 * np.abs(R).max()
+        np.testing.assert_allclose(R, R.T, rtol=0, atol=1e-15 * np.abs(R).max())
+        S, _ = o.structure_factor(f)
+        for k in range(Lx):
+            for nq in range(Lz):
+                E = np.exp(1j * 2 * np.pi * nq / Lz * (z[:, None] - z[None, :]))
+                v = (E * C[k]).sum() / Lz
+                assert abs(v.imag) < 1e-12 * S.max() and abs(v.real - S[nq, k]) < 1e-12 * S.max(), (f, k, nq)
+    # diagonal: the mean square per row, from the fields at the sample steps
+    o2 = oracle.OracleLattice(Lx, Lz, kT=1e-4, G=0.3, grad_c0=0.02, seed=3)
+    o2.step(5)
+    fl = o2.fields()  # the pre-collision fields of step 5, which is sampled next
+    o2.set_sampling(5, 1)
+    o2.set_correlations(["c"])
+    o2.step(1)
+    zz = np.arange(Lz) + 0.5 - Lz / 2
+    dc = fl["rhoA"] / (fl["rhoA"] + fl["rhoB"]) - (0.5 + 0.02 * zz)[:, None]
+    R1, _ = o2.correlation("c")
+    np.testing.assert_allclose(np.diag(R1), (dc ** 2).mean(axis=1), rtol=1e-12)
+
+
 # ---------------------------------------------------------------- Fourier transform
 def test_dft_power_single_mode_and_parseval():
     """Appendix: S(q) = |delta phi(q)|^2 with the unitary lattice transform.  A single plane
