@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--profile-precision", default="dev32", choices=["dev32", "fp64"])
     ap.add_argument("--profile-generic", action="store_true", help="small case with per-thread staging")
     ap.add_argument("--profile-tile", type=int, default=128, help="tile width of the small case")
-    ap.add_argument("--profile-rows", type=int, default=64, help="rows per block of the small case")
+    ap.add_argument("--profile-rows", type=int, default=None,
+                    help="rows per block of the profiling cases (default 64 small, 256 ensemble)")
     ap.add_argument("--profile-ensemble", type=int, default=0,
                     help="run the ensemble with this many seeds for 6 steps (for ncu captures)")
     return ap.parse_args()
@@ -351,15 +352,16 @@ def run_profile_small(kT, precision, bulk=True, tile=128, rows=64):
     print("profile-small ok")
 
 
-def run_profile_ensemble(n_seeds):
-    """The ensemble mix with fewer seeds (8 seeds: 96 lattices, 8.4 M sites, 1.2 GB of state),
-    the benchmark's precision and tile, 6 steps (for ncu captures)."""
+def run_profile_ensemble(n_seeds, rows=256):
+    """The ensemble mix with fewer seeds (8 seeds: 96 lattices, 8.4 M sites, 1.2 GB of state;
+    16 seeds: 2.4 GB), the benchmark's precision, 128-column tiles of `rows` rows, 6 steps (for
+    ncu captures)."""
     import torch
 
     from paper_1808_05168_gb300 import Simulation, workloads
 
     with Simulation(workloads.c3(n_seeds=n_seeds), precision="dev32") as sim:
-        sim.set_tile(128, 256)
+        sim.set_tile(128, rows)
         sim.step(6)
         sim.synchronize()
     torch.cuda.synchronize()
@@ -369,10 +371,10 @@ def run_profile_ensemble(n_seeds):
 if __name__ == "__main__":
     a = parse()
     if a.profile_ensemble:
-        run_profile_ensemble(a.profile_ensemble)
+        run_profile_ensemble(a.profile_ensemble, rows=a.profile_rows or 256)
     elif a.profile_small:
         run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic, tile=a.profile_tile,
-                          rows=a.profile_rows)
+                          rows=a.profile_rows or 64)
     elif a.impl == "reference":
         run_reference(a)
     else:

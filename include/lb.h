@@ -139,6 +139,28 @@ int lb_structure_factor(lb_ctx* ctx, int lattice, int field, int mode, double* h
  * LB_ERR_SIZE.  Zeros before the first sample; *n_samples (may be NULL) receives the count. */
 int lb_profile(lb_ctx* ctx, int lattice, int field, double* host_out, size_t n_out, int64_t* n_samples);
 
+/* Two-point correlations of the sampled fields (Sec. III.A-B real-space correlations,
+ * Eqs. VELOCITY_CORR and CONCENTRATION_CORR; Appendix A mixed correlation C(q_x, z, z')),
+ * accumulated on every sample step from this call on (the count restarts here and at
+ * lb_reset_statistics).  field_mask: bit f set for field f (LB_FIELD_RHO .. LB_FIELD_UZ), 0 turns
+ * them off; modes: n_modes <= LB_CORR_MAX_MODES mode indices k (q_x = 2 pi k / Lx, 0 <= k < Lx of
+ * every lattice) whose mixed correlations are kept.  Same lattice-size rule as lb_set_sampling.
+ * Device memory: 8 (4 + 8 n_modes) sum_lattices Lz^2 bytes. */
+#define LB_CORR_MAX_MODES 16
+int lb_set_correlations(lb_ctx* ctx, int field_mask, int n_modes, const int* modes);
+
+/* Equal-x real-space correlation <dphi(x, z) dphi(x, z')> of one field of one lattice, averaged
+ * over x and the samples: host_out[z * Lz + z'], n_out == Lz * Lz doubles (LB_ERR_SIZE otherwise);
+ * LB_ERR_STATE if the field is not enabled by lb_set_correlations. */
+int lb_correlation(lb_ctx* ctx, int lattice, int field, double* host_out, size_t n_out, int64_t* n_samples);
+
+/* Mixed correlation C(q_x, z, z') = <dphi(q_x, z)^* dphi(q_x, z')> of Appendix A for the
+ * mode_index-th mode of lb_set_correlations, with the unitary partial transform
+ * dphi(q_x, z) = Lx^(-1/2) sum_x dphi(x, z) exp(-i q_x x): host_out[2 (z * Lz + z') + {0, 1}] =
+ * (real, imaginary) part, n_out == 2 Lz^2 doubles; errors as lb_correlation. */
+int lb_mode_correlation(lb_ctx* ctx, int lattice, int field, int mode_index, double* host_out, size_t n_out,
+                        int64_t* n_samples);
+
 /* Spatial mean of the mechanical pressure (Sec. III.C) at the latest sample, and its average
  * over all samples (compensated double-precision sum).  Either pointer may be NULL. */
 int lb_mean_pressure(lb_ctx* ctx, int lattice, double* last, double* time_avg);

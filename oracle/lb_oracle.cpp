@@ -199,6 +199,7 @@ struct Sim {
   // correlation (1/Lx) sum_x dphi(x, z) dphi(x, z') (Sec. III.A-B) and, for the q_x mode
   // indices in corr_modes, C(q_x, z, z') = dphi(q_x, z)^* dphi(q_x, z') (Appendix A)
   int corr_mask = 0;
+  int64_t corr_nsamples = 0;  // samples since the correlations were (re)enabled
   std::vector<int> corr_modes;
   std::vector<double> R_acc;  // [4][Lz][Lz]
   std::vector<double> C_acc;  // [4][modes][Lz][Lz][re, im]
@@ -443,6 +444,7 @@ void correlate(Sim<R>& S, const Pre<R>& P) {
   const size_t LL = (size_t)Lz * Lz, nm = S.corr_modes.size();
   const double two_pi = 6.283185307179586476925286766559;
   std::vector<double> field, re((size_t)Lz), im((size_t)Lz);
+  S.corr_nsamples += 1;
   for (int fld = 0; fld < 4; ++fld) {
     if (!(S.corr_mask & (1 << fld))) continue;
     sampled_field(S, P, fld, field);
@@ -694,6 +696,7 @@ int64_t olb_structure_factor(void* h, int field, double* out) {
 void olb_set_correlations(void* h, int mask, int n_modes, const int* modes) {
   olb_sim* S = (olb_sim*)h;
   S->corr_mask = mask & 15;
+  S->corr_nsamples = 0;
   S->corr_modes.assign(modes, modes + n_modes);
   const size_t LL = (size_t)S->Lz * S->Lz;
   S->R_acc.assign(4 * LL, 0.0);
@@ -704,16 +707,18 @@ void olb_set_correlations(void* h, int mask, int n_modes, const int* modes) {
 int64_t olb_correlation(void* h, int field, double* out) {
   olb_sim* S = (olb_sim*)h;
   const size_t LL = (size_t)S->Lz * S->Lz;
-  for (size_t i = 0; i < LL; ++i) out[i] = S->nsamples ? S->R_acc[field * LL + i] / (double)S->nsamples : 0.0;
-  return S->nsamples;
+  const int64_t n = S->corr_nsamples;
+  for (size_t i = 0; i < LL; ++i) out[i] = n ? S->R_acc[field * LL + i] / (double)n : 0.0;
+  return n;
 }
 
 int64_t olb_mode_correlation(void* h, int field, int mode_index, double* out) {
   olb_sim* S = (olb_sim*)h;
   const size_t LL = (size_t)S->Lz * S->Lz, nm = S->corr_modes.size();
   const double* C = S->C_acc.data() + ((size_t)field * nm + mode_index) * LL * 2;
-  for (size_t i = 0; i < 2 * LL; ++i) out[i] = S->nsamples ? C[i] / (double)S->nsamples : 0.0;
-  return S->nsamples;
+  const int64_t n = S->corr_nsamples;
+  for (size_t i = 0; i < 2 * LL; ++i) out[i] = n ? C[i] / (double)n : 0.0;
+  return n;
 }
 
 // Time-averaged row means of field k (0 rho, 1 c, 2 Ux, 3 Uz, 4 P) at rows 0..Lz-1.

@@ -136,6 +136,28 @@ class Simulation:
         n = capi.lb_profile(self.h, lattice, FIELDS.get(field, field), out)
         return out, n
 
+    def set_correlations(self, fields=("c", "ux"), modes=()):
+        """Accumulate, from the next sample on, the real-space correlations of `fields` and their
+        mixed correlations C(q_x, z, z') for the q_x mode indices `modes`."""
+        mask = 0
+        for f in fields:
+            mask |= 1 << FIELDS.get(f, f)
+        capi.lb_set_correlations(self.h, mask, list(modes))
+
+    def correlation(self, field: str = "c", lattice: int = 0):
+        """<dphi(x, z) dphi(x, z')> averaged over x and the samples, (Lz, Lz), and the count."""
+        Lz = self.shape(lattice)[1]
+        out = np.empty((Lz, Lz), np.float64)
+        n = capi.lb_correlation(self.h, lattice, FIELDS.get(field, field), out)
+        return out, n
+
+    def mode_correlation(self, field: str = "c", mode_index: int = 0, lattice: int = 0):
+        """C(q_x, z, z') of the mode_index-th requested mode, (Lz, Lz) complex, and the count."""
+        Lz = self.shape(lattice)[1]
+        out = np.empty((Lz, Lz, 2), np.float64)
+        n = capi.lb_mode_correlation(self.h, lattice, FIELDS.get(field, field), mode_index, out)
+        return out[..., 0] + 1j * out[..., 1], n
+
     def mean_pressure(self, lattice: int = 0):
         return capi.lb_mean_pressure(self.h, lattice)
 

@@ -39,11 +39,12 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 # Every symbol declared in include/lb.h.
 EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "lb_set_tile", "lb_get_tile",
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
-           "lb_profile", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
+           "lb_profile", "lb_set_correlations", "lb_correlation", "lb_mode_correlation", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
            "lb_debug_box_muller",
            "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient")
 LB_NOALLOC_MAX_POINTS = 1 << 18
+LB_CORR_MAX_MODES = 16
 
 
 class LBError(RuntimeError):
@@ -95,6 +96,9 @@ def load():
             "lb_structure_factor": [vp, i, i, i, dp, sz, i64p],
             "lb_mean_pressure": [vp, i, dp, dp],
             "lb_profile": [vp, i, i, dp, sz, i64p],
+            "lb_set_correlations": [vp, i, i, ip],
+            "lb_correlation": [vp, i, i, dp, sz, i64p],
+            "lb_mode_correlation": [vp, i, i, i, dp, sz, i64p],
             "lb_mass": [vp, i, dp],
             "lb_get_populations": [vp, i, dp, sz],
             "lb_set_populations": [vp, i, dp, sz],
@@ -200,6 +204,24 @@ def lb_structure_factor(h, lattice, field, mode, out: np.ndarray):
 def lb_profile(h, lattice, field, out: np.ndarray):
     n = ctypes.c_int64()
     _check(load().lb_profile(h, int(lattice), int(field), _dptr(out), out.size, ctypes.byref(n)), "lb_profile")
+    return n.value
+
+
+def lb_set_correlations(h, field_mask, modes=()):
+    m = (ctypes.c_int * max(1, len(modes)))(*[int(k) for k in modes])
+    _check(load().lb_set_correlations(h, int(field_mask), len(modes), m), "lb_set_correlations")
+
+
+def lb_correlation(h, lattice, field, out: np.ndarray):
+    n = ctypes.c_int64()
+    _check(load().lb_correlation(h, int(lattice), int(field), _dptr(out), out.size, ctypes.byref(n)), "lb_correlation")
+    return n.value
+
+
+def lb_mode_correlation(h, lattice, field, mode_index, out: np.ndarray):
+    n = ctypes.c_int64()
+    _check(load().lb_mode_correlation(h, int(lattice), int(field), int(mode_index), _dptr(out), out.size,
+                                      ctypes.byref(n)), "lb_mode_correlation")
     return n.value
 
 

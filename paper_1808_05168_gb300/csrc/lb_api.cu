@@ -64,6 +64,17 @@ struct lb_ctx {
   double* prof_sum = nullptr;   // 5 * n_rows: z-profiles
   double* prof_comp = nullptr;
   int* d_row_lat = nullptr;     // n_rows: lattice of each global row
+  // two-point correlations (lb_set_correlations)
+  int corr_mask = 0;
+  std::vector<int> corr_modes;
+  double* corr_R = nullptr;
+  double* corr_C = nullptr;
+  size_t corr_R_n = 0, corr_C_n = 0;  // doubles
+  int4* d_corr_real = nullptr;
+  int4* d_corr_mode = nullptr;
+  int* d_corr_modes = nullptr;
+  int n_corr_real = 0, n_corr_mode = 0;
+  int64_t corr_samples = 0;
   void* tmp = nullptr;      // 4 * n_sites complex
   double* acc_sum = nullptr;
   double* acc_comp = nullptr;
@@ -410,6 +421,13 @@ cudaError_t enqueue_sample(lb_ctx* c) {
                             c->prof_sum, c->prof_comp, c->stream);
   if (e != cudaSuccess) return e;
   c->launches += 4;
+  if (c->corr_mask) {
+    CorrPlan cp{c->d_diag, c->d_corr_real, c->n_corr_real, c->d_corr_mode, c->n_corr_mode, c->d_corr_modes,
+                (int)c->corr_modes.size()};
+    e = launch_corr<real>(cp, (const real*)c->fields, c->tmp, c->corr_R, c->corr_C, c->stream);
+    if (e != cudaSuccess) return e;
+    c->launches += (c->n_corr_real > 0) + (c->n_corr_mode > 0);
+  }
   return launch_finalize(c->d_diag, c->n_lat, c->partials, c->stats, c->stream);
 }
 
@@ -578,6 +596,7 @@ int step_impl(lb_ctx* c, int64_t n) {
     }
     if (e != cudaSuccess) return cuda_err(e);
     c->nsamples += (int64_t)so.size();
+    if (c->corr_mask) c->corr_samples += (int64_t)so.size();
     if (seg & 1) c->cur ^= 1;
     c->t += seg;
     done += seg;
@@ -955,6 +974,134 @@ int lb_structure_factor(lb_ctx* c, int lattice, int field, int mode, double* out
   return LB_OK;
 }
 
+namespace {
+void corr_free(lb_ctx* c) {
+  void* ptrs[] = {c->corr_R, c->corr_C, c->d_corr_real, c->d_corr_mode, c->d_corr_modes};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->bytes -= (c->corr_R_n + c->corr_C_n) * sizeof(double) +
+              ((size_t)c->n_corr_real + (size_t)c->n_corr_mode) * sizeof(int4) + c->corr_modes.size() * sizeof(int);
+  c->corr_R = c->corr_C = nullptr;
+  c->d_corr_real = c->d_corr_mode = nullptr;
+  c->d_corr_modes = nullptr;
+  c->corr_R_n = c->corr_C_n = 0;
+  c->n_corr_real = c->n_corr_mode = 0;
+  c->corr_modes.clear();
+  c->corr_mask = 0;
+  c->corr_samples = 0;
+}
+}  // namespace
+
+int lb_set_correlations(lb_ctx* c, int field_mask, int n_modes, const int* modes) {
+  if (!c || field_mask < 0 || field_mask > 15 || n_modes < 0 || n_modes > LB_CORR_MAX_MODES ||
+      (n_modes > 0 && !modes))
+    return LB_ERR_BAD_PARAM;
+  for (int m = 0; m < n_modes; ++m)
+    for (const lb_params& p : c->params)
+      if (modes[m] < 0 || modes[m] >= p.Lx) return LB_ERR_BAD_PARAM;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  drop_graphs(c);
+  corr_free(c);
+  if (field_mask == 0) return LB_OK;
+  for (const lb_params& p : c->params)
+    if (!is_pow2(p.Lx) || !is_pow2(p.Lz) || p.Lx < 2 || p.Lx > 8192 || p.Lz > 8192) return LB_ERR_BAD_PARAM;
+  rc = alloc_diag(c);
+  if (rc) return rc;
+  // offsets and tiles
+  std::vector<int4> rt, mt;
+  size_t rn = 0, cn = 0;
+  for (int i = 0; i < c->n_lat; ++i) {
+    const int Lz = c->params[i].Lz, nt = (Lz + CORR_TILE - 1) / CORR_TILE;
+    c->diag[i].r_off = (int64_t)rn;
+    c->diag[i].c_off = (int64_t)cn;
+    rn += 4 * (size_t)Lz * Lz;
+    cn += 4 * (size_t)n_modes * Lz * Lz * 2;
+    for (int f = 0; f < 4; ++f) {
+      if (!(field_mask & (1 << f))) continue;
+      for (int a = 0; a < nt; ++a)
+        for (int b = 0; b < nt; ++b) {
+          rt.push_back(make_int4(i, f, a, b));
+          for (int m = 0; m < n_modes; ++m) mt.push_back(make_int4(i, f * n_modes + m, a, b));
+        }
+    }
+  }
+  // each size is recorded once its buffer exists, so that corr_free releases exactly those
+  rc = dev_alloc(c, &c->corr_R, rn * sizeof(double));
+  if (!rc) c->corr_R_n = rn;
+  if (!rc && cn) rc = dev_alloc(c, &c->corr_C, cn * sizeof(double));
+  if (!rc) c->corr_C_n = cn;
+  if (!rc) rc = dev_alloc(c, &c->d_corr_real, rt.size() * sizeof(int4));
+  if (!rc) c->n_corr_real = (int)rt.size();
+  if (!rc && !mt.empty()) rc = dev_alloc(c, &c->d_corr_mode, mt.size() * sizeof(int4));
+  if (!rc) c->n_corr_mode = (int)mt.size();
+  if (!rc && n_modes) rc = dev_alloc(c, &c->d_corr_modes, (size_t)n_modes * sizeof(int));
+  if (!rc) c->corr_modes.assign(modes, modes + n_modes);
+  if (rc) {
+    corr_free(c);
+    return rc;
+  }
+  if (cudaMemset(c->corr_R, 0, rn * sizeof(double)) != cudaSuccess ||
+      (cn && cudaMemset(c->corr_C, 0, cn * sizeof(double)) != cudaSuccess) ||
+      cudaMemcpy(c->d_corr_real, rt.data(), rt.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!mt.empty() &&
+       cudaMemcpy(c->d_corr_mode, mt.data(), mt.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (n_modes && cudaMemcpy(c->d_corr_modes, modes, (size_t)n_modes * sizeof(int), cudaMemcpyHostToDevice) !=
+                      cudaSuccess) ||
+      cudaMemcpy(c->d_diag, c->diag.data(), c->diag.size() * sizeof(DiagLattice), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    corr_free(c);
+    return LB_ERR_CUDA;
+  }
+  c->corr_mask = field_mask;
+  return LB_OK;
+}
+
+int lb_correlation(lb_ctx* c, int lattice, int field, double* out, size_t n_out, int64_t* n_samples) {
+  if (!lattice_ok(c, lattice) || field < 0 || field > 3 || !out) return LB_ERR_BAD_PARAM;
+  const int Lz = c->params[lattice].Lz;
+  const size_t LL = (size_t)Lz * Lz;
+  if (n_out != LL) return LB_ERR_SIZE;
+  if (!(c->corr_mask & (1 << field))) return LB_ERR_STATE;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  if (n_samples) *n_samples = c->corr_samples;
+  if (c->corr_samples == 0) {
+    std::fill(out, out + LL, 0.0);
+    return LB_OK;
+  }
+  if (cudaMemcpy(out, c->corr_R + c->diag[lattice].r_off + (size_t)field * LL, LL * sizeof(double),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LB_ERR_CUDA;
+  const double inv = 1.0 / (double)c->corr_samples;
+  for (size_t i = 0; i < LL; ++i) out[i] *= inv;
+  return LB_OK;
+}
+
+int lb_mode_correlation(lb_ctx* c, int lattice, int field, int mode_index, double* out, size_t n_out,
+                        int64_t* n_samples) {
+  if (!lattice_ok(c, lattice) || field < 0 || field > 3 || !out || mode_index < 0 ||
+      mode_index >= (int)c->corr_modes.size())
+    return LB_ERR_BAD_PARAM;
+  const int Lz = c->params[lattice].Lz;
+  const size_t LL = (size_t)Lz * Lz, nm = c->corr_modes.size();
+  if (n_out != 2 * LL) return LB_ERR_SIZE;
+  if (!(c->corr_mask & (1 << field))) return LB_ERR_STATE;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  if (n_samples) *n_samples = c->corr_samples;
+  if (c->corr_samples == 0) {
+    std::fill(out, out + 2 * LL, 0.0);
+    return LB_OK;
+  }
+  const size_t off = c->diag[lattice].c_off + (((size_t)field * nm + mode_index) * LL) * 2;
+  if (cudaMemcpy(out, c->corr_C + off, 2 * LL * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LB_ERR_CUDA;
+  const double inv = 1.0 / (double)c->corr_samples;
+  for (size_t i = 0; i < 2 * LL; ++i) out[i] *= inv;
+  return LB_OK;
+}
+
 int lb_profile(lb_ctx* c, int lattice, int field, double* out, size_t n_out, int64_t* n_samples) {
   if (!lattice_ok(c, lattice) || field < 0 || field > LB_FIELD_P || !out) return LB_ERR_BAD_PARAM;
   const lb_params& p = c->params[lattice];
@@ -1060,6 +1207,10 @@ int lb_reset_statistics(lb_ctx* c) {
         cudaMemset(c->prof_comp, 0, 5 * (size_t)c->n_rows * sizeof(double)) != cudaSuccess)
       return LB_ERR_CUDA;
   }
+  c->corr_samples = 0;
+  if ((c->corr_R && cudaMemset(c->corr_R, 0, c->corr_R_n * sizeof(double)) != cudaSuccess) ||
+      (c->corr_C && cudaMemset(c->corr_C, 0, c->corr_C_n * sizeof(double)) != cudaSuccess))
+    return LB_ERR_CUDA;
   return LB_OK;
 }
 
@@ -1098,7 +1249,8 @@ void lb_destroy(lb_ctx* c) {
   void* ptrs[] = {c->d_lat,   c->d_rows,     c->d_items,    c->f[0],      c->f[1],       c->fields,
                   c->tmp,     c->acc_sum,    c->acc_comp,   c->partials,  c->stats,      c->d_diag,
                   c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass,
-                  c->pfield, c->prof_sum, c->prof_comp, c->d_row_lat};
+                  c->pfield, c->prof_sum, c->prof_comp, c->d_row_lat, c->corr_R, c->corr_C, c->d_corr_real,
+                  c->d_corr_mode, c->d_corr_modes};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;

@@ -452,6 +452,67 @@ cudaError_t launch_profiles(const DiagLattice* lat, const int* row_lat, int n_ro
   return cudaGetLastError();
 }
 
+// Real-space correlation of one sample: block (CORR_TILE^2 threads) per (lattice, field, z tile,
+// z' tile); x runs in chunks of 32 staged in shared memory, each chunk's products summed in the
+// working precision and the chunk sums in double.
+template <class real>
+__global__ void corr_real_kernel(const DiagLattice* __restrict__ lat, const int4* __restrict__ tasks,
+                                 const real* __restrict__ fields, double* __restrict__ R) {
+  constexpr int T = CORR_TILE;
+  __shared__ real a[32][T + 1], b[32][T + 1];
+  const int4 t = tasks[blockIdx.x];
+  const DiagLattice& L = lat[t.x];
+  const int Lx = L.Lx, Lz = L.Lz, fld = t.y, z0 = t.z * T, zp0 = t.w * T;
+  const int tz = threadIdx.x % T, tzp = threadIdx.x / T;
+  const real* f = fields + 4 * L.site_off + (int64_t)fld * Lx * Lz;
+  double acc = 0.0;
+  for (int x0 = 0; x0 < Lx; x0 += 32) {
+    for (int i = threadIdx.x; i < 32 * T; i += T * T) {
+      const int xx = i & 31, zz = i >> 5, x = x0 + xx, z = z0 + zz, zp = zp0 + zz;
+      a[xx][zz] = (x < Lx && z < Lz) ? f[(int64_t)z * Lx + x] : real(0);
+      b[xx][zz] = (x < Lx && zp < Lz) ? f[(int64_t)zp * Lx + x] : real(0);
+    }
+    __syncthreads();
+    real sum = 0;
+#pragma unroll 8
+    for (int xx = 0; xx < 32; ++xx) sum += a[xx][tz] * b[xx][tzp];
+    acc += (double)sum;
+    __syncthreads();
+  }
+  const int z = z0 + tz, zp = zp0 + tzp;
+  if (z < Lz && zp < Lz) R[L.r_off + ((int64_t)fld * Lz + z) * Lz + zp] += acc / (double)Lx;
+}
+
+// Mode correlation of one sample: thread per (z, z') of a tile, from the row transforms
+// X(q, z) = sum_x dphi(x, z) exp(-i q x) (unnormalised): C += conj(X(q, z)) X(q, z') / Lx.
+template <class real>
+__global__ void corr_mode_kernel(const DiagLattice* __restrict__ lat, const int4* __restrict__ tasks,
+                                 const int* __restrict__ modes, int n_modes, const Cplx<real>* __restrict__ tmp,
+                                 double* __restrict__ C) {
+  constexpr int T = CORR_TILE;
+  const int4 t = tasks[blockIdx.x];
+  const DiagLattice& L = lat[t.x];
+  const int Lx = L.Lx, Lz = L.Lz, fld = t.y / n_modes, m = t.y - fld * n_modes, k = modes[m];
+  const int z = t.z * T + (int)threadIdx.x % T, zp = t.w * T + (int)threadIdx.x / T;
+  if (z >= Lz || zp >= Lz) return;
+  const Cplx<real>* X = tmp + 4 * L.site_off + (int64_t)fld * Lz * Lx;
+  const Cplx<real> u = X[(int64_t)z * Lx + k], v = X[(int64_t)zp * Lx + k];
+  const double ur = u.re, ui = u.im, vr = v.re, vi = v.im, inv = 1.0 / (double)Lx;
+  double* c = C + L.c_off + ((((int64_t)fld * n_modes + m) * Lz + z) * Lz + zp) * 2;
+  c[0] += (ur * vr + ui * vi) * inv;
+  c[1] += (ur * vi - ui * vr) * inv;
+}
+
+template <class real>
+cudaError_t launch_corr(const CorrPlan& p, const real* fields, const void* tmp, double* R, double* C, cudaStream_t s) {
+  if (p.n_real_tasks > 0)
+    corr_real_kernel<real><<<p.n_real_tasks, CORR_TILE * CORR_TILE, 0, s>>>(p.lat, p.real_tasks, fields, R);
+  if (p.n_mode_tasks > 0)
+    corr_mode_kernel<real><<<p.n_mode_tasks, CORR_TILE * CORR_TILE, 0, s>>>(
+        p.lat, p.mode_tasks, p.modes, p.n_modes, (const Cplx<real>*)tmp, C);
+  return cudaGetLastError();
+}
+
 #define LB_INST(real)                                                                                        \
   template size_t sf_smem_bytes<real>(int);                                                                  \
   template cudaError_t prepare_sf<real>(int, int);                                                           \
@@ -462,7 +523,8 @@ cudaError_t launch_profiles(const DiagLattice* lat, const int* row_lat, int n_ro
   template cudaError_t launch_from_absolute<real>(const double*, const BgParams&, real*, cudaStream_t);      \
   template cudaError_t launch_init_rest<real>(real*, const BgParams&, cudaStream_t);                         \
   template cudaError_t launch_profiles<real>(const DiagLattice*, const int*, int, const real*, const real*,    \
-                                             double*, double*, cudaStream_t);
+                                             double*, double*, cudaStream_t);                                \
+  template cudaError_t launch_corr<real>(const CorrPlan&, const real*, const void*, double*, double*, cudaStream_t);
 LB_INST(float)
 LB_INST(double)
 

@@ -244,6 +244,8 @@ struct DiagLattice {
   int Lx, Lz;
   int64_t site_off;    // offset in sites of this lattice in fields / spectra
   int row_off;         // offset of row 0 in the per-row tables (profiles)
+  int64_t r_off;       // offset (doubles) of the real-space correlations [4][Lz][Lz]
+  int64_t c_off;       // offset (doubles) of the mode correlations [4][modes][Lz][Lz][re, im]
   int item_begin, item_end;
   double P_bg_mean;    // spatial mean of the background pressure (FP64 mode: 0)
   double mass_bg[2];   // background mass per species (FP64 mode: 0)
@@ -285,6 +287,24 @@ int sf_column_strip(int max_Lz);
 template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
                       cudaStream_t s);
+
+// Two-point correlations of one sample (Sec. III.A-B, Appendix A), in tiles of CORR_TILE x
+// CORR_TILE rows (z, z'): real_tasks = (lattice, field, z tile, z' tile) add
+// (1/Lx) sum_x dphi(x, z) dphi(x, z') to R; mode_tasks = (lattice, field * n_modes + m, z tile,
+// z' tile) add dphi(q_m, z)^* dphi(q_m, z') (unitary partial transform in x) to C, from the row
+// transforms the structure-factor pass leaves in tmp.
+constexpr int CORR_TILE = 16;
+struct CorrPlan {
+  const DiagLattice* lat;
+  const int4* real_tasks;
+  int n_real_tasks;
+  const int4* mode_tasks;
+  int n_mode_tasks;
+  const int* modes;
+  int n_modes;
+};
+template <class real>
+cudaError_t launch_corr(const CorrPlan& p, const real* fields, const void* tmp, double* R, double* C, cudaStream_t s);
 
 // z-profiles (Sec. III.C): adds the row means of delta rho, delta c, Ux, Uz and the pressure
 // (deviation) of the sampled fields to per-row compensated sums [5][n_rows]; row_lat[r] is the

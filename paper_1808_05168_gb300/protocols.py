@@ -59,3 +59,19 @@ def ensemble_spectra(base: LatticeParams, seeds, steps: int, discard: int, every
             S = np.array([sim.structure_factor(f, lattice=i)[0] for i in range(len(runs))])
             out[f] = (S.mean(axis=0), S.std(axis=0, ddof=1) / np.sqrt(len(runs)) if len(runs) > 1 else 0 * S[0])
     return out
+
+
+def ensemble_correlations(base: LatticeParams, seeds, steps: int, discard: int, every: int = 10,
+                          fields=("c", "ux"), precision: str = "dev32"):
+    """Real-space correlations <dphi(x, z) dphi(x, z')>_x averaged over seeds (one batch).
+    Returns {field: (mean, stderr)} with arrays of shape (Lz, Lz)."""
+    runs = _batch_ids([replace(base, seed=s) for s in seeds])
+    out = {}
+    with Simulation(runs, precision=precision) as sim:
+        sim.set_sampling(discard, every)
+        sim.set_correlations(fields)
+        sim.step(steps)
+        for f in fields:
+            R = np.array([sim.correlation(f, lattice=i)[0] for i in range(len(runs))])
+            out[f] = (R.mean(axis=0), R.std(axis=0, ddof=1) / np.sqrt(len(runs)) if len(runs) > 1 else 0 * R[0])
+    return out

@@ -316,3 +316,50 @@ def test_box_muller_normals_of_both_precisions():
     err = np.abs(got32 - want)
     assert np.max(err) < 3e-6, (np.max(err), int(np.argmax(err)))
     assert capi.lb_debug_box_muller(capi.LB_PREC_DEV32, np.zeros(0, np.uint32)).size == 0
+    # the kernels form two pairs at a time in packed instructions and an odd one alone: shifted
+    # by one pair, every pair changes lane or form, and the values may not change
+    shifted = capi.lb_debug_box_muller(capi.LB_PREC_DEV32, words[2:])
+    np.testing.assert_array_equal(shifted, got32[2:])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_correlations_of_a_batch(prec):
+    """Sec. III.A-B real-space correlations <dphi(x, z) dphi(x, z')>_x and the Appendix A mixed
+    correlations C(q_x, z, z') of every field, for each lattice of a heterogeneous batch, against
+    the oracle.  FP32 deviations: within 1e-4 of the largest entry (the fields' own FP32
+    representation, squared)."""
+    ps = [LatticeParams(32, 16, kT=1e-4, G=0.5, grad_c0=0.3 / 16, seed=4, lattice_id=0),
+          LatticeParams(64, 8, kT=2e-4, G=0.3, grad_c0=-0.2 / 8, seed=4, lattice_id=1)]
+    fields = ("rho", "c", "ux", "uz")
+    modes = [0, 1, 5]
+    with Simulation(ps, precision=prec) as sim:
+        sim.set_sampling(10, 4)
+        sim.step(30)
+        sim.set_correlations(fields, modes)  # counts from here: samples at 30, 34, ...
+        sim.step(53)
+        R = {(i, f): sim.correlation(f, lattice=i) for i in range(2) for f in fields}
+        C = {(i, f, m): sim.mode_correlation(f, m, lattice=i) for i in range(2) for f in fields
+             for m in range(len(modes))}
+        with pytest.raises(capi.LBError):
+            capi.lb_mode_correlation(sim.h, 0, 0, len(modes), np.empty((16, 16, 2)))
+        sim.set_correlations(("c",))
+        with pytest.raises(capi.LBError):  # not enabled any more
+            sim.correlation("ux")
+    for i, p in enumerate(ps):
+        o = oracle_of(p)
+        o.set_sampling(10, 4)
+        o.step(30)
+        o.set_correlations(fields, modes)
+        o.step(53)
+        for f in fields:
+            want, n = o.correlation(f)
+            got, ng = R[(i, f)]
+            assert n == ng == 14
+            tol = (1e-12 if prec == "fp64" else 1e-4) * np.abs(want).max()
+            assert np.max(np.abs(got - want)) <= tol, (i, f, np.max(np.abs(got - want)), np.abs(want).max())
+            for m in range(len(modes)):
+                cw, _ = o.mode_correlation(f, m)
+                cg, _ = C[(i, f, m)]
+                # FP64: the bar of the structure factors (row transforms by FFT against direct sums)
+                tol = (1e-9 if prec == "fp64" else 1e-4) * np.abs(cw).max()
+                assert np.max(np.abs(cg - cw)) <= tol, (i, f, m)

@@ -1,6 +1,8 @@
 """The CUDA path against the paper's closed forms and scaling statements, on seed ensembles
 (statistical tolerances, stated per test).  Set-up of Sec. III: Lx = 4 L, L = 32, kT = 1e-4,
 lambda_s = lambda_d = 1 (D = nu = 1/6 by Eqs. diff and vis), FP32 deviation storage."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -54,6 +56,33 @@ def test_nonequilibrium_spectra():
     mean_ratio = enh[k].sum() / (phi * qt[k] ** -4.0).sum()
     sigma = np.sqrt((err[k] ** 2).sum()) / (phi * qt[k] ** -4.0).sum()
     assert abs(mean_ratio - 1) < 0.15 + 3 * sigma, (mean_ratio, sigma)
+
+
+def test_real_space_correlations():
+    """Sec. III.A-B, Eqs. (VELOCITY_CORR), (CONCENTRATION_CORR): at equilibrium the equal-x
+    correlations are delta-like, <U U> = (kT/rho_bar) delta_zz' and <dc dc> = 0.75 kT delta_zz';
+    with grad c_0 = 0.01 the velocity correlations stay delta-like while the concentration ones
+    become long-ranged (positive well off the diagonal, across much of the channel)."""
+    interior = slice(2, 30)
+    base = LatticeParams(128, 32, kT=KT, G=0.0, grad_c0=0.0, **RATES)
+    eq = protocols.ensemble_correlations(base, range(300, 332), steps=22000, discard=2000, every=10,
+                                         fields=("c", "ux", "uz"))
+    for f, w in [("ux", KT), ("uz", KT), ("c", 0.75 * KT)]:
+        R = eq[f][0] / w
+        d = np.diag(R)[interior]
+        assert abs(d.mean() - 1) < 0.02, (f, d.mean())
+        off = R[interior, interior] - np.diag(np.diag(R[interior, interior]))
+        assert np.max(np.abs(off)) < 0.03, (f, np.max(np.abs(off)))
+    ne = protocols.ensemble_correlations(replace(base, grad_c0=0.01), range(400, 464), steps=42000, discard=2000,
+                                         every=10, fields=("c", "ux"))
+    Rc = ne["c"][0] / (0.75 * KT)
+    Ru = ne["ux"][0] / KT
+    offu = Ru[interior, interior] - np.diag(np.diag(Ru[interior, interior]))
+    assert np.max(np.abs(offu)) < 0.03
+    band = lambda R, k: np.mean([R[z, z + k] for z in range(4, 28 - k)])
+    near, far = band(Rc, 1), band(Rc, 8)
+    eq_far = np.max(np.abs([band(eq["c"][0] / (0.75 * KT), k) for k in (6, 8, 10)]))
+    assert near > 0.002 and far > 0.2 * near and far > 5 * eq_far, (near, far, eq_far)
 
 
 def test_nonequilibrium_pressure_protocol():
