@@ -56,7 +56,7 @@ struct LatticeDev {
 
 // Per-row constants of the background (zero in FP64 mode), rows 0..Lz-1.
 template <class real>
-struct RowConst {
+struct __align__(4 * sizeof(real)) RowConst {  // aligned: the first four load as one vector
   real bgA, bgB;    // rho_bar c^S_0(z)
   real dbgA, dbgB;  // background part of sum_l w_l c_lz rho^S(z + c_lz), wall ghosts included
   real nbA, nbB;    // background part of sum_l w_l |c_l|^2 rho^S(z + c_lz), ghosts included

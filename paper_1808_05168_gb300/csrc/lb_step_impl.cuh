@@ -322,12 +322,17 @@ __device__ __forceinline__ void collide_out(const Mom<real>& m, Pr<real> d, Pr<r
     M8 = mul2(pr(K.kA[8]), m.m8);
   }
   if (NOISE != NOISE_OFF) {
-    const P a1 = mul2(pr(K.kN[1]), cm), a6 = mul2(pr(K.kN[6]), cq), a8 = mul2(pr(K.kN[8]), cq);
+    // hom noise: the amplitude factors are constants, so the coefficients need no product
+    const bool loc = NOISE == NOISE_LOC;
+    const P a1 = loc ? mul2(pr(K.kN[1]), cm) : pr(K.kN[1], -K.kN[1]);
+    const P a3 = loc ? mul2(pr(K.kN[3]), cq) : pr(K.kN[3]), a4 = loc ? mul2(pr(K.kN[4]), cq) : pr(K.kN[4]);
+    const P a5 = loc ? mul2(pr(K.kN[5]), cq) : pr(K.kN[5]), a6 = loc ? mul2(pr(K.kN[6]), cq) : pr(K.kN[6]);
+    const P a8 = loc ? mul2(pr(K.kN[8]), cq) : pr(K.kN[8]);
     M1 = fma2(a1, nz[1], M1);
     M2 = fma2(a1, nz[2], M2);
-    M3 = fma2(mul2(pr(K.kN[3]), cq), nz[3], M3);
-    M4 = fma2(mul2(pr(K.kN[4]), cq), nz[4], M4);
-    M5 = fma2(mul2(pr(K.kN[5]), cq), nz[5], M5);
+    M3 = fma2(a3, nz[3], M3);
+    M4 = fma2(a4, nz[4], M4);
+    M5 = fma2(a5, nz[5], M5);
     if (UNIT) {
       M6 = mul2(a6, nz[6]);
       M7 = mul2(a6, nz[7]);
@@ -395,6 +400,40 @@ __device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float
 template <>
 __device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, double& n0, double& n1) {
   box_muller<double>(a, b, n0, n1);
+}
+
+// Two Box-Muller pairs at once, (a0, b0) and (a1, b1): normal_pair's arithmetic with its FP32
+// steps in packed two-lane instructions; n0 = (n0 of the first pair, n0 of the second), n1
+// likewise.  FP64: two normal_pair calls.
+template <class real>
+__device__ __forceinline__ void normal_pair2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, real& n00,
+                                             real& n01, real& n10, real& n11) {
+  normal_pair<real>(a0, b0, n00, n01);
+  normal_pair<real>(a1, b1, n10, n11);
+}
+template <>
+__device__ __forceinline__ void normal_pair2<float>(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, float& n00,
+                                                    float& n01, float& n10, float& n11) {
+  const float2 x1 = make_float2(unit_interval_bits(a0), unit_interval_bits(a1));
+  const float2 u1 = __fadd2_rn(x1, make_float2(-0.999999940395355224609375f, -0.999999940395355224609375f));
+  const float2 v = __ffma2_rn(u1, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  const float2 tl = __fmul2_rn(make_float2(-1.38629436111989061f, -1.38629436111989061f),
+                               make_float2(lg2_ftz(u1.x), lg2_ftz(u1.y)));
+  const float2 ts = __fmul2_rn(
+      v, __ffma2_rn(v, __ffma2_rn(v, make_float2(0.666666666666666667f, 0.666666666666666667f), make_float2(1.0f, 1.0f)),
+                    make_float2(2.0f, 2.0f)));
+  const float2 t = make_float2(v.x < 0.015625f ? ts.x : tl.x, v.y < 0.015625f ? ts.y : tl.y);
+  const float2 r = __fmul2_rn(t, make_float2(rsqrt_ftz(t.x), rsqrt_ftz(t.y)));
+  const float2 phi = __ffma2_rn(make_float2(6.28318530717959f, 6.28318530717959f),
+                                make_float2(unit_interval_bits(b0), unit_interval_bits(b1)),
+                                make_float2(-9.42477758729298f, -9.42477758729298f));
+  float s0, c0, s1, c1;
+  sincos_ftz(phi.x, s0, c0);
+  sincos_ftz(phi.y, s1, c1);
+  n00 = -r.x * c0;
+  n01 = -r.x * s0;
+  n10 = -r.y * c1;
+  n11 = -r.y * s1;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -467,12 +506,9 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
     U4 w4[4];
     philox_site(site, step, K.lid, K.key0, K.key1, w4);
     real g[14];
-    normal_pair<real>(w4[0].x, w4[0].y, g[0], g[1]);
-    normal_pair<real>(w4[0].z, w4[0].w, g[2], g[3]);
-    normal_pair<real>(w4[1].x, w4[1].y, g[4], g[5]);
-    normal_pair<real>(w4[1].z, w4[1].w, g[6], g[7]);
-    normal_pair<real>(w4[2].x, w4[2].y, g[8], g[9]);
-    normal_pair<real>(w4[2].z, w4[2].w, g[10], g[11]);
+    normal_pair2<real>(w4[0].x, w4[0].y, w4[0].z, w4[0].w, g[0], g[1], g[2], g[3]);
+    normal_pair2<real>(w4[1].x, w4[1].y, w4[1].z, w4[1].w, g[4], g[5], g[6], g[7]);
+    normal_pair2<real>(w4[2].x, w4[2].y, w4[2].z, w4[2].w, g[8], g[9], g[10], g[11]);
     normal_pair<real>(w4[3].x, w4[3].y, g[12], g[13]);
     if (NOISE == NOISE_LOC) {
       const real sm = sqrt_pos<real>(rs.x * rs.y * inv);
@@ -720,7 +756,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   const int my_plane = (tid & 31) * NW + (tid >> 5);
   auto stage_row = [&](int r) {
     if (r < 0 || r >= Lz || r > z1) return;
-    const int slot = r % NSI;
+    const int slot = (unsigned)r % NSI;  // r >= 0
     uint64_t* bar = bars + slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
     if (my_plane < 18) {
@@ -749,7 +785,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     }
   };
   auto wait_row = [&](int r) {
-    const int slot = r % NSI;
+    const int slot = (unsigned)r % NSI;  // r >= 0
     const unsigned par = (ph >> slot) & 1u;
     if (!mbar_try_wait(bars + slot, par)) {
       const uint64_t t0 = global_ns();
@@ -765,7 +801,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     ph ^= 1u << slot;
   };
   auto rho_at = [&](int r, int j) {
-    const real* sb = instage + (r % NSI) * 18 * SW;
+    const real* sb = instage + ((unsigned)r % NSI) * 18 * SW;
     Pr<real> v[9];
     read_bulk<real, SW>(sb, j, r > 0, r < Lz - 1, k9, k36, v);
     return sum9<real>(v);
@@ -816,7 +852,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real* sb = instage + (z % NSI) * 18 * SW;
+      const real* sb = instage + ((unsigned)z % NSI) * 18 * SW;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
       // both variants are inlined; the branch is uniform over the block (one lattice per item)
@@ -1082,21 +1118,27 @@ cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nste
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
 }
 
-// The normals of the step kernels for given Philox word pairs (test hook).
+// The normals of the step kernels for given Philox word pairs (test hook): thread j forms pairs
+// 2j and 2j + 1 together as the step kernels do, a trailing odd pair alone.
 template <class real>
 __global__ void debug_normals_kernel(const uint32_t* __restrict__ words, int64_t n_pairs, double* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pairs) return;
-  real n0, n1;
-  normal_pair<real>(words[2 * i], words[2 * i + 1], n0, n1);
-  out[2 * i] = (double)n0;
-  out[2 * i + 1] = (double)n1;
+  const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i + 1 < n_pairs) {
+    real n[4];
+    normal_pair2<real>(words[2 * i], words[2 * i + 1], words[2 * i + 2], words[2 * i + 3], n[0], n[1], n[2], n[3]);
+    for (int k = 0; k < 4; ++k) out[2 * i + k] = (double)n[k];
+  } else if (i < n_pairs) {
+    real n0, n1;
+    normal_pair<real>(words[2 * i], words[2 * i + 1], n0, n1);
+    out[2 * i] = (double)n0;
+    out[2 * i + 1] = (double)n1;
+  }
 }
 
 template <class real>
 cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double* out, cudaStream_t s) {
   if (n_pairs <= 0) return cudaSuccess;
-  const int64_t blocks = (n_pairs + 255) / 256;
+  const int64_t blocks = ((n_pairs + 1) / 2 + 255) / 256;
   debug_normals_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(words, n_pairs, out);
   return cudaGetLastError();
 }
