@@ -445,7 +445,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Everything of one site after its moments are known and the densities of its row and the two
 // neighbouring rows sit in the ring: forces, velocity, optional sampling, noise, collision of
 // both species and the output.
-template <class real, bool SAMPLE, int NOISE, bool UNIT, bool TO_GLOBAL, int STRIDE>
+template <class real, bool SAMPLE, int NOISE, bool UNIT, bool ASTAR, bool TO_GLOBAL, int STRIDE>
 __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& m,
                                             const Pr<real>* ring, int bc, int bu, int bd, uint32_t site,
                                             uint32_t step, real* fl, real* pl, int LzLx, double& acc_p,
@@ -467,7 +467,7 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
   const real FnAx = gA * sx.y, FnAz = gA * sz.y, FnBx = gB * sx.x, FnBz = gB * sz.x;
   const real FNx = FnAx + FnBx, FNz = FnAz + FnBz;
   P Fx, Fz;
-  if (flags & DF_ASTAR) {
+  if (ASTAR) {
     // a* makes the non-ideal acceleration common: rho^S a^S = (rho^S / rho) F_NI
     const P cs = mul2(rs, pr(inv));
     Fx = mul2(cs, pr(FNx));
@@ -677,19 +677,24 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
       const real* sb = stage + (z & (NS - 1)) * 18 * W;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
-      // both variants are inlined; the branch is uniform over the block (one lattice per item)
-      auto site = [&](auto unit) {
+      // the variants are inlined; the branches are uniform over the block (one lattice per item)
+      auto site = [&](auto unit, auto astar) {
         Pr<real> v[9];
         read_generic(sb, W, tid + 1, below, above, k9, k36, v);
         Mom<real> m = moments<real>(v);
         if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
-        site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
+        site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
             K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags);
       };
-      if (flags & DF_UNIT) site(BoolC<true>());
-      else site(BoolC<false>());
+      if (flags & DF_UNIT) {
+        if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>());
+        else site(BoolC<true>(), BoolC<false>());
+      } else {
+        if (flags & DF_ASTAR) site(BoolC<false>(), BoolC<true>());
+        else site(BoolC<false>(), BoolC<false>());
+      }
     }
   }
   cp_wait<0>();  // nothing may land in shared memory after the item
@@ -855,19 +860,24 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       const real* sb = instage + ((unsigned)z % NSI) * 18 * SW;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
-      // both variants are inlined; the branch is uniform over the block (one lattice per item)
-      auto site = [&](auto unit) {
+      // the variants are inlined; the branches are uniform over the block (one lattice per item)
+      auto site = [&](auto unit, auto astar) {
         Pr<real> v[9];
         read_bulk<real, SW>(sb, tid + PAD, below, above, k9, k36, v);
         Mom<real> m = moments<real>(v);
         if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
-        site_update<real, SAMPLE, NOISE, decltype(unit)::value, true, 0>(
+        site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
             K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags);
       };
-      if (flags & DF_UNIT) site(BoolC<true>());
-      else site(BoolC<false>());
+      if (flags & DF_UNIT) {
+        if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>());
+        else site(BoolC<true>(), BoolC<false>());
+      } else {
+        if (flags & DF_ASTAR) site(BoolC<false>(), BoolC<true>());
+        else site(BoolC<false>(), BoolC<false>());
+      }
     }
   }
   if (!ok) {
