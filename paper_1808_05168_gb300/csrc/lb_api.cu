@@ -415,6 +415,9 @@ cudaError_t enqueue_sample(lb_ctx* c) {
   p.max_Lx = c->max_Lx;
   p.max_Lz = c->max_Lz;
   p.col_strip = c->col_strip;
+  p.prof_sum = c->prof_sum;
+  p.prof_comp = c->prof_comp;
+  p.n_rows = c->n_rows;
   cudaError_t e = launch_sf<real>(p, (const real*)c->fields, c->tmp, c->acc_sum, c->acc_comp, c->stream);
   if (e != cudaSuccess) return e;
   e = launch_profiles<real>(c->d_diag, c->d_row_lat, c->n_rows, (const real*)c->fields, (const real*)c->pfield,

@@ -71,13 +71,21 @@ __host__ __device__ __forceinline__ int rows_per_block(int Lx, int Lz) {
   return r < Lz ? r : Lz;
 }
 
+__device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v) {
+  const double t = sum + v;
+  if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
+  else comp += (v - t) + sum;
+  sum = t;
+}
+
 template <class real>
-__global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const real* fields, Cplx<real>* tmp) {
+__global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const real* fields, Cplx<real>* tmp,
+                               double* prof_sum, double* prof_comp, int n_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int2 task = tasks[blockIdx.x];
   const DiagLattice L = lat[task.x];
-  const int n = L.Lx, logn = ilog2(n), half = n >> 1;
-  const int R = rows_per_block(L.Lx, L.Lz), lr = ilog2(R);
+  const int n = L.Lx, logn = ilog2(n), half = n >> 1, H = sf_half(n);
+  const int R = rows_per_block(L.Lx, L.Lz);
   Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
   Cplx<real>* s = tw + (half > 0 ? half : 1);
   fill_twiddles<real>(tw, n);
@@ -102,8 +110,17 @@ __global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const 
     }
     __syncthreads();
   }
-  (void)lr;
-  for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) tmp[off + idx] = s[idx];
+  // q_x = 0 .. Lx/2 of each row; the q_x = 0 bin is the row sum, whose mean goes to the profile
+  const int64_t offh = 4 * L.site_off + (int64_t)task.y * H;
+  for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
+    const int r = idx / H, q = idx - r * H;
+    tmp[offh + idx] = s[r * n + q];
+  }
+  const int fld = task.y / L.Lz, z0 = task.y - fld * L.Lz;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const int64_t k = (int64_t)fld * n_rows + L.row_off + z0 + r;
+    neumaier_add(prof_sum[k], prof_comp[k], (double)s[r * n].re / (double)n);
+  }
 }
 
 // Kahan summation of non-negative terms: the estimate of the total is sum - comp.
@@ -114,12 +131,6 @@ __device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
   sum = t;
 }
 
-__device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v) {
-  const double t = sum + v;
-  if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
-  else comp += (v - t) + sum;
-  sum = t;
-}
 
 // Column pass: one block per (lattice, field, strip of cq adjacent q_x), cq = min(CQ, Lx), so that
 // every row of the strip is read and accumulated with contiguous accesses.  The fields are
@@ -138,11 +149,13 @@ __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const 
   Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
   Cplx<real>* s = tw + (half > 0 ? half : 1);
   fill_twiddles<real>(tw, n);
-  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx0;
+  const int H = sf_half(Lx);
+  const int64_t tbase = 4 * L.site_off + (int64_t)fld * H * n + qx0;  // compact row transforms
+  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx0;  // accumulators
   for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
     const int j = idx >> lcq, c = idx & (cq - 1);
     const int r = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[c * n + r] = tmp[base + (int64_t)j * Lx + c];
+    s[c * n + r] = qx0 + c < H ? tmp[tbase + (int64_t)j * H + c] : Cplx<real>{real(0), real(0)};
   }
   __syncthreads();
   for (int lg = 1; lg <= logn; ++lg) {
@@ -165,6 +178,7 @@ __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const 
   const real scale = real(1) / ((real)Lx * (real)n);
   for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
     const int j = idx >> lcq, c = idx & (cq - 1);
+    if (qx0 + c >= H) continue;
     const Cplx<real> v = s[c * n + j];
     const int64_t o = base + (int64_t)j * Lx + c;
     double sm = acc_sum[o], cp = acc_comp[o];
@@ -352,7 +366,8 @@ template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
                       cudaStream_t s) {
   const size_t smr = sf_smem_bytes<real>(p.max_Lx), smc = sf_cols_smem_bytes<real>(p.max_Lz, p.col_strip);
-  sf_rows_kernel<real><<<p.n_row_tasks, 256, smr, s>>>(p.lat, p.row_tasks, fields, (Cplx<real>*)tmp);
+  sf_rows_kernel<real><<<p.n_row_tasks, 256, smr, s>>>(p.lat, p.row_tasks, fields, (Cplx<real>*)tmp, p.prof_sum,
+                                                       p.prof_comp, p.n_rows);
   sf_cols_kernel<real><<<p.n_col_tasks, 256, smc, s>>>(p.lat, p.col_tasks, (const Cplx<real>*)tmp, acc_sum,
                                                        acc_comp, p.col_strip);
   return cudaGetLastError();
@@ -410,37 +425,28 @@ cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* o
   return cudaGetLastError();
 }
 
-// z-profiles (Sec. III.C): warp r of the grid sums global row r over x in a fixed order
-// (lane-strided partial sums, then a butterfly) for the four sampled fields and the pressure, and
-// adds the row means to the compensated per-row sums [5][n_rows].
+// z-profile of the pressure (Sec. III.C): warp r of the grid sums global row r of the sampled
+// pressure over x in a fixed order (lane-strided partial sums in the working precision, four
+// values at a time, then in double and a butterfly) and adds the row mean to the compensated sum.
 template <class real>
 __global__ void profile_kernel(const DiagLattice* __restrict__ lat, const int* __restrict__ row_lat, int n_rows,
-                               const real* __restrict__ fields, const real* __restrict__ pfield,
-                               double* __restrict__ prof_sum, double* __restrict__ prof_comp) {
+                               const real* __restrict__ pfield, double* __restrict__ prof_sum,
+                               double* __restrict__ prof_comp) {
   const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (r >= n_rows) return;  // whole warps
   const DiagLattice& L = lat[row_lat[r]];
   const int Lx = L.Lx, z = r - L.row_off;
-  const int64_t LzLx = (int64_t)Lx * L.Lz;
-  const real* f0 = fields + 4 * L.site_off + (int64_t)z * Lx;
   const real* p0 = pfield + L.site_off + (int64_t)z * Lx;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int x = lane; x < Lx; x += 32) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] += (double)f0[k * LzLx + x];
-    acc[4] += (double)p0[x];
+  double acc = 0.0;
+  if ((Lx & 3) == 0) {
+    for (int x = lane * 4; x < Lx; x += 128) acc += (double)((p0[x] + p0[x + 1]) + (p0[x + 2] + p0[x + 3]));
+  } else {
+    for (int x = lane; x < Lx; x += 32) acc += (double)p0[x];
   }
 #pragma unroll
-  for (int k = 0; k < 5; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-  if (lane == 0) {
-    const double inv = 1.0 / (double)Lx;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) neumaier_add(prof_sum[(int64_t)k * n_rows + r], prof_comp[(int64_t)k * n_rows + r],
-                                             acc[k] * inv);
-  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) neumaier_add(prof_sum[4 * (int64_t)n_rows + r], prof_comp[4 * (int64_t)n_rows + r], acc / (double)Lx);
 }
 
 template <class real>
@@ -448,7 +454,8 @@ cudaError_t launch_profiles(const DiagLattice* lat, const int* row_lat, int n_ro
                             const real* pfield, double* prof_sum, double* prof_comp, cudaStream_t s) {
   if (n_rows <= 0) return cudaSuccess;
   const int64_t blocks = ((int64_t)n_rows * 32 + 255) / 256;
-  profile_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(lat, row_lat, n_rows, fields, pfield, prof_sum, prof_comp);
+  profile_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(lat, row_lat, n_rows, pfield, prof_sum, prof_comp);
+  (void)fields;
   return cudaGetLastError();
 }
 
@@ -495,9 +502,13 @@ __global__ void corr_mode_kernel(const DiagLattice* __restrict__ lat, const int4
   const int Lx = L.Lx, Lz = L.Lz, fld = t.y / n_modes, m = t.y - fld * n_modes, k = modes[m];
   const int z = t.z * T + (int)threadIdx.x % T, zp = t.w * T + (int)threadIdx.x / T;
   if (z >= Lz || zp >= Lz) return;
-  const Cplx<real>* X = tmp + 4 * L.site_off + (int64_t)fld * Lz * Lx;
-  const Cplx<real> u = X[(int64_t)z * Lx + k], v = X[(int64_t)zp * Lx + k];
-  const double ur = u.re, ui = u.im, vr = v.re, vi = v.im, inv = 1.0 / (double)Lx;
+  const int H = sf_half(Lx);
+  const Cplx<real>* X = tmp + 4 * L.site_off + (int64_t)fld * Lz * H;
+  // q_x > Lx/2 from the conjugate symmetry of a real field's transform
+  const int kk = k < H ? k : Lx - k;
+  const double sg = k < H ? 1.0 : -1.0;
+  const Cplx<real> u = X[(int64_t)z * H + kk], v = X[(int64_t)zp * H + kk];
+  const double ur = u.re, ui = sg * (double)u.im, vr = v.re, vi = sg * (double)v.im, inv = 1.0 / (double)Lx;
   double* c = C + L.c_off + ((((int64_t)fld * n_modes + m) * Lz + z) * Lz + zp) * 2;
   c[0] += (ur * vr + ui * vi) * inv;
   c[1] += (ur * vi - ui * vr) * inv;

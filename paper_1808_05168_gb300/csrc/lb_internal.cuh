@@ -268,7 +268,15 @@ struct SfPlan {
   int n_row_tasks, n_col_tasks;
   int max_Lx, max_Lz;
   int col_strip;  // q_x columns per column-pass block
+  // z-profiles of the four fields: the q_x = 0 bin of each row transform is the row sum
+  double* prof_sum;
+  double* prof_comp;
+  int n_rows;
 };
+
+// The row transforms of a sample in tmp: the fields are real, so only q_x = 0 .. Lx/2 is kept,
+// H = Lx/2 + 1 values per row, row (field, z) of a lattice at 4 site_off + (field Lz + z) H.
+__host__ __device__ __forceinline__ int sf_half(int Lx) { return Lx / 2 + 1; }
 
 // What the utility kernels need to rebuild the background w_l rho_bar c^S_0(z) in double.
 struct BgParams {
@@ -306,9 +314,9 @@ struct CorrPlan {
 template <class real>
 cudaError_t launch_corr(const CorrPlan& p, const real* fields, const void* tmp, double* R, double* C, cudaStream_t s);
 
-// z-profiles (Sec. III.C): adds the row means of delta rho, delta c, Ux, Uz and the pressure
-// (deviation) of the sampled fields to per-row compensated sums [5][n_rows]; row_lat[r] is the
-// lattice of global row r.
+// z-profiles (Sec. III.C): the row pass of launch_sf adds the row means of delta rho, delta c, Ux
+// and Uz to the per-row compensated sums [5][n_rows]; this adds those of the sampled pressure
+// (deviation), slot 4; row_lat[r] is the lattice of global row r.
 template <class real>
 cudaError_t launch_profiles(const DiagLattice* lat, const int* row_lat, int n_rows, const real* fields,
                             const real* pfield, double* prof_sum, double* prof_comp, cudaStream_t s);

@@ -1011,22 +1011,52 @@ size_t step_smem_bytes(int tile_x) {
   return Smem<real>::bytes(tile_x);
 }
 
+// ---- kernel families ------------------------------------------------------------------
+// The kernels come in families that are compiled in translation units of their own (so that the
+// build runs in parallel): TX = 0 is the generic path (any tile width), TX = 32, 64, 128 the bulk
+// path of that width.  A family prepares its kernels' shared-memory limits, launches one step
+// and hands out its persistent kernel; the dispatch below only sees these declarations.
+template <class real, int TX>
+cudaError_t family_prepare(int max_tile_x);
+template <class real, int TX>
+void family_launch(const StepArgs<real>& a, int tile_x, bool sample, int noise, cudaStream_t s);
+template <class real, int TX>
+const void* family_persistent(int tile_x, int noise, size_t* smem);
+
+#ifdef LB_STEP_FAMILY_DEFS
 static cudaError_t set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <class real, int TX>
-static cudaError_t prepare_bulk() {
-  const size_t b = SmemBulk<real, TX>::bytes;
-  const void* fns[] = {(const void*)step_kernel_bulk<real, TX, true, NOISE_OFF>,
-                       (const void*)step_kernel_bulk<real, TX, true, NOISE_HOM>,
-                       (const void*)step_kernel_bulk<real, TX, true, NOISE_LOC>,
-                       (const void*)step_kernel_bulk<real, TX, false, NOISE_OFF>,
-                       (const void*)step_kernel_bulk<real, TX, false, NOISE_HOM>,
-                       (const void*)step_kernel_bulk<real, TX, false, NOISE_LOC>,
-                       (const void*)persistent_kernel_bulk<real, TX, NOISE_OFF>,
-                       (const void*)persistent_kernel_bulk<real, TX, NOISE_HOM>,
-                       (const void*)persistent_kernel_bulk<real, TX, NOISE_LOC>};
+struct Family {
+  static size_t smem(int tile_x) { return TX == 0 ? Smem<real>::bytes(tile_x) : SmemBulk<real, TX == 0 ? 32 : TX>::bytes; }
+  template <bool SAMPLE, int NOISE>
+  static const void* step_fn() {
+    if constexpr (TX == 0) return (const void*)step_kernel<real, SAMPLE, NOISE>;
+    else return (const void*)step_kernel_bulk<real, TX, SAMPLE, NOISE>;
+  }
+  template <int NOISE>
+  static const void* persistent_fn() {
+    if constexpr (TX == 0) return (const void*)persistent_kernel<real, NOISE>;
+    else return (const void*)persistent_kernel_bulk<real, TX, NOISE>;
+  }
+  template <bool SAMPLE, int NOISE>
+  static void launch(const StepArgs<real>& a, int tile_x, cudaStream_t s) {
+    if constexpr (TX == 0) step_kernel<real, SAMPLE, NOISE><<<a.n_items, tile_x, smem(tile_x), s>>>(a);
+    else step_kernel_bulk<real, TX, SAMPLE, NOISE><<<a.n_items, TX, smem(TX), s>>>(a);
+  }
+};
+
+template <class real, int TX>
+cudaError_t family_prepare(int max_tile_x) {
+  using F = Family<real, TX>;
+  const size_t b = F::smem(max_tile_x);
+  const void* fns[] = {F::template step_fn<true, NOISE_OFF>(),  F::template step_fn<true, NOISE_HOM>(),
+                       F::template step_fn<true, NOISE_LOC>(),  F::template step_fn<false, NOISE_OFF>(),
+                       F::template step_fn<false, NOISE_HOM>(), F::template step_fn<false, NOISE_LOC>(),
+                       F::template persistent_fn<NOISE_OFF>(),  F::template persistent_fn<NOISE_HOM>(),
+                       F::template persistent_fn<NOISE_LOC>()};
   for (const void* fn : fns) {
     cudaError_t e = set_smem(fn, b);
     if (e != cudaSuccess) return e;
@@ -1034,76 +1064,60 @@ static cudaError_t prepare_bulk() {
   return cudaSuccess;
 }
 
+template <class real, int TX>
+void family_launch(const StepArgs<real>& a, int tile_x, bool sample, int noise, cudaStream_t s) {
+  using F = Family<real, TX>;
+  if (sample) {
+    if (noise == NOISE_HOM) F::template launch<true, NOISE_HOM>(a, tile_x, s);
+    else if (noise == NOISE_LOC) F::template launch<true, NOISE_LOC>(a, tile_x, s);
+    else F::template launch<true, NOISE_OFF>(a, tile_x, s);
+  } else {
+    if (noise == NOISE_HOM) F::template launch<false, NOISE_HOM>(a, tile_x, s);
+    else if (noise == NOISE_LOC) F::template launch<false, NOISE_LOC>(a, tile_x, s);
+    else F::template launch<false, NOISE_OFF>(a, tile_x, s);
+  }
+}
+
+template <class real, int TX>
+const void* family_persistent(int tile_x, int noise, size_t* smem) {
+  using F = Family<real, TX>;
+  *smem = F::smem(tile_x);
+  if (noise == NOISE_HOM) return F::template persistent_fn<NOISE_HOM>();
+  if (noise == NOISE_LOC) return F::template persistent_fn<NOISE_LOC>();
+  return F::template persistent_fn<NOISE_OFF>();
+}
+
+#define LB_STEP_FAMILY_INST(real, TX)                                                                            \
+  template cudaError_t family_prepare<real, TX>(int);                                                            \
+  template void family_launch<real, TX>(const StepArgs<real>&, int, bool, int, cudaStream_t);                    \
+  template const void* family_persistent<real, TX>(int, int, size_t*);
+#endif  // LB_STEP_FAMILY_DEFS
+
 template <class real>
 cudaError_t prepare_step(int max_tile_x) {
-  const size_t bytes = Smem<real>::bytes(max_tile_x);
-  const void* fns[] = {(const void*)step_kernel<real, true, NOISE_OFF>,  (const void*)step_kernel<real, true, NOISE_HOM>,
-                       (const void*)step_kernel<real, true, NOISE_LOC>,  (const void*)step_kernel<real, false, NOISE_OFF>,
-                       (const void*)step_kernel<real, false, NOISE_HOM>, (const void*)step_kernel<real, false, NOISE_LOC>,
-                       (const void*)persistent_kernel<real, NOISE_OFF>,  (const void*)persistent_kernel<real, NOISE_HOM>,
-                       (const void*)persistent_kernel<real, NOISE_LOC>};
-  for (const void* fn : fns) {
-    cudaError_t e = set_smem(fn, bytes);
-    if (e != cudaSuccess) return e;
-  }
-  cudaError_t e = prepare_bulk<real, 32>();
-  if (e == cudaSuccess) e = prepare_bulk<real, 64>();
-  if (e == cudaSuccess) e = prepare_bulk<real, 128>();
+  cudaError_t e = family_prepare<real, 0>(max_tile_x);
+  if (e == cudaSuccess) e = family_prepare<real, 32>(32);
+  if (e == cudaSuccess) e = family_prepare<real, 64>(64);
+  if (e == cudaSuccess) e = family_prepare<real, 128>(128);
   return e;
-}
-
-template <class real, bool SAMPLE>
-static void launch_generic(const StepArgs<real>& a, int tile_x, int noise, cudaStream_t s) {
-  const size_t smem = Smem<real>::bytes(tile_x);
-  if (noise == NOISE_HOM) step_kernel<real, SAMPLE, NOISE_HOM><<<a.n_items, tile_x, smem, s>>>(a);
-  else if (noise == NOISE_LOC) step_kernel<real, SAMPLE, NOISE_LOC><<<a.n_items, tile_x, smem, s>>>(a);
-  else step_kernel<real, SAMPLE, NOISE_OFF><<<a.n_items, tile_x, smem, s>>>(a);
-}
-
-template <class real, int TX, bool SAMPLE>
-static void launch_bulk(const StepArgs<real>& a, int noise, cudaStream_t s) {
-  const size_t smem = SmemBulk<real, TX>::bytes;
-  if (noise == NOISE_HOM) step_kernel_bulk<real, TX, SAMPLE, NOISE_HOM><<<a.n_items, TX, smem, s>>>(a);
-  else if (noise == NOISE_LOC) step_kernel_bulk<real, TX, SAMPLE, NOISE_LOC><<<a.n_items, TX, smem, s>>>(a);
-  else step_kernel_bulk<real, TX, SAMPLE, NOISE_OFF><<<a.n_items, TX, smem, s>>>(a);
 }
 
 template <class real>
 cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, bool bulk, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
-  if (bulk && tile_x == 32) {
-    if (sample) launch_bulk<real, 32, true>(a, noise, s);
-    else launch_bulk<real, 32, false>(a, noise, s);
-  } else if (bulk && tile_x == 64) {
-    if (sample) launch_bulk<real, 64, true>(a, noise, s);
-    else launch_bulk<real, 64, false>(a, noise, s);
-  } else if (bulk && tile_x == 128) {
-    if (sample) launch_bulk<real, 128, true>(a, noise, s);
-    else launch_bulk<real, 128, false>(a, noise, s);
-  } else {
-    if (sample) launch_generic<real, true>(a, tile_x, noise, s);
-    else launch_generic<real, false>(a, tile_x, noise, s);
-  }
+  if (bulk && tile_x == 32) family_launch<real, 32>(a, tile_x, sample, noise, s);
+  else if (bulk && tile_x == 64) family_launch<real, 64>(a, tile_x, sample, noise, s);
+  else if (bulk && tile_x == 128) family_launch<real, 128>(a, tile_x, sample, noise, s);
+  else family_launch<real, 0>(a, tile_x, sample, noise, s);
   return cudaGetLastError();
-}
-
-template <class real, int TX>
-static const void* persistent_bulk_fn(int noise, size_t* smem) {
-  *smem = SmemBulk<real, TX>::bytes;
-  if (noise == NOISE_HOM) return (const void*)persistent_kernel_bulk<real, TX, NOISE_HOM>;
-  if (noise == NOISE_LOC) return (const void*)persistent_kernel_bulk<real, TX, NOISE_LOC>;
-  return (const void*)persistent_kernel_bulk<real, TX, NOISE_OFF>;
 }
 
 template <class real>
 static const void* persistent_fn(int tile_x, int noise, bool bulk, size_t* smem) {
-  if (bulk && tile_x == 32) return persistent_bulk_fn<real, 32>(noise, smem);
-  if (bulk && tile_x == 64) return persistent_bulk_fn<real, 64>(noise, smem);
-  if (bulk && tile_x == 128) return persistent_bulk_fn<real, 128>(noise, smem);
-  *smem = Smem<real>::bytes(tile_x);
-  if (noise == NOISE_HOM) return (const void*)persistent_kernel<real, NOISE_HOM>;
-  if (noise == NOISE_LOC) return (const void*)persistent_kernel<real, NOISE_LOC>;
-  return (const void*)persistent_kernel<real, NOISE_OFF>;
+  if (bulk && tile_x == 32) return family_persistent<real, 32>(tile_x, noise, smem);
+  if (bulk && tile_x == 64) return family_persistent<real, 64>(tile_x, noise, smem);
+  if (bulk && tile_x == 128) return family_persistent<real, 128>(tile_x, noise, smem);
+  return family_persistent<real, 0>(tile_x, noise, smem);
 }
 
 template <class real>

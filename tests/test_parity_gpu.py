@@ -363,3 +363,23 @@ def test_correlations_of_a_batch(prec):
                 # FP64: the bar of the structure factors (row transforms by FFT against direct sums)
                 tol = (1e-9 if prec == "fp64" else 1e-4) * np.abs(cw).max()
                 assert np.max(np.abs(cg - cw)) <= tol, (i, f, m)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_degenerate_lattices_in_one_batch(prec):
+    """The smallest lattices the method allows, in one batch: one column (every link wraps onto
+    the site itself), two and three columns, and two rows (both rows are wall rows, every vertical
+    link is reflected), with the bulk-copy path on a 4-column (16-byte) lattice beside them."""
+    shapes = [(1, 2), (1, 5), (2, 2), (3, 3), (4, 2), (5, 7)]
+    ps = [LatticeParams(Lx, Lz, lambda_s=1.1, lambda_d=0.9, kT=1e-4, G=0.4, grad_c0=0.3 / Lz, seed=8,
+                        lattice_id=i) for i, (Lx, Lz) in enumerate(shapes)]
+    with Simulation(ps, precision=prec) as sim:
+        sim.step(60)
+        got = [sim.populations(i) for i in range(len(ps))]
+    for i, p in enumerate(ps):
+        o = oracle_of(p)
+        o.step(60)
+        if prec == "fp64":
+            assert_fp64_parity(got[i], o.populations())
+        else:
+            assert_dev32_parity(got[i], o.populations(), background(p.Lx, p.Lz, p.grad_c0))
