@@ -960,9 +960,11 @@ int lb_structure_factor(lb_ctx* c, int lattice, int field, int mode, double* out
   }
   const size_t full = (size_t)Lx * Lz;
   const size_t off = 4 * (size_t)c->site_off[lattice] + (size_t)field * full;
-  std::vector<double> s(full), k(full);
-  if (cudaMemcpy(s.data(), c->acc_sum + off, full * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(k.data(), c->acc_comp + off, full * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+  // LB_SF_QX needs the q_z = 0 row only (q_x > Lx/2 comes from row 0 as well)
+  const size_t ncopy = mode == LB_SF_QXQZ ? full : (size_t)Lx;
+  std::vector<double> s(ncopy), k(ncopy);
+  if (cudaMemcpy(s.data(), c->acc_sum + off, ncopy * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(k.data(), c->acc_comp + off, ncopy * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return LB_ERR_CUDA;
   // accumulated: q_x = 0 .. Lx/2 (Kahan sums: total = sum - comp); the rest by S(q) = S(-q)
   const double inv = 1.0 / (double)c->nsamples;

@@ -36,10 +36,10 @@ namespace {
 
 constexpr int NS = 4;   // generic path: rows of staged populations (power of two)
 #ifndef LB_BULK_NSI
-#define LB_BULK_NSI 4
+#define LB_BULK_NSI 3
 #endif
 #ifndef LB_BULK_BLOCKS_F32
-#define LB_BULK_BLOCKS_F32 5  // resident 128-column blocks per SM the float bulk kernels target
+#define LB_BULK_BLOCKS_F32 6  // resident 128-column blocks per SM the float bulk kernels target
 #endif
 constexpr int NSI = LB_BULK_NSI;  // bulk path: input row slots
 constexpr int WAIT_MS = 2000;
@@ -759,9 +759,9 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   // k % NW, so that every warp issues about the same number of copies
   constexpr int NW = TX / 32;
   const int my_plane = (tid & 31) * NW + (tid >> 5);
-  auto stage_row = [&](int r) {
+  // row r goes to input slot r mod NSI; the callers carry the slots along
+  auto stage_row = [&](int r, int slot) {
     if (r < 0 || r >= Lz || r > z1) return;
-    const int slot = (unsigned)r % NSI;  // r >= 0
     uint64_t* bar = bars + slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
     if (my_plane < 18) {
@@ -789,8 +789,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       }
     }
   };
-  auto wait_row = [&](int r) {
-    const int slot = (unsigned)r % NSI;  // r >= 0
+  auto wait_row = [&](int slot) {
     const unsigned par = (ph >> slot) & 1u;
     if (!mbar_try_wait(bars + slot, par)) {
       const uint64_t t0 = global_ns();
@@ -805,18 +804,18 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     }
     ph ^= 1u << slot;
   };
-  auto rho_at = [&](int r, int j) {
-    const real* sb = instage + ((unsigned)r % NSI) * 18 * SW;
+  auto rho_at = [&](int r, int slot, int j) {
+    const real* sb = instage + slot * 18 * SW;
     Pr<real> v[9];
     read_bulk<real, SW>(sb, j, r > 0, r < Lz - 1, k9, k36, v);
     return sum9<real>(v);
   };
-  auto put_rho = [&](int r) {
-    wait_row(r);
+  auto put_rho = [&](int r, int slot) {
+    wait_row(slot);
     const int b = ring_slot(r) * W;
-    if (active) ring[b + tid + 1] = rho_at(r, tid + PAD);
-    if (do_left) ring[b] = rho_at(r, PAD - 1);
-    if (do_right) ring[b + nact + 1] = rho_at(r, nact + PAD);
+    if (active) ring[b + tid + 1] = rho_at(r, slot, tid + PAD);
+    if (do_left) ring[b] = rho_at(r, slot, PAD - 1);
+    if (do_right) ring[b + nact + 1] = rho_at(r, slot, nact + PAD);
   };
   auto ghost_row = [&](int zg, int za) {
     const int bg = ring_slot(zg) * W, ba = ring_slot(za) * W;
@@ -836,28 +835,30 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     if (do_right) copy1(nact + 1);
   };
   // prologue: rows z0-1 .. z0+NSI-2 in flight
-  for (int r = z0 - 1; r <= z0 + NSI - 2; ++r) stage_row(r);
-  if (z0 > 0) put_rho(z0 - 1);
-  put_rho(z0);
+  auto slot_of = [](int r) { return (int)((unsigned)(r + NSI) % NSI); };  // r >= -1
+  for (int r = z0 - 1; r <= z0 + NSI - 2; ++r) stage_row(r, slot_of(r));
+  if (z0 > 0) put_rho(z0 - 1, slot_of(z0 - 1));
+  put_rho(z0, slot_of(z0));
   if (z0 == 0) ghost_row(-1, 0);
+  int sp = slot_of(z0 - 1), sc = slot_of(z0), sn = slot_of(z0 + 1);  // slots of rows z-1, z, z+1
 
   const SiteK<real> K = site_constants<real, NOISE>(L);
   double acc_p = 0.0, acc_a = 0.0, acc_b = 0.0;
   bool ok = true;
 
   for (int z = z0; z < z1; ++z) {
-    if (z + 1 < Lz) put_rho(z + 1);
+    if (z + 1 < Lz) put_rho(z + 1, sn);
     else ghost_row(Lz, Lz - 1);
     __syncthreads();
     if (*abort_flag) {
       ok = false;
       break;
     }
-    stage_row(z + NSI - 1);  // into the slot of row z-1, read by every thread before the barrier
+    stage_row(z + NSI - 1, sp);  // row z+NSI-1 shares the slot of row z-1, read by all before the barrier
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real* sb = instage + ((unsigned)z % NSI) * 18 * SW;
+      const real* sb = instage + sc * 18 * SW;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
       // the variants are inlined; the branches are uniform over the block (one lattice per item)
@@ -879,6 +880,9 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
         else site(BoolC<false>(), BoolC<false>());
       }
     }
+    sp = sc;
+    sc = sn;
+    sn = sn + 1 == NSI ? 0 : sn + 1;
   }
   if (!ok) {
     // drain the input rows still in flight (bounded), then stop
