@@ -861,24 +861,30 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       const real* sb = instage + sc * 18 * SW;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
-      // the variants are inlined; the branches are uniform over the block (one lattice per item)
-      auto site = [&](auto unit, auto astar) {
+      // the variants are inlined; the branches are uniform over the block (one lattice per item,
+      // one row at a time): unit rates, a*, and interior rows (no wall within one link)
+      auto site = [&](auto unit, auto astar, auto inner) {
+        constexpr bool IN = decltype(inner)::value;
         Pr<real> v[9];
-        read_bulk<real, SW>(sb, tid + PAD, below, above, k9, k36, v);
+        read_bulk<real, SW>(sb, tid + PAD, IN || below, IN || above, k9, k36, v);
         Mom<real> m = moments<real>(v);
-        if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
+        if (IN) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
             K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags);
       };
-      if (flags & DF_UNIT) {
-        if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>());
-        else site(BoolC<true>(), BoolC<false>());
-      } else {
-        if (flags & DF_ASTAR) site(BoolC<false>(), BoolC<true>());
-        else site(BoolC<false>(), BoolC<false>());
-      }
+      auto rates = [&](auto inner) {
+        if (flags & DF_UNIT) {
+          if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>(), inner);
+          else site(BoolC<true>(), BoolC<false>(), inner);
+        } else {
+          if (flags & DF_ASTAR) site(BoolC<false>(), BoolC<true>(), inner);
+          else site(BoolC<false>(), BoolC<false>(), inner);
+        }
+      };
+      if (below && above) rates(BoolC<true>());
+      else rates(BoolC<false>());
     }
     sp = sc;
     sc = sn;
@@ -918,6 +924,12 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepA
 template <class real>
 struct BulkBlocks {  // 128-thread blocks per SM the bulk kernels are compiled for
   static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 : 2;
+};
+// The persistent kernel holds the grid-barrier state on top: one block fewer, so that it keeps
+// its registers (no spills).
+template <class real>
+struct PersistentBlocks {
+  static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 - 1 : 2;
 };
 
 template <class real, int TX, bool SAMPLE, int NOISE>
@@ -985,7 +997,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
 }
 
 template <class real, int TX, int NOISE>
-__global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX)
+__global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
     persistent_kernel_bulk(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
