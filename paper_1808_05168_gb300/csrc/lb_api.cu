@@ -354,7 +354,7 @@ int alloc_diag(lb_ctx* c) {
   for (int i = 0; i < c->n_lat; ++i) {
     const int Lx = c->params[i].Lx, cq = std::min(c->col_strip, Lx);
     const int Lz = c->params[i].Lz;
-    const int R = std::min(std::max(1, 2048 / Lx), Lz);  // rows per block of the row pass
+    const int R = std::min(std::max(1, 4096 / Lx), Lz);  // rows per block of the row pass
     for (int fld = 0; fld < 4; ++fld)
       for (int z0 = 0; z0 < Lz; z0 += R) rt.push_back(make_int2(i, fld * Lz + z0));
     for (int fld = 0; fld < 4; ++fld)

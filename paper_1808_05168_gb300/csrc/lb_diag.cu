@@ -53,6 +53,40 @@ __device__ void fft_inplace(Cplx<real>* s, const Cplx<real>* tw, int n, int logn
 
 __device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
 
+// Twiddle tables of the sample-step transforms, exp(-2 pi i k / n) for k < n/2, every power of
+// two n = 2 .. 8192 at offset n/2 - 1; filled once per device by prepare_sf.
+constexpr int TW_TABLE = 8192;
+__device__ Cplx<float> g_tw_f[TW_TABLE];
+__device__ Cplx<double> g_tw_d[TW_TABLE];
+template <class real>
+__device__ __forceinline__ Cplx<real>* tw_table();
+template <>
+__device__ __forceinline__ Cplx<float>* tw_table<float>() { return g_tw_f; }
+template <>
+__device__ __forceinline__ Cplx<double>* tw_table<double>() { return g_tw_d; }
+
+template <class real>
+__global__ void fill_tw_tables_kernel() {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < TW_TABLE - 1; i += gridDim.x * blockDim.x) {
+    const int n = 2 << (31 - __clz(i + 1));  // the table holding entry i: n/2 - 1 <= i < n - 1
+    const int k = i - (n / 2 - 1);
+    real c, sn;
+    twiddle<real>(k, n, c, sn);
+    tw_table<real>()[i] = Cplx<real>{c, sn};
+  }
+}
+
+// Shared-memory index of point i of the sample-step transforms: one pad element per 32 keeps the
+// bit-reversed scatter and the strided column accesses free of bank conflicts.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+
+// The twiddles of an n-point transform into shared memory, from the table.
+template <class real>
+__device__ void load_twiddles(Cplx<real>* tw, int n) {
+  const Cplx<real>* t = tw_table<real>() + (n / 2 - 1);
+  for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) tw[k] = t[k];
+}
+
 template <class real>
 __device__ void fill_twiddles(Cplx<real>* tw, int n) {
   for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) {
@@ -66,7 +100,7 @@ __device__ void fill_twiddles(Cplx<real>* tw, int n) {
 // z0 ..), so that short rows share one twiddle table and every thread has butterflies to do.
 // Task = (lattice, field * Lz + z0).
 __host__ __device__ __forceinline__ int rows_per_block(int Lx, int Lz) {
-  int r = 2048 / Lx;
+  int r = 4096 / Lx;
   if (r < 1) r = 1;
   return r < Lz ? r : Lz;
 }
@@ -88,25 +122,24 @@ __global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const 
   const int R = rows_per_block(L.Lx, L.Lz);
   Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
   Cplx<real>* s = tw + (half > 0 ? half : 1);
-  fill_twiddles<real>(tw, n);
+  load_twiddles<real>(tw, n);
   const int64_t off = 4 * L.site_off + (int64_t)task.y * n;  // first row of the group
   for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) {
     const int r = idx >> logn, j = idx & (n - 1);
     const int b = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[r * n + b] = Cplx<real>{fields[off + idx], real(0)};
+    s[spad(r * n + b)] = Cplx<real>{fields[off + idx], real(0)};
   }
   __syncthreads();
   for (int lg = 1; lg <= logn; ++lg) {
     const int hs = 1 << (lg - 1), stride = n >> lg;
     for (int idx = threadIdx.x; idx < R * half; idx += blockDim.x) {
       const int r = idx >> (logn - 1), jj = idx & (half - 1);
-      Cplx<real>* sr = s + r * n;
       const int pos = jj & (hs - 1);
-      const int i0 = ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
-      const Cplx<real> w = tw[pos * stride], b = sr[i1], a = sr[i0];
+      const int i0 = r * n + ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
+      const Cplx<real> w = tw[pos * stride], b = s[spad(i1)], a = s[spad(i0)];
       const real tr = w.re * b.re - w.im * b.im, ti = w.re * b.im + w.im * b.re;
-      sr[i0] = Cplx<real>{a.re + tr, a.im + ti};
-      sr[i1] = Cplx<real>{a.re - tr, a.im - ti};
+      s[spad(i0)] = Cplx<real>{a.re + tr, a.im + ti};
+      s[spad(i1)] = Cplx<real>{a.re - tr, a.im - ti};
     }
     __syncthreads();
   }
@@ -114,12 +147,12 @@ __global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const 
   const int64_t offh = 4 * L.site_off + (int64_t)task.y * H;
   for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
     const int r = idx / H, q = idx - r * H;
-    tmp[offh + idx] = s[r * n + q];
+    tmp[offh + idx] = s[spad(r * n + q)];
   }
   const int fld = task.y / L.Lz, z0 = task.y - fld * L.Lz;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     const int64_t k = (int64_t)fld * n_rows + L.row_off + z0 + r;
-    neumaier_add(prof_sum[k], prof_comp[k], (double)s[r * n].re / (double)n);
+    neumaier_add(prof_sum[k], prof_comp[k], (double)s[spad(r * n)].re / (double)n);
   }
 }
 
@@ -148,30 +181,29 @@ __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const 
   const int fld = task.y / Lx, qx0 = task.y - fld * Lx;
   Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
   Cplx<real>* s = tw + (half > 0 ? half : 1);
-  fill_twiddles<real>(tw, n);
+  load_twiddles<real>(tw, n);
   const int H = sf_half(Lx);
   const int64_t tbase = 4 * L.site_off + (int64_t)fld * H * n + qx0;  // compact row transforms
   const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx0;  // accumulators
   for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
     const int j = idx >> lcq, c = idx & (cq - 1);
     const int r = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[c * n + r] = qx0 + c < H ? tmp[tbase + (int64_t)j * H + c] : Cplx<real>{real(0), real(0)};
+    s[spad(c * n + r)] = qx0 + c < H ? tmp[tbase + (int64_t)j * H + c] : Cplx<real>{real(0), real(0)};
   }
   __syncthreads();
   for (int lg = 1; lg <= logn; ++lg) {
     const int hs = 1 << (lg - 1);
     const int stride = n >> lg;
     for (int idx = threadIdx.x; idx < half * cq; idx += blockDim.x) {
-      const int c = idx / half, jj = idx - c * half;
-      Cplx<real>* sc = s + c * n;
+      const int c = idx >> (logn - 1), jj = idx & (half - 1);
       const int pos = jj & (hs - 1);
-      const int i0 = ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
+      const int i0 = c * n + ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
       const Cplx<real> w = tw[pos * stride];
-      const Cplx<real> b = sc[i1], a = sc[i0];
+      const Cplx<real> b = s[spad(i1)], a = s[spad(i0)];
       const real tr = w.re * b.re - w.im * b.im;
       const real ti = w.re * b.im + w.im * b.re;
-      sc[i0] = Cplx<real>{a.re + tr, a.im + ti};
-      sc[i1] = Cplx<real>{a.re - tr, a.im - ti};
+      s[spad(i0)] = Cplx<real>{a.re + tr, a.im + ti};
+      s[spad(i1)] = Cplx<real>{a.re - tr, a.im - ti};
     }
     __syncthreads();
   }
@@ -179,7 +211,7 @@ __global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const 
   for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
     const int j = idx >> lcq, c = idx & (cq - 1);
     if (qx0 + c >= H) continue;
-    const Cplx<real> v = s[c * n + j];
+    const Cplx<real> v = s[spad(c * n + j)];
     const int64_t o = base + (int64_t)j * Lx + c;
     double sm = acc_sum[o], cp = acc_comp[o];
     kahan_add(sm, cp, (double)((v.re * v.re + v.im * v.im) * scale));
@@ -335,28 +367,31 @@ __global__ void init_rest_kernel(real* f, BgParams bp) {
 }  // namespace
 
 template <class real>
-size_t sf_smem_bytes(int n) {  // row pass: the larger of one row and 2048 points, plus twiddles
-  const int pts = n > 2048 ? n : 2048;
-  return (size_t)pts * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
+size_t sf_smem_bytes(int n) {  // row pass: the larger of one row and 4096 points, plus twiddles
+  const int pts = n > 4096 ? n : 4096;
+  return (size_t)(pts + pts / 32 + 1) * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
 }
 
 // Columns per column-pass block: up to 16, fewer when Lz is long (shared memory budget).
 template <class real>
 int sf_column_strip(int max_Lz) {
   int cq = 16;
-  while (cq > 1 && ((size_t)max_Lz * cq + max_Lz / 2 + 1) * sizeof(Cplx<real>) > 160 * 1024) cq >>= 1;
+  while (cq > 1 && ((size_t)max_Lz * cq * 33 / 32 + 1 + max_Lz / 2 + 1) * sizeof(Cplx<real>) > 160 * 1024) cq >>= 1;
   return cq;
 }
 
 template <class real>
 size_t sf_cols_smem_bytes(int max_Lz, int cq) {
-  return ((size_t)max_Lz * cq + max_Lz / 2 + 1) * sizeof(Cplx<real>);
+  return ((size_t)max_Lz * cq * 33 / 32 + 1 + max_Lz / 2 + 1) * sizeof(Cplx<real>);
 }
 
 template <class real>
 cudaError_t prepare_sf(int max_Lx, int max_Lz) {
-  cudaError_t e = cudaFuncSetAttribute(sf_rows_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sf_smem_bytes<real>(max_Lx));
+  fill_tw_tables_kernel<real><<<(TW_TABLE + 255) / 256, 256>>>();
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(sf_rows_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sf_smem_bytes<real>(max_Lx));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sf_cols_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sf_cols_smem_bytes<real>(max_Lz, sf_column_strip<real>(max_Lz)));

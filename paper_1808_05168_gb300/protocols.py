@@ -46,6 +46,35 @@ def ne_pressure(base: LatticeParams, kT: float, grad_c0: float, seeds, steps: in
                 P_kT_0=float(P_k0.mean()), P_0_0=float(P_00))
 
 
+def ne_pressure_scan(base: LatticeParams, kT: float, grads, seeds, steps: int, discard: int, every: int = 10,
+                     precision: str = "dev32"):
+    """Pbar_NE (Eq. NEQP) for several gradients at one (L, kT) in one batch, the equilibrium
+    companions (kT, grad 0) and (0, 0) shared.  Returns a list of dict(grad_c0, P_ne, stderr)."""
+    seeds = list(seeds)
+    grads = list(grads)
+    runs = []
+    for s in seeds:
+        runs += [replace(base, kT=kT, grad_c0=g, seed=s) for g in grads]
+        runs.append(replace(base, kT=kT, grad_c0=0.0, seed=s))
+    runs += [replace(base, kT=0.0, grad_c0=g) for g in grads]
+    runs.append(replace(base, kT=0.0, grad_c0=0.0))
+    runs = _batch_ids(runs)
+    m = len(grads) + 1
+    with Simulation(runs, precision=precision) as sim:
+        sim.set_sampling(discard, every)
+        sim.step(steps)
+        P = np.array([sim.mean_pressure(i)[1] for i in range(len(runs))])
+    n = len(seeds)
+    noisy = P[: n * m].reshape(n, m)
+    quiet = P[n * m:]
+    out = []
+    for k, g in enumerate(grads):
+        per_seed = (noisy[:, k] - quiet[k]) - (noisy[:, -1] - quiet[-1])
+        out.append(dict(grad_c0=g, P_ne=float(per_seed.mean()),
+                        stderr=float(per_seed.std(ddof=1) / np.sqrt(n)) if n > 1 else float("nan")))
+    return out
+
+
 def ensemble_spectra(base: LatticeParams, seeds, steps: int, discard: int, every: int = 10,
                      fields=("rho", "c", "ux", "uz"), precision: str = "dev32"):
     """Structure factors S(q_z, q_x) averaged over seeds (one batch).  Returns {field: (mean,

@@ -101,3 +101,16 @@ def test_nonequilibrium_pressure_protocol():
     assert abs(r64["P_ne"] - r32["P_ne"]) < 3 * np.hypot(r32["stderr"], r64["stderr"]), (r32, r64)
     # the equilibrium thermal shift dP_eq is present and G-dependent only weakly
     assert ideal["dP_eq"] > 0 and r32["dP_eq"] > 0
+
+
+def test_nonequilibrium_pressure_grows_as_the_squared_gradient():
+    """Sec. III.C, Fig. 4 (top): at fixed L the NE pressure scales as (grad c_0)^2.  L = 32,
+    G = 0.3, kT = 1e-4, wall-to-wall differences 0.24 and 0.48 on 1536 seeds: the exponent
+    log(P2/P1)/log 2 agrees with 2 within three standard errors."""
+    base = LatticeParams(128, 32, G=0.3, **RATES)
+    lo, hi = protocols.ne_pressure_scan(base, KT, [0.24 / 32, 0.48 / 32], range(3000, 4536), steps=40000,
+                                        discard=4000)
+    assert lo["P_ne"] > 3 * lo["stderr"] and hi["P_ne"] > 3 * hi["stderr"], (lo, hi)
+    expo = np.log(hi["P_ne"] / lo["P_ne"]) / np.log(2.0)
+    sig = np.hypot(lo["stderr"] / lo["P_ne"], hi["stderr"] / hi["P_ne"]) / np.log(2.0)
+    assert abs(expo - 2.0) < 3 * sig, (expo, sig, lo, hi)
