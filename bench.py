@@ -219,6 +219,7 @@ def run_ours(args):
         res["fp64_plain"] = measure_plain(torch, workloads.c4(), "fp64", steps=10)
         res["dev32_large"] = measure_plain(torch, workloads.c4(), "dev32", steps=40)
         res["e2e"] = measure_e2e(torch, lattices, K, P)
+        res["adjoint_c5"] = measure_adjoint(torch)
         res["cpu_baseline"] = cpu_baseline()
     elif not args.no_extras:
         res["e2e"] = measure_e2e(torch, lattices, K, P)
@@ -227,6 +228,27 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res))
+
+
+def measure_adjoint(torch):
+    """The gradient of the mean-pressure shift on the 256 x 128 lattice (2000 steps from rest,
+    checkpoints every 100): wall time of the two forward runs alone and of forward + reverse
+    sweep, per precision."""
+    from paper_1808_05168_gb300 import Simulation, workloads
+
+    (p,) = workloads.c5()
+    out = {"workload": "256x128, G=0.5, dc=0.5, kT=1e-5, 2000 steps, checkpoints every 100"}
+    for prec in ("fp64", "dev32"):
+        with Simulation(p, precision=prec) as sim:
+            sim.pressure_shift_gradient(100, 100)  # set-up and first-use costs
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.pressure_shift_gradient(2000, 100, want_grad=False)
+            t1 = time.perf_counter()
+            sim.pressure_shift_gradient(2000, 100)
+            t2 = time.perf_counter()
+        out[prec] = {"loss_only_s": t1 - t0, "loss_and_gradient_s": t2 - t1, "ratio": (t2 - t1) / (t1 - t0)}
+    return out
 
 
 def measure_plain(torch, lattices, precision, steps):
