@@ -136,6 +136,9 @@ __device__ __forceinline__ real dsigma(real sigma, real lam) {
   return sigma * (1 - lam) / ((2 - lam) * lam);
 }
 
+// The fourteen normals of a site.  FP32: exactly those of the forward FP32 kernel.  FP64: the
+// library Box-Muller; the forward FP64 kernel's table-driven normals agree with it to a few units
+// in the last place, far below what the gradient resolves.
 template <class real>
 __device__ __forceinline__ void normals14(uint32_t site, uint32_t step, const LatticeDev<real>& L, real n[14]);
 template <>
@@ -158,18 +161,7 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
   const uint32_t k[16] = {w[0].x, w[0].y, w[0].z, w[0].w, w[1].x, w[1].y, w[1].z, w[1].w,
                           w[2].x, w[2].y, w[2].z, w[2].w, w[3].x, w[3].y, w[3].z, w[3].w};
 #pragma unroll
-  for (int p = 0; p < 7; ++p) {
-    // same formulas as the forward FP32 kernel
-    const float u1 = uniform01<float>(k[2 * p]);
-    const float t = -2.0f * logf(u1);
-    const float r = t * rsqrtf(t);
-    const float phi = fmaf(6.28318530717959f, __uint_as_float(0x3F800000u | (k[2 * p + 1] & 0x7FFFFFu)),
-                           -9.42477758729298f);
-    float sn, cs;
-    __sincosf(phi, &sn, &cs);
-    n[2 * p] = -r * cs;
-    n[2 * p + 1] = -r * sn;
-  }
+  for (int p = 0; p < 7; ++p) normal_pair<float>(k[2 * p], k[2 * p + 1], n[2 * p], n[2 * p + 1], nullptr);
 }
 
 // The local part of the transposed step at every site (see the file comment).  alpha: weight of

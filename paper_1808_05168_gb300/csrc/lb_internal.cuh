@@ -193,6 +193,158 @@ __device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, doubl
   n1 = r * s;
 }
 
+// ---- normals of the step kernels ----------------------------------------------------------
+// The hardware approximations in their flush-to-zero forms: their arguments here are never
+// subnormal (u1 >= 2^-24, t > 2^-24, phi a multiple of 2^-44), so the results are those of the
+// plain forms without their subnormal handling.
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void sincos_ftz(float x, float& s, float& c) {
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
+}
+
+// Tables of the double-precision Box-Muller (the table-driven method of P. T. P. Tang for the
+// logarithm and for sine/cosine): cs[j] = (cos, sin)(2 pi j / 1024) and ln[j] = (ln y_j, 1 / y_j)
+// with y_j = 3/4 + j/256, j = 0 .. 192.  The single-precision path needs none.
+template <class real>
+struct BmTables {};
+template <>
+struct BmTables<double> {
+  double2 cs[1024];
+  double2 ln[193];
+};
+
+// All threads of the block fill the tables (from the correctly rounded library functions); the
+// caller synchronises the block before use.
+template <class real>
+__device__ __forceinline__ void fill_bm_tables(BmTables<real>* T) {
+  if constexpr (sizeof(real) == 8) {
+    for (int j = threadIdx.x; j < 1024; j += blockDim.x) {
+      double sn, cs;
+      sincospi((double)j / 512.0, &sn, &cs);
+      T->cs[j] = make_double2(cs, sn);
+    }
+    for (int j = threadIdx.x; j < 193; j += blockDim.x) {
+      const double y = 0.75 + (double)j / 256.0;
+      T->ln[j] = make_double2(log(y), 1.0 / y);
+    }
+  }
+}
+
+// Box-Muller pair of the working precision, (r cos 2 pi u2, r sin 2 pi u2) with r = sqrt(-2 ln u1).
+// FP32: t = -2 ln u1 from the hardware base-2 logarithm, whose absolute error (~2^-22) the square
+// root would magnify where t is small; there (v = 1 - u1 < 2^-6, v exact) the series
+// -ln(1 - v) = v + v^2/2 + v^3/3 + ... is used instead (next term below 1e-6 of t).  The radius
+// is t / sqrt(t) through the reciprocal square root, and the angle is reduced to (-pi, pi) for
+// the fast sine/cosine: cos 2 pi u2 = -cos phi and sin 2 pi u2 = -sin phi with
+// phi = 2 pi u2 - pi.  Absolute error below 3e-6 on a normal.
+// FP64, table-driven: u = m 2^-24 with m = 2 (k mod 2^23) + 1.  ln u1 = (e - 24) ln 2 + ln y with
+// m = 2^e y, y in [3/4, 3/2); ln y = ln y_j + ln(1 + t), y_j the table point nearest y and
+// t = (y - y_j) / y_j, |t| <= 2^-9 / (3/4), from its series to t^6.  The angle 2 pi m 2^-24 is
+// the table angle 2 pi (m >> 14) / 1024 plus d = 2 pi (m mod 2^14) 2^-24 < 6.2e-3, whose sine and
+// cosine come from their series (to d^5 and d^6) and the addition theorems.  Within a few units
+// in the last place of the library functions.
+template <class real>
+__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, real& n0, real& n1, const BmTables<real>* T);
+template <>
+__device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float& n0, float& n1,
+                                                   const BmTables<float>*) {
+  const float u1 = uniform01<float>(a);
+  const float v = 1.0f - u1;
+  const float t_log = -1.38629436111989061f * lg2_ftz(u1);
+  const float t_ser = v * fmaf(v, fmaf(v, 0.666666666666666667f, 1.0f), 2.0f);
+  const float t = v < 0.015625f ? t_ser : t_log;
+  const float r = t * rsqrt_ftz(t);
+  // phi = 2 pi u2 - pi = 2 pi x2 - 3 pi + 2 pi 2^-24 with x2 = u2 + 1 - 2^-24 built from the bits
+  const float phi = fmaf(6.28318530717959f, unit_interval_bits(b), -9.42477758729298f);
+  float s, c;
+  sincos_ftz(phi, s, c);
+  n0 = -r * c;
+  n1 = -r * s;
+}
+template <>
+__device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, double& n0, double& n1,
+                                                    const BmTables<double>* T) {
+  // ln 2 split so that (e - 24) ln2_hi is exact (ln2_hi: ln 2 rounded to 24 bits)
+  const double ln2_hi = 0.693147182464599609375, ln2_lo = -1.904654299957768e-09;
+  const uint32_t m1 = 2u * (a & 0x7FFFFFu) + 1u;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong((double)m1);
+  int e = (int)(bits >> 52) - 1023;
+  unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+  int j;
+  double y;
+  if (mant >= (1ull << 51)) {  // y0 = m1 / 2^e in [3/2, 2): y = y0 / 2 in [3/4, 1)
+    e += 1;
+    y = __longlong_as_double((long long)(0x3FE0000000000000ull | mant));
+    j = (int)(((mant - (1ull << 51)) + (1ull << 44)) >> 45);
+  } else {  // y in [1, 3/2)
+    y = __longlong_as_double((long long)(0x3FF0000000000000ull | mant));
+    j = 64 + (int)((mant + (1ull << 43)) >> 44);
+  }
+  const double2 L = T->ln[j];
+  const double yj = fma((double)j, 0.00390625, 0.75);
+  const double t = (y - yj) * L.y;
+  const double p = fma(t, fma(t, fma(t, fma(t, fma(t, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5), 1.0);
+  const double ne = (double)(e - 24);
+  const double lnu = fma(ne, ln2_hi, L.x + fma(t, p, ne * ln2_lo));
+  const double r = sqrt(-2.0 * lnu);
+  // angle
+  const uint32_t m2 = 2u * (b & 0x7FFFFFu) + 1u;
+  const double2 CS = T->cs[m2 >> 14];
+  const double d = (double)(m2 & 0x3FFFu) * (6.283185307179586476925286766559 * 5.9604644775390625e-08);
+  const double d2 = d * d;
+  const double sd = fma(d * d2, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);
+  const double cm1 = d2 * fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5);  // cos d - 1
+  const double cs = fma(-CS.y, sd, fma(CS.x, cm1, CS.x));
+  const double sn = fma(CS.x, sd, fma(CS.y, cm1, CS.y));
+  n0 = r * cs;
+  n1 = r * sn;
+}
+
+// Two Box-Muller pairs at once, (a0, b0) and (a1, b1): normal_pair's arithmetic with its FP32
+// steps in packed two-lane instructions; n0 = (n0 of the first pair, n0 of the second), n1
+// likewise.  FP64: two normal_pair calls.
+template <class real>
+__device__ __forceinline__ void normal_pair2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, real& n00,
+                                             real& n01, real& n10, real& n11, const BmTables<real>* T) {
+  normal_pair<real>(a0, b0, n00, n01, T);
+  normal_pair<real>(a1, b1, n10, n11, T);
+}
+template <>
+__device__ __forceinline__ void normal_pair2<float>(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, float& n00,
+                                                    float& n01, float& n10, float& n11, const BmTables<float>*) {
+  const float2 x1 = make_float2(unit_interval_bits(a0), unit_interval_bits(a1));
+  const float2 u1 = __fadd2_rn(x1, make_float2(-0.999999940395355224609375f, -0.999999940395355224609375f));
+  const float2 v = __ffma2_rn(u1, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  const float2 tl = __fmul2_rn(make_float2(-1.38629436111989061f, -1.38629436111989061f),
+                               make_float2(lg2_ftz(u1.x), lg2_ftz(u1.y)));
+  const float2 ts = __fmul2_rn(
+      v, __ffma2_rn(v, __ffma2_rn(v, make_float2(0.666666666666666667f, 0.666666666666666667f), make_float2(1.0f, 1.0f)),
+                    make_float2(2.0f, 2.0f)));
+  const float2 t = make_float2(v.x < 0.015625f ? ts.x : tl.x, v.y < 0.015625f ? ts.y : tl.y);
+  const float2 r = __fmul2_rn(t, make_float2(rsqrt_ftz(t.x), rsqrt_ftz(t.y)));
+  const float2 phi = __ffma2_rn(make_float2(6.28318530717959f, 6.28318530717959f),
+                                make_float2(unit_interval_bits(b0), unit_interval_bits(b1)),
+                                make_float2(-9.42477758729298f, -9.42477758729298f));
+  float s0, c0, s1, c1;
+  sincos_ftz(phi.x, s0, c0);
+  sincos_ftz(phi.y, s1, c1);
+  n00 = -r.x * c0;
+  n01 = -r.x * s0;
+  n10 = -r.y * c1;
+  n11 = -r.y * s1;
+}
+
+
 template <class real>
 __device__ __forceinline__ real sqrt_pos(real v);
 template <>

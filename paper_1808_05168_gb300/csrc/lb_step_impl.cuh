@@ -362,80 +362,6 @@ __device__ __forceinline__ void collide_out(const Mom<real>& m, Pr<real> d, Pr<r
   }
 }
 
-// The hardware approximations in their flush-to-zero forms: their arguments here are never
-// subnormal (u1 >= 2^-24, t > 2^-24, phi a multiple of 2^-44), so the results are those of the
-// plain forms without their subnormal handling.
-__device__ __forceinline__ float lg2_ftz(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ void sincos_ftz(float x, float& s, float& c) {
-  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
-  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
-}
-
-template <class real>
-__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, real& n0, real& n1);
-template <>
-__device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float& n0, float& n1) {
-  const float u1 = uniform01<float>(a);
-  const float v = 1.0f - u1;
-  const float t_log = -1.38629436111989061f * lg2_ftz(u1);
-  const float t_ser = v * fmaf(v, fmaf(v, 0.666666666666666667f, 1.0f), 2.0f);
-  const float t = v < 0.015625f ? t_ser : t_log;
-  const float r = t * rsqrt_ftz(t);
-  // phi = 2 pi u2 - pi = 2 pi x2 - 3 pi + 2 pi 2^-24 with x2 = u2 + 1 - 2^-24 built from the bits
-  const float phi = fmaf(6.28318530717959f, unit_interval_bits(b), -9.42477758729298f);
-  float s, c;
-  sincos_ftz(phi, s, c);
-  n0 = -r * c;
-  n1 = -r * s;
-}
-template <>
-__device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, double& n0, double& n1) {
-  box_muller<double>(a, b, n0, n1);
-}
-
-// Two Box-Muller pairs at once, (a0, b0) and (a1, b1): normal_pair's arithmetic with its FP32
-// steps in packed two-lane instructions; n0 = (n0 of the first pair, n0 of the second), n1
-// likewise.  FP64: two normal_pair calls.
-template <class real>
-__device__ __forceinline__ void normal_pair2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, real& n00,
-                                             real& n01, real& n10, real& n11) {
-  normal_pair<real>(a0, b0, n00, n01);
-  normal_pair<real>(a1, b1, n10, n11);
-}
-template <>
-__device__ __forceinline__ void normal_pair2<float>(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, float& n00,
-                                                    float& n01, float& n10, float& n11) {
-  const float2 x1 = make_float2(unit_interval_bits(a0), unit_interval_bits(a1));
-  const float2 u1 = __fadd2_rn(x1, make_float2(-0.999999940395355224609375f, -0.999999940395355224609375f));
-  const float2 v = __ffma2_rn(u1, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
-  const float2 tl = __fmul2_rn(make_float2(-1.38629436111989061f, -1.38629436111989061f),
-                               make_float2(lg2_ftz(u1.x), lg2_ftz(u1.y)));
-  const float2 ts = __fmul2_rn(
-      v, __ffma2_rn(v, __ffma2_rn(v, make_float2(0.666666666666666667f, 0.666666666666666667f), make_float2(1.0f, 1.0f)),
-                    make_float2(2.0f, 2.0f)));
-  const float2 t = make_float2(v.x < 0.015625f ? ts.x : tl.x, v.y < 0.015625f ? ts.y : tl.y);
-  const float2 r = __fmul2_rn(t, make_float2(rsqrt_ftz(t.x), rsqrt_ftz(t.y)));
-  const float2 phi = __ffma2_rn(make_float2(6.28318530717959f, 6.28318530717959f),
-                                make_float2(unit_interval_bits(b0), unit_interval_bits(b1)),
-                                make_float2(-9.42477758729298f, -9.42477758729298f));
-  float s0, c0, s1, c1;
-  sincos_ftz(phi.x, s0, c0);
-  sincos_ftz(phi.y, s1, c1);
-  n00 = -r.x * c0;
-  n01 = -r.x * s0;
-  n10 = -r.y * c1;
-  n11 = -r.y * s1;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -450,7 +376,7 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
                                             const Pr<real>* ring, int bc, int bu, int bd, uint32_t site,
                                             uint32_t step, real* fl, real* pl, int LzLx, double& acc_p,
                                             double& acc_a, double& acc_b, real* outA, real* outB, int ostride,
-                                            int flags) {
+                                            int flags, const BmTables<real>* bm) {
   using P = Pr<real>;
   const P c9 = pr(real(1) / 9), c36 = pr(real(1) / 36);
   const P d = ring[bc];
@@ -506,10 +432,10 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
     U4 w4[4];
     philox_site(site, step, K.lid, K.key0, K.key1, w4);
     real g[14];
-    normal_pair2<real>(w4[0].x, w4[0].y, w4[0].z, w4[0].w, g[0], g[1], g[2], g[3]);
-    normal_pair2<real>(w4[1].x, w4[1].y, w4[1].z, w4[1].w, g[4], g[5], g[6], g[7]);
-    normal_pair2<real>(w4[2].x, w4[2].y, w4[2].z, w4[2].w, g[8], g[9], g[10], g[11]);
-    normal_pair<real>(w4[3].x, w4[3].y, g[12], g[13]);
+    normal_pair2<real>(w4[0].x, w4[0].y, w4[0].z, w4[0].w, g[0], g[1], g[2], g[3], bm);
+    normal_pair2<real>(w4[1].x, w4[1].y, w4[1].z, w4[1].w, g[4], g[5], g[6], g[7], bm);
+    normal_pair2<real>(w4[2].x, w4[2].y, w4[2].z, w4[2].w, g[8], g[9], g[10], g[11], bm);
+    normal_pair<real>(w4[3].x, w4[3].y, g[12], g[13], bm);
     if (NOISE == NOISE_LOC) {
       const real sm = sqrt_pos<real>(rs.x * rs.y * inv);
       cm = pr(sm, -sm);
@@ -556,15 +482,24 @@ __device__ __forceinline__ void block_partials(double acc_p, double acc_a, doubl
 // Generic: reduction scratch, lattice constants, density ring (2 x 4 rows of TX + 2), stage
 // (NS rows x 18 links x (TX + 2)).
 template <class real>
+struct BmBytes {
+  static constexpr size_t value = sizeof(real) == 8 ? sizeof(BmTables<double>) : 0;
+};
+
+template <class real>
 struct Smem {
   static constexpr size_t red = 0;
   static constexpr size_t lat = 8 * 3 * sizeof(double);
   static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
   __host__ __device__ static size_t stage(int tx) { return ring + (size_t)8 * (tx + 2) * sizeof(real); }
-  __host__ __device__ static size_t bytes(int tx) { return stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real); }
+  __host__ __device__ static size_t bm(int tx) {
+    return ((stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real) + 15) / 16) * 16;
+  }
+  __host__ __device__ static size_t bytes(int tx) { return bm(tx) + BmBytes<real>::value; }
 };
 
-// Bulk: as generic, then input slots (NSI x 18 x SW), NSI mbarriers and an abort flag.
+// Bulk: as generic, then input slots (NSI x 18 x SW), NSI mbarriers and an abort flag.  Both end
+// with the double-precision Box-Muller tables (FP64 kernels only).
 template <class real, int TX>
 struct SmemBulk {
   static constexpr int PAD = 16 / (int)sizeof(real);
@@ -575,7 +510,9 @@ struct SmemBulk {
   static constexpr size_t in = ring + ((8 * (TX + 2) * sizeof(real) + 15) / 16) * 16;
   static constexpr size_t bars = in + (size_t)NSI * 18 * SW * sizeof(real);
   static constexpr size_t abort_flag = bars + NSI * sizeof(uint64_t);
-  static constexpr size_t bytes = abort_flag + 16;
+  static constexpr size_t bm = ((abort_flag + 16 + 15) / 16) * 16;  // 16-byte entries
+  static constexpr size_t bytes = bm + BmBytes<real>::value;
+  static_assert(in % 16 == 0 && bars % 8 == 0 && bm % 16 == 0, "shared-memory regions must stay aligned");
 };
 
 // ======================================================================================
@@ -586,6 +523,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
                                              real* __restrict__ dst, int item_index, uint32_t step,
                                              unsigned char* smem) {
   double* red = reinterpret_cast<double*>(smem + Smem<real>::red);
+  const BmTables<real>* bm = reinterpret_cast<const BmTables<real>*>(smem + Smem<real>::bm(blockDim.x));
   LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + Smem<real>::lat);
   const int TX = blockDim.x, W = TX + 2;
   Pr<real>* ring = reinterpret_cast<Pr<real>*>(smem + Smem<real>::ring);
@@ -686,7 +624,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
             K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
-            g + 9 * LzLx + r0, LzLx, flags);
+            g + 9 * LzLx + r0, LzLx, flags, bm);
       };
       if (flags & DF_UNIT) {
         if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>());
@@ -725,6 +663,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   using SM = SmemBulk<real, TX>;
   constexpr int PAD = SM::PAD, SW = SM::SW, W = TX + 2;
   double* red = reinterpret_cast<double*>(smem + SM::red);
+  const BmTables<real>* bm = reinterpret_cast<const BmTables<real>*>(smem + SM::bm);
   LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + SM::lat);
   Pr<real>* ring = reinterpret_cast<Pr<real>*>(smem + SM::ring);
   real* instage = reinterpret_cast<real*>(smem + SM::in);
@@ -872,7 +811,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
             K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
-            g + 9 * LzLx + r0, LzLx, flags);
+            g + 9 * LzLx + r0, LzLx, flags, bm);
       };
       auto rates = [&](auto inner) {
         if (flags & DF_UNIT) {
@@ -909,6 +848,15 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
 // ======================================================================================
 // Kernels.
 // ======================================================================================
+// The FP64 noise tables of the block (before its first item; none in FP32 or without noise).
+template <class real, int NOISE>
+__device__ __forceinline__ void prepare_bm(unsigned char* p) {
+  if constexpr (sizeof(real) == 8 && NOISE != NOISE_OFF) {
+    fill_bm_tables<real>(reinterpret_cast<BmTables<real>*>(p));
+    __syncthreads();
+  }
+}
+
 template <class real>
 struct MinBlocks {
   static constexpr int value = sizeof(real) == 4 ? 2 : 1;
@@ -918,6 +866,7 @@ template <class real, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepArgs<real> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
+  prepare_bm<real, NOISE>(smem + Smem<real>::bm(blockDim.x));
   process_item<real, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem);
 }
 
@@ -938,6 +887,7 @@ __global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX) step_k
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
   bulk_init<real, TX>(smem);
+  prepare_bm<real, NOISE>(smem + SmemBulk<real, TX>::bm);
   uint32_t ph = 0;
   process_item_bulk<real, TX, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem, ph);
 }
@@ -981,6 +931,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
     persistent_kernel(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
+  prepare_bm<real, NOISE>(smem + Smem<real>::bm(blockDim.x));
   for (int k = 0; k < nsteps; ++k) {
     const real* src = (k & 1) ? a.dst : a.src;
     real* dst = (k & 1) ? const_cast<real*>(a.src) : a.dst;
@@ -1002,6 +953,7 @@ __global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   bulk_init<real, TX>(smem);
+  prepare_bm<real, NOISE>(smem + SmemBulk<real, TX>::bm);
   uint32_t ph = 0;
   for (int k = 0; k < nsteps; ++k) {
     const real* src = (k & 1) ? a.dst : a.src;
@@ -1162,14 +1114,18 @@ cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nste
 // 2j and 2j + 1 together as the step kernels do, a trailing odd pair alone.
 template <class real>
 __global__ void debug_normals_kernel(const uint32_t* __restrict__ words, int64_t n_pairs, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  prepare_bm<real, NOISE_HOM>(smem);
+  const BmTables<real>* bm = reinterpret_cast<const BmTables<real>*>(smem);
   const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (i + 1 < n_pairs) {
     real n[4];
-    normal_pair2<real>(words[2 * i], words[2 * i + 1], words[2 * i + 2], words[2 * i + 3], n[0], n[1], n[2], n[3]);
+    normal_pair2<real>(words[2 * i], words[2 * i + 1], words[2 * i + 2], words[2 * i + 3], n[0], n[1], n[2], n[3],
+                       bm);
     for (int k = 0; k < 4; ++k) out[2 * i + k] = (double)n[k];
   } else if (i < n_pairs) {
     real n0, n1;
-    normal_pair<real>(words[2 * i], words[2 * i + 1], n0, n1);
+    normal_pair<real>(words[2 * i], words[2 * i + 1], n0, n1, bm);
     out[2 * i] = (double)n0;
     out[2 * i + 1] = (double)n1;
   }
@@ -1179,7 +1135,13 @@ template <class real>
 cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double* out, cudaStream_t s) {
   if (n_pairs <= 0) return cudaSuccess;
   const int64_t blocks = ((n_pairs + 1) / 2 + 255) / 256;
-  debug_normals_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(words, n_pairs, out);
+  const size_t smem = BmBytes<real>::value;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(debug_normals_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  debug_normals_kernel<real><<<(unsigned)blocks, 256, smem, s>>>(words, n_pairs, out);
   return cudaGetLastError();
 }
 
