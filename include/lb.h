@@ -98,6 +98,19 @@ int lb_create(lb_ctx** out, int Lx, int Lz, double lambda_s, double lambda_d, do
  * parameters), advanced together by lb_step in one launch per step. */
 int lb_create_batch(lb_ctx** out, int n, const lb_params* params, int flags);
 
+/* Device memory from the caller: as lb_create_batch, but every device buffer the context holds
+ * (state, tables, diagnostics, correlations, and the temporaries of lb_pressure_shift_gradient)
+ * is obtained with alloc_fn(bytes, user) and returned with free_fn(ptr, user), e.g. from a
+ * framework's caching allocator on the current device.  alloc_fn returns a device pointer
+ * aligned to at least 256 bytes, or NULL (the call then fails with LB_ERR_OOM); free_fn is called
+ * once for every pointer, after the context's work on it has finished, at the latest in
+ * lb_destroy.  Both functions must stay valid for the context's lifetime; both are required
+ * (LB_ERR_BAD_PARAM otherwise).  lb_power_spectrum is not affected (it takes no context). */
+typedef void* (*lb_alloc_fn)(size_t bytes, void* user);
+typedef void (*lb_free_fn)(void* ptr, void* user);
+int lb_create_batch_with_allocator(lb_ctx** out, int n, const lb_params* params, int flags, lb_alloc_fn alloc_fn,
+                                   lb_free_fn free_fn, void* user);
+
 /* Run on a caller-owned cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream);
  * NULL selects the context's own non-blocking stream (the default after lb_create).
  * Pending work on the previous stream is waited for first. */

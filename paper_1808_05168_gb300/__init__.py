@@ -52,7 +52,9 @@ class Simulation:
 
     def __init__(self, lattices, precision: str = "fp64", astar: bool = True, wall_fixed: bool = False,
                  noise_loc: bool = False, graph: bool = False, persistent: bool = False, autotune: bool = False,
-                 bulk: bool = True):
+                 bulk: bool = True, allocator=None):
+        """allocator: None (the library allocates with cudaMalloc), "torch" (torch's caching
+        allocator on the current device) or an (alloc, free) pair of capi callbacks."""
         if isinstance(lattices, LatticeParams):
             lattices = [lattices]
         self.lattices = list(lattices)
@@ -66,7 +68,12 @@ class Simulation:
         flags |= 0 if bulk else capi.LB_NO_BULK
         self.flags = flags
         self.precision = precision
-        self.h = capi.lb_create_batch([p.to_c() for p in self.lattices], flags)
+        if allocator is None:
+            self.h = capi.lb_create_batch([p.to_c() for p in self.lattices], flags)
+        else:
+            # the callbacks must outlive the context: they are kept on the object
+            self._allocator = capi.torch_allocator() if allocator == "torch" else tuple(allocator)
+            self.h = capi.lb_create_batch_with_allocator([p.to_c() for p in self.lattices], flags, *self._allocator)
 
     def close(self):
         if getattr(self, "h", None):

@@ -37,7 +37,7 @@ LB_SF_QXQZ, LB_SF_QX = 0, 1
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblb_gb300.so")
 
 # Every symbol declared in include/lb.h.
-EXPORTS = ("lb_create", "lb_create_batch", "lb_set_stream", "lb_set_sampling", "lb_set_tile", "lb_get_tile",
+EXPORTS = ("lb_create", "lb_create_batch", "lb_create_batch_with_allocator", "lb_set_stream", "lb_set_sampling", "lb_set_tile", "lb_get_tile",
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
            "lb_profile", "lb_set_correlations", "lb_correlation", "lb_mode_correlation", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
@@ -84,6 +84,8 @@ def load():
         sig = {
             "lb_create": [ctypes.POINTER(vp), i, i, d, d, d, d, d, d, d, d, u64, i],
             "lb_create_batch": [ctypes.POINTER(vp), i, ctypes.POINTER(lb_params), i],
+            "lb_create_batch_with_allocator": [ctypes.POINTER(vp), i, ctypes.POINTER(lb_params), i, LB_ALLOC_FN,
+                                               LB_FREE_FN, vp],
             "lb_set_stream": [vp, vp],
             "lb_set_sampling": [vp, i64, i64],
             "lb_set_tile": [vp, i, i],
@@ -139,6 +141,41 @@ def lb_create(Lx, Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G,
     _check(lib.lb_create(ctypes.byref(h), int(Lx), int(Lz), float(lambda_s), float(lambda_d), float(lambda_e),
                          float(lambda_q), float(lambda_eps), float(kT), float(G), float(grad_c0), int(seed),
                          int(flags)), "lb_create")
+    return h
+
+
+# Callback types of lb_create_batch_with_allocator: alloc(bytes, user) -> device pointer or NULL,
+# free(ptr, user).
+LB_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+LB_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def torch_allocator(device=None):
+    """(alloc, free) callbacks that take the context's device memory from torch's caching
+    allocator on `device` (the current device by default).  Keep them alive as long as the
+    context."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:
+            return None
+
+    def free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return LB_ALLOC_FN(alloc), LB_FREE_FN(free)
+
+
+def lb_create_batch_with_allocator(params, flags, alloc_cb, free_cb):
+    lib = load()
+    arr = (lb_params * len(params))(*params)
+    h = ctypes.c_void_p()
+    _check(lib.lb_create_batch_with_allocator(ctypes.byref(h), len(params), arr, int(flags), alloc_cb, free_cb, None),
+           "lb_create_batch_with_allocator")
     return h
 
 

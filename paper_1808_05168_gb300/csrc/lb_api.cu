@@ -38,6 +38,10 @@ struct GraphKey {
 }  // namespace
 
 struct lb_ctx {
+  // device memory: the caller's allocator when one was given, else cudaMalloc / cudaFree
+  lb_alloc_fn alloc_fn = nullptr;
+  lb_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
   int n_lat = 0;
   int flags = 0;
   bool dev32 = false;
@@ -109,16 +113,29 @@ struct lb_ctx {
 
 namespace {
 
+// Every device buffer of a context comes from here and goes back through dev_free.
+void* ctx_malloc(lb_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (c->alloc_fn) return c->alloc_fn(bytes, c->alloc_user);
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return q;
+}
+
+void dev_free(lb_ctx* c, void* p) {
+  if (!p) return;
+  if (c->free_fn) c->free_fn(p, c->alloc_user);
+  else cudaFree(p);
+}
+
 template <class T>
 int dev_alloc(lb_ctx* c, T** p, size_t bytes) {
-  *p = nullptr;
-  if (bytes == 0) bytes = 16;
-  if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return LB_ERR_OOM;
-  }
-  c->bytes += bytes;
+  *p = (T*)ctx_malloc(c, bytes);
+  if (!*p) return LB_ERR_OOM;
+  c->bytes += bytes ? bytes : 16;
   return LB_OK;
 }
 
@@ -303,7 +320,7 @@ int build_items(lb_ctx* c, int tile_x, int rows) {
   }
   if ((int)items.size() > c->d_items_cap) {
     if (c->d_items) {
-      cudaFree(c->d_items);
+      dev_free(c, c->d_items);
       c->bytes -= (size_t)c->d_items_cap * sizeof(WorkItem);
     }
     int rc = dev_alloc(c, &c->d_items, items.size() * sizeof(WorkItem));
@@ -312,7 +329,7 @@ int build_items(lb_ctx* c, int tile_x, int rows) {
   }
   if ((int)items.size() > c->partials_cap) {
     if (c->partials) {
-      cudaFree(c->partials);
+      dev_free(c, c->partials);
       c->bytes -= (size_t)c->partials_cap * 3 * sizeof(double);
     }
     int rc = dev_alloc(c, &c->partials, items.size() * 3 * sizeof(double));
@@ -607,7 +624,8 @@ int step_impl(lb_ctx* c, int64_t n) {
   return LB_OK;
 }
 
-int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
+int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn alloc_fn = nullptr,
+                lb_free_fn free_fn = nullptr, void* alloc_user = nullptr) {
   if (!out) return LB_ERR_BAD_PARAM;
   *out = nullptr;
   if (n < 1 || !ps) return LB_ERR_BAD_PARAM;
@@ -618,8 +636,12 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags) {
     int rc = check_params(ps[i]);
     if (rc) return rc;
   }
+  if (!alloc_fn != !free_fn) return LB_ERR_BAD_PARAM;
   lb_ctx* c = new (std::nothrow) lb_ctx();
   if (!c) return LB_ERR_OOM;
+  c->alloc_fn = alloc_fn;
+  c->free_fn = free_fn;
+  c->alloc_user = alloc_user;
   c->n_lat = n;
   c->flags = flags;
   c->dev32 = flags & LB_PREC_DEV32;
@@ -726,17 +748,13 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   cudaStream_t st = c->stream;
   std::vector<void*> owned;
   auto alloc = [&](size_t bytes) -> void* {
-    void* q = nullptr;
-    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    owned.push_back(q);
+    void* q = ctx_malloc(c, bytes);
+    if (q) owned.push_back(q);
     return q;
   };
   auto release = [&]() {
     cudaStreamSynchronize(st);
-    for (void* q : owned) cudaFree(q);
+    for (void* q : owned) dev_free(c, q);
   };
   real* ck = (real*)alloc(nck * S * sizeof(real));
   real* ring = want_grad ? (real*)alloc(C * S * sizeof(real)) : nullptr;
@@ -870,6 +888,15 @@ int lb_create_batch(lb_ctx** out, int n, const lb_params* params, int flags) {
   return create_impl(out, n, params, flags);
 }
 
+int lb_create_batch_with_allocator(lb_ctx** out, int n, const lb_params* params, int flags, lb_alloc_fn alloc_fn,
+                                   lb_free_fn free_fn, void* user) {
+  if (!alloc_fn || !free_fn) {
+    if (out) *out = nullptr;
+    return LB_ERR_BAD_PARAM;
+  }
+  return create_impl(out, n, params, flags, alloc_fn, free_fn, user);
+}
+
 int lb_set_stream(lb_ctx* c, void* stream) {
   if (!c) return LB_ERR_BAD_PARAM;
   cudaStream_t s = stream ? (cudaStream_t)stream : c->own_stream;
@@ -982,8 +1009,7 @@ int lb_structure_factor(lb_ctx* c, int lattice, int field, int mode, double* out
 namespace {
 void corr_free(lb_ctx* c) {
   void* ptrs[] = {c->corr_R, c->corr_C, c->d_corr_real, c->d_corr_mode, c->d_corr_modes};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dev_free(c, p);
   c->bytes -= (c->corr_R_n + c->corr_C_n) * sizeof(double) +
               ((size_t)c->n_corr_real + (size_t)c->n_corr_mode) * sizeof(int4) + c->corr_modes.size() * sizeof(int);
   c->corr_R = c->corr_C = nullptr;
@@ -1256,8 +1282,7 @@ void lb_destroy(lb_ctx* c) {
                   c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass,
                   c->pfield, c->prof_sum, c->prof_comp, c->d_row_lat, c->corr_R, c->corr_C, c->d_corr_real,
                   c->d_corr_mode, c->d_corr_modes};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dev_free(c, p);
   delete c;
 }
 

@@ -63,6 +63,11 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lb_mass(None, 0, None) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_debug_barrier(0, 1, 10) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_profile(None, 0, capi.LB_FIELD_P, None, 0, None) == capi.LB_ERR_BAD_PARAM
+    h = ctypes.c_void_p()
+    p = capi.lb_params(8, 8, 1.0, 0.8, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0, 1, 0, 0)
+    assert lib.lb_create_batch_with_allocator(ctypes.byref(h), 1, (capi.lb_params * 1)(p), 0, capi.LB_ALLOC_FN(),
+                                              capi.LB_FREE_FN(), None) == capi.LB_ERR_BAD_PARAM
+    assert not h.value
     assert lib.lb_debug_box_muller(7, None, 1, None) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_debug_box_muller(capi.LB_PREC_DEV32, None, -1, None) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_debug_box_muller(capi.LB_PREC_DEV32, None, 1, None) == capi.LB_ERR_BAD_PARAM

@@ -383,3 +383,32 @@ def test_degenerate_lattices_in_one_batch(prec):
             assert_fp64_parity(got[i], o.populations())
         else:
             assert_dev32_parity(got[i], o.populations(), background(p.Lx, p.Lz, p.grad_c0))
+
+
+def test_device_memory_from_the_callers_allocator():
+    """lb_create_batch_with_allocator with torch's caching allocator: the same results as the
+    library's own allocations, torch accounts for the context's memory while it lives, and every
+    buffer goes back when it is destroyed."""
+    import torch
+
+    p = LatticeParams(64, 32, kT=1e-4, G=0.5, grad_c0=0.3 / 32, seed=12)
+    out = []
+    for allocator in (None, "torch"):
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        with Simulation(p, precision="dev32", allocator=allocator) as sim:
+            sim.set_sampling(5, 5)
+            sim.set_correlations(("c",), [1])
+            sim.step(40)
+            loss, grad = sim.pressure_shift_gradient(20, 10)
+            held = torch.cuda.memory_allocated() - before
+            nbytes = capi.lb_device_bytes(sim.h)
+            out.append((sim.populations(), sim.structure_factor("c")[0], sim.correlation("c")[0], loss, grad))
+        torch.cuda.synchronize()
+        if allocator == "torch":
+            assert held >= nbytes > 0
+            assert torch.cuda.memory_allocated() == before
+        else:
+            assert held == 0
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
