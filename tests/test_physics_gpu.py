@@ -114,3 +114,23 @@ def test_nonequilibrium_pressure_grows_as_the_squared_gradient():
     expo = np.log(hi["P_ne"] / lo["P_ne"]) / np.log(2.0)
     sig = np.hypot(lo["stderr"] / lo["P_ne"], hi["stderr"] / hi["P_ne"]) / np.log(2.0)
     assert abs(expo - 2.0) < 3 * sig, (expo, sig, lo, hi)
+
+
+def test_nonequilibrium_enhancement_follows_the_viscosity():
+    """Sec. III.B, Fig. 2: changing the kinematic viscosity at fixed D changes the NE enhancement
+    of S_c(q, 0) as phi ~ 1 / ((nu + D) D) (Eq. prefactor), with no fit.  lambda_d = 1 (D = 1/6)
+    and lambda_s = 1 (nu = 1/6) or 1.5 (nu = 1/18, Eq. vis): at qL = 14 .. 17, where the bulk law
+    holds, the enhancements stand in the ratio (1/6 + 1/6) / (1/18 + 1/6) = 1.5."""
+    qt = 2 * np.pi * np.arange(128) / 128 * 32
+    k = np.arange(9, 12)
+    enh = {}
+    for ls in (1.0, 1.5):
+        base = LatticeParams(128, 32, kT=KT, G=0.0, grad_c0=0.01, lambda_s=ls, lambda_d=1.0, lambda_e=ls)
+        sp = protocols.ensemble_spectra(base, range(500, 564), steps=42000, discard=2000, every=10, fields=("c",))
+        e = sp["c"][0][0] / (0.75 * KT) - 1
+        err = sp["c"][1][0] / (0.75 * KT)
+        enh[ls] = (e[k].sum(), np.sqrt((err[k] ** 2).sum()))
+    (a, sa), (b, sb) = enh[1.0], enh[1.5]
+    ratio = b / a
+    sig = ratio * np.hypot(sa / a, sb / b)
+    assert abs(ratio - 1.5) < 0.1 * 1.5 + 3 * sig, (ratio, sig)
