@@ -874,11 +874,11 @@ template <class real>
 struct BulkBlocks {  // 128-thread blocks per SM the bulk kernels are compiled for
   static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 : 2;
 };
-// The persistent kernel holds the grid-barrier state on top: one block fewer, so that it keeps
-// its registers (no spills).
+// The persistent kernel holds both sample variants and the grid-barrier state on top: two blocks
+// fewer per SM (128 registers), so that it keeps its values in registers (no spills).
 template <class real>
 struct PersistentBlocks {
-  static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 - 1 : 2;
+  static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 - 2 : 2;
 };
 
 template <class real, int TX, bool SAMPLE, int NOISE>
