@@ -90,7 +90,8 @@ struct lb_ctx {
   int2* d_col_tasks = nullptr;
   int n_row_tasks = 0, n_col_tasks = 0;
   int max_Lx = 0, max_Lz = 0;
-  int col_strip = 1;
+  int sf_threads = 256, sf_cap = 4096;  // sample-step transforms (sf_threads, SfPlan)
+  size_t sf_smem_rows = 0, sf_smem_cols = 0;
   int64_t* d_t = nullptr;
   unsigned* d_barrier = nullptr;
   int* d_err = nullptr;
@@ -366,16 +367,21 @@ int alloc_diag(lb_ctx* c) {
   if (!rc) rc = dev_alloc(c, &c->acc_sum, 4 * (size_t)c->n_sites * sizeof(double));
   if (!rc) rc = dev_alloc(c, &c->acc_comp, 4 * (size_t)c->n_sites * sizeof(double));
   if (rc) return rc;
-  c->col_strip = c->dev32 ? sf_column_strip<float>(c->max_Lz) : sf_column_strip<double>(c->max_Lz);
+  c->sf_threads = sf_threads(c->max_Lx, c->max_Lz);
+  c->sf_cap = 16 * c->sf_threads;
+  c->sf_smem_rows = c->sf_smem_cols = 0;
+  const size_t cs = 2 * rs;  // one complex point
   std::vector<int2> rt, ct;
   for (int i = 0; i < c->n_lat; ++i) {
-    const int Lx = c->params[i].Lx, cq = std::min(c->col_strip, Lx);
-    const int Lz = c->params[i].Lz;
-    const int R = std::min(std::max(1, 4096 / Lx), Lz);  // rows per block of the row pass
+    const int Lx = c->params[i].Lx, Lz = c->params[i].Lz;
+    const int R = sf_row_group(Lx, Lz, c->sf_cap), cq = sf_col_strip(Lx, Lz, c->sf_cap);
     for (int fld = 0; fld < 4; ++fld)
       for (int z0 = 0; z0 < Lz; z0 += R) rt.push_back(make_int2(i, fld * Lz + z0));
     for (int fld = 0; fld < 4; ++fld)
       for (int q = 0; q <= Lx / 2; q += cq) ct.push_back(make_int2(i, fld * Lx + q));  // S(-q) = S(q)
+    // twiddles (n/2 + 1 slots) and the sequences, as laid out by the two kernels
+    c->sf_smem_rows = std::max(c->sf_smem_rows, ((size_t)(Lx / 2 + 1) + (size_t)((R + 1) / 2) * sf_seq_stride(Lx)) * cs);
+    c->sf_smem_cols = std::max(c->sf_smem_cols, ((size_t)(Lz / 2 + 1) + (size_t)cq * sf_seq_stride(Lz)) * cs);
   }
   rc = dev_alloc(c, &c->d_row_tasks, rt.size() * sizeof(int2));
   if (!rc) rc = dev_alloc(c, &c->d_col_tasks, ct.size() * sizeof(int2));
@@ -429,9 +435,10 @@ cudaError_t enqueue_sample(lb_ctx* c) {
   p.col_tasks = c->d_col_tasks;
   p.n_row_tasks = c->n_row_tasks;
   p.n_col_tasks = c->n_col_tasks;
-  p.max_Lx = c->max_Lx;
-  p.max_Lz = c->max_Lz;
-  p.col_strip = c->col_strip;
+  p.threads = c->sf_threads;
+  p.cap = c->sf_cap;
+  p.smem_rows = c->sf_smem_rows;
+  p.smem_cols = c->sf_smem_cols;
   p.prof_sum = c->prof_sum;
   p.prof_comp = c->prof_comp;
   p.n_rows = c->n_rows;
@@ -915,7 +922,8 @@ int lb_set_sampling(lb_ctx* c, int64_t discard, int64_t every) {
       if (!is_pow2(p.Lx) || !is_pow2(p.Lz) || p.Lx < 2 || p.Lx > 8192 || p.Lz > 8192) return LB_ERR_BAD_PARAM;
     int rc = alloc_diag(c);
     if (rc) return rc;
-    cudaError_t e = c->dev32 ? prepare_sf<float>(c->max_Lx, c->max_Lz) : prepare_sf<double>(c->max_Lx, c->max_Lz);
+    cudaError_t e = c->dev32 ? prepare_sf<float>(c->sf_smem_rows, c->sf_smem_cols)
+                             : prepare_sf<double>(c->sf_smem_rows, c->sf_smem_cols);
     if (e != cudaSuccess) return cuda_err(e);
   }
   c->discard = discard;

@@ -4,9 +4,10 @@
 // utility kernels that convert between stored and absolute populations.
 //
 // Structure factors: the step kernel writes the four fields of every site on a sample step;
-// here one block per (lattice, field, row) transforms a row along x in shared memory and
-// one block per (lattice, field, q_x) transforms the column along z, squares, scales by
-// 1 / (Lx Lz) and adds the result to double-precision Neumaier (compensated) accumulators.
+// here one block per group of rows transforms them along x (two real rows per complex
+// transform) and one block per strip of adjacent q_x transforms the columns along z, squares,
+// scales by 1 / (Lx Lz) and adds the result to double-precision Kahan (compensated)
+// accumulators.
 #include "lb_internal.cuh"
 
 namespace lbk {
@@ -76,10 +77,6 @@ __global__ void fill_tw_tables_kernel() {
   }
 }
 
-// Shared-memory index of point i of the sample-step transforms: one pad element per 32 keeps the
-// bit-reversed scatter and the strided column accesses free of bank conflicts.
-__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
-
 // The twiddles of an n-point transform into shared memory, from the table.
 template <class real>
 __device__ void load_twiddles(Cplx<real>* tw, int n) {
@@ -96,15 +93,6 @@ __device__ void fill_twiddles(Cplx<real>* tw, int n) {
   }
 }
 
-// Row pass: one block per (lattice, field, group of R = rows_per_block(Lx, Lz) consecutive rows
-// z0 ..), so that short rows share one twiddle table and every thread has butterflies to do.
-// Task = (lattice, field * Lz + z0).
-__host__ __device__ __forceinline__ int rows_per_block(int Lx, int Lz) {
-  int r = 4096 / Lx;
-  if (r < 1) r = 1;
-  return r < Lz ? r : Lz;
-}
-
 __device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v) {
   const double t = sum + v;
   if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
@@ -112,47 +100,205 @@ __device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v
   sum = t;
 }
 
+// ---- sample-step transforms: self-sorting (Stockham) radix-16/8/4/2 passes --------------------
+// A pass of radix R over sequences of n points that have already been combined in spans of Ns
+// (Ns = product of the earlier radices): butterfly j (k = j mod Ns) takes the points j + r n/R,
+// r = 0 .. R-1, turns point r by exp(-2 pi i r k / (Ns R)), forms their R-point DFT in registers
+// and stores output q at (j - k) R + k + q Ns.  After the last pass the sequence holds its DFT
+// X_k = sum_j x_j exp(-2 pi i j k / n) in natural order (the autosort formulation of Stockham's
+// FFT, e.g. Govindaraju et al., SC 2008).  Each thread holds 16 points per pass; a barrier
+// separates its loads from its stores, so one buffer serves every pass.
+
 template <class real>
-__global__ void sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const real* fields, Cplx<real>* tmp,
-                               double* prof_sum, double* prof_comp, int n_rows) {
+__device__ __forceinline__ Cplx<real> cmul(Cplx<real> a, Cplx<real> b) {
+  return Cplx<real>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// cos and sin of 2 pi k / 16, k = 0 .. 7
+__host__ __device__ constexpr double cos16(int k) {
+  return k == 0 ? 1.0
+       : k == 1 ? 0.92387953251128675613
+       : k == 2 ? 0.70710678118654752440
+       : k == 3 ? 0.38268343236508977173
+       : k == 4 ? 0.0
+       : k == 5 ? -0.38268343236508977173
+       : k == 6 ? -0.70710678118654752440
+                : -0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin16(int k) { return k <= 4 ? cos16(4 - k) : cos16(k - 4); }
+
+// x exp(-2 pi i k / 16) for a compile-time k in 0 .. 7 (after unrolling), without products where
+// the factor is 1 or -i.
+template <class real>
+__device__ __forceinline__ Cplx<real> turn16(Cplx<real> x, int k) {
+  if (k == 0) return x;
+  if (k == 4) return Cplx<real>{x.im, -x.re};
+  const real c = (real)cos16(k), s = (real)sin16(k);
+  return Cplx<real>{x.re * c + x.im * s, x.im * c - x.re * s};
+}
+
+// i (0 .. 2^bits - 1, bits <= 4) with its bits reversed
+__host__ __device__ constexpr int bitrev_small(int i, int bits) {
+  return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
+}
+
+// In-order R-point DFT of v[0 .. R-1] in registers (R = 2, 4, 8, 16): radix-2 butterflies on the
+// bit-reversed inputs.
+template <class real, int R>
+__device__ __forceinline__ void dft_regs(Cplx<real>* v) {
+  constexpr int bits = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
+  Cplx<real> t[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) t[i] = v[bitrev_small(i, bits)];
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+    for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+      for (int p = 0; p < h; ++p) {
+        const Cplx<real> a = t[g + p], b = turn16(t[g + p + h], p * (8 / h));
+        t[g + p] = Cplx<real>{a.re + b.re, a.im + b.im};
+        t[g + p + h] = Cplx<real>{a.re - b.re, a.im - b.im};
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// One pass over `seqs` sequences of n points at s + seq * sf_seq_stride(n) (point p at p + p/16);
+// tw: exp(-2 pi i e / n) for e < n/2.
+template <class real, int R>
+__device__ __forceinline__ void stockham_pass(Cplx<real>* s, const Cplx<real>* tw, int n, int Ns, int seqs) {
+  constexpr int BPT = 16 / R;  // butterflies per thread
+  const int nb = n / R, lnb = 31 - __clz(nb);
+  const int total = seqs * nb, SS = sf_seq_stride(n);
+  const int unit = n / (Ns * R), h = n >> 1;
+  Cplx<real> v[16];
+#pragma unroll
+  for (int i = 0; i < BPT; ++i) {
+    const int b = threadIdx.x + i * blockDim.x;
+    if (b < total) {
+      const int seq = b >> lnb, j = b & (nb - 1), k = j & (Ns - 1);
+      const Cplx<real>* src = s + seq * SS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int p = j + r * nb;
+        v[i * R + r] = src[p + (p >> 4)];
+      }
+      if (k != 0) {
+        const int st = k * unit;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const int e = r * st;  // < n
+          const Cplx<real> w = tw[e < h ? e : e - h];
+          const Cplx<real> ws = e < h ? w : Cplx<real>{-w.re, -w.im};
+          v[i * R + r] = cmul(v[i * R + r], ws);
+        }
+      }
+      dft_regs<real, R>(v + i * R);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < BPT; ++i) {
+    const int b = threadIdx.x + i * blockDim.x;
+    if (b < total) {
+      const int seq = b >> lnb, j = b & (nb - 1), k = j & (Ns - 1);
+      Cplx<real>* dst = s + seq * SS;
+      const int d = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int p = d + r * Ns;
+        dst[p + (p >> 4)] = v[i * R + r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// DFT of `seqs` sequences of n = 2^m points in place (seqs n <= 16 blockDim.x): radix-16 passes,
+// then one pass of the remaining radix.
+template <class real>
+__device__ void stockham_fft(Cplx<real>* s, const Cplx<real>* tw, int n, int seqs) {
+  int left = 31 - __clz(n), Ns = 1;
+  for (; left >= 4; left -= 4, Ns <<= 4) stockham_pass<real, 16>(s, tw, n, Ns, seqs);
+  if (left == 3) stockham_pass<real, 8>(s, tw, n, Ns, seqs);
+  else if (left == 2) stockham_pass<real, 4>(s, tw, n, Ns, seqs);
+  else if (left == 1) stockham_pass<real, 2>(s, tw, n, Ns, seqs);
+}
+
+// Global loads per thread that the transforms issue before they wait for the first (row pass,
+// column pass; fewer in double precision, whose registers hold the 16 points of a pass).
+template <class real>
+struct SfBatch {
+  static constexpr int rows = sizeof(real) == 4 ? 8 : 4, cols = sizeof(real) == 4 ? 4 : 2;
+};
+
+// Row pass: one block per (lattice, field * Lz + z0), rows z0 .. z0 + R - 1 with
+// R = sf_row_group(Lx, Lz, cap).  Rows 2c and 2c + 1 of the group enter as the real and imaginary
+// parts of sequence c, so one complex transform gives both: with Z = DFT(a + i b),
+// A_q = (Z_q + conj Z_{n-q}) / 2 and B_q = (Z_q - conj Z_{n-q}) / (2 i).  q_x = 0 .. Lx/2 of every
+// row goes to tmp; the q_x = 0 bin is the row sum, whose mean goes to the profile.
+template <class real>
+__global__ void __launch_bounds__(512) sf_rows_kernel(const DiagLattice* lat, const int2* tasks, const real* fields, Cplx<real>* tmp,
+                               double* prof_sum, double* prof_comp, int n_rows, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int2 task = tasks[blockIdx.x];
   const DiagLattice L = lat[task.x];
-  const int n = L.Lx, logn = ilog2(n), half = n >> 1, H = sf_half(n);
-  const int R = rows_per_block(L.Lx, L.Lz);
+  const int n = L.Lx, logn = 31 - __clz(n), H = sf_half(n), SS = sf_seq_stride(n);
+  const int R = sf_row_group(n, L.Lz, cap), seqs = (R + 1) >> 1;
   Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
-  Cplx<real>* s = tw + (half > 0 ? half : 1);
+  Cplx<real>* s = tw + ((n >> 1) + 1);
   load_twiddles<real>(tw, n);
-  const int64_t off = 4 * L.site_off + (int64_t)task.y * n;  // first row of the group
-  for (int idx = threadIdx.x; idx < R * n; idx += blockDim.x) {
-    const int r = idx >> logn, j = idx & (n - 1);
-    const int b = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[spad(r * n + b)] = Cplx<real>{fields[off + idx], real(0)};
+  const real* src = fields + 4 * L.site_off + (int64_t)task.y * n;
+  const int total = seqs * n, T = blockDim.x;
+  // loads in batches of SfBatch<real>::rows per thread, all issued before their shared-memory stores
+  for (int base = threadIdx.x; base < total; base += SfBatch<real>::rows * T) {
+    real a[SfBatch<real>::rows], b[SfBatch<real>::rows];
+#pragma unroll
+    for (int i = 0; i < SfBatch<real>::rows; ++i) {
+      const int idx = base + i * T;
+      if (idx < total) {
+        const int c = idx >> logn, j = idx & (n - 1);
+        a[i] = src[(int64_t)(2 * c) * n + j];
+        b[i] = 2 * c + 1 < R ? src[(int64_t)(2 * c + 1) * n + j] : real(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < SfBatch<real>::rows; ++i) {
+      const int idx = base + i * T;
+      if (idx < total) {
+        const int c = idx >> logn, j = idx & (n - 1);
+        s[c * SS + j + (j >> 4)] = Cplx<real>{a[i], b[i]};
+      }
+    }
   }
   __syncthreads();
-  for (int lg = 1; lg <= logn; ++lg) {
-    const int hs = 1 << (lg - 1), stride = n >> lg;
-    for (int idx = threadIdx.x; idx < R * half; idx += blockDim.x) {
-      const int r = idx >> (logn - 1), jj = idx & (half - 1);
-      const int pos = jj & (hs - 1);
-      const int i0 = r * n + ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
-      const Cplx<real> w = tw[pos * stride], b = s[spad(i1)], a = s[spad(i0)];
-      const real tr = w.re * b.re - w.im * b.im, ti = w.re * b.im + w.im * b.re;
-      s[spad(i0)] = Cplx<real>{a.re + tr, a.im + ti};
-      s[spad(i1)] = Cplx<real>{a.re - tr, a.im - ti};
+  stockham_fft<real>(s, tw, n, seqs);
+  Cplx<real>* out = tmp + 4 * L.site_off + (int64_t)task.y * H;
+  {
+    const int dc = T / H, dq = T - dc * H;
+    int c = threadIdx.x / H, q = threadIdx.x - c * H;
+    for (int idx = threadIdx.x; idx < seqs * H; idx += T) {
+      const int qm = (n - q) & (n - 1);
+      const Cplx<real> Z = s[c * SS + q + (q >> 4)], M = s[c * SS + qm + (qm >> 4)];
+      const real hf = real(0.5);
+      out[(int64_t)(2 * c) * H + q] = Cplx<real>{hf * (Z.re + M.re), hf * (Z.im - M.im)};
+      if (2 * c + 1 < R) out[(int64_t)(2 * c + 1) * H + q] = Cplx<real>{hf * (Z.im + M.im), hf * (M.re - Z.re)};
+      c += dc;
+      q += dq;
+      if (q >= H) {
+        q -= H;
+        ++c;
+      }
     }
-    __syncthreads();
-  }
-  // q_x = 0 .. Lx/2 of each row; the q_x = 0 bin is the row sum, whose mean goes to the profile
-  const int64_t offh = 4 * L.site_off + (int64_t)task.y * H;
-  for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
-    const int r = idx / H, q = idx - r * H;
-    tmp[offh + idx] = s[spad(r * n + q)];
   }
   const int fld = task.y / L.Lz, z0 = task.y - fld * L.Lz;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const Cplx<real> Z0 = s[(r >> 1) * SS];
     const int64_t k = (int64_t)fld * n_rows + L.row_off + z0 + r;
-    neumaier_add(prof_sum[k], prof_comp[k], (double)s[spad(r * n)].re / (double)n);
+    neumaier_add(prof_sum[k], prof_comp[k], (double)((r & 1) ? Z0.im : Z0.re) / (double)n);
   }
 }
 
@@ -164,59 +310,80 @@ __device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
   sum = t;
 }
 
-
-// Column pass: one block per (lattice, field, strip of cq adjacent q_x), cq = min(CQ, Lx), so that
-// every row of the strip is read and accumulated with contiguous accesses.  The fields are
-// real, so S(-q) = S(q): strips cover q_x = 0 .. Lx/2 only and the rest is filled by symmetry
-// when the spectrum is read out.  The power is formed in the working precision and added to a
-// double-precision Kahan sum.
+// Column pass: one block per (lattice, field * Lx + q_x0), the strip of cq = sf_col_strip(Lx, Lz,
+// cap) adjacent q_x from q_x0 (fewer at the end of q_x = 0 .. Lx/2; the fields are real, so
+// S(-q) = S(q) and the rest is filled by symmetry when the spectrum is read out).  Rows of the
+// strip are read and accumulated with contiguous accesses; the power is formed in the working
+// precision and added to a double-precision Kahan sum.
 template <class real>
-__global__ void sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const Cplx<real>* tmp, double* acc_sum,
-                               double* acc_comp, int CQ) {
+__global__ void __launch_bounds__(512) sf_cols_kernel(const DiagLattice* lat, const int2* tasks, const Cplx<real>* tmp, double* acc_sum,
+                               double* acc_comp, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int2 task = tasks[blockIdx.x];
   const DiagLattice L = lat[task.x];
-  const int n = L.Lz, logn = ilog2(n), Lx = L.Lx, half = n >> 1;
-  const int cq = min(CQ, Lx), lcq = ilog2(cq);
+  const int n = L.Lz, Lx = L.Lx, H = sf_half(Lx), SS = sf_seq_stride(n);
   const int fld = task.y / Lx, qx0 = task.y - fld * Lx;
+  const int cq = sf_col_strip(Lx, n, cap), w = min(cq, H - qx0);
   Cplx<real>* tw = reinterpret_cast<Cplx<real>*>(smem);
-  Cplx<real>* s = tw + (half > 0 ? half : 1);
+  Cplx<real>* s = tw + ((n >> 1) + 1);
   load_twiddles<real>(tw, n);
-  const int H = sf_half(Lx);
-  const int64_t tbase = 4 * L.site_off + (int64_t)fld * H * n + qx0;  // compact row transforms
-  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx0;  // accumulators
-  for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
-    const int j = idx >> lcq, c = idx & (cq - 1);
-    const int r = (int)(__brev((unsigned)j) >> (32 - logn));
-    s[spad(c * n + r)] = qx0 + c < H ? tmp[tbase + (int64_t)j * H + c] : Cplx<real>{real(0), real(0)};
+  const Cplx<real>* in = tmp + 4 * L.site_off + (int64_t)fld * H * n + qx0;  // compact row transforms
+  const int64_t base = 4 * L.site_off + (int64_t)fld * Lx * n + qx0;     // accumulators
+  // point idx = j w + c of the strip (row j, column c); threads step idx by T, so (j, c) advance
+  // by (dj, dc) with a carry
+  const int T = blockDim.x, total = w * n, dj = T / w, dc = T - dj * w;
+  const int j0 = threadIdx.x / w, c0 = threadIdx.x - j0 * w;
+  auto advance = [&](int& j, int& c) {
+    j += dj;
+    c += dc;
+    if (c >= w) {
+      c -= w;
+      ++j;
+    }
+  };
+  {
+    int j = j0, c = c0;
+    for (int b0 = threadIdx.x; b0 < total; b0 += SfBatch<real>::cols * T) {
+      Cplx<real> x[SfBatch<real>::cols];
+      int at[SfBatch<real>::cols];
+#pragma unroll
+      for (int i = 0; i < SfBatch<real>::cols; ++i) {
+        if (b0 + i * T < total) x[i] = in[(int64_t)j * H + c];
+        at[i] = c * SS + j + (j >> 4);
+        advance(j, c);
+      }
+#pragma unroll
+      for (int i = 0; i < SfBatch<real>::cols; ++i)
+        if (b0 + i * T < total) s[at[i]] = x[i];
+    }
   }
   __syncthreads();
-  for (int lg = 1; lg <= logn; ++lg) {
-    const int hs = 1 << (lg - 1);
-    const int stride = n >> lg;
-    for (int idx = threadIdx.x; idx < half * cq; idx += blockDim.x) {
-      const int c = idx >> (logn - 1), jj = idx & (half - 1);
-      const int pos = jj & (hs - 1);
-      const int i0 = c * n + ((jj >> (lg - 1)) << lg) + pos, i1 = i0 + hs;
-      const Cplx<real> w = tw[pos * stride];
-      const Cplx<real> b = s[spad(i1)], a = s[spad(i0)];
-      const real tr = w.re * b.re - w.im * b.im;
-      const real ti = w.re * b.im + w.im * b.re;
-      s[spad(i0)] = Cplx<real>{a.re + tr, a.im + ti};
-      s[spad(i1)] = Cplx<real>{a.re - tr, a.im - ti};
-    }
-    __syncthreads();
-  }
+  stockham_fft<real>(s, tw, n, w);
   const real scale = real(1) / ((real)Lx * (real)n);
-  for (int idx = threadIdx.x; idx < n * cq; idx += blockDim.x) {
-    const int j = idx >> lcq, c = idx & (cq - 1);
-    if (qx0 + c >= H) continue;
-    const Cplx<real> v = s[spad(c * n + j)];
-    const int64_t o = base + (int64_t)j * Lx + c;
-    double sm = acc_sum[o], cp = acc_comp[o];
-    kahan_add(sm, cp, (double)((v.re * v.re + v.im * v.im) * scale));
-    acc_sum[o] = sm;
-    acc_comp[o] = cp;
+  int j = j0, c = c0;
+  for (int b0 = threadIdx.x; b0 < total; b0 += SfBatch<real>::cols * T) {
+    double sm[SfBatch<real>::cols], cp[SfBatch<real>::cols];
+    real pw[SfBatch<real>::cols];
+    int64_t o[SfBatch<real>::cols];
+#pragma unroll
+    for (int i = 0; i < SfBatch<real>::cols; ++i) {
+      if (b0 + i * T < total) {
+        const Cplx<real> v = s[c * SS + j + (j >> 4)];
+        pw[i] = (v.re * v.re + v.im * v.im) * scale;
+        o[i] = base + (int64_t)j * Lx + c;
+        sm[i] = acc_sum[o[i]];
+        cp[i] = acc_comp[o[i]];
+      }
+      advance(j, c);
+    }
+#pragma unroll
+    for (int i = 0; i < SfBatch<real>::cols; ++i) {
+      if (b0 + i * T < total) {
+        kahan_add(sm[i], cp[i], (double)pw[i]);
+        acc_sum[o[i]] = sm[i];
+        acc_comp[o[i]] = cp[i];
+      }
+    }
   }
 }
 
@@ -367,44 +534,22 @@ __global__ void init_rest_kernel(real* f, BgParams bp) {
 }  // namespace
 
 template <class real>
-size_t sf_smem_bytes(int n) {  // row pass: the larger of one row and 4096 points, plus twiddles
-  const int pts = n > 4096 ? n : 4096;
-  return (size_t)(pts + pts / 32 + 1) * sizeof(Cplx<real>) + (size_t)(n / 2 + 1) * sizeof(Cplx<real>);
-}
-
-// Columns per column-pass block: up to 16, fewer when Lz is long (shared memory budget).
-template <class real>
-int sf_column_strip(int max_Lz) {
-  int cq = 16;
-  while (cq > 1 && ((size_t)max_Lz * cq * 33 / 32 + 1 + max_Lz / 2 + 1) * sizeof(Cplx<real>) > 160 * 1024) cq >>= 1;
-  return cq;
-}
-
-template <class real>
-size_t sf_cols_smem_bytes(int max_Lz, int cq) {
-  return ((size_t)max_Lz * cq * 33 / 32 + 1 + max_Lz / 2 + 1) * sizeof(Cplx<real>);
-}
-
-template <class real>
-cudaError_t prepare_sf(int max_Lx, int max_Lz) {
+cudaError_t prepare_sf(size_t smem_rows, size_t smem_cols) {
   fill_tw_tables_kernel<real><<<(TW_TABLE + 255) / 256, 256>>>();
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sf_rows_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sf_smem_bytes<real>(max_Lx));
+  e = cudaFuncSetAttribute(sf_rows_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sf_cols_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sf_cols_smem_bytes<real>(max_Lz, sf_column_strip<real>(max_Lz)));
+  return cudaFuncSetAttribute(sf_cols_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols);
 }
 
 template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
                       cudaStream_t s) {
-  const size_t smr = sf_smem_bytes<real>(p.max_Lx), smc = sf_cols_smem_bytes<real>(p.max_Lz, p.col_strip);
-  sf_rows_kernel<real><<<p.n_row_tasks, 256, smr, s>>>(p.lat, p.row_tasks, fields, (Cplx<real>*)tmp, p.prof_sum,
-                                                       p.prof_comp, p.n_rows);
-  sf_cols_kernel<real><<<p.n_col_tasks, 256, smc, s>>>(p.lat, p.col_tasks, (const Cplx<real>*)tmp, acc_sum,
-                                                       acc_comp, p.col_strip);
+  sf_rows_kernel<real><<<p.n_row_tasks, p.threads, p.smem_rows, s>>>(p.lat, p.row_tasks, fields, (Cplx<real>*)tmp,
+                                                                     p.prof_sum, p.prof_comp, p.n_rows, p.cap);
+  sf_cols_kernel<real><<<p.n_col_tasks, p.threads, p.smem_cols, s>>>(p.lat, p.col_tasks, (const Cplx<real>*)tmp,
+                                                                     acc_sum, acc_comp, p.cap);
   return cudaGetLastError();
 }
 
@@ -560,9 +705,7 @@ cudaError_t launch_corr(const CorrPlan& p, const real* fields, const void* tmp, 
 }
 
 #define LB_INST(real)                                                                                        \
-  template size_t sf_smem_bytes<real>(int);                                                                  \
-  template cudaError_t prepare_sf<real>(int, int);                                                           \
-  template int sf_column_strip<real>(int);                                                                   \
+  template cudaError_t prepare_sf<real>(size_t, size_t);                                                     \
   template cudaError_t launch_sf<real>(const SfPlan&, const real*, void*, double*, double*, cudaStream_t);   \
   template cudaError_t launch_mass<real>(const real*, const BgParams&, double*, cudaStream_t);               \
   template cudaError_t launch_to_absolute<real>(const real*, const BgParams&, double*, cudaStream_t);        \

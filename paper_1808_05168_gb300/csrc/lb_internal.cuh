@@ -411,15 +411,16 @@ struct DiagStats {  // per lattice, updated by the finalize kernel
   int pad;
 };
 
-// Transform tasks of one sample: one block per (lattice, field * Lz + z0) group of rows (see
-// rows_per_block in lb_diag.cu) and per (lattice, field * Lx + q_x0) strip of columns.
+// Transform tasks of one sample: one block per (lattice, field * Lz + z0) group of rows and per
+// (lattice, field * Lx + q_x0) strip of columns (sf_row_group, sf_col_strip below).
 struct SfPlan {
   const DiagLattice* lat;
   const int2* row_tasks;
   const int2* col_tasks;
   int n_row_tasks, n_col_tasks;
-  int max_Lx, max_Lz;
-  int col_strip;  // q_x columns per column-pass block
+  int threads;                 // threads per transform block
+  int cap;                     // complex points one block holds, 16 per thread
+  size_t smem_rows, smem_cols;  // dynamic shared memory of the two passes
   // z-profiles of the four fields: the q_x = 0 bin of each row transform is the row sum
   double* prof_sum;
   double* prof_comp;
@@ -430,6 +431,27 @@ struct SfPlan {
 // H = Lx/2 + 1 values per row, row (field, z) of a lattice at 4 site_off + (field Lz + z) H.
 __host__ __device__ __forceinline__ int sf_half(int Lx) { return Lx / 2 + 1; }
 
+// Sizes of the sample-step transforms.  A block of `threads` threads holds cap = 16 threads
+// complex points in shared memory: two real rows of x form one complex sequence, and a column
+// strip is a set of adjacent q_x.  cap covers the longest sequence of the batch.
+inline int sf_threads(int max_Lx, int max_Lz) {
+  const int m = max_Lx > max_Lz ? max_Lx : max_Lz;
+  return m > 4096 ? m / 16 : 256;
+}
+// Real rows z0 .. z0 + R - 1 of one row-pass block (R even unless it is all of Lz).
+__host__ __device__ __forceinline__ int sf_row_group(int Lx, int Lz, int cap) {
+  const int r = 2 * (cap / Lx);
+  return r < Lz ? r : Lz;
+}
+// q_x columns of one column-pass block.
+__host__ __device__ __forceinline__ int sf_col_strip(int Lx, int Lz, int cap) {
+  const int c = cap / Lz, H = sf_half(Lx);
+  return c < H ? c : H;
+}
+// Shared-memory stride of one sequence of n points: one pad point after every 16 and one per
+// sequence, so that strided and transposing accesses spread over the banks.
+__host__ __device__ __forceinline__ int sf_seq_stride(int n) { return n + (n >> 4) + 1; }
+
 // What the utility kernels need to rebuild the background w_l rho_bar c^S_0(z) in double.
 struct BgParams {
   int Lx, Lz;
@@ -438,11 +460,7 @@ struct BgParams {
 };
 
 template <class real>
-size_t sf_smem_bytes(int n);
-template <class real>
-cudaError_t prepare_sf(int max_Lx, int max_Lz);
-template <class real>
-int sf_column_strip(int max_Lz);
+cudaError_t prepare_sf(size_t smem_rows, size_t smem_cols);
 
 template <class real>
 cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* acc_sum, double* acc_comp,
