@@ -479,7 +479,9 @@ cudaError_t enqueue_direct(lb_ctx* c, int cur, int64_t n, const std::vector<int6
   return launch_advance(c->d_t, n, c->stream);
 }
 
-// Persistent: one cooperative launch per run of steps ending with (at most) one sample step.
+// Persistent: one cooperative launch per run of plain steps; a sample step that ends a run is an
+// ordinary launch after it (with its sampling kernels), so that the persistent kernel carries the
+// plain variant only.
 template <class real>
 cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& sample_offsets) {
   if (c->coop_grid < 0) c->coop_grid = persistent_grid<real>(c->tile_x, c->noise_mode, c->bulk_ok);
@@ -495,18 +497,26 @@ cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<
       sample = true;
       ++si;
     }
-    const int64_t len = end - k;
-    cudaError_t e = cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), c->stream);
-    if (e != cudaSuccess) return e;
-    e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)len, sample, c->noise_mode,
-                                     c->bulk_ok, c->d_barrier, c->d_err, grid, 2000, c->stream);
-    if (e != cudaSuccess) return e;
-    c->launches += 1;
+    const int64_t plain = end - k - (sample ? 1 : 0);
+    cudaError_t e;
+    if (plain > 0) {
+      e = cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), c->stream);
+      if (e != cudaSuccess) return e;
+      e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)plain, c->noise_mode,
+                                       c->bulk_ok, c->d_barrier, c->d_err, grid, 2000, c->stream);
+      if (e != cudaSuccess) return e;
+      c->launches += 1;
+      if (plain & 1) cur ^= 1;
+    }
     if (sample) {
+      e = launch_step<real>(step_args<real>(c, cur, (int)(end - 1)), c->tile_x, true, c->noise_mode, c->bulk_ok,
+                            c->stream);
+      if (e != cudaSuccess) return e;
+      c->launches += 1;
       e = enqueue_sample<real>(c);
       if (e != cudaSuccess) return e;
+      cur ^= 1;
     }
-    if (len & 1) cur ^= 1;
     k = end;
   }
   c->launches += 1;

@@ -383,8 +383,8 @@ template <class real>
 cudaError_t prepare_step(int max_tile_x);
 
 template <class real>
-cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, int noise,
-                                   bool bulk, unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s);
+cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, int noise, bool bulk,
+                                   unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s);
 
 template <class real>
 int persistent_grid(int tile_x, int noise, bool bulk);

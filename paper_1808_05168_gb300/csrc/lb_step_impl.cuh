@@ -874,11 +874,11 @@ template <class real>
 struct BulkBlocks {  // 128-thread blocks per SM the bulk kernels are compiled for
   static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 : 2;
 };
-// The persistent kernel holds both sample variants and the grid-barrier state on top: two blocks
-// fewer per SM (128 registers), so that it keeps its values in registers (no spills).
+// The persistent kernel runs plain steps only (a sample step is an ordinary launch after it), so
+// it targets the blocks per SM of the step kernels.
 template <class real>
 struct PersistentBlocks {
-  static constexpr int value = sizeof(real) == 4 ? LB_BULK_BLOCKS_F32 - 2 : 2;
+  static constexpr int value = BulkBlocks<real>::value;
 };
 
 template <class real, int TX, bool SAMPLE, int NOISE>
@@ -926,9 +926,10 @@ static __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, i
   return ok_s != 0;
 }
 
+// nsteps plain steps in one cooperative launch, a bounded grid barrier between them.
 template <class real, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value)
-    persistent_kernel(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
+    persistent_kernel(StepArgs<real> a, int nsteps, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   prepare_bm<real, NOISE>(smem + Smem<real>::bm(blockDim.x));
@@ -936,11 +937,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
     const real* src = (k & 1) ? a.dst : a.src;
     real* dst = (k & 1) ? const_cast<real*>(a.src) : a.dst;
     const uint32_t step = (uint32_t)(t0 + k);
-    const bool sample = sample_last && k == nsteps - 1;
-    for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) {
-      if (sample) process_item<real, true, NOISE>(a, src, dst, i, step, smem);
-      else process_item<real, false, NOISE>(a, src, dst, i, step, smem);
-    }
+    for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) process_item<real, false, NOISE>(a, src, dst, i, step, smem);
     if (k + 1 < nsteps) {
       if (!grid_barrier(bar, err, gridDim.x, limit_ms)) return;
     }
@@ -949,7 +946,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
 
 template <class real, int TX, int NOISE>
 __global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
-    persistent_kernel_bulk(StepArgs<real> a, int nsteps, int sample_last, unsigned* bar, int* err, int limit_ms) {
+    persistent_kernel_bulk(StepArgs<real> a, int nsteps, unsigned* bar, int* err, int limit_ms) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   bulk_init<real, TX>(smem);
@@ -959,11 +956,9 @@ __global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
     const real* src = (k & 1) ? a.dst : a.src;
     real* dst = (k & 1) ? const_cast<real*>(a.src) : a.dst;
     const uint32_t step = (uint32_t)(t0 + k);
-    const bool sample = sample_last && k == nsteps - 1;
     for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) {
-      const bool ok = sample ? process_item_bulk<real, TX, true, NOISE>(a, src, dst, i, step, smem, ph)
-                             : process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, step, smem, ph);
-      if (!ok) return;  // the others give up at their next barrier (bounded)
+      if (!process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, step, smem, ph))
+        return;  // the others give up at their next barrier (bounded)
     }
     if (k + 1 < nsteps) {
       if (!grid_barrier(bar, err, gridDim.x, limit_ms)) return;
@@ -1100,11 +1095,11 @@ int persistent_grid(int tile_x, int noise, bool bulk) {
 }
 
 template <class real>
-cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, bool sample_last, int noise,
-                                   bool bulk, unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
+cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, int noise, bool bulk,
+                                   unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
   StepArgs<real> aa = a;
-  int ns = nsteps, sl = sample_last ? 1 : 0;
-  void* args[] = {&aa, &ns, &sl, &barrier, &err, &limit_ms};
+  int ns = nsteps;
+  void* args[] = {&aa, &ns, &barrier, &err, &limit_ms};
   size_t smem = 0;
   const void* fn = persistent_fn<real>(tile_x, noise, bulk, &smem);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
