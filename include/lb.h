@@ -241,10 +241,12 @@ int lb_device_bytes(lb_ctx* ctx, size_t* bytes);
 const char* lb_error_string(int code);
 void lb_destroy(lb_ctx* ctx);
 
-/* Test hook for the bounded grid barrier of LB_PERSISTENT: launches a grid of `blocks`
- * co-resident blocks that wait at a barrier expecting `expected` arrivals.  With expected >
- * blocks the wait must give up after its spin limit and the call returns LB_ERR_TIMEOUT; with
- * expected == blocks it returns LB_OK. */
+/* Test hook for the bounded waits of LB_PERSISTENT (an item waits until the items around it
+ * have completed the previous step): launches a grid of `blocks` co-resident blocks; each marks
+ * itself done and waits until blocks 0 .. expected-1 are.  With expected > blocks the wait must
+ * give up after spin_limit milliseconds and the call returns LB_ERR_TIMEOUT; with expected <=
+ * blocks it returns LB_OK.  1 <= blocks, expected <= 64 and 1 <= spin_limit <= 10000, else
+ * LB_ERR_BAD_PARAM. */
 int lb_debug_barrier(int blocks, int expected, int spin_limit);
 
 /* Test hook for the Gaussian noise of the step kernels (Sec. II.B): the Box-Muller normals that

@@ -27,11 +27,11 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 struct GraphKey {
   int64_t nsteps;
-  int64_t sample_mask;  // bit k: step k of the segment samples (segments of <= 63 steps)
+  std::vector<int64_t> samples;  // the steps of the segment that sample
   int cur;
   int mode;
   bool operator<(const GraphKey& o) const {
-    return std::tie(nsteps, sample_mask, cur, mode) < std::tie(o.nsteps, o.sample_mask, o.cur, o.mode);
+    return std::tie(nsteps, samples, cur, mode) < std::tie(o.nsteps, o.samples, o.cur, o.mode);
   }
 };
 
@@ -93,7 +93,11 @@ struct lb_ctx {
   int sf_threads = 256, sf_cap = 4096;  // sample-step transforms (sf_threads, SfPlan)
   size_t sf_smem_rows = 0, sf_smem_cols = 0;
   int64_t* d_t = nullptr;
-  unsigned* d_barrier = nullptr;
+  unsigned* d_barrier = nullptr;  // the persistent launch's ticket counter (64-bit)
+  unsigned* d_done = nullptr;     // persistent launch: steps completed per item
+  int* d_nbr_off = nullptr;       // persistent launch: dependency lists of the items (CSR)
+  int* d_nbr = nullptr;
+  int sched_items_cap = 0, sched_nbr_cap = 0;
   int* d_err = nullptr;
   double* d_scratch = nullptr;  // 18 * max_lattice_sites doubles (populations I/O)
   double* d_mass = nullptr;
@@ -304,6 +308,68 @@ void drop_graphs(lb_ctx* c) {
 
 // Work items: lattices with more rows per item first (longest work first), each lattice's
 // items contiguous so that its partial sums can be reduced in a fixed order.
+// Dependency lists of the persistent launch (see the persistent kernels): for every item, the
+// items of its lattice whose regions meet its rows z0 - 2 .. z1 + 1 and its columns x0 - 4 ..
+// x0 + w + 3 (periodic in x), itself included.  The items of a lattice are ordered row chunk
+// by row chunk, column strip by column strip, from range[lattice].first.
+int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vector<std::pair<int, int>>& range,
+                   int tile_x, int rows) {
+  std::vector<int> off(items.size() + 1, 0), nbr;
+  nbr.reserve(items.size() * 9);
+  std::vector<int> strips;
+  for (size_t i = 0; i < items.size(); ++i) {
+    const WorkItem& it = items[i];
+    const lb_params& p = c->params[it.lattice];
+    const int begin = range[it.lattice].first;
+    const int nstrips = (p.Lx + tile_x - 1) / tile_x;
+    const int w = std::min(tile_x, p.Lx - it.x0);
+    const int ca = std::max(0, it.z0 - 2) / rows, cb = std::min(p.Lz - 1, it.z1 + 1) / rows;
+    strips.clear();
+    const int len = w + 8;
+    if (len >= p.Lx) {
+      for (int sx = 0; sx < nstrips; ++sx) strips.push_back(sx);
+    } else {
+      const int xs = ((it.x0 - 4) % p.Lx + p.Lx) % p.Lx, xe = xs + len;  // columns [xs, xe), wrapping once
+      for (int sx = xs / tile_x; sx <= (std::min(xe, p.Lx) - 1) / tile_x; ++sx) strips.push_back(sx);
+      if (xe > p.Lx)
+        for (int sx = 0; sx <= (xe - p.Lx - 1) / tile_x; ++sx) strips.push_back(sx);
+      std::sort(strips.begin(), strips.end());
+      strips.erase(std::unique(strips.begin(), strips.end()), strips.end());
+    }
+    for (int ch = ca; ch <= cb; ++ch)
+      for (int sx : strips) nbr.push_back(begin + ch * nstrips + sx);
+    off[i + 1] = (int)nbr.size();
+  }
+  const int n = (int)items.size(), m = (int)nbr.size();
+  if (n + 1 > c->sched_items_cap) {
+    if (c->d_done) {
+      dev_free(c, c->d_done);
+      dev_free(c, c->d_nbr_off);
+      c->bytes -= (size_t)c->sched_items_cap * (sizeof(unsigned) + sizeof(int));
+      c->d_done = nullptr;
+      c->d_nbr_off = nullptr;
+    }
+    int rc = dev_alloc(c, &c->d_done, (size_t)(n + 1) * sizeof(unsigned));
+    if (!rc) rc = dev_alloc(c, &c->d_nbr_off, (size_t)(n + 1) * sizeof(int));
+    if (rc) return rc;
+    c->sched_items_cap = n + 1;
+  }
+  if (m > c->sched_nbr_cap) {
+    if (c->d_nbr) {
+      dev_free(c, c->d_nbr);
+      c->bytes -= (size_t)c->sched_nbr_cap * sizeof(int);
+      c->d_nbr = nullptr;
+    }
+    int rc = dev_alloc(c, &c->d_nbr, (size_t)m * sizeof(int));
+    if (rc) return rc;
+    c->sched_nbr_cap = m;
+  }
+  if (cudaMemcpy(c->d_nbr_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (m > 0 && cudaMemcpy(c->d_nbr, nbr.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+    return LB_ERR_CUDA;
+  return LB_OK;
+}
+
 int build_items(lb_ctx* c, int tile_x, int rows) {
   std::vector<int> order(c->n_lat);
   for (int i = 0; i < c->n_lat; ++i) order[i] = i;
@@ -339,6 +405,8 @@ int build_items(lb_ctx* c, int tile_x, int rows) {
   }
   if (cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
     return LB_ERR_CUDA;
+  int rc = build_schedule(c, items, range, tile_x, rows);
+  if (rc) return rc;
   c->items = items;
   for (int i = 0; i < c->n_lat; ++i) {
     c->diag[i].item_begin = range[i].first;
@@ -500,10 +568,13 @@ cudaError_t enqueue_persistent(lb_ctx* c, int cur, int64_t n, const std::vector<
     const int64_t plain = end - k - (sample ? 1 : 0);
     cudaError_t e;
     if (plain > 0) {
-      e = cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), c->stream);
+      e = cudaMemsetAsync(c->d_barrier, 0, sizeof(unsigned long long), c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->d_done, 0, c->items.size() * sizeof(unsigned), c->stream);
       if (e != cudaSuccess) return e;
+      const PersistArgs pa{reinterpret_cast<unsigned long long*>(c->d_barrier), c->d_done, c->d_nbr_off, c->d_nbr,
+                           c->d_err, 2000, 0};
       e = launch_step_persistent<real>(step_args<real>(c, cur, (int)k), c->tile_x, (int)plain, c->noise_mode,
-                                       c->bulk_ok, c->d_barrier, c->d_err, grid, 2000, c->stream);
+                                       c->bulk_ok, pa, grid, c->stream);
       if (e != cudaSuccess) return e;
       c->launches += 1;
       if (plain & 1) cur ^= 1;
@@ -531,8 +602,10 @@ cudaError_t enqueue(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& s
 template <class real>
 int autotune(lb_ctx* c) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int64_t, int, int, int, int>, std::pair<int, int>> cache;
-  const auto key = std::make_tuple(c->n_lat, c->n_sites, c->max_Lx, c->max_Lz, (int)c->dev32, c->noise_mode);
+  static std::map<std::tuple<int, int64_t, int, int, int, int, int>, std::pair<int, int>> cache;
+  const bool persistent = c->flags & LB_PERSISTENT;
+  const auto key =
+      std::make_tuple(c->n_lat, c->n_sites, c->max_Lx, c->max_Lz, (int)c->dev32, c->noise_mode, (int)persistent);
   {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
@@ -553,13 +626,29 @@ int autotune(lb_ctx* c) {
       if (rr == last) continue;
       last = rr;
       if (build_items(c, tx, rr) != LB_OK) continue;
-      // state is untouched: every trial reads f[cur] and writes f[cur ^ 1]
-      for (int k = 0; k < 2; ++k)
-        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->bulk_ok, c->stream);
+      // state is untouched: every trial reads f[cur] and writes f[cur ^ 1]; the persistent
+      // launch is timed as it schedules (tickets, per-item waits) in its trial mode, in which
+      // every step reads f[cur]
+      const int reps = persistent ? 6 : 4;
+      const int grid =
+          persistent ? std::min<int>(persistent_grid<real>(tx, c->noise_mode, c->bulk_ok), (int)c->items.size()) : 0;
+      auto trial = [&](int steps) {
+        if (!persistent) {
+          for (int k = 0; k < steps; ++k)
+            launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->bulk_ok, c->stream);
+          return;
+        }
+        cudaMemsetAsync(c->d_barrier, 0, sizeof(unsigned long long), c->stream);
+        cudaMemsetAsync(c->d_done, 0, c->items.size() * sizeof(unsigned), c->stream);
+        const PersistArgs pa{reinterpret_cast<unsigned long long*>(c->d_barrier), c->d_done, c->d_nbr_off, c->d_nbr,
+                             c->d_err, 2000, 1};
+        launch_step_persistent<real>(step_args<real>(c, c->cur, 0), tx, steps, c->noise_mode, c->bulk_ok, pa, grid,
+                                     c->stream);
+      };
+      if (persistent && grid <= 0) continue;
+      trial(2);
       cudaEventRecord(e0, c->stream);
-      const int reps = 4;
-      for (int k = 0; k < reps; ++k)
-        launch_step<real>(step_args<real>(c, c->cur, 0), tx, false, c->noise_mode, c->bulk_ok, c->stream);
+      trial(reps);
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         cudaGetLastError();
@@ -594,19 +683,18 @@ int step_impl(lb_ctx* c, int64_t n) {
   const bool graph = c->flags & LB_GRAPH;
   int64_t done = 0;
   while (done < n) {
-    // segment: up to 63 steps (graph) or everything left (direct)
-    const int64_t seg = graph ? std::min<int64_t>(n - done, 63) : (n - done);
+    // segment: everything left (direct launches), or what one graph holds: up to 64 per-step
+    // launches, or up to 4096 steps in persistent launches
+    int64_t cap = persistent ? 4096 : 64;
+    if (c->every > 0 && c->every <= cap) cap -= cap % c->every;  // full segments share their sample phase
+    const int64_t seg = graph ? std::min<int64_t>(n - done, cap) : (n - done);
     std::vector<int64_t> so;
-    int64_t mask = 0;
     for (int64_t k = 0; k < seg; ++k)
-      if (is_sample(c, c->t + done + k)) {
-        so.push_back(k);
-        if (k < 63) mask |= (int64_t)1 << k;
-      }
+      if (is_sample(c, c->t + done + k)) so.push_back(k);
     if (!so.empty() && !c->diag_ready) return LB_ERR_STATE;
     cudaError_t e;
     if (graph) {
-      const GraphKey key{seg, mask, c->cur, persistent ? 1 : 0};
+      const GraphKey key{seg, so, c->cur, persistent ? 1 : 0};
       auto it = c->graphs.find(key);
       if (it == c->graphs.end()) {
         cudaGraph_t gr;
@@ -696,7 +784,7 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn
   if (!rc) rc = dev_alloc(c, &c->stats, n * sizeof(DiagStats));
   if (!rc) rc = dev_alloc(c, &c->d_diag, n * sizeof(DiagLattice));
   if (!rc) rc = dev_alloc(c, &c->d_t, sizeof(int64_t));
-  if (!rc) rc = dev_alloc(c, &c->d_barrier, 2 * sizeof(unsigned));
+  if (!rc) rc = dev_alloc(c, &c->d_barrier, 4 * sizeof(unsigned));
   if (!rc) rc = dev_alloc(c, &c->d_err, sizeof(int));
   if (!rc) rc = dev_alloc(c, &c->d_mass, 2 * sizeof(double));
   if (!rc && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) rc = LB_ERR_CUDA;
@@ -1299,7 +1387,7 @@ void lb_destroy(lb_ctx* c) {
                   c->tmp,     c->acc_sum,    c->acc_comp,   c->partials,  c->stats,      c->d_diag,
                   c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass,
                   c->pfield, c->prof_sum, c->prof_comp, c->d_row_lat, c->corr_R, c->corr_C, c->d_corr_real,
-                  c->d_corr_mode, c->d_corr_modes};
+                  c->d_corr_mode, c->d_corr_modes, c->d_done, c->d_nbr_off, c->d_nbr};
   for (void* p : ptrs) dev_free(c, p);
   delete c;
 }
@@ -1351,29 +1439,36 @@ int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* st
 }
 
 int lb_debug_barrier(int blocks, int expected, int spin_limit) {
-  if (blocks < 1 || blocks > 64 || expected < 1 || spin_limit < 1 || spin_limit > 10000) return LB_ERR_BAD_PARAM;
+  if (blocks < 1 || blocks > 64 || expected < 1 || expected > 64 || spin_limit < 1 || spin_limit > 10000)
+    return LB_ERR_BAD_PARAM;
   int dev = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) return LB_ERR_STATE;
-  unsigned* bar = nullptr;
+  unsigned* done = nullptr;
+  int* list = nullptr;
   int* err = nullptr;
-  if (cudaMalloc(&bar, 2 * sizeof(unsigned)) != cudaSuccess) return LB_ERR_OOM;
-  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
-    cudaFree(bar);
-    return LB_ERR_OOM;
-  }
-  cudaMemset(bar, 0, 2 * sizeof(unsigned));
-  cudaMemset(err, 0, sizeof(int));
+  int hl[64];
+  for (int i = 0; i < expected; ++i) hl[i] = i;
   int rc = LB_OK;
-  cudaError_t e = launch_barrier_probe(blocks, expected, spin_limit, bar, err, nullptr);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) rc = LB_ERR_CUDA;
+  if (cudaMalloc(&done, 64 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&list, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+    rc = LB_ERR_OOM;
+  if (!rc && (cudaMemset(done, 0, 64 * sizeof(unsigned)) != cudaSuccess || cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+              cudaMemcpy(list, hl, expected * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = LB_ERR_CUDA;
+  if (!rc) {
+    cudaError_t e = launch_barrier_probe(blocks, expected, spin_limit, done, list, err, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = LB_ERR_CUDA;
+  }
   int h = 0;
   if (!rc && cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = LB_ERR_CUDA;
   if (!rc && h) rc = LB_ERR_TIMEOUT;
-  cudaFree(bar);
-  cudaFree(err);
+  cudaGetLastError();
+  if (done) cudaFree(done);
+  if (list) cudaFree(list);
+  if (err) cudaFree(err);
   return rc;
 }
 

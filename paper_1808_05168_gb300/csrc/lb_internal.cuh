@@ -382,9 +382,21 @@ size_t step_smem_bytes(int tile_x);
 template <class real>
 cudaError_t prepare_step(int max_tile_x);
 
+// The persistent launch's scheduling state (see the persistent kernels): the ticket counter and
+// done[] zeroed before each launch, and the dependency lists of the items (CSR).
+struct PersistArgs {
+  unsigned long long* counter;
+  unsigned* done;
+  const int* nbr_off;
+  const int* nbr;
+  int* err;
+  int limit_ms;
+  int trial;  // autotuner's trial mode: every step reads src and writes dst (the state is untouched)
+};
+
 template <class real>
 cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, int noise, bool bulk,
-                                   unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s);
+                                   const PersistArgs& p, int grid, cudaStream_t s);
 
 template <class real>
 int persistent_grid(int tile_x, int noise, bool bulk);
@@ -520,7 +532,9 @@ cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* 
 template <class real>
 cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double* out, cudaStream_t s);
 
-cudaError_t launch_barrier_probe(int blocks, int expected, int spin_limit, unsigned* barrier, int* err,
+// Test hook of the bounded waits of the persistent launch: `blocks` co-resident blocks each set
+// done[b] and wait until done[list[0 .. expected)] are set.
+cudaError_t launch_barrier_probe(int blocks, int expected, int spin_limit, unsigned* done, const int* list, int* err,
                                  cudaStream_t s);
 
 }  // namespace lbk

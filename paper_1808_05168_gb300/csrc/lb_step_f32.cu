@@ -12,8 +12,8 @@ namespace lbk {
   template cudaError_t prepare_step<real>(int);                                                                    \
   template cudaError_t launch_step<real>(const StepArgs<real>&, int, bool, int, bool, cudaStream_t);               \
   template int persistent_grid<real>(int, int, bool);                                                              \
-  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, int, bool, unsigned*,        \
-                                                    int*, int, int, cudaStream_t);                  \
+  template cudaError_t launch_step_persistent<real>(const StepArgs<real>&, int, int, int, bool, const PersistArgs&, \
+                                                    int, cudaStream_t);                                         \
   template cudaError_t launch_debug_normals<real>(const uint32_t*, int64_t, double*, cudaStream_t);
 LB_STEP_INST(float)
 

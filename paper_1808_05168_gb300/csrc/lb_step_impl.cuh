@@ -892,77 +892,118 @@ __global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX) step_k
   process_item_bulk<real, TX, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem, ph);
 }
 
-// ---- bounded grid barrier for the persistent launch --------------------------------
-// bar[0]: arrivals, bar[1]: generation.  Returns false if the wait gave up after limit_ms
-// (err is then set) or another block reported an error.
-static __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, int limit_ms) {
+// ---- the persistent launch: items handed out in order, per-item dependencies -------------
+// Tickets t = 0, 1, ... come from one counter (PersistArgs::counter, zero at launch): ticket t is
+// item t mod n_items of step t / n_items of the launch, so the items of a step go to whichever
+// block is free, longest first, and blocks roll on into the next step without a grid-wide
+// barrier.  done[i] counts the steps of the launch that item i has completed.  Item i may run
+// step k once every item whose region lies within the rows and columns it reads (its own and
+// the two-row / four-column halo of its streaming, density and aligned staging windows:
+// nbr[nbr_off[i] .. nbr_off[i + 1]), itself included) has completed step k - 1: then everything
+// it reads is written, and no one still reads the region it overwrites.  The relation is
+// symmetric and the tickets an item waits on were all handed out before its own, so with every
+// block resident (cooperative launch) each wait ends; it is bounded all the same.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until done[list[q]] >= need for all q (pausing 32 ns .. 1 us between polls);
+// false, for the whole block, if the wait gave up after limit_ms (err is then set) or another
+// block reported an error.  The data behind the flags are then read through bulk copies (the
+// async proxy), hence the proxy fence.
+static __device__ bool wait_items(const unsigned* done, const int* list, int cnt, unsigned need, int* err, int limit_ms) {
   __shared__ int ok_s;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
     int ok = 1;
-    if (arrived == nblocks) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const uint64_t t0 = global_ns(), lim = (uint64_t)limit_ms * 1000000ull;
-      while (*vgen == gen) {
+    const uint64_t t0 = global_ns(), lim = (uint64_t)limit_ms * 1000000ull;
+    for (int q = 0; q < cnt && ok; ++q) {
+      unsigned pause = 32;
+      while (ld_acquire(done + list[q]) < need) {
+        if (*(volatile int*)err) {
+          ok = 0;
+          break;
+        }
         if (global_ns() - t0 > lim) {
           atomicExch(err, 1);
           ok = 0;
           break;
         }
-        __nanosleep(128);
+        __nanosleep(pause);
+        if (pause < 1024) pause <<= 1;
       }
-      __threadfence();
     }
-    ok_s = ok && (*(volatile int*)err == 0);
+    ok_s = ok;
   }
   __syncthreads();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
   return ok_s != 0;
 }
 
-// nsteps plain steps in one cooperative launch, a bounded grid barrier between them.
+// Every thread of the block has issued its stores of the item; thread 0 makes them visible and
+// then sets done[i] = value.
+__device__ __forceinline__ void publish_item(unsigned* done, int i, unsigned value) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(done + i, value);
+  }
+}
+
+// The next ticket of the block (thread 0 draws it; block-uniform result).  The item's own first
+// barrier orders every read of the shared copy before thread 0 replaces it.
+__device__ __forceinline__ unsigned long long next_ticket(unsigned long long* counter) {
+  __shared__ unsigned long long t_s;
+  if (threadIdx.x == 0) t_s = atomicAdd(counter, 1ull);
+  __syncthreads();
+  return t_s;
+}
+
+// nsteps plain steps in one cooperative launch.
 template <class real, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value)
-    persistent_kernel(StepArgs<real> a, int nsteps, unsigned* bar, int* err, int limit_ms) {
+    persistent_kernel(StepArgs<real> a, int nsteps, PersistArgs p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   prepare_bm<real, NOISE>(smem + Smem<real>::bm(blockDim.x));
-  for (int k = 0; k < nsteps; ++k) {
-    const real* src = (k & 1) ? a.dst : a.src;
-    real* dst = (k & 1) ? const_cast<real*>(a.src) : a.dst;
-    const uint32_t step = (uint32_t)(t0 + k);
-    for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) process_item<real, false, NOISE>(a, src, dst, i, step, smem);
-    if (k + 1 < nsteps) {
-      if (!grid_barrier(bar, err, gridDim.x, limit_ms)) return;
-    }
+  const unsigned long long n = (unsigned)a.n_items, total = (unsigned long long)nsteps * n;
+  for (unsigned long long t; (t = next_ticket(p.counter)) < total;) {
+    const int k = (int)(t / n), i = (int)(t - (unsigned long long)k * n);
+    if (k > 0 && !wait_items(p.done, p.nbr + p.nbr_off[i], p.nbr_off[i + 1] - p.nbr_off[i], (unsigned)k, p.err,
+                             p.limit_ms))
+      return;
+    const bool odd = (k & 1) && !p.trial;
+    const real* src = odd ? a.dst : a.src;
+    real* dst = odd ? const_cast<real*>(a.src) : a.dst;
+    process_item<real, false, NOISE>(a, src, dst, i, (uint32_t)(t0 + k), smem);
+    publish_item(p.done, i, (unsigned)(k + 1));
   }
 }
 
 template <class real, int TX, int NOISE>
 __global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
-    persistent_kernel_bulk(StepArgs<real> a, int nsteps, unsigned* bar, int* err, int limit_ms) {
+    persistent_kernel_bulk(StepArgs<real> a, int nsteps, PersistArgs p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   bulk_init<real, TX>(smem);
   prepare_bm<real, NOISE>(smem + SmemBulk<real, TX>::bm);
   uint32_t ph = 0;
-  for (int k = 0; k < nsteps; ++k) {
-    const real* src = (k & 1) ? a.dst : a.src;
-    real* dst = (k & 1) ? const_cast<real*>(a.src) : a.dst;
-    const uint32_t step = (uint32_t)(t0 + k);
-    for (int i = blockIdx.x; i < a.n_items; i += gridDim.x) {
-      if (!process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, step, smem, ph))
-        return;  // the others give up at their next barrier (bounded)
-    }
-    if (k + 1 < nsteps) {
-      if (!grid_barrier(bar, err, gridDim.x, limit_ms)) return;
-    }
+  const unsigned long long n = (unsigned)a.n_items, total = (unsigned long long)nsteps * n;
+  for (unsigned long long t; (t = next_ticket(p.counter)) < total;) {
+    const int k = (int)(t / n), i = (int)(t - (unsigned long long)k * n);
+    if (k > 0 && !wait_items(p.done, p.nbr + p.nbr_off[i], p.nbr_off[i + 1] - p.nbr_off[i], (unsigned)k, p.err,
+                             p.limit_ms))
+      return;
+    const bool odd = (k & 1) && !p.trial;
+    const real* src = odd ? a.dst : a.src;
+    real* dst = odd ? const_cast<real*>(a.src) : a.dst;
+    if (!process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, (uint32_t)(t0 + k), smem, ph))
+      return;  // the blocks that wait on this item give up (bounded)
+    publish_item(p.done, i, (unsigned)(k + 1));
   }
 }
 
@@ -1096,10 +1137,11 @@ int persistent_grid(int tile_x, int noise, bool bulk) {
 
 template <class real>
 cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nsteps, int noise, bool bulk,
-                                   unsigned* barrier, int* err, int grid, int limit_ms, cudaStream_t s) {
+                                   const PersistArgs& p, int grid, cudaStream_t s) {
   StepArgs<real> aa = a;
   int ns = nsteps;
-  void* args[] = {&aa, &ns, &barrier, &err, &limit_ms};
+  PersistArgs pp = p;
+  void* args[] = {&aa, &ns, &pp};
   size_t smem = 0;
   const void* fn = persistent_fn<real>(tile_x, noise, bulk, &smem);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tile_x), args, smem, s);
@@ -1144,8 +1186,10 @@ cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double*
 // Kernels and helpers that do not depend on the precision (compiled once).
 __global__ void advance_kernel(int64_t* d_t, int64_t k) { *d_t += k; }
 
-__global__ void barrier_probe_kernel(unsigned* bar, int* err, unsigned expected, int limit_ms) {
-  grid_barrier(bar, err, expected, limit_ms);
+// Block b marks itself done and waits (bounded) until blocks list[0 .. expected) are.
+__global__ void barrier_probe_kernel(unsigned* done, const int* list, int* err, int expected, int limit_ms) {
+  publish_item(done, blockIdx.x, 1u);
+  wait_items(done, list, expected, 1u, err, limit_ms);
 }
 
 cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s) {
@@ -1153,10 +1197,9 @@ cudaError_t launch_advance(int64_t* d_t, int64_t k, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_barrier_probe(int blocks, int expected, int limit_ms, unsigned* barrier, int* err,
+cudaError_t launch_barrier_probe(int blocks, int expected, int limit_ms, unsigned* done, const int* list, int* err,
                                  cudaStream_t s) {
-  unsigned ex = (unsigned)expected;
-  void* args[] = {&barrier, &err, &ex, &limit_ms};
+  void* args[] = {&done, &list, &err, &expected, &limit_ms};
   return cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(blocks), dim3(32), args, 0, s);
 }
 
