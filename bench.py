@@ -109,14 +109,26 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def kernel_code_hash():
+    """sha256 of the step kernels' source with comments and blank lines removed (a comment edit
+    does not change the kernel)."""
+    lines = []
+    with open(os.path.join(ROOT, "paper_1808_05168_gb300", "csrc", "lb_step_impl.cuh")) as f:
+        for ln in f.read().splitlines():
+            i = ln.find("//")
+            ln = (ln if i < 0 else ln[:i]).rstrip()
+            if ln:
+                lines.append(ln)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def kernel_traffic(kind):
     """DRAM bytes per LB step of the dominant kernel at full size from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
     try:
-        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "persistent_kernel_bulk_traffic_c3.json")) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1808_05168_gb300", "csrc", "lb_step_impl.cuh"), "rb").read()
-        if d.get("lb_step_cu_sha256") != hashlib.sha256(src).hexdigest():
+        if d.get("kernel_code_sha256") != kernel_code_hash():
             return None
         e = d.get(kind)
         return None if e is None else float(e["bytes_per_step_full_size"])

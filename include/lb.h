@@ -55,8 +55,10 @@ extern "C" {
 #define LB_NOISE_LOC 0x08  /* noise variances with the local densities ("loc", Sec. III.B)
                               instead of the reference values ("hom")                      */
 #define LB_GRAPH 0x10      /* run lb_step through captured CUDA graphs                     */
-#define LB_PERSISTENT 0x20 /* one cooperative launch per run of steps, all lattices of the
-                              batch, with a bounded grid barrier between steps            */
+#define LB_PERSISTENT 0x20 /* one cooperative launch per run of plain steps, all lattices of
+                              the batch: work items handed out in order, each waiting
+                              (bounded) for its neighbours' previous step; a sample step
+                              follows as an ordinary launch                              */
 #define LB_AUTOTUNE 0x40   /* time the candidate tile shapes on the first lb_step          */
 #define LB_NO_BULK 0x80    /* stage populations with per-thread copies even where rows are
                               16-byte aligned (bulk copies are used by default there)     */

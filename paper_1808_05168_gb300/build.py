@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblb_gb300.so")
-SOURCES = ["lb_step_f32_b128.cu", "lb_step_f64_b128.cu", "lb_step_f32_b64.cu", "lb_step_f64_b64.cu",
+SOURCES = ["lb_step_f32_b128.cu", "lb_step_f64_b128.cu", "lb_step_f32_b256.cu", "lb_step_f64_b256.cu", "lb_step_f32_b64.cu", "lb_step_f64_b64.cu",
            "lb_step_f32_gen.cu", "lb_step_f64_gen.cu", "lb_step_f32.cu", "lb_step_f64.cu", "lb_diag.cu", "lb_api.cu",
            "lb_noalloc.cu", "lb_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

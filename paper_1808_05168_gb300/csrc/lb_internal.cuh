@@ -370,7 +370,7 @@ struct StepArgs {
   int* err;            // set to 1 by a device-side wait that gave up
 };
 
-// bulk: stage rows with bulk copies (tile_x 128 or 256, every lattice's Lx a multiple of
+// bulk: stage rows with bulk copies (tile_x 32, 64, 128 or 256, every lattice's Lx a multiple of
 // 16 bytes); otherwise per-thread copies.
 template <class real>
 cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int noise, bool bulk, cudaStream_t s);

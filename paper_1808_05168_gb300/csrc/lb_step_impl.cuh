@@ -1,6 +1,6 @@
 // lb_step_impl.cuh -- the fused per-step kernel of the fluctuating two-species D2Q9 MRT method
-// (Eq. LB with Eq. MRT), one launch per step for every lattice of a batch, or one
-// cooperative launch with a bounded grid barrier between steps.
+// (Eq. LB with Eq. MRT), one launch per step for every lattice of a batch, or one cooperative
+// launch for a run of steps whose work items wait only for their neighbours' previous step.
 //
 // Work decomposition: a block of TX threads owns TX consecutive columns x of one lattice and
 // marches up rows z0..z1-1 of that lattice.  The 18 populations arriving at each site (Eq. LB;
@@ -8,7 +8,7 @@
 // ahead of the row being collided, so that every stored value is read once per step from HBM
 // and no population is held in registers across rows.  Two staging paths compute the same
 // numbers bit for bit:
-//  - bulk (rows 16-byte aligned, TX = 32, 64 or 128): for each of the 18 (species, link)
+//  - bulk (rows 16-byte aligned, TX = 32, 64, 128 or 256): for each of the 18 (species, link)
 //    planes one lane issues a bulk asynchronous copy of the row window [x0 - PAD, x0 + TX + PAD)
 //    (PAD = 16 bytes; wrapped periodically at the lattice's x edges) into a ring of NSI row
 //    slots, completion tracked by one mbarrier per slot; a one-warp block (TX = 32) marches
@@ -640,7 +640,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
 }
 
 // ======================================================================================
-// Bulk path (rows 16-byte aligned, TX = 32, 64 or 128).
+// Bulk path (rows 16-byte aligned, TX = 32, 64, 128 or 256).
 // ======================================================================================
 template <class real, int TX>
 __device__ __forceinline__ void bulk_init(unsigned char* smem) {
@@ -883,7 +883,7 @@ struct PersistentBlocks {
 
 template <class real, int TX, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX) step_kernel_bulk(StepArgs<real> a) {
-  static_assert(TX == 32 || TX == 64 || TX == 128, "bulk tiles are 32, 64 or 128 columns");
+  static_assert(TX == 32 || TX == 64 || TX == 128 || TX == 256, "bulk tiles are 32, 64, 128 or 256 columns");
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
   bulk_init<real, TX>(smem);
@@ -1103,6 +1103,7 @@ cudaError_t prepare_step(int max_tile_x) {
   if (e == cudaSuccess) e = family_prepare<real, 32>(32);
   if (e == cudaSuccess) e = family_prepare<real, 64>(64);
   if (e == cudaSuccess) e = family_prepare<real, 128>(128);
+  if (e == cudaSuccess) e = family_prepare<real, 256>(256);
   return e;
 }
 
@@ -1112,6 +1113,7 @@ cudaError_t launch_step(const StepArgs<real>& a, int tile_x, bool sample, int no
   if (bulk && tile_x == 32) family_launch<real, 32>(a, tile_x, sample, noise, s);
   else if (bulk && tile_x == 64) family_launch<real, 64>(a, tile_x, sample, noise, s);
   else if (bulk && tile_x == 128) family_launch<real, 128>(a, tile_x, sample, noise, s);
+  else if (bulk && tile_x == 256) family_launch<real, 256>(a, tile_x, sample, noise, s);
   else family_launch<real, 0>(a, tile_x, sample, noise, s);
   return cudaGetLastError();
 }
@@ -1121,6 +1123,7 @@ static const void* persistent_fn(int tile_x, int noise, bool bulk, size_t* smem)
   if (bulk && tile_x == 32) return family_persistent<real, 32>(tile_x, noise, smem);
   if (bulk && tile_x == 64) return family_persistent<real, 64>(tile_x, noise, smem);
   if (bulk && tile_x == 128) return family_persistent<real, 128>(tile_x, noise, smem);
+  if (bulk && tile_x == 256) return family_persistent<real, 256>(tile_x, noise, smem);
   return family_persistent<real, 0>(tile_x, noise, smem);
 }
 
