@@ -234,6 +234,8 @@ def run_ours(args):
 
     if not args.no_extras and rank == 0:
         res["fp64_plain"] = measure_plain(torch, workloads.c4(), "fp64", steps=10)
+        res["fp64_plain"]["GLUPS_one_launch_per_step"] = measure_plain(torch, workloads.c4(), "fp64", steps=10,
+                                                                       persistent=False)["GLUPS"]
         res["dev32_large"] = measure_plain(torch, workloads.c4(), "dev32", steps=40)
         res["e2e"] = measure_e2e(torch, lattices, K, P)
         res["adjoint_c5"] = measure_adjoint(torch)
@@ -268,13 +270,14 @@ def measure_adjoint(torch):
     return out
 
 
-def measure_plain(torch, lattices, precision, steps):
-    """Plain per-step launches of one large lattice (no sampling): GLUPS and HBM fraction."""
+def measure_plain(torch, lattices, precision, steps, persistent=True):
+    """Plain steps of one large lattice (no sampling), one persistent launch or one launch per
+    step: GLUPS and HBM fraction."""
     from paper_1808_05168_gb300 import Simulation, workloads
 
     sites = workloads.sites(lattices)
     stream = torch.cuda.Stream()
-    with Simulation(lattices, precision=precision, autotune=True) as sim:
+    with Simulation(lattices, precision=precision, autotune=True, persistent=persistent) as sim:
         sim.set_stream(stream)
         sim.step(3)
         sim.synchronize()
@@ -289,6 +292,7 @@ def measure_plain(torch, lattices, precision, steps):
         gbs = BYTES_PER_SITE[precision] * sites / (ms / 1e3) / 1e9
         Lx, Lz = sim.shape(0)
         return {"workload": f"{Lx}x{Lz} single lattice, G=0.5, dc=0.5, kT=1e-5", "precision": precision,
+                "launch": "persistent" if persistent else "one per step",
                 "GLUPS": sites / (ms / 1e3) / 1e9, "ms_per_lb_step": ms, "hbm_GBps": gbs, "hbm_frac": gbs / peak,
                 "tile": list(sim.tile())}
 

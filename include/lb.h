@@ -251,6 +251,19 @@ void lb_destroy(lb_ctx* ctx);
  * LB_ERR_BAD_PARAM. */
 int lb_debug_barrier(int blocks, int expected, int spin_limit);
 
+/* Host-only test hook (needs no GPU) for the work decomposition of lb_create_batch and the
+ * dependency lists of LB_PERSISTENT: for n_lat lattices of Lx[i] x Lz[i] sites (>= 1 each, at
+ * most 2^26 sites in all) cut into items of tile_x columns x `rows` rows, items_out receives 4
+ * ints per item (lattice, x0, z0, z1: columns x0 .. x0 + tile_x - 1 clipped to Lx, rows z0 ..
+ * z1 - 1) in launch order, off_out n_items + 1 offsets and nbr_out the item indices each item
+ * waits for in the persistent launch (nbr_out[off_out[i] .. off_out[i + 1])).  *n_items and
+ * *n_nbr are always set; buffers smaller than those (items_cap in items, nbr_cap in indices)
+ * return LB_ERR_SIZE without writing them, so a first call with zero capacities sizes them.
+ * All buffers are caller-owned host memory; off_out holds n_items + 1 ints. */
+int lb_debug_schedule(int n_lat, const int* Lx, const int* Lz, int tile_x, int rows, int* items_out,
+                      int64_t items_cap, int* off_out, int* nbr_out, int64_t nbr_cap, int64_t* n_items,
+                      int64_t* n_nbr);
+
 /* Test hook for the Gaussian noise of the step kernels (Sec. II.B): the Box-Muller normals that
  * the kernels of precision `precision` (LB_PREC_FP64 or LB_PREC_DEV32) form from Philox word
  * pairs.  host_words: 2 n_pairs words (a_0, b_0, a_1, b_1, ...), u1 from a_i sets the radius

@@ -41,7 +41,7 @@ EXPORTS = ("lb_create", "lb_create_batch", "lb_create_batch_with_allocator", "lb
            "lb_step", "lb_synchronize", "lb_time", "lb_num_lattices", "lb_lattice_shape", "lb_structure_factor",
            "lb_profile", "lb_set_correlations", "lb_correlation", "lb_mode_correlation", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
-           "lb_debug_box_muller",
+           "lb_debug_box_muller", "lb_debug_schedule",
            "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient")
 LB_NOALLOC_MAX_POINTS = 1 << 18
 LB_CORR_MAX_MODES = 16
@@ -110,6 +110,7 @@ def load():
             "lb_destroy": [vp],
             "lb_debug_barrier": [i, i, i],
             "lb_debug_box_muller": [i, ctypes.POINTER(ctypes.c_uint32), i64, dp],
+            "lb_debug_schedule": [i, ip, ip, i, i, ip, i64, ip, ip, i64, i64p, i64p],
             "lb_power_spectrum": [vp, i, i, vp, vp],
             "lb_power_spectrum_noalloc": [vp, i, i, vp, vp],
             "lb_pressure_shift_gradient": [vp, i64, i64, dp, dp],
@@ -133,6 +134,12 @@ def _dptr(a: np.ndarray):
     if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
         raise TypeError("expected a C-contiguous float64 array")
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    if a.dtype != np.int32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous int32 array")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 
 
 def lb_create(Lx, Lz, lambda_s, lambda_d, lambda_e, lambda_q, lambda_eps, kT, G, grad_c0, seed, flags):
@@ -332,6 +339,27 @@ def lb_pressure_shift_gradient(h, steps, ckpt_every, want_grad=True):
 
 def lb_debug_barrier(blocks, expected, limit_ms):
     return int(load().lb_debug_barrier(int(blocks), int(expected), int(limit_ms)))
+
+
+def lb_debug_schedule(shapes, tile_x, rows):
+    """(items [n, 4] = lattice, x0, z0, z1; off [n + 1]; nbr) of lattices shapes = [(Lx, Lz), ...]
+    cut into tile_x x rows items: the work list and the persistent launch's dependency lists
+    (host only; see include/lb.h)."""
+    lx = np.ascontiguousarray([int(a) for a, _ in shapes], dtype=np.int32)
+    lz = np.ascontiguousarray([int(b) for _, b in shapes], dtype=np.int32)
+    ni, nn = ctypes.c_int64(), ctypes.c_int64()
+    lib = load()
+    rc = lib.lb_debug_schedule(len(shapes), _iptr(lx), _iptr(lz), int(tile_x), int(rows), None, 0, None, None, 0,
+                               ctypes.byref(ni), ctypes.byref(nn))
+    if rc not in (LB_OK, LB_ERR_SIZE):
+        _check(rc, "lb_debug_schedule")
+    items = np.zeros((ni.value, 4), np.int32)
+    off = np.zeros(ni.value + 1, np.int32)
+    nbr = np.zeros(max(nn.value, 1), np.int32)
+    _check(lib.lb_debug_schedule(len(shapes), _iptr(lx), _iptr(lz), int(tile_x), int(rows), _iptr(items), ni.value,
+                                 _iptr(off), _iptr(nbr), nn.value, ctypes.byref(ni), ctypes.byref(nn)),
+           "lb_debug_schedule")
+    return items, off, nbr[: nn.value]
 
 
 def lb_debug_box_muller(precision, words):

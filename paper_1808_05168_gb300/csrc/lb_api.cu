@@ -308,31 +308,53 @@ void drop_graphs(lb_ctx* c) {
 
 // Work items: lattices with more rows per item first (longest work first), each lattice's
 // items contiguous so that its partial sums can be reduced in a fixed order.
-// Dependency lists of the persistent launch (see the persistent kernels): for every item, the
-// items of its lattice whose regions meet its rows z0 - 2 .. z1 + 1 and its columns x0 - 4 ..
-// x0 + w + 3 (periodic in x), itself included.  The items of a lattice are ordered row chunk
-// by row chunk, column strip by column strip, from range[lattice].first.
-int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vector<std::pair<int, int>>& range,
-                   int tile_x, int rows) {
-  std::vector<int> off(items.size() + 1, 0), nbr;
+// Work items of a batch (host only): per lattice, row chunks of `rows` rows, each split into
+// column strips of tile_x columns; lattices with the longest chunks first.  range[i]: the items
+// of lattice i.
+void plan_items(const std::vector<int>& Lx, const std::vector<int>& Lz, int tile_x, int rows,
+                std::vector<WorkItem>& items, std::vector<std::pair<int, int>>& range) {
+  const int n = (int)Lx.size();
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return std::min(rows, Lz[a]) > std::min(rows, Lz[b]); });
+  items.clear();
+  range.assign(n, {0, 0});
+  for (int i : order) {
+    const int begin = (int)items.size();
+    for (int z0 = 0; z0 < Lz[i]; z0 += rows)
+      for (int x0 = 0; x0 < Lx[i]; x0 += tile_x) items.push_back(WorkItem{i, x0, z0, std::min(z0 + rows, Lz[i])});
+    range[i] = {begin, (int)items.size()};
+  }
+}
+
+// Dependency lists of the persistent launch (host only; see the persistent kernels): for every
+// item, the items of its lattice whose regions meet its rows z0 - 2 .. z1 + 1 and its columns
+// x0 - 4 .. x0 + w + 3 (periodic in x), itself included.  The items of a lattice are ordered
+// row chunk by row chunk, column strip by column strip, from range[lattice].first.
+void plan_dependencies(const std::vector<int>& Lx, const std::vector<int>& Lz, const std::vector<WorkItem>& items,
+                       const std::vector<std::pair<int, int>>& range, int tile_x, int rows, std::vector<int>& off,
+                       std::vector<int>& nbr) {
+  off.assign(items.size() + 1, 0);
+  nbr.clear();
   nbr.reserve(items.size() * 9);
   std::vector<int> strips;
   for (size_t i = 0; i < items.size(); ++i) {
     const WorkItem& it = items[i];
-    const lb_params& p = c->params[it.lattice];
+    const int lx = Lx[it.lattice], lz = Lz[it.lattice];
     const int begin = range[it.lattice].first;
-    const int nstrips = (p.Lx + tile_x - 1) / tile_x;
-    const int w = std::min(tile_x, p.Lx - it.x0);
-    const int ca = std::max(0, it.z0 - 2) / rows, cb = std::min(p.Lz - 1, it.z1 + 1) / rows;
+    const int nstrips = (lx + tile_x - 1) / tile_x;
+    const int w = std::min(tile_x, lx - it.x0);
+    const int ca = std::max(0, it.z0 - 2) / rows, cb = std::min(lz - 1, it.z1 + 1) / rows;
     strips.clear();
     const int len = w + 8;
-    if (len >= p.Lx) {
+    if (len >= lx) {
       for (int sx = 0; sx < nstrips; ++sx) strips.push_back(sx);
     } else {
-      const int xs = ((it.x0 - 4) % p.Lx + p.Lx) % p.Lx, xe = xs + len;  // columns [xs, xe), wrapping once
-      for (int sx = xs / tile_x; sx <= (std::min(xe, p.Lx) - 1) / tile_x; ++sx) strips.push_back(sx);
-      if (xe > p.Lx)
-        for (int sx = 0; sx <= (xe - p.Lx - 1) / tile_x; ++sx) strips.push_back(sx);
+      const int xs = ((it.x0 - 4) % lx + lx) % lx, xe = xs + len;  // columns [xs, xe), wrapping once
+      for (int sx = xs / tile_x; sx <= (std::min(xe, lx) - 1) / tile_x; ++sx) strips.push_back(sx);
+      if (xe > lx)
+        for (int sx = 0; sx <= (xe - lx - 1) / tile_x; ++sx) strips.push_back(sx);
       std::sort(strips.begin(), strips.end());
       strips.erase(std::unique(strips.begin(), strips.end()), strips.end());
     }
@@ -340,6 +362,23 @@ int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vec
       for (int sx : strips) nbr.push_back(begin + ch * nstrips + sx);
     off[i + 1] = (int)nbr.size();
   }
+}
+
+void lattice_shapes(const lb_ctx* c, std::vector<int>& Lx, std::vector<int>& Lz) {
+  Lx.resize(c->n_lat);
+  Lz.resize(c->n_lat);
+  for (int i = 0; i < c->n_lat; ++i) {
+    Lx[i] = c->params[i].Lx;
+    Lz[i] = c->params[i].Lz;
+  }
+}
+
+// The dependency lists of the items on the device.
+int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vector<std::pair<int, int>>& range,
+                   int tile_x, int rows) {
+  std::vector<int> Lx, Lz, off, nbr;
+  lattice_shapes(c, Lx, Lz);
+  plan_dependencies(Lx, Lz, items, range, tile_x, rows, off, nbr);
   const int n = (int)items.size(), m = (int)nbr.size();
   if (n + 1 > c->sched_items_cap) {
     if (c->d_done) {
@@ -371,19 +410,12 @@ int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vec
 }
 
 int build_items(lb_ctx* c, int tile_x, int rows) {
-  std::vector<int> order(c->n_lat);
-  for (int i = 0; i < c->n_lat; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return std::min(rows, c->params[a].Lz) > std::min(rows, c->params[b].Lz);
-  });
   std::vector<WorkItem> items;
-  std::vector<std::pair<int, int>> range(c->n_lat);
-  for (int i : order) {
-    const lb_params& p = c->params[i];
-    const int begin = (int)items.size();
-    for (int z0 = 0; z0 < p.Lz; z0 += rows)
-      for (int x0 = 0; x0 < p.Lx; x0 += tile_x) items.push_back(WorkItem{i, x0, z0, std::min(z0 + rows, p.Lz)});
-    range[i] = {begin, (int)items.size()};
+  std::vector<std::pair<int, int>> range;
+  {
+    std::vector<int> Lx, Lz;
+    lattice_shapes(c, Lx, Lz);
+    plan_items(Lx, Lz, tile_x, rows, items, range);
   }
   if ((int)items.size() > c->d_items_cap) {
     if (c->d_items) {
@@ -1470,6 +1502,37 @@ int lb_debug_barrier(int blocks, int expected, int spin_limit) {
   if (list) cudaFree(list);
   if (err) cudaFree(err);
   return rc;
+}
+
+int lb_debug_schedule(int n_lat, const int* Lx, const int* Lz, int tile_x, int rows, int* items_out,
+                      int64_t items_cap, int* off_out, int* nbr_out, int64_t nbr_cap, int64_t* n_items,
+                      int64_t* n_nbr) {
+  if (n_lat < 1 || !Lx || !Lz || tile_x < 1 || rows < 1 || !n_items || !n_nbr) return LB_ERR_BAD_PARAM;
+  int64_t sites = 0;
+  for (int i = 0; i < n_lat; ++i) {
+    if (Lx[i] < 1 || Lz[i] < 1) return LB_ERR_BAD_PARAM;
+    sites += (int64_t)Lx[i] * Lz[i];
+  }
+  if (sites > (int64_t(1) << 26)) return LB_ERR_BAD_PARAM;
+  const std::vector<int> lx(Lx, Lx + n_lat), lz(Lz, Lz + n_lat);
+  std::vector<WorkItem> items;
+  std::vector<std::pair<int, int>> range;
+  std::vector<int> off, nbr;
+  plan_items(lx, lz, tile_x, rows, items, range);
+  plan_dependencies(lx, lz, items, range, tile_x, rows, off, nbr);
+  *n_items = (int64_t)items.size();
+  *n_nbr = (int64_t)nbr.size();
+  if (items_cap < *n_items || nbr_cap < *n_nbr) return LB_ERR_SIZE;
+  if (!items_out || !off_out || (*n_nbr > 0 && !nbr_out)) return LB_ERR_BAD_PARAM;
+  for (size_t i = 0; i < items.size(); ++i) {
+    items_out[4 * i + 0] = items[i].lattice;
+    items_out[4 * i + 1] = items[i].x0;
+    items_out[4 * i + 2] = items[i].z0;
+    items_out[4 * i + 3] = items[i].z1;
+  }
+  std::copy(off.begin(), off.end(), off_out);
+  std::copy(nbr.begin(), nbr.end(), nbr_out);
+  return LB_OK;
 }
 
 int lb_debug_box_muller(int precision, const uint32_t* host_words, int64_t n_pairs, double* host_out) {
