@@ -44,6 +44,7 @@ def parse():
                     help="run a small single-lattice case only (for ncu captures)")
     ap.add_argument("--profile-kT", type=float, default=1e-5, help="kT of the small case")
     ap.add_argument("--profile-persistent", action="store_true", help="ensemble case as one persistent launch")
+    ap.add_argument("--profile-no-tensor-maps", action="store_true", help="ensemble case with 1-d bulk copies only")
     ap.add_argument("--profile-precision", default="dev32", choices=["dev32", "fp64"])
     ap.add_argument("--profile-generic", action="store_true", help="small case with per-thread staging")
     ap.add_argument("--profile-tile", type=int, default=128, help="tile width of the small case")
@@ -395,7 +396,7 @@ def run_profile_small(kT, precision, bulk=True, tile=128, rows=64):
     print("profile-small ok")
 
 
-def run_profile_ensemble(n_seeds, rows=256, persistent=False):
+def run_profile_ensemble(n_seeds, rows=256, persistent=False, tensor_maps=True):
     """The ensemble mix with fewer seeds (8 seeds: 96 lattices, 8.4 M sites, 1.2 GB of state;
     16 seeds: 2.4 GB), the benchmark's precision, 128-column tiles of `rows` rows, 6 steps (for
     ncu captures): six launches of the step kernel, or one persistent launch of six steps."""
@@ -403,7 +404,8 @@ def run_profile_ensemble(n_seeds, rows=256, persistent=False):
 
     from paper_1808_05168_gb300 import Simulation, workloads
 
-    with Simulation(workloads.c3(n_seeds=n_seeds), precision="dev32", persistent=persistent) as sim:
+    with Simulation(workloads.c3(n_seeds=n_seeds), precision="dev32", persistent=persistent,
+                    tensor_maps=tensor_maps) as sim:
         sim.set_tile(128, rows)
         sim.step(6)
         sim.synchronize()
@@ -414,7 +416,8 @@ def run_profile_ensemble(n_seeds, rows=256, persistent=False):
 if __name__ == "__main__":
     a = parse()
     if a.profile_ensemble:
-        run_profile_ensemble(a.profile_ensemble, rows=a.profile_rows or 256, persistent=a.profile_persistent)
+        run_profile_ensemble(a.profile_ensemble, rows=a.profile_rows or 256, persistent=a.profile_persistent,
+                             tensor_maps=not a.profile_no_tensor_maps)
     elif a.profile_small:
         run_profile_small(a.profile_kT, a.profile_precision, bulk=not a.profile_generic, tile=a.profile_tile,
                           rows=a.profile_rows or 64)

@@ -62,6 +62,9 @@ extern "C" {
 #define LB_AUTOTUNE 0x40   /* time the candidate tile shapes on the first lb_step          */
 #define LB_NO_BULK 0x80    /* stage populations with per-thread copies even where rows are
                               16-byte aligned (bulk copies are used by default there)     */
+#define LB_NO_TENSOR_MAPS 0x100 /* bulk staging with 1-d copies only: no 4-d tensor copies of
+                              runs of links (used by default for strips away from the
+                              periodic x edges with tiles of up to 128 columns)           */
 
 /* ---- structure-factor fields and modes (Appendix A) ---------------------------------- */
 #define LB_FIELD_RHO 0 /* delta rho = rho - rho_bar                                         */

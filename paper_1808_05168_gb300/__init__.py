@@ -52,7 +52,7 @@ class Simulation:
 
     def __init__(self, lattices, precision: str = "fp64", astar: bool = True, wall_fixed: bool = False,
                  noise_loc: bool = False, graph: bool = False, persistent: bool = False, autotune: bool = False,
-                 bulk: bool = True, allocator=None):
+                 bulk: bool = True, tensor_maps: bool = True, allocator=None):
         """allocator: None (the library allocates with cudaMalloc), "torch" (torch's caching
         allocator on the current device) or an (alloc, free) pair of capi callbacks."""
         if isinstance(lattices, LatticeParams):
@@ -66,6 +66,7 @@ class Simulation:
         flags |= capi.LB_PERSISTENT if persistent else 0
         flags |= capi.LB_AUTOTUNE if autotune else 0
         flags |= 0 if bulk else capi.LB_NO_BULK
+        flags |= 0 if tensor_maps else capi.LB_NO_TENSOR_MAPS
         self.flags = flags
         self.precision = precision
         if allocator is None:

@@ -30,6 +30,7 @@ LB_GRAPH = 0x10
 LB_PERSISTENT = 0x20
 LB_AUTOTUNE = 0x40
 LB_NO_BULK = 0x80
+LB_NO_TENSOR_MAPS = 0x100
 
 LB_FIELD_RHO, LB_FIELD_C, LB_FIELD_UX, LB_FIELD_UZ, LB_FIELD_P = 0, 1, 2, 3, 4
 LB_SF_QXQZ, LB_SF_QX = 0, 1

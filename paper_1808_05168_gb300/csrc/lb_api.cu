@@ -98,6 +98,8 @@ struct lb_ctx {
   int* d_nbr_off = nullptr;       // persistent launch: dependency lists of the items (CSR)
   int* d_nbr = nullptr;
   int sched_items_cap = 0, sched_nbr_cap = 0;
+  CUtensorMap* d_tmaps = nullptr;  // bulk staging: 4-d tensor maps [buffer][lattice][run of 1, 2 links]
+  bool tma = false;                // d_tmaps holds maps for the current tile
   int* d_err = nullptr;
   double* d_scratch = nullptr;  // 18 * max_lattice_sites doubles (populations I/O)
   double* d_mass = nullptr;
@@ -409,6 +411,66 @@ int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vec
   return LB_OK;
 }
 
+// The 4-d tensor maps of the bulk staging (see the bulk path of the step kernels): for both state
+// buffers and every lattice with strips away from its x edges (Lx > 2 tile_x), the populations
+// as [species][link][z][x] with a box of tile_x + 32 bytes' worth of columns, one row, one or
+// two links and both species.  Any map the driver does not accept switches the tensor copies
+// off for the context (the 1-d copies remain).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+int build_tmaps(lb_ctx* c, int tile_x) {
+  c->tma = false;
+  const int es = c->dev32 ? 4 : 8, pad = 16 / es, bw = tile_x + 2 * pad;
+  if (!c->bulk_ok || (c->flags & LB_NO_TENSOR_MAPS) || !(tile_x == 32 || tile_x == 64 || tile_x == 128) || bw > 256)
+    return LB_OK;
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return LB_OK;
+  const size_t n = 4 * (size_t)c->n_lat;
+  if (!c->d_tmaps) {
+    int rc = dev_alloc(c, &c->d_tmaps, n * sizeof(CUtensorMap));
+    if (rc) return rc;
+  }
+  std::vector<CUtensorMap> maps(n);
+  std::memset(maps.data(), 0, n * sizeof(CUtensorMap));
+  for (int buf = 0; buf < 2; ++buf)
+    for (int i = 0; i < c->n_lat; ++i) {
+      const lb_params& p = c->params[i];
+      if (p.Lx <= 2 * tile_x) continue;  // no strip away from the x edges
+      const cuuint64_t dims[4] = {(cuuint64_t)p.Lx, (cuuint64_t)p.Lz, 9, 2};
+      const cuuint64_t strides[3] = {(cuuint64_t)p.Lx * es, (cuuint64_t)p.Lx * p.Lz * es, 9ull * p.Lx * p.Lz * es};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      for (int run = 1; run <= 2; ++run) {
+        const cuuint32_t box[4] = {(cuuint32_t)bw, 1, (cuuint32_t)run, 2};
+        void* base = (char*)c->f[buf] + (size_t)c->f_off[i] * es;
+        CUresult r = enc(&maps[((size_t)buf * c->n_lat + i) * 2 + (run - 1)],
+                         c->dev32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return LB_OK;
+      }
+    }
+  if (cudaMemcpy(c->d_tmaps, maps.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LB_ERR_CUDA;
+  c->tma = true;
+  return LB_OK;
+}
+
 int build_items(lb_ctx* c, int tile_x, int rows) {
   std::vector<WorkItem> items;
   std::vector<std::pair<int, int>> range;
@@ -452,7 +514,7 @@ int build_items(lb_ctx* c, int tile_x, int rows) {
   c->rows_per_item = rows;
   c->coop_grid = -1;
   drop_graphs(c);
-  return LB_OK;
+  return build_tmaps(c, tile_x);
 }
 
 int alloc_diag(lb_ctx* c) {
@@ -524,6 +586,9 @@ StepArgs<real> step_args(lb_ctx* c, int cur, int t_offset) {
   a.pfield = (real*)c->pfield;
   a.partials = c->partials;
   a.err = c->d_err;
+  a.tmaps = c->tma ? c->d_tmaps : nullptr;
+  a.n_lat = c->n_lat;
+  a.src_buf = cur;
   return a;
 }
 
@@ -767,7 +832,7 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn
   *out = nullptr;
   if (n < 1 || !ps) return LB_ERR_BAD_PARAM;
   const int known = LB_PREC_DEV32 | LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC | LB_GRAPH | LB_PERSISTENT | LB_AUTOTUNE |
-                    LB_NO_BULK;
+                    LB_NO_BULK | LB_NO_TENSOR_MAPS;
   if (flags & ~known) return LB_ERR_BAD_PARAM;
   for (int i = 0; i < n; ++i) {
     int rc = check_params(ps[i]);
@@ -1419,7 +1484,7 @@ void lb_destroy(lb_ctx* c) {
                   c->tmp,     c->acc_sum,    c->acc_comp,   c->partials,  c->stats,      c->d_diag,
                   c->d_row_tasks, c->d_col_tasks, c->d_t, c->d_barrier, c->d_err, c->d_scratch, c->d_mass,
                   c->pfield, c->prof_sum, c->prof_comp, c->d_row_lat, c->corr_R, c->corr_C, c->d_corr_real,
-                  c->d_corr_mode, c->d_corr_modes, c->d_done, c->d_nbr_off, c->d_nbr};
+                  c->d_corr_mode, c->d_corr_modes, c->d_done, c->d_nbr_off, c->d_nbr, c->d_tmaps};
   for (void* p : ptrs) dev_free(c, p);
   delete c;
 }

@@ -6,6 +6,7 @@
 // post-collision population in LB_PREC_FP64 mode (where the background is zero).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -368,6 +369,36 @@ struct StepArgs {
                        // deviation mode (sample steps only)
   double* partials;    // per item: pressure deviation sum, mass deviation A, B
   int* err;            // set to 1 by a device-side wait that gave up
+  // bulk path: 4-d tensor maps [x][z][link][species] of the populations, per state buffer and
+  // lattice, for runs of one and of two links (index (buffer n_lat + lattice) 2 + run length - 1),
+  // or null; src_buf: the state buffer src points to
+  const CUtensorMap* tmaps;
+  int n_lat;
+  int src_buf;
+};
+
+// The input row slot of the bulk path: the 18 (species, link) planes grouped in the six runs of
+// consecutive links with equal c_z, (0 1) (2) (3) (4) (5 6) (7 8).  Run j holds
+// [species][link of the run][BW columns] at a 128-byte aligned base: the layout one 4-d bulk
+// tensor copy writes (a box of BW columns, one row, the run's links, both species).
+__host__ __device__ constexpr int run_of(int l) { return l < 2 ? 0 : (l < 5 ? l - 1 : (l < 7 ? 4 : 5)); }
+__host__ __device__ constexpr int run_l0(int j) { return j == 0 ? 0 : (j <= 3 ? j + 1 : (j == 4 ? 5 : 7)); }
+__host__ __device__ constexpr int run_n(int j) { return (j == 0 || j >= 4) ? 2 : 1; }
+template <int BW, int ES>
+struct SlotLayout {
+  static constexpr int ALIGN = 128 / ES;  // elements per 128 bytes
+  __host__ __device__ static constexpr int run_size(int j) { return ((2 * run_n(j) * BW + ALIGN - 1) / ALIGN) * ALIGN; }
+  __host__ __device__ static constexpr int base(int j) { return j == 0 ? 0 : base(j - 1) + run_size(j - 1); }
+  // element offset of plane (species s, link l) in the slot
+  __host__ __device__ static constexpr int plane(int s, int l) {
+    return base(run_of(l)) + (s * run_n(run_of(l)) + l - run_l0(run_of(l))) * BW;
+  }
+  static constexpr int slot = base(6);  // elements per slot (a multiple of 128 bytes)
+  // base(j) for a run index known only at run time
+  __host__ __device__ static int base_of(int j) {
+    constexpr int b1 = base(1), b2 = base(2), b3 = base(3), b4 = base(4), b5 = base(5);
+    return j == 0 ? 0 : (j == 1 ? b1 : (j == 2 ? b2 : (j == 3 ? b3 : (j == 4 ? b4 : b5))));
+  }
 };
 
 // bulk: stage rows with bulk copies (tile_x 32, 64, 128 or 256, every lattice's Lx a multiple of

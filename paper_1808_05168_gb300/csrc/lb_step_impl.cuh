@@ -86,6 +86,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, unsign
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// One box of a 4-d tensor map (coordinates x, z, link, species) into shared memory (128-byte
+// aligned), completion counted on the mbarrier.
+__device__ __forceinline__ void tensor_g2s(void* dst_smem, const CUtensorMap* map, int x, int z, int l, int s,
+                                           uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst_smem)),
+      "l"(map), "r"(x), "r"(z), "r"(l), "r"(s), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src_smem, unsigned bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src_smem)),
                "r"(bytes)
@@ -203,18 +213,22 @@ __device__ __forceinline__ void read_generic(const real* st, int W, int c, bool 
   deviations(v, below, above, k9, k36);
 }
 
-// Bulk path: plane k of a slot holds the source row window, so link l of the site at window
-// column j sits at column j - c_lx (at j on reflected links, whose plane holds the opposite
-// link's own row).
+// Bulk path: plane (s, l) of a slot (SlotLayout) holds the source row window of link l, so link
+// l of the site at window column j sits at column j - c_lx (at j on reflected links, whose plane
+// holds the opposite link's own row).
 template <class real, int SW>
 __device__ __forceinline__ void read_bulk(const real* st, int j, bool below, bool above, real k9, real k36,
                                           Pr<real> v[9]) {
+  using LAY = SlotLayout<SW, (int)sizeof(real)>;
+  constexpr int oa[9] = {LAY::plane(0, 0), LAY::plane(0, 1), LAY::plane(0, 2), LAY::plane(0, 3), LAY::plane(0, 4),
+                         LAY::plane(0, 5), LAY::plane(0, 6), LAY::plane(0, 7), LAY::plane(0, 8)};
+  constexpr int ob[9] = {LAY::plane(1, 0), LAY::plane(1, 1), LAY::plane(1, 2), LAY::plane(1, 3), LAY::plane(1, 4),
+                         LAY::plane(1, 5), LAY::plane(1, 6), LAY::plane(1, 7), LAY::plane(1, 8)};
   const real* a = st + j;
-  const real* b = st + 9 * SW + j;
   const int j5 = below ? -1 : 0, j6 = below ? 1 : 0, j7 = above ? 1 : 0, j8 = above ? -1 : 0;
-  const int o[9] = {0, SW - 1, 2 * SW, 3 * SW + 1, 4 * SW, 5 * SW + j5, 6 * SW + j6, 7 * SW + j7, 8 * SW + j8};
+  const int dx[9] = {0, -1, 0, 1, 0, j5, j6, j7, j8};
 #pragma unroll
-  for (int l = 0; l < 9; ++l) v[l] = pr(a[o[l]], b[o[l]]);
+  for (int l = 0; l < 9; ++l) v[l] = pr(a[oa[l] + dx[l]], a[ob[l] + dx[l]]);
   deviations(v, below, above, k9, k36);
 }
 
@@ -498,21 +512,28 @@ struct Smem {
   __host__ __device__ static size_t bytes(int tx) { return bm(tx) + BmBytes<real>::value; }
 };
 
-// Bulk: as generic, then input slots (NSI x 18 x SW), NSI mbarriers and an abort flag.  Both end
-// with the double-precision Box-Muller tables (FP64 kernels only).
+// Bulk: as generic, then input slots (NSI slots of SlotLayout, 128-byte aligned: the dynamic
+// shared memory is declared 128-byte aligned), NSI mbarriers and an abort flag.  Both end with
+// the double-precision Box-Muller tables (FP64 kernels only).
 template <class real, int TX>
 struct SmemBulk {
   static constexpr int PAD = 16 / (int)sizeof(real);
   static constexpr int SW = TX + 2 * PAD;
+  using LAY = SlotLayout<SW, (int)sizeof(real)>;
   static constexpr size_t red = 0;
   static constexpr size_t lat = 8 * 3 * sizeof(double);
   static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
-  static constexpr size_t in = ring + ((8 * (TX + 2) * sizeof(real) + 15) / 16) * 16;
-  static constexpr size_t bars = in + (size_t)NSI * 18 * SW * sizeof(real);
+  static constexpr size_t in = ((ring + 8 * (TX + 2) * sizeof(real) + 127) / 128) * 128;
+  static constexpr size_t bars = in + (size_t)NSI * LAY::slot * sizeof(real);
   static constexpr size_t abort_flag = bars + NSI * sizeof(uint64_t);
-  static constexpr size_t bm = ((abort_flag + 16 + 15) / 16) * 16;  // 16-byte entries
+  static constexpr size_t tmap = abort_flag + 8;  // the item's tensor maps (pointer), or null
+  // per-plane and per-run copy descriptors (int4 each), filled once per launch by bulk_init
+  static constexpr size_t ptab = ((tmap + 8 + 15) / 16) * 16;
+  static constexpr size_t rtab = ptab + 18 * 16;
+  static constexpr size_t bm = rtab + 6 * 16;  // 16-byte entries
   static constexpr size_t bytes = bm + BmBytes<real>::value;
-  static_assert(in % 16 == 0 && bars % 8 == 0 && bm % 16 == 0, "shared-memory regions must stay aligned");
+  static_assert(in % 128 == 0 && bars % 8 == 0 && tmap % 8 == 0 && ptab % 16 == 0 && bm % 16 == 0,
+                "shared-memory regions must stay aligned");
 };
 
 // ======================================================================================
@@ -645,11 +666,24 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
 template <class real, int TX>
 __device__ __forceinline__ void bulk_init(unsigned char* smem) {
   using SM = SmemBulk<real, TX>;
+  using LAY = typename SM::LAY;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
   if (threadIdx.x == 0) {
     for (int i = 0; i < NSI; ++i) mbar_init(bars + i, 1);
     *reinterpret_cast<volatile int*>(smem + SM::abort_flag) = 0;
     mbar_fence_init();
+  }
+  // plane k = 9 s + l: (slot offset, c_z, source plane, source plane on a reflected link);
+  // run j: (slot offset, first link, first link when reflected, run length + 4 (c_z + 1))
+  const int t = threadIdx.x;
+  if (t < 18) {
+    const int s = t / 9, l = t - 9 * s, j = run_of(l);
+    reinterpret_cast<int4*>(smem + SM::ptab)[t] =
+        make_int4(LAY::base_of(j) + (s * run_n(j) + l - run_l0(j)) * SM::SW, LB_CZ(l), t, 9 * s + LB_OPP(l));
+  } else if (t < 24) {
+    const int j = t - 18, l0 = run_l0(j);
+    reinterpret_cast<int4*>(smem + SM::rtab)[j] =
+        make_int4(LAY::base_of(j), l0, LB_OPP(l0), run_n(j) + 4 * (LB_CZ(l0) + 1));
   }
   __syncthreads();
 }
@@ -659,8 +693,9 @@ __device__ __forceinline__ void bulk_init(unsigned char* smem) {
 template <class real, int TX, bool SAMPLE, int NOISE>
 __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const real* __restrict__ src,
                                                   real* __restrict__ dst, int item_index, uint32_t step,
-                                                  unsigned char* smem, uint32_t& ph) {
+                                                  unsigned char* smem, uint32_t& ph, int src_buf) {
   using SM = SmemBulk<real, TX>;
+  using LAY = typename SM::LAY;
   constexpr int PAD = SM::PAD, SW = SM::SW, W = TX + 2;
   double* red = reinterpret_cast<double*>(smem + SM::red);
   const BmTables<real>* bm = reinterpret_cast<const BmTables<real>*>(smem + SM::bm);
@@ -670,12 +705,22 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::abort_flag);
 
+  const CUtensorMap* const* tmap_s = reinterpret_cast<const CUtensorMap* const*>(smem + SM::tmap);
+  const int4* ptab = reinterpret_cast<const int4*>(smem + SM::ptab);
+  const int4* rtab = reinterpret_cast<const int4*>(smem + SM::rtab);
+
   const WorkItem it = a.items[item_index];
   __syncthreads();  // shared memory may still be read for the previous item
   {
     const uint32_t* s32 = reinterpret_cast<const uint32_t*>(a.lat + it.lattice);
     uint32_t* d32 = reinterpret_cast<uint32_t*>(Ls);
     for (int i = threadIdx.x; i < (int)(sizeof(LatticeDev<real>) / 4); i += TX) d32[i] = s32[i];
+    // the tensor maps of this lattice in the source buffer (kept in shared memory, not
+    // registers); null if the input slots were not 128-byte aligned after all
+    if (threadIdx.x == 0)
+      *const_cast<const CUtensorMap**>(tmap_s) = a.tmaps && (smem_u32(instage) & 127u) == 0
+                                                     ? a.tmaps + ((size_t)src_buf * a.n_lat + it.lattice) * 2
+                                                     : nullptr;
   }
   __syncthreads();
   const LatticeDev<real>& L = *Ls;
@@ -694,26 +739,49 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   const int z0 = it.z0, z1 = it.z1;
   const unsigned row_bytes = 18u * (unsigned)(nact + 2 * PAD) * (unsigned)sizeof(real);
 
-  // plane k of row r (its source row, reflected at the walls) is copied by lane k / NW of warp
-  // k % NW, so that every warp issues about the same number of copies
+  // copy k of row r (plane k, or run k on the tensor path; its source row, reflected at the
+  // walls) is issued by lane k / NW of warp k % NW, so that every warp issues about the same
+  // number of copies
   constexpr int NW = TX / 32;
   const int my_plane = (tid & 31) * NW + (tid >> 5);
   // row r goes to input slot r mod NSI; the callers carry the slots along
   auto stage_row = [&](int r, int slot) {
     if (r < 0 || r >= Lz || r > z1) return;
     uint64_t* bar = bars + slot;
+    real* sbase = instage + slot * LAY::slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
-    if (my_plane < 18) {
-      const int k = my_plane;
-      const int s = k / 9, l = k - 9 * s;
-      const int cz = LB_CZ(l);
-      int sr = r - cz, p = k;
+    // interior strips (no periodic wrap) with tensor maps: one 4-d tensor copy per run of links
+    // (both species); otherwise one 1-d bulk copy (or up to three at the x edges) per plane
+    if (TX + 2 * PAD <= 256 && a.tmaps != nullptr && x0 > 0 && x0 + nact < Lx) {
+      if (my_plane < 6) {
+        const CUtensorMap* maps = *tmap_s;
+        const int4 e = rtab[my_plane];
+        const int n = e.w & 3;
+        int sr = r - ((e.w >> 2) - 1), ls = e.y;
+        if (sr < 0 || sr >= Lz) {
+          sr = r;
+          ls = e.z;
+        }
+        real* d = sbase + e.x;
+        if (maps) {
+          tensor_g2s(d, maps + (n - 1), x0 - PAD, sr, ls, 0, bar);
+        } else {  // the same box as 1-d copies, one per plane
+          for (int q = 0; q < 2 * n; ++q) {
+            const int s = q / n, l = ls + q - s * n;
+            bulk_g2s(d + q * SW, f + (size_t)(9 * s + l) * LzLx + (size_t)sr * Lx + x0 - PAD,
+                     (unsigned)SW * (unsigned)sizeof(real), bar);
+          }
+        }
+      }
+    } else if (my_plane < 18) {
+      const int4 e = ptab[my_plane];
+      int sr = r - e.y, p = e.z;
       if (sr < 0 || sr >= Lz) {
         sr = r;
-        p = 9 * s + LB_OPP(l);
+        p = e.w;
       }
       const real* rowp = f + (size_t)p * LzLx + (size_t)sr * Lx;
-      real* d = instage + (slot * 18 + k) * SW;
+      real* d = sbase + e.x;
       const unsigned sz = (unsigned)sizeof(real);
       if (x0 > 0 && x0 + nact < Lx) {
         bulk_g2s(d, rowp + x0 - PAD, (unsigned)(nact + 2 * PAD) * sz, bar);
@@ -744,7 +812,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     ph ^= 1u << slot;
   };
   auto rho_at = [&](int r, int slot, int j) {
-    const real* sb = instage + slot * 18 * SW;
+    const real* sb = instage + slot * LAY::slot;
     Pr<real> v[9];
     read_bulk<real, SW>(sb, j, r > 0, r < Lz - 1, k9, k36, v);
     return sum9<real>(v);
@@ -797,7 +865,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real* sb = instage + sc * 18 * SW;
+      const real* sb = instage + sc * LAY::slot;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
       // the variants are inlined; the branches are uniform over the block (one lattice per item,
@@ -864,7 +932,7 @@ struct MinBlocks {
 
 template <class real, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value) step_kernel(StepArgs<real> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
   prepare_bm<real, NOISE>(smem + Smem<real>::bm(blockDim.x));
   process_item<real, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem);
@@ -884,12 +952,12 @@ struct PersistentBlocks {
 template <class real, int TX, bool SAMPLE, int NOISE>
 __global__ void __launch_bounds__(TX, BulkBlocks<real>::value * 128 / TX) step_kernel_bulk(StepArgs<real> a) {
   static_assert(TX == 32 || TX == 64 || TX == 128 || TX == 256, "bulk tiles are 32, 64, 128 or 256 columns");
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t step = (uint32_t)(*a.d_t + a.t_offset);
   bulk_init<real, TX>(smem);
   prepare_bm<real, NOISE>(smem + SmemBulk<real, TX>::bm);
   uint32_t ph = 0;
-  process_item_bulk<real, TX, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem, ph);
+  process_item_bulk<real, TX, SAMPLE, NOISE>(a, a.src, a.dst, blockIdx.x, step, smem, ph, a.src_buf);
 }
 
 // ---- the persistent launch: items handed out in order, per-item dependencies -------------
@@ -967,7 +1035,7 @@ __device__ __forceinline__ unsigned long long next_ticket(unsigned long long* co
 template <class real, int NOISE>
 __global__ void __launch_bounds__(256, MinBlocks<real>::value)
     persistent_kernel(StepArgs<real> a, int nsteps, PersistArgs p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   prepare_bm<real, NOISE>(smem + Smem<real>::bm(blockDim.x));
   const unsigned long long n = (unsigned)a.n_items, total = (unsigned long long)nsteps * n;
@@ -987,7 +1055,7 @@ __global__ void __launch_bounds__(256, MinBlocks<real>::value)
 template <class real, int TX, int NOISE>
 __global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
     persistent_kernel_bulk(StepArgs<real> a, int nsteps, PersistArgs p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int64_t t0 = *a.d_t + a.t_offset;
   bulk_init<real, TX>(smem);
   prepare_bm<real, NOISE>(smem + SmemBulk<real, TX>::bm);
@@ -1001,7 +1069,8 @@ __global__ void __launch_bounds__(TX, PersistentBlocks<real>::value * 128 / TX)
     const bool odd = (k & 1) && !p.trial;
     const real* src = odd ? a.dst : a.src;
     real* dst = odd ? const_cast<real*>(a.src) : a.dst;
-    if (!process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, (uint32_t)(t0 + k), smem, ph))
+    if (!process_item_bulk<real, TX, false, NOISE>(a, src, dst, i, (uint32_t)(t0 + k), smem, ph,
+                                                   a.src_buf ^ (odd ? 1 : 0)))
       return;  // the blocks that wait on this item give up (bounded)
     publish_item(p.done, i, (unsigned)(k + 1));
   }
@@ -1154,7 +1223,7 @@ cudaError_t launch_step_persistent(const StepArgs<real>& a, int tile_x, int nste
 // 2j and 2j + 1 together as the step kernels do, a trailing odd pair alone.
 template <class real>
 __global__ void debug_normals_kernel(const uint32_t* __restrict__ words, int64_t n_pairs, double* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   prepare_bm<real, NOISE_HOM>(smem);
   const BmTables<real>* bm = reinterpret_cast<const BmTables<real>*>(smem);
   const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);

@@ -188,6 +188,36 @@ def test_profiles_of_a_batch(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_tensor_copies_of_link_runs_match_plane_copies_and_oracle(prec):
+    """Strips away from the periodic x edges are staged by 4-d tensor copies of runs of links
+    (both species per copy); the result is bit-identical to per-plane 1-d copies, for every tile
+    width that uses them, per-step and persistent launches, and matches the oracle."""
+    p = LatticeParams(512, 32, kT=1e-5, G=0.5, grad_c0=0.4 / 32, seed=13)
+    o = oracle_of(p)
+    o.set_sampling(0, 5)
+    o.step(20)
+    want = o.populations()
+    base = None
+    for tile in [(128, 7), (64, 32), (32, 5)]:
+        for kw in (dict(tensor_maps=False), dict(), dict(persistent=True), dict(persistent=True, graph=True)):
+            with Simulation(p, precision=prec, **kw) as sim:
+                sim.set_tile(*tile)
+                sim.set_sampling(0, 5)
+                sim.step(20)
+                r = (sim.populations(), sim.structure_factor("c")[0], sim.mean_pressure())
+            if base is None:
+                base = r
+                if prec == "fp64":
+                    assert_fp64_parity(r[0], want)
+                else:
+                    assert_dev32_parity(r[0], want, background(p.Lx, p.Lz, p.grad_c0))
+            else:
+                np.testing.assert_array_equal(r[0], base[0])
+                np.testing.assert_array_equal(r[1], base[1])
+                np.testing.assert_allclose(r[2], base[2], rtol=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
 def test_launch_modes_and_tiles_are_bit_identical(prec):
     """Direct launches, CUDA graphs, the persistent cooperative launch and every tile shape
     compute each site identically."""
