@@ -214,8 +214,8 @@ __device__ __forceinline__ void sincos_ftz(float x, float& s, float& c) {
 }
 
 // Tables of the double-precision Box-Muller (the table-driven method of P. T. P. Tang for the
-// logarithm and for sine/cosine): cs[j] = (cos, sin)(2 pi j / 1024) and ln[j] = (ln y_j, 1 / y_j)
-// with y_j = 3/4 + j/256, j = 0 .. 192.  The single-precision path needs none.
+// logarithm and for sine/cosine): cs[j] = (cos, sin)(2 pi j / 1024) and ln[j] = (-2 ln y_j,
+// 1 / y_j) with y_j = 3/4 + j/256, j = 0 .. 192.  The single-precision path needs none.
 template <class real>
 struct BmTables {};
 template <>
@@ -236,7 +236,7 @@ __device__ __forceinline__ void fill_bm_tables(BmTables<real>* T) {
     }
     for (int j = threadIdx.x; j < 193; j += blockDim.x) {
       const double y = 0.75 + (double)j / 256.0;
-      T->ln[j] = make_double2(log(y), 1.0 / y);
+      T->ln[j] = make_double2(-2.0 * log(y), 1.0 / y);  // -2 ln y_j (an exact scaling), 1 / y_j
     }
   }
 }
@@ -294,10 +294,13 @@ __device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, doub
   const double2 L = T->ln[j];
   const double yj = fma((double)j, 0.00390625, 0.75);
   const double t = (y - yj) * L.y;
-  const double p = fma(t, fma(t, fma(t, fma(t, fma(t, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5), 1.0);
+  // -2 ln u1 directly: every term and coefficient scaled by -2, a power of two, so the result is
+  // bit for bit -2 times the logarithm formed term by term
+  const double p2 =
+      fma(t, fma(t, fma(t, fma(t, fma(t, 1.0 / 3.0, -0.4), 0.5), -2.0 / 3.0), 1.0), -2.0);  // -2 p(t)
   const double ne = (double)(e - 24);
-  const double lnu = fma(ne, ln2_hi, L.x + fma(t, p, ne * ln2_lo));
-  const double r = sqrt(-2.0 * lnu);
+  const double m2lnu = fma(ne, -2.0 * ln2_hi, L.x + fma(t, p2, ne * (-2.0 * ln2_lo)));
+  const double r = sqrt(m2lnu);
   // angle
   const uint32_t m2 = 2u * (b & 0x7FFFFFu) + 1u;
   const double2 CS = T->cs[m2 >> 14];

@@ -217,6 +217,27 @@ def test_tensor_copies_of_link_runs_match_plane_copies_and_oracle(prec):
                 np.testing.assert_allclose(r[2], base[2], rtol=1e-14)
 
 
+def test_tensor_copies_in_a_mixed_batch():
+    """A batch of lattices of different widths (tensor maps per lattice and state buffer):
+    persistent launches with tensor copies equal 1-d copies bit for bit, and every lattice
+    matches its oracle."""
+    ps = [LatticeParams(1024, 16, kT=1e-5, G=0.5, grad_c0=0.3 / 16, seed=21, lattice_id=0),
+          LatticeParams(256, 32, kT=1e-5, G=0.5, grad_c0=0.5 / 32, seed=22, lattice_id=1),
+          LatticeParams(512, 8, kT=1e-5, G=0.3, grad_c0=0.1 / 8, seed=23, lattice_id=2)]
+    res = []
+    for tm in (True, False):
+        with Simulation(ps, precision="fp64", persistent=True, graph=True, tensor_maps=tm) as sim:
+            sim.set_tile(64, 16)
+            sim.step(11)
+            res.append([sim.populations(i) for i in range(len(ps))])
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)
+    for i, p in enumerate(ps):
+        o = oracle_of(p)
+        o.step(11)
+        assert_fp64_parity(res[0][i], o.populations())
+
+
 @pytest.mark.parametrize("prec", ["fp64", "dev32"])
 def test_launch_modes_and_tiles_are_bit_identical(prec):
     """Direct launches, CUDA graphs, the persistent cooperative launch and every tile shape
