@@ -53,7 +53,13 @@ class Simulation:
     def __init__(self, lattices, precision: str = "fp64", astar: bool = True, wall_fixed: bool = False,
                  noise_loc: bool = False, graph: bool = False, persistent: bool = False, autotune: bool = False,
                  bulk: bool = True, tensor_maps: bool = True, allocator=None):
-        """allocator: None (the library allocates with cudaMalloc), "torch" (torch's caching
+        """precision: "fp64" (FP64 populations) or "dev32" (FP32 deviations from the background).
+        graph: lb_step through captured CUDA graphs; persistent: one cooperative launch per run of
+        plain steps (items handed out in order, each waiting only for its neighbours' previous
+        step), the fastest launch for batches; autotune: time tile shapes on the first step.
+        bulk / tensor_maps: stage rows with bulk copies / with 4-d tensor copies of link runs
+        where possible (both default; results are bit-identical either way).
+        allocator: None (the library allocates with cudaMalloc), "torch" (torch's caching
         allocator on the current device) or an (alloc, free) pair of capi callbacks."""
         if isinstance(lattices, LatticeParams):
             lattices = [lattices]
