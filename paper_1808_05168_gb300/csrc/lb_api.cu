@@ -209,10 +209,11 @@ LatticeDev<real> make_lattice(const lb_params& p, int flags, bool dev, int64_t f
     L.sig[a] = (real)std::sqrt(v * rA);
     L.pref[a] = (real)std::sqrt(v);
   }
-  // folded coefficients (see LatticeDev::kA): constant factors of m^eq_3 (3), S_3 (6), S_4 (2)
+  // folded coefficients (see LatticeDev::kA): constant factors of m^eq_3 (3), S_3 (6), S_4 (2),
+  // and the weight 1/36 of the diagonal links, which the inverse transform then needs no more
   const bool loc = flags & LB_NOISE_LOC;
   for (int a = 0; a < 9; ++a) {
-    const double invN = 1.0 / kNorm[a];
+    const double invN = 1.0 / (36.0 * kNorm[a]);
     const double qf = a == 3 ? 3.0 : 1.0, sf = a == 3 ? 6.0 : (a == 4 ? 2.0 : 1.0);
     L.kA[a] = (real)((1.0 - lam[a]) * invN);
     L.kB[a] = (real)(a >= 1 && a <= 5 ? lam[a] * qf * invN : 0.0);

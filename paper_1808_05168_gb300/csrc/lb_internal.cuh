@@ -48,10 +48,11 @@ struct LatticeDev {
                      // reference densities of both species are rho_bar / 2 (c_bar0 = 1/2)
   real pref_mom;     // loc noise: sqrt((2 - l_d) l_d kT)
   real pref[9];      // loc noise: sqrt(3 (2 - l_a) l_a N_a kT)
-  // Eq. MRT divided by N_a, as used by the step kernels: m*_a / N_a = kA[a] m_a + kB[a] q_a +
-  // kC[a] s_a + kN[a] n_a, with q_a, s_a the equilibrium and forcing moments without their
-  // constant factors (q_3 = rho |U|^2, s_3 = U.F, s_4 = U_x F_x - U_z F_z) and n_a a standard
-  // normal (kN: hom amplitudes; for loc, times sqrt of the local density)
+  // Eq. MRT divided by 36 N_a, as used by the step kernels: m*_a / (36 N_a) = kA[a] m_a +
+  // kB[a] q_a + kC[a] s_a + kN[a] n_a, with q_a, s_a the equilibrium and forcing moments without
+  // their constant factors (q_3 = rho |U|^2, s_3 = U.F, s_4 = U_x F_x - U_z F_z) and n_a a
+  // standard normal (kN: hom amplitudes; for loc, times sqrt of the local density); 1/36 is the
+  // weight of the diagonal links in the inverse transform
   real kA[9], kB[9], kC[9], kN[9];
 };
 

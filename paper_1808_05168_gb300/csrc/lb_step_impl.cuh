@@ -358,17 +358,25 @@ __device__ __forceinline__ void collide_out(const Mom<real>& m, Pr<real> d, Pr<r
     }
   }
   // links of opposite velocity pair up as f = u + v and f_opp = u - v (u: the even moments,
-  // v: the odd ones)
-  const P c9 = pr(real(1) / 9), c36 = pr(real(1) / 36);
-  const P base4 = fma2(pr(real(-4)), M8, add2(d, M3));
-  const P base5 = fma2(pr(real(8)), M8, fma2(pr(real(4)), M3, d));
-  const P u13 = mul2(c9, add2(base4, M4)), v13 = mul2(c9, sub2(M1, M6));
-  const P u24 = mul2(c9, sub2(base4, M4)), v24 = mul2(c9, sub2(M2, M7));
-  const P u57 = mul2(c36, add2(base5, M5)), v57 = mul2(c36, fma2(pr(real(2)), add2(M6, M7), add2(M1, M2)));
-  const P u68 = mul2(c36, sub2(base5, M5)), v68 = mul2(c36, fma2(pr(real(2)), sub2(M6, M7), sub2(M1, M2)));
-  const P f0 = mul2(pr(real(4) / 9), fma2(pr(real(2)), M8, fma2(pr(real(-2)), M3, d)));
-  const P f[9] = {f0,             add2(u13, v13), add2(u24, v24), sub2(u13, v13), sub2(u24, v24),
-                  add2(u57, v57), sub2(u68, v68), sub2(u57, v57), add2(u68, v68)};
+  // v: the odd ones).  The coefficients carry the weight 1/36 of the diagonal links (M here is
+  // m* / (36 N_a)), so those need no product; the others have weight 4/36 and the rest link 16/36.
+  const P dq = mul2(pr(real(1) / 36), d);
+  const P base4 = fma2(pr(real(-4)), M8, add2(dq, M3));
+  const P base5 = fma2(pr(real(8)), M8, fma2(pr(real(4)), M3, dq));
+  const P u13 = mul2(pr(real(4)), add2(base4, M4)), v13 = sub2(M1, M6);
+  const P u24 = mul2(pr(real(4)), sub2(base4, M4)), v24 = sub2(M2, M7);
+  const P u57 = add2(base5, M5), v57 = fma2(pr(real(2)), add2(M6, M7), add2(M1, M2));
+  const P u68 = sub2(base5, M5), v68 = fma2(pr(real(2)), sub2(M6, M7), sub2(M1, M2));
+  const P f0 = mul2(pr(real(16)), fma2(pr(real(2)), M8, fma2(pr(real(-2)), M3, dq)));
+  const P f[9] = {f0,
+                  fma2(pr(real(4)), v13, u13),
+                  fma2(pr(real(4)), v24, u24),
+                  fma2(pr(real(-4)), v13, u13),
+                  fma2(pr(real(-4)), v24, u24),
+                  add2(u57, v57),
+                  sub2(u68, v68),
+                  sub2(u57, v57),
+                  add2(u68, v68)};
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     put<real, TO_GLOBAL, STRIDE>(outA, stride, l, f[l].x);
