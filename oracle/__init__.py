@@ -6,7 +6,9 @@ mean pressure; Appendix structure factors).
 TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the benchmark's CPU
 baseline are the only users; the product library never imports this package.  The C++
 source (``lb_oracle.cpp``) is compiled with ``-O2 -ffp-contract=off`` so that every
-operation rounds as written.
+operation rounds as written: once plain (``liblb_oracle.so``, one thread) and once with
+``-fopenmp`` (``liblb_oracle_omp.so``), which runs the loops over the lattice rows on several
+host cores and gives the same results bit for bit.
 """
 from __future__ import annotations
 
@@ -20,30 +22,35 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lb_oracle.cpp")
 _OUT_DIR = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_OUT_DIR, "liblb_oracle.so")
+_LIB_PATHS = {False: os.path.join(_OUT_DIR, "liblb_oracle.so"),
+              True: os.path.join(_OUT_DIR, "liblb_oracle_omp.so")}
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liblb_oracle.so`` (host compiler only)."""
+def build(force: bool = False, omp: bool = None) -> str:
+    """Compile the oracle into ``oracle/_build/`` (host compiler only): the plain library, the
+    OpenMP one, or both (omp=None, the default; returns the plain library's path)."""
+    if omp is None:
+        build(force, True)
+        return build(force, False)
+    path = _LIB_PATHS[omp]
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC]
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = (["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared"] + (["-fopenmp"] if omp else [])
+           + ["-o", tmp, _SRC])
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
+        if omp in _libs:
+            return _libs[omp]
+        lib = ctypes.CDLL(build(omp=omp))
         c_dbl, c_int, c_i64, c_u64, c_u32, vp = (ctypes.c_double, ctypes.c_int, ctypes.c_int64,
                                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p)
         dp = ctypes.POINTER(ctypes.c_double)
@@ -83,8 +90,15 @@ def _load():
         lib.olb_pressure_shift_grad.argtypes = create_args + [c_i64, dp, dp]
         lib.olb_pressure_shift.argtypes = create_args + [c_i64]
         lib.olb_pressure_shift.restype = c_dbl
-        _lib = lib
+        lib.olb_set_threads.argtypes = [c_int]
+        lib.olb_set_threads.restype = c_int
+        _libs[omp] = lib
         return lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the OpenMP oracle's row loops (n > 0 sets them); returns the count in use."""
+    return int(_load(True).olb_set_threads(int(n)))
 
 
 def _dptr(a: np.ndarray):
@@ -103,8 +117,9 @@ class OracleLattice:
 
     def __init__(self, Lx, Lz, lambda_s=1.0, lambda_d=0.8, lambda_e=None, lambda_q=1.0, lambda_eps=1.0,
                  kT=0.0, G=0.0, grad_c0=0.0, seed=1, lattice_id=0, astar=True, wall_fixed=False,
-                 noise_loc=False):
-        self.lib = _load()
+                 noise_loc=False, omp=False):
+        """omp: run on the OpenMP build (the row loops on several host cores, same results)."""
+        self.lib = _load(omp)
         if lambda_e is None:
             lambda_e = lambda_s
         self.Lx, self.Lz = int(Lx), int(Lz)
@@ -288,3 +303,23 @@ def pressure_shift_grad(Lx, Lz, nsteps, lambda_s=1.0, lambda_d=0.8, lambda_e=Non
     grad = np.empty(3, np.float64)
     lib.olb_pressure_shift_grad(*args, int(nsteps), ctypes.byref(loss), _dptr(grad))
     return loss.value, grad
+
+
+def _sampled_run(job):
+    """One oracle lattice run with sampling (a worker of sampled_runs): its structure factors."""
+    kwargs, Lx, Lz, steps, discard, every, fields = job
+    o = OracleLattice(Lx, Lz, **kwargs)
+    o.set_sampling(discard, every)
+    o.step(steps)
+    return {f: o.structure_factor(f) for f in fields}
+
+
+def sampled_runs(jobs, processes=None):
+    """Independent oracle runs, one per job (kwargs of OracleLattice, Lx, Lz, steps, discard,
+    every, fields), in a pool of spawned processes (plain build, one thread each); returns, per
+    job, {field: (S(q_z, q_x) average, sample count)}."""
+    import multiprocessing as mp
+
+    build()
+    with mp.get_context("spawn").Pool(processes or os.cpu_count() or 1) as pool:
+        return pool.map(_sampled_run, list(jobs))

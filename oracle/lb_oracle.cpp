@@ -11,9 +11,13 @@
  * as easy as 1, 2, 3").
  *
  * Everything is written for clarity, not speed: dense 9x9 moment transforms, whole-lattice
- * arrays for every intermediate, a separable O(n^2) discrete Fourier transform.
+ * arrays for every intermediate, a separable O(n^2) discrete Fourier transform.  The loops over
+ * the rows of the lattice carry OpenMP pragmas: the same source compiled with -fopenmp runs them
+ * on several host cores.  Every site is then still computed by the same operations in the same
+ * order, and every sum across sites (mean pressure, mass, loss, profiles, correlations) stays in
+ * one thread, so both builds give identical results.
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent:
  *  - forcing moments: the second-order (Guo-type) source; its moments S_a are taken
  *    with the factor (1 - lambda_a/2), so F_{1,2} = (1 - lambda_d/2) rho^S a^S (Sec. II,
  *    "First order moments");
@@ -30,6 +34,9 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -265,6 +272,7 @@ void compute_pre(const Sim<R>& S, Pre<R>& P) {
 
   // 1. Streaming, Eq. (LB): f_l(r, t) = f*_l(r - c_l, t - 1); periodic in x; a link whose
   //    source row lies beyond a wall is reflected at the mid-way wall: f_l(r) = f*_opp(l)(r).
+#pragma omp parallel for collapse(3) schedule(static)
   for (int s = 0; s < 2; ++s)
     for (int l = 0; l < 9; ++l)
       for (int z = 0; z < Lz; ++z)
@@ -278,6 +286,7 @@ void compute_pre(const Sim<R>& S, Pre<R>& P) {
         }
 
   // 2. rho^S = sum_l f^S_l, j^S = sum_l c_l f^S_l.
+#pragma omp parallel for collapse(2) schedule(static)
   for (int s = 0; s < 2; ++s)
     for (int z = 0; z < Lz; ++z)
       for (int x = 0; x < Lx; ++x) {
@@ -296,6 +305,7 @@ void compute_pre(const Sim<R>& S, Pre<R>& P) {
   // 3. Accelerations.  Eq. (aNI): a^A_NI = -G sum_l w_l c_l rho^B(r + c_l), and A <-> B.
   //    Footnote to Eq. (ne-acc): a^A_* = (1-c)(a^B_NI - a^A_NI), a^B_* = c (a^A_NI - a^B_NI).
   //    Eq. (ne-acc): a^A_NE = (1/3)(0, grad_c0 / c), a^B_NE = (1/3)(0, grad_c0 / (c - 1)).
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < Lz; ++z)
     for (int x = 0; x < Lx; ++x) {
       R sA_x(0.0), sA_z(0.0), sB_x(0.0), sB_z(0.0);  // sum_l w_l c_l rho^{A,B}(r + c_l)
@@ -338,6 +348,7 @@ template <class R>
 void pressure_field(const Sim<R>& S, const Pre<R>& P, std::vector<R>& out) {
   const int Lx = S.Lx, Lz = S.Lz, n = Lx * Lz;
   out.assign((size_t)n, R(0.0));
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < Lz; ++z)
     for (int x = 0; x < Lx; ++x) {
       const int i = z * Lx + x;
@@ -393,6 +404,7 @@ void site_noise(const Sim<R>& S, const R& rhoA_loc, const R& rhoB_loc, uint32_t 
 void dft2_power(const double* phi, int Lx, int Lz, double* out) {
   const double two_pi = 6.283185307179586476925286766559;
   std::vector<double> re((size_t)Lz * Lx), im((size_t)Lz * Lx);
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < Lz; ++z)
     for (int k = 0; k < Lx; ++k) {
       double sr = 0.0, si = 0.0;
@@ -404,6 +416,7 @@ void dft2_power(const double* phi, int Lx, int Lz, double* out) {
       re[z * Lx + k] = sr;
       im[z * Lx + k] = si;
     }
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < Lx; ++k)
     for (int q = 0; q < Lz; ++q) {
       double sr = 0.0, si = 0.0;
@@ -537,6 +550,7 @@ void step(Sim<R>& S) {
     for (int i = 0; i < n; ++i) mean += p[i];
     S.loss_sum += mean / (double)n;
   }
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < Lz; ++z)
     for (int x = 0; x < Lx; ++x) {
       const int i = z * Lx + x;
@@ -747,6 +761,18 @@ void olb_site_noise(void* h, int x, int z, int64_t step_index, double* out) {
   site_noise(*S, P.rho[i], P.rho[n + i], site_counter(*S, x, z), (uint32_t)step_index, xi);
   for (int s = 0; s < 2; ++s)
     for (int a = 0; a < 9; ++a) out[s * 9 + a] = xi[s][a];
+}
+
+// Threads of the row loops in a build with OpenMP (n > 0 sets them); returns the count in use,
+// 1 in the plain build.
+int olb_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 void olb_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {

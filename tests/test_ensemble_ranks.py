@@ -47,7 +47,7 @@ def _free_port():
 def test_two_ranks_combine_to_the_serial_ensemble_average():
     oracle.build()
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = [np.array(out[r]) for r in range(world)]

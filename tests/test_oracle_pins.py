@@ -206,7 +206,73 @@ def test_noise_local_densities():
 
 
 # ---------------------------------------------------------------- forces and pressure
-def test_equation_of_state_in_uniform_state():
+def _resting(rhoA, rhoB):
+    """Populations with all of rho^S on the rest link: streaming leaves them in place, so the
+    pre-collision densities of the next step are rhoA, rhoB ([Lz, Lx]) and every j^S is zero,
+    whence rho U = F / 2 (Eq. bar) with F the total force density."""
+    Lz, Lx = rhoA.shape
+    f = np.zeros((2, 9, Lz, Lx))
+    f[0, 0], f[1, 0] = rhoA, rhoB
+    return f
+
+
+def test_fixed_wall_composition_ghosts_cancel_the_normal_force():
+    """Sec. II.A wall ghosts of the non-ideal force (Eq. aNI), fixed-composition rule: beyond the
+    bottom wall the ghost row holds the adjacent row's total density split c_0(-Lz/2) :
+    1 - c_0(-Lz/2) between A and B, beyond the top wall c_0(+Lz/2) : 1 - c_0(+Lz/2).  The normal
+    component of sum_l w_l c_l rho(r + c_l) at a wall row is (1/6) x (the row above minus the row
+    below) for any x-dependence, so if the first interior row equals the ghost row the total
+    normal force there vanishes and U_z = 0 (the gradient force cancels in the sum, Eq. NEcond;
+    a* moves force between the species only).  The state below builds exactly that for both
+    walls (c_0(-Lz/2) = 0.35, c_0(+Lz/2) = 0.65) with wall rows of other compositions: U_z must
+    vanish at both wall rows under the fixed rule and not under the copy rule, and the rows
+    that see no ghost must not depend on the rule."""
+    Lx, Lz, g = 6, 4, 0.075
+    cw_bot, cw_top = 0.5 - g * Lz / 2, 0.5 + g * Lz / 2
+    rng = np.random.default_rng(5)
+    rho0, rho3 = 0.9 + 0.2 * rng.random(Lx), 0.9 + 0.2 * rng.random(Lx)
+    c_0, c_3 = 0.2 + 0.1 * rng.random(Lx), 0.75 + 0.1 * rng.random(Lx)  # far from the walls' values
+    rhoA = np.stack([rho0 * c_0, rho0 * cw_bot, rho3 * cw_top, rho3 * c_3])
+    rhoB = np.stack([rho0 * (1 - c_0), rho0 * (1 - cw_bot), rho3 * (1 - cw_top), rho3 * (1 - c_3)])
+    fl = {}
+    for fixed in (True, False):
+        o = oracle.OracleLattice(Lx, Lz, G=0.7, kT=0, grad_c0=g, wall_fixed=fixed)
+        o.set_populations(_resting(rhoA, rhoB))
+        fl[fixed] = o.fields()
+        np.testing.assert_allclose(fl[fixed]["rhoA"], rhoA, rtol=0, atol=1e-15)
+    uz = fl[True]["uz"]
+    assert np.max(np.abs(uz[[0, Lz - 1]])) < 1e-15, uz
+    assert np.min(np.abs(fl[False]["uz"][[0, Lz - 1]])) > 1e-3, fl[False]["uz"]
+    np.testing.assert_array_equal(fl[True]["uz"][1:Lz - 1], fl[False]["uz"][1:Lz - 1])
+    np.testing.assert_array_equal(fl[True]["ux"][1:Lz - 1], fl[False]["ux"][1:Lz - 1])
+
+
+def test_fixed_wall_composition_equals_copy_rule_at_the_wall_composition():
+    """Sec. II.A: when the wall rows carry exactly the wall compositions c_0(-Lz/2) and
+    c_0(+Lz/2), the fixed-composition ghosts equal the copied ones, so one step (noise on, so
+    that every term of Eq. MRT enters) and the pre-collision pressure (Sec. III.C interaction
+    part) agree between the two rules; on a state whose wall rows carry other compositions they
+    differ.  (Those must not be 1/2: with a* the update depends on the ghosts only through the
+    total force, whose ghost term rho^A(r) rho^B_ghost + rho^B(r) rho^A_ghost does not depend on
+    how the ghost's density is split when c(r) = 1/2; so does the pressure's.)"""
+    Lx, Lz, g = 8, 5, 0.05
+    cw_bot, cw_top = 0.5 - g * Lz / 2, 0.5 + g * Lz / 2
+    rng = np.random.default_rng(6)
+    rho = 0.8 + 0.4 * rng.random((Lz, Lx))
+    c = 0.3 + 0.4 * rng.random((Lz, Lx))
+    c[0], c[Lz - 1] = cw_bot, cw_top
+    res = {}
+    for name, cc in (("at_cw", c), ("other", np.where(np.arange(Lz)[:, None] % (Lz - 1) == 0, 0.2, c))):
+        for fixed in (True, False):
+            o = oracle.OracleLattice(Lx, Lz, lambda_s=1.2, lambda_d=0.9, kT=1e-3, G=0.6, grad_c0=g, seed=4,
+                                     wall_fixed=fixed)
+            o.set_populations(_resting(rho * cc, rho * (1 - cc)))
+            p = o.fields()["p"]
+            o.step(1)
+            res[name, fixed] = (o.populations(), p)
+    for k in (0, 1):
+        np.testing.assert_allclose(res["at_cw", True][k], res["at_cw", False][k], rtol=1e-14, atol=1e-16)
+        assert np.max(np.abs(res["other", True][k] - res["other", False][k])) > 1e-4
     """Eq. (EQUATIONofSTATE): at rest and uniform, P = rho/3 + G rho^A rho^B / 3, and the
     uniform state is stationary (the non-ideal force vanishes)."""
     rA, rB, G = 0.6, 0.45, 0.7
@@ -391,6 +457,63 @@ def test_equilibrium_structure_factors_are_flat_fdt_values():
         along_z = np.nanmean(Sq, axis=1)[1:]
         assert np.max(np.abs(along_x / w - 1)) < 0.1, (fld, along_x / w)
         assert np.max(np.abs(along_z / w - 1)) < 0.1, (fld, along_z / w)
+
+
+@pytest.mark.slow
+def test_nonequilibrium_concentration_spectrum_follows_the_prefactor_law():
+    """Sec. III.B, Eqs. (decompose) and (prefactor): under an imposed gradient the concentration
+    structure factor along the walls is S_c(q, 0) = 0.75 kT [1 + phi S_NE(qL)] with
+    phi = (1/3) L^4 (grad c_0)^2 / (c_bar (1 - c_bar) (nu + D) D) and S_NE -> (qL)^-4 for qL >> 1,
+    approached from below because of the confinement.  L = 16, Lx = 64, grad c_0 = 0.03,
+    kT = 1e-4, every rate 1 (nu = D = 1/6, Eqs. diff and vis), eight seeds of 20000 steps (3000
+    discarded, a sample every 20) on eight processes: the enhancement is large at the smallest
+    qL (about 3.7, where the unbounded law would give 230), falls monotonically with q, its ratio
+    to phi (qL)^-4 rises monotonically towards 1, and over qL = 7.9 .. 12.6 the enhancement
+    summed is within a loose band (0.4 .. 1.2) of the law summed, with no fit; the velocity
+    spectra keep the equilibrium value kT / rho_bar (Sec. III.B)."""
+    Lx, Lz, g, kT = 64, 16, 0.03, 1e-4
+    kw = dict(lambda_s=1.0, lambda_d=1.0, lambda_e=1.0, lambda_q=1.0, lambda_eps=1.0, kT=kT, G=0.0, grad_c0=g)
+    jobs = [(dict(kw, seed=100 + i), Lx, Lz, 20000, 3000, 20, ("c", "ux", "uz")) for i in range(8)]
+    res = oracle.sampled_runs(jobs, processes=8)
+    assert all(r["c"][1] == 850 for r in res)
+    Sc = np.array([r["c"][0][0] for r in res])  # q_z = 0, every q_x
+    enh = Sc.mean(0) / (0.75 * kT) - 1
+    nu = D = (1 / 1.0 - 0.5) / 3
+    phi = (1 / 3) * Lz ** 4 * g ** 2 / (0.25 * (nu + D) * D)
+    qt = 2 * np.pi * np.arange(Lx) / Lx * Lz
+    law = np.zeros(Lx)
+    law[1:] = phi * qt[1:] ** -4.0
+    ratio = enh[1:7] / law[1:7]
+    assert enh[1] > 2.0, enh[1]
+    assert np.all(np.diff(enh[1:7]) < 0), enh[1:7]
+    assert np.all(np.diff(ratio[:5]) > 0) and ratio[0] < 0.05, ratio
+    k = np.arange(5, 9)
+    band = enh[k].sum() / law[k].sum()
+    assert 0.4 < band < 1.2, band
+    for f in ("ux", "uz"):
+        S = np.mean([r[f][0] for r in res], axis=0)
+        S[0, 0] = np.nan
+        assert abs(np.nanmean(S) / kT - 1) < 0.02, f
+
+
+def test_openmp_build_gives_identical_results():
+    """The same oracle source compiled with -fopenmp (its row loops on several host cores; used to
+    time the oracle on every core) gives the plain build's results bit for bit: populations,
+    structure factors, mean pressure and profiles, with noise, G > 0 and both wall rules."""
+    threads = oracle.set_threads(4)
+    assert threads == 4
+    for fixed in (False, True):
+        kw = dict(kT=1e-4, G=0.5, grad_c0=0.02, seed=3, wall_fixed=fixed, lambda_s=1.2, lambda_d=0.9)
+        a, b = oracle.OracleLattice(32, 12, **kw), oracle.OracleLattice(32, 12, omp=True, **kw)
+        for o in (a, b):
+            o.set_sampling(3, 4)
+            o.step(31)
+        np.testing.assert_array_equal(a.populations(), b.populations())
+        for f in ("rho", "c", "ux", "uz"):
+            np.testing.assert_array_equal(a.structure_factor(f)[0], b.structure_factor(f)[0])
+        assert a.mean_pressure() == b.mean_pressure()
+        np.testing.assert_array_equal(a.profile("p")[0], b.profile("p")[0])
+    oracle.set_threads(os.cpu_count() or 1)
 
 
 # ---------------------------------------------------------------- gradient reference

@@ -60,7 +60,7 @@ def _free_port():
 def test_two_slabs_with_halo_exchange_equal_the_whole_lattice():
     oracle.build()
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = {r: [np.array(s).reshape(2, 9, LZ, LX // world) for s in out[r]] for r in range(world)}
