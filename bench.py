@@ -52,6 +52,9 @@ def parse():
                     help="rows per block of the profiling cases (default 64 small, 256 ensemble)")
     ap.add_argument("--profile-ensemble", type=int, default=0,
                     help="run the ensemble with this many seeds for 6 steps (for ncu captures)")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="one mean-pressure-shift gradient on the 256 x 128 lattice (2000 steps, checkpoints "
+                         "every 100), in --profile-precision (for ncu captures)")
     return ap.parse_args()
 
 
@@ -235,6 +238,7 @@ def run_ours(args):
 
     if not args.no_extras and rank == 0:
         res["fp64_plain"] = measure_plain(torch, workloads.c4(), "fp64", steps=10)
+        res["fp64_plain"]["roofline"] = fp64_roofline(res["fp64_plain"]["GLUPS"])
         res["fp64_plain"]["GLUPS_one_launch_per_step"] = measure_plain(torch, workloads.c4(), "fp64", steps=10,
                                                                        persistent=False)["GLUPS"]
         res["dev32_large"] = measure_plain(torch, workloads.c4(), "dev32", steps=40)
@@ -248,6 +252,24 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(res))
+
+
+# Double-precision arithmetic instructions (DFMA + DADD + DMUL, each one issue of the FP64 pipe)
+# per lattice update of the FP64 step kernel, from ncu's sm__sass_thread_inst_executed_op_d*
+# counters (profiles/step_kernel_bulk_f64_small.md).
+FP64_INSTR_PER_LU = 428.4
+
+
+def fp64_roofline(glups):
+    """The FP64 path is bound by its double-precision arithmetic: its FP64 instruction rate against
+    the device's FP64 FMA issue rate, measured live by the library (lb_debug_fma_rate)."""
+    from paper_1808_05168_gb300 import capi
+
+    peak = capi.lb_debug_fma_rate(capi.LB_PREC_FP64) / 2 / 1e12  # FMA instructions per second, 1e12
+    achieved = FP64_INSTR_PER_LU * glups * 1e9 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP64 instructions/s",
+            "frac": achieved / peak, "fp64_instr_per_lu": FP64_INSTR_PER_LU,
+            "peak_source": "measured DFMA rate (lb_debug_fma_rate), 2 flops per DFMA"}
 
 
 def measure_adjoint(torch):
@@ -327,24 +349,40 @@ def measure_e2e(torch, lattices, K, P):
                     "of every lattice to host"}
 
 
-def cpu_baseline(budget_s=15.0):
-    """The oracle, as it stands, on one host core: one Lz = 256 member of the ensemble
-    (1024 x 256 sites) stepped for about budget_s seconds."""
+def _oracle_member(omp):
+    """The oracle on the largest member of the ensemble (1024 x 256 sites, wall-to-wall difference
+    0.5): the plain build (one core) or the OpenMP build of the same source (its row loops on
+    every host core; bit-identical results)."""
     import oracle
     from paper_1808_05168_gb300 import workloads
 
     p = [q for q in workloads.c3(n_seeds=1) if q.Lz == 256 and abs(q.grad_c0 * q.Lz - 0.5) < 1e-12][0]
     o = oracle.OracleLattice(p.Lx, p.Lz, lambda_s=p.lambda_s, lambda_d=p.lambda_d, lambda_e=p.lambda_e,
                              lambda_q=p.lambda_q, lambda_eps=p.lambda_eps, kT=p.kT, G=p.G, grad_c0=p.grad_c0,
-                             seed=p.seed, lattice_id=p.lattice_id)
-    o.step(1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
+                             seed=p.seed, lattice_id=p.lattice_id, omp=omp)
+    cores = oracle.set_threads(os.cpu_count() or 1) if omp else 1
+    return p, o, cores
+
+
+def cpu_baseline(budget_s=10.0):
+    """The oracle, as it stands, on the host's cores (OpenMP build, one thread per core) and on
+    one core (plain build): one Lz = 256 member of the ensemble stepped for about budget_s
+    seconds each."""
+    out = {}
+    for omp in (True, False):
+        p, o, cores = _oracle_member(omp)
         o.step(1)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": p.Lx * p.Lz * n / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n} steps of the 1024x256 (dc=0.5) ensemble member, single thread, FP64, -O2"}
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            o.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        out[omp] = {"value": p.Lx * p.Lz * n / dt / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                    "sample": f"{n} steps of the 1024x256 (dc=0.5) ensemble member, FP64, -O2, "
+                              + (f"OpenMP over rows on {cores} host cores" if omp else "single thread")}
+    res = out[True]
+    res["single_core"] = out[False]
+    return res
 
 
 # ---------------------------------------------------------------- reference arm: the oracle
@@ -352,15 +390,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-    from paper_1808_05168_gb300 import workloads
-
-    p = [q for q in workloads.c3(n_seeds=1) if q.Lz == 256 and abs(q.grad_c0 * q.Lz - 0.5) < 1e-12][0]
-    o = oracle.OracleLattice(p.Lx, p.Lz, lambda_s=p.lambda_s, lambda_d=p.lambda_d, lambda_e=p.lambda_e,
-                             lambda_q=p.lambda_q, lambda_eps=p.lambda_eps, kT=p.kT, G=p.G, grad_c0=p.grad_c0,
-                             seed=p.seed, lattice_id=p.lattice_id)
+    p, o, cores = _oracle_member(True)
     o.set_sampling(0, LB_STEPS_PER_STEP)
-    per = 2  # LB steps of the 1024 x 256 member per benchmark step (a bounded sample)
+    per = 8  # LB steps of the 1024 x 256 member per benchmark step (a bounded sample)
     for _ in range(args.warmup):
         o.step(per)
     t0 = time.perf_counter()
@@ -368,14 +400,15 @@ def run_reference(args):
         o.step(per)
     dt = time.perf_counter() - t0
     v = p.Lx * p.Lz * per * args.steps / dt / 1e9
-    sample = f"{per} LB steps of the 1024x256 (dc=0.5) ensemble member per step, single thread, FP64"
+    sample = (f"{per} LB steps of the 1024x256 (dc=0.5) ensemble member per step, FP64, OpenMP over rows on "
+              f"{cores} host cores")
     print(json.dumps({
         "impl": "reference", "metric": "two-species D2Q9 GLUPS (FP32-deviation batched ensemble)", "value": v,
         "unit": "GLUPS", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "c3 batched ensemble (oracle on a bounded sample: its largest member)"},
-        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -413,9 +446,25 @@ def run_profile_ensemble(n_seeds, rows=256, persistent=False, tensor_maps=True):
     print("profile-ensemble ok")
 
 
+def run_profile_adjoint(precision):
+    """One gradient of the mean-pressure shift on the 256 x 128 lattice (2000 steps from rest,
+    checkpoints every 100), as the benchmark's adjoint leg times it."""
+    import torch
+
+    from paper_1808_05168_gb300 import Simulation, workloads
+
+    (p,) = workloads.c5()
+    with Simulation(p, precision=precision) as sim:
+        loss, grad = sim.pressure_shift_gradient(2000, 100)
+    torch.cuda.synchronize()
+    print("profile-adjoint ok", loss, list(grad))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.profile_ensemble:
+    if a.profile_adjoint:
+        run_profile_adjoint(a.profile_precision)
+    elif a.profile_ensemble:
         run_profile_ensemble(a.profile_ensemble, rows=a.profile_rows or 256, persistent=a.profile_persistent,
                              tensor_maps=not a.profile_no_tensor_maps)
     elif a.profile_small:

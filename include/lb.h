@@ -122,7 +122,10 @@ int lb_create_batch_with_allocator(lb_ctx** out, int n, const lb_params* params,
 int lb_set_stream(lb_ctx* ctx, void* cuda_stream);
 
 /* Sample the diagnostics on steps t >= discard with (t - discard) % every == 0; every = 0
- * turns sampling off (the default).  Sampling uses the pre-collision state of step t. */
+ * turns sampling off (the default).  Sampling uses the pre-collision state of step t.  The
+ * structure factors are taken by power-of-two transforms: with every > 0 each lattice must have
+ * Lx and Lz powers of two with 2 <= Lx <= 8192 and Lz <= 8192 (LB_ERR_BAD_PARAM otherwise; the
+ * paper's lattices are all of that kind). */
 int lb_set_sampling(lb_ctx* ctx, int64_t discard, int64_t every);
 
 /* Fix the tile shape: tile_x columns per block (32, 64, 128 or 256) and rows_per_item rows
@@ -194,11 +197,44 @@ int lb_mass(lb_ctx* ctx, int lattice, double out[2]);
 int lb_get_populations(lb_ctx* ctx, int lattice, double* host_out, size_t n);
 int lb_set_populations(lb_ctx* ctx, int lattice, const double* host_in, size_t n);
 
+/* ---- x-slab decomposition of one large lattice ---------------------------------------------
+ * The lattice is periodic in x and its walls bound z (Sec. II.A), so it can be cut into slabs of
+ * columns, one per process (or GPU).  A site's update reads the populations within two columns
+ * (streaming brings them from one column away and the non-ideal force, Eq. aNI, needs the
+ * densities of the neighbouring columns), so a slab owning columns [x0, x0 + w) of a lattice
+ * Lx_global wide is stepped as a lattice of w + 4 columns whose first and last two are halo
+ * columns: after every step its own w columns are exact, and the halos are refilled from the
+ * neighbours' boundary columns (two each side) before the next step.  The windows' results then
+ * equal the undivided lattice's bit for bit.  Diagnostics (sampling, correlations, the
+ * mean-pressure gradient) see the whole window, halos included, and are not meant for slabs. */
+
+/* Noise counters of an x-slab window: from this call on, the Philox site counter of column x,
+ * row z of the lattice is z * Lx_global + (x + x0) mod Lx_global, that of column x + x0 of the
+ * undivided lattice (Sec. II.B noise; the default is x0 = 0, Lx_global = Lx).  For a slab owning
+ * [x_s, x_s + w) with two halo columns on each side, x0 = (x_s - 2) mod Lx_global.  Requires
+ * Lx <= Lx_global, 0 <= x0 < Lx_global and Lx_global * Lz < 2^31 (LB_ERR_BAD_PARAM otherwise).
+ * Synchronises the context's stream; lb_pressure_shift_gradient refuses a context with a
+ * non-default map (LB_ERR_STATE). */
+int lb_set_site_map(lb_ctx* ctx, int lattice, int x0, int Lx_global);
+
+/* Copy columns [x_first, x_first + n_cols) of all 18 planes of the lattice's current stored state
+ * to (export) or from (import) a packed device buffer laid out [species * 9 + link][z][column],
+ * 18 * Lz * n_cols values of the storage type: float deviations from the background
+ * w_l rho_bar c^S_0(z) with LB_PREC_DEV32, absolute doubles with LB_PREC_FP64 (two slabs of one
+ * lattice share the background, so the raw values move between them unchanged).  The buffer is
+ * device (or managed) memory of the current device, owned by the caller (the halo exchange sends
+ * it to the neighbour).  Stream-ordered on the context's stream; returns before the copy is done.
+ * 1 <= n_cols, 0 <= x_first <= Lx - n_cols; a host pointer or another device's memory returns
+ * LB_ERR_BAD_PARAM before anything is launched. */
+int lb_export_columns(lb_ctx* ctx, int lattice, int x_first, int n_cols, void* device_out);
+int lb_import_columns(lb_ctx* ctx, int lattice, int x_first, int n_cols, const void* device_in);
+
 /* Power spectrum of one snapshot of a real field (Appendix A, Eqs. SF1 and integral on the
  * lattice): out[n * Lx + k] = |sum_{x,z} phi[z * Lx + x] exp(-2 pi i (k x / Lx + n z / Lz))|^2
  * / (Lx Lz).  field and out are device pointers to Lx * Lz doubles (x fastest; out may not
- * alias field); Lx and Lz are powers of two in 2..8192.  Host pointers or other sizes return
- * LB_ERR_BAD_PARAM.  Stream-ordered on `stream` (NULL: legacy default stream), which also
+ * alias field), in memory of the current device (or managed memory); Lx and Lz are powers of two
+ * in 2..8192.  Host pointers, another device's memory or other sizes return LB_ERR_BAD_PARAM
+ * before anything is launched.  Stream-ordered on `stream` (NULL: legacy default stream), which also
  * orders a device scratch of Lx * Lz * 16 bytes allocated and freed with cudaMallocAsync /
  * cudaFreeAsync; returns before the result is ready. */
 int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* stream);
@@ -207,8 +243,9 @@ int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* st
  * counterpart; this is a deployment aid).  Some callers cannot call cudaMalloc, cudaFree or any
  * allocating routine where they need a spectrum: code running while another owner captures a
  * CUDA graph, processes whose device memory is owned by another framework's pool, or loops that
- * must never wait on an allocator.  Same arguments, result and stream ordering as
- * lb_power_spectrum, with Lx * Lz <= LB_NOALLOC_MAX_POINTS (larger sizes return LB_ERR_SIZE);
+ * must never wait on an allocator.  Same arguments, checks (LB_ERR_BAD_PARAM), result and stream
+ * ordering as lb_power_spectrum, and in addition Lx * Lz <= LB_NOALLOC_MAX_POINTS (larger
+ * products return LB_ERR_SIZE);
  * the intermediate transform lives in a fixed 4 MiB array compiled into the library, which
  * every GPU that loads the library holds until the process exits.  The first call on a device
  * (with that device current) looks up the array's device address and sets the kernels'
@@ -274,6 +311,14 @@ int lb_debug_schedule(int n_lat, const int* Lx, const int* Lz, int tile_x, int r
  * host_out: 2 n_pairs doubles, the pair (r cos 2 pi u2, r sin 2 pi u2) of each.  Both buffers are
  * caller-owned host memory; 0 <= n_pairs <= 2^24, else LB_ERR_BAD_PARAM.  Synchronous. */
 int lb_debug_box_muller(int precision, const uint32_t* host_words, int64_t n_pairs, double* host_out);
+
+/* Measurement aid (the paper has no counterpart): the fused multiply-add rate of the current
+ * device in flops per second (2 per FMA), LB_PREC_FP64 for double and LB_PREC_DEV32 for float
+ * scalar FMAs, from a kernel of eight independent FMA chains per thread over 8 blocks of 256
+ * threads per SM, best of five timed launches after a warm-up; the ceiling against which the
+ * FP64 path, bound by its double-precision arithmetic, is measured.  Synchronous; allocates and
+ * frees a scratch of 8 bytes per thread. */
+int lb_debug_fma_rate(int precision, double* flops_per_s);
 
 #ifdef __cplusplus
 }

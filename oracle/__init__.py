@@ -264,8 +264,10 @@ def basis():
     return T, w, N
 
 
-def dft2_power(phi: np.ndarray):
-    lib = _load()
+def dft2_power(phi: np.ndarray, omp: bool = False):
+    """The O(n^2) separable transform's power |phi(q)|^2 / (Lx Lz), [q_z][q_x]; omp: on the
+    OpenMP build (its rows and columns on every host core; same result)."""
+    lib = _load(omp)
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     Lz, Lx = phi.shape
     out = np.empty_like(phi)

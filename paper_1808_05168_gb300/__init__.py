@@ -189,6 +189,35 @@ class Simulation:
         capi.lb_get_populations(self.h, lattice, out)
         return out
 
+    # ---- x-slab decomposition (one large lattice cut into windows of columns)
+    def set_site_map(self, x0: int, Lx_global: int, lattice: int = 0):
+        """Noise counters of column x of this lattice: those of column (x + x0) mod Lx_global of
+        the undivided lattice (an x-slab window)."""
+        capi.lb_set_site_map(self.h, lattice, x0, Lx_global)
+
+    def export_columns(self, x_first: int, n_cols: int, out=None, lattice: int = 0):
+        """Columns [x_first, x_first + n_cols) of the stored state as a torch tensor on the current
+        device, [18][Lz][n_cols] in the storage type (ordered on the context's stream)."""
+        import torch
+        Lz = self.shape(lattice)[1]
+        dt = torch.float32 if self.precision == "dev32" else torch.float64
+        if out is None:
+            out = torch.empty((18, Lz, n_cols), dtype=dt, device="cuda")
+        if out.dtype != dt or out.numel() != 18 * Lz * n_cols or not out.is_contiguous():
+            raise ValueError("export buffer: contiguous [18][Lz][n_cols] of the storage type")
+        capi.lb_export_columns(self.h, lattice, x_first, n_cols, out.data_ptr())
+        return out
+
+    def import_columns(self, x_first: int, cols, lattice: int = 0):
+        """Overwrite columns [x_first, x_first + n) of the stored state with a device tensor
+        [18][Lz][n] in the storage type (ordered on the context's stream)."""
+        import torch
+        Lz = self.shape(lattice)[1]
+        dt = torch.float32 if self.precision == "dev32" else torch.float64
+        if cols.dtype != dt or cols.dim() != 3 or cols.shape[:2] != (18, Lz) or not cols.is_contiguous():
+            raise ValueError("import buffer: contiguous [18][Lz][n] of the storage type")
+        capi.lb_import_columns(self.h, lattice, x_first, cols.shape[2], cols.data_ptr())
+
     def set_populations(self, f: np.ndarray, lattice: int = 0):
         Lx, Lz = self.shape(lattice)
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, 9, Lz, Lx)

@@ -43,7 +43,8 @@ EXPORTS = ("lb_create", "lb_create_batch", "lb_create_batch_with_allocator", "lb
            "lb_profile", "lb_set_correlations", "lb_correlation", "lb_mode_correlation", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
            "lb_debug_box_muller", "lb_debug_schedule",
-           "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient")
+           "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient", "lb_set_site_map",
+           "lb_export_columns", "lb_import_columns", "lb_debug_fma_rate")
 LB_NOALLOC_MAX_POINTS = 1 << 18
 LB_CORR_MAX_MODES = 16
 
@@ -115,6 +116,10 @@ def load():
             "lb_power_spectrum": [vp, i, i, vp, vp],
             "lb_power_spectrum_noalloc": [vp, i, i, vp, vp],
             "lb_pressure_shift_gradient": [vp, i64, i64, dp, dp],
+            "lb_set_site_map": [vp, i, i, i],
+            "lb_export_columns": [vp, i, i, i, vp],
+            "lb_import_columns": [vp, i, i, i, vp],
+            "lb_debug_fma_rate": [i, dp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -313,6 +318,28 @@ def lb_error_string(code):
 def lb_destroy(h):
     if h:
         load().lb_destroy(h)
+
+
+def lb_debug_fma_rate(precision) -> float:
+    """Measured FMA rate of the current device in flop/s (LB_PREC_FP64: double, LB_PREC_DEV32: float)."""
+    out = ctypes.c_double()
+    _check(load().lb_debug_fma_rate(int(precision), ctypes.byref(out)), "lb_debug_fma_rate")
+    return out.value
+
+
+def lb_set_site_map(h, lattice, x0, Lx_global):
+    _check(load().lb_set_site_map(h, int(lattice), int(x0), int(Lx_global)), "lb_set_site_map")
+
+
+def lb_export_columns(h, lattice, x_first, n_cols, device_ptr):
+    """device_ptr: device address of 18 * Lz * n_cols values of the storage type."""
+    _check(load().lb_export_columns(h, int(lattice), int(x_first), int(n_cols), ctypes.c_void_p(int(device_ptr))),
+           "lb_export_columns")
+
+
+def lb_import_columns(h, lattice, x_first, n_cols, device_ptr):
+    _check(load().lb_import_columns(h, int(lattice), int(x_first), int(n_cols), ctypes.c_void_p(int(device_ptr))),
+           "lb_import_columns")
 
 
 def lb_power_spectrum(field_ptr, Lx, Lz, out_ptr, stream_handle=0):

@@ -167,7 +167,8 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
 // The local part of the transposed step at every site (see the file comment).  alpha: weight of
 // the site's pressure in the loss.  Outputs: fl[18][N] (local sensitivity of the pulled
 // populations), sb[4][N] (sensitivity of sum_l w_l c_l rho^A, rho^B (r + c_l): x, z for A then
-// B), and per block the three parameter partials (G, lambda_s, lambda_d).
+// B), and per block the three parameter partials (G, lambda_s, lambda_d), added to the block's own
+// slot of `partials` (zeroed before the sweep; one fixed summation order, step after step).
 // The state may be single precision (FP32 deviations); the transposed step is evaluated in double
 // precision throughout, since the loss is a small difference of two runs' pressures.
 template <class real, bool NOISE>
@@ -347,9 +348,9 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
       b += red[1][w];
       c += red[2][w];
     }
-    partials[3 * blockIdx.x + 0] = a;
-    partials[3 * blockIdx.x + 1] = b;
-    partials[3 * blockIdx.x + 2] = c;
+    partials[3 * blockIdx.x + 0] += a;
+    partials[3 * blockIdx.x + 1] += b;
+    partials[3 * blockIdx.x + 2] += c;
   }
 }
 
@@ -394,17 +395,23 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const double
   }
 }
 
-__global__ void adj_sum_partials(const double* partials, int n, double sign, double* grad) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// grad[k] = sum over the blocks of partials[3 b + k]: one warp, lanes strided over the blocks, then
+// a fixed butterfly (deterministic).
+__global__ void adj_sum_partials(const double* partials, int n, double* grad) {
   double a = 0, b = 0, c = 0;
-  for (int k = 0; k < n; ++k) {
+  for (int k = threadIdx.x; k < n; k += 32) {
     a += partials[3 * k];
     b += partials[3 * k + 1];
     c += partials[3 * k + 2];
   }
-  grad[0] += sign * a;
-  grad[1] += sign * b;
-  grad[2] += sign * c;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if (threadIdx.x == 0) {
+    grad[0] = a;
+    grad[1] = b;
+    grad[2] = c;
+  }
 }
 
 }  // namespace
@@ -412,24 +419,27 @@ __global__ void adj_sum_partials(const double* partials, int n, double sign, dou
 template <class real>
 cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* fbar_prev, const LatticeDev<real>* lat,
                                 const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
-                                double sign, double* rho, double* fl, double* sb, double* partials, double* grad,
-                                cudaStream_t s) {
-  const int B = 128, nb = (n_sites + B - 1) / B;
-  adj_rho_kernel<real><<<nb, B, 0, s>>>(f_prev, lat, rows, rho);
+                                double* rho, double* fl, double* sb, double* partials, cudaStream_t s) {
+  const int nb = adjoint_blocks(n_sites);
+  adj_rho_kernel<real><<<nb, kAdjBlock, 0, s>>>(f_prev, lat, rows, rho);
   if (noise)
-    adj_local_kernel<real, true><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
+    adj_local_kernel<real, true><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
   else
-    adj_local_kernel<real, false><<<nb, B, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
-  adj_gather_push_kernel<real><<<nb, B, 0, s>>>(lat, rho, fl, sb, alpha, fbar_prev);
-  adj_sum_partials<<<1, 32, 0, s>>>(partials, nb, sign, grad);
+    adj_local_kernel<real, false><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
+  adj_gather_push_kernel<real><<<nb, kAdjBlock, 0, s>>>(lat, rho, fl, sb, alpha, fbar_prev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double* grad, cudaStream_t s) {
+  adj_sum_partials<<<1, 32, 0, s>>>(partials, adjoint_blocks(n_sites), grad);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_adjoint_step<float>(const float*, const double*, double*, const LatticeDev<float>*,
-                                                const RowConst<float>*, int, uint32_t, bool, double, double, double*,
-                                                double*, double*, double*, double*, cudaStream_t);
+                                                const RowConst<float>*, int, uint32_t, bool, double, double*, double*,
+                                                double*, double*, cudaStream_t);
 template cudaError_t launch_adjoint_step<double>(const double*, const double*, double*, const LatticeDev<double>*,
-                                                 const RowConst<double>*, int, uint32_t, bool, double, double, double*,
-                                                 double*, double*, double*, double*, cudaStream_t);
+                                                 const RowConst<double>*, int, uint32_t, bool, double, double*,
+                                                 double*, double*, double*, cudaStream_t);
 
 }  // namespace lbk

@@ -46,6 +46,7 @@ struct lb_ctx {
   int flags = 0;
   bool dev32 = false;
   std::vector<lb_params> params;
+  std::vector<std::pair<int, int>> site_map;  // per lattice: (x0, Lx of the whole lattice), lb_set_site_map
   std::vector<int64_t> f_off, site_off;
   std::vector<int> row_off;
   int64_t n_f = 0, n_sites = 0;
@@ -185,6 +186,8 @@ LatticeDev<real> make_lattice(const lb_params& p, int flags, bool dev, int64_t f
   L.key0 = (uint32_t)(p.seed & 0xffffffffu);
   L.key1 = (uint32_t)(p.seed >> 32);
   L.lattice_id = p.lattice_id;
+  L.site_x0 = 0;
+  L.site_Lx = p.Lx;
   const double lam[9] = {1.0, p.lambda_d, p.lambda_d, p.lambda_e, p.lambda_s, p.lambda_s, p.lambda_q, p.lambda_q,
                          p.lambda_eps};
   bool unit = true;
@@ -268,6 +271,8 @@ int upload_tables(lb_ctx* c) {
   for (int i = 0; i < c->n_lat; ++i) {
     const lb_params& p = c->params[i];
     lat[i] = make_lattice<real>(p, c->flags, c->dev32, c->f_off[i], c->site_off[i], c->row_off[i]);
+    lat[i].site_x0 = c->site_map[i].first;
+    lat[i].site_Lx = c->site_map[i].second;
     const std::vector<RowD> rd = make_rows(p, c->flags, c->dev32);
     double Pbg = 0.0, mA = 0.0, mB = 0.0;
     for (int z = 0; z < p.Lz; ++z) {
@@ -864,6 +869,7 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn
   c->flags = flags;
   c->dev32 = flags & LB_PREC_DEV32;
   c->params.assign(ps, ps + n);
+  for (int i = 0; i < n; ++i) c->site_map.emplace_back(0, ps[i].Lx);
   int64_t foff = 0, soff = 0;
   int roff = 0;
   for (int i = 0; i < n; ++i) {
@@ -953,6 +959,54 @@ int ensure_scratch(lb_ctx* c) {
 
 }  // namespace
 
+namespace lbk {
+
+namespace {
+// Device (or managed) memory that the current device can address without peer access: memory of
+// the current device, or managed memory.
+bool device_pointer_here(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  if (at.type != cudaMemoryTypeDevice) return false;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.device == dev;
+}
+}  // namespace
+
+int power_spectrum_args_ok(const double* field, int Lx, int Lz, const double* out) {
+  if (!field || !out || !is_pow2(Lx) || !is_pow2(Lz) || Lx < 2 || Lz < 2 || Lx > 8192 || Lz > 8192)
+    return LB_ERR_BAD_PARAM;
+  if (!device_pointer_here(field) || !device_pointer_here(out)) return LB_ERR_BAD_PARAM;
+  return LB_OK;
+}
+
+int prepare_power_spectrum_current_device() {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return LB_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  if (!done[dev]) {
+    if (prepare_power_spectrum() != cudaSuccess) return LB_ERR_CUDA;
+    done[dev] = true;
+  }
+  return LB_OK;
+}
+
+}  // namespace lbk
+
 namespace {
 
 // ---- adjoint sweep for the gradient of the mean-pressure shift -----------------------------
@@ -983,13 +1037,13 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   double* rho = want_grad ? (double*)alloc(2 * (size_t)N * sizeof(double)) : nullptr;
   double* fl = want_grad ? (double*)alloc(S * sizeof(double)) : nullptr;
   double* sb = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;
-  const int nb = (N + 127) / 128;
-  double* partials = (double*)alloc((size_t)3 * std::max<int>(nb, (int)c->items.size()) * sizeof(double));
+  double* partials = (double*)alloc((size_t)3 * c->items.size() * sizeof(double));
+  double* gpart = want_grad ? (double*)alloc((size_t)3 * adjoint_blocks(N) * sizeof(double)) : nullptr;
   double* d_grad = (double*)alloc(3 * sizeof(double));
   DiagStats* stats = (DiagStats*)alloc(sizeof(DiagStats));
   int64_t* zero_t = (int64_t*)alloc(sizeof(int64_t));
-  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb)) || !cur || !fields || !pfield || !partials || !d_grad || !stats ||
-      !zero_t) {
+  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb || !gpart)) || !cur || !fields || !pfield || !partials ||
+      !d_grad || !stats || !zero_t) {
     release();
     return LB_ERR_OOM;
   }
@@ -999,6 +1053,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   };
   ok(cudaMemsetAsync(zero_t, 0, sizeof(int64_t), st));
   ok(cudaMemsetAsync(d_grad, 0, 3 * sizeof(double), st));
+  if (want_grad) ok(cudaMemsetAsync(gpart, 0, (size_t)3 * adjoint_blocks(N) * sizeof(double), st));
   auto args = [&](const real* src, real* dst, int64_t k) {
     StepArgs<real> a = step_args<real>(c, 0, 0);
     a.src = src;
@@ -1049,12 +1104,13 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
       for (int64_t k = c0 + len - 1; k >= c0 && e == cudaSuccess; --k) {
         ok(launch_adjoint_step<real>(ring + (k - c0) * S, fb + fcur * S, fb + (1 - fcur) * S,
                                      (const LatticeDev<real>*)c->d_lat, (const RowConst<real>*)c->d_rows, N,
-                                     (uint32_t)k, noise != NOISE_OFF, alpha, 1.0, rho, fl, sb, partials, d_grad, st));
+                                     (uint32_t)k, noise != NOISE_OFF, alpha, rho, fl, sb, gpart, st));
         fcur = 1 - fcur;
       }
     }
   }
   if (e == cudaSuccess && want_grad) {
+    ok(launch_adjoint_gradient(gpart, N, d_grad, st));
     ok(cudaMemcpyAsync(grad, d_grad, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     ok(cudaStreamSynchronize(st));
   }
@@ -1076,6 +1132,7 @@ extern "C" {
 int lb_pressure_shift_gradient(lb_ctx* c, int64_t steps, int64_t ckpt_every, double grad[3], double* loss) {
   if (!c || steps < 1 || ckpt_every < 1 || ckpt_every > steps) return LB_ERR_BAD_PARAM;
   if (c->n_lat != 1 || (c->flags & (LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC))) return LB_ERR_STATE;
+  if (c->site_map[0] != std::make_pair(0, c->params[0].Lx)) return LB_ERR_STATE;
   if (steps >= ((int64_t)1 << 31)) return LB_ERR_BAD_PARAM;
   int rc = sync_and_check(c);
   if (rc) return rc;
@@ -1444,6 +1501,62 @@ int lb_set_populations(lb_ctx* c, int lattice, const double* in, size_t n) {
   return sync_and_check(c);
 }
 
+int lb_set_site_map(lb_ctx* c, int lattice, int x0, int Lx_global) {
+  if (!lattice_ok(c, lattice)) return LB_ERR_BAD_PARAM;
+  const lb_params& p = c->params[lattice];
+  if (Lx_global < p.Lx || x0 < 0 || x0 >= Lx_global || (int64_t)Lx_global * p.Lz >= ((int64_t)1 << 31))
+    return LB_ERR_BAD_PARAM;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  c->site_map[lattice] = {x0, Lx_global};
+  // the lattice's device constants, rebuilt with the new map (graphs read them at run time)
+  if (c->dev32) {
+    LatticeDev<float> L = make_lattice<float>(p, c->flags, true, c->f_off[lattice], c->site_off[lattice],
+                                              c->row_off[lattice]);
+    L.site_x0 = x0;
+    L.site_Lx = Lx_global;
+    if (cudaMemcpy((LatticeDev<float>*)c->d_lat + lattice, &L, sizeof(L), cudaMemcpyHostToDevice) != cudaSuccess)
+      return LB_ERR_CUDA;
+  } else {
+    LatticeDev<double> L = make_lattice<double>(p, c->flags, false, c->f_off[lattice], c->site_off[lattice],
+                                                c->row_off[lattice]);
+    L.site_x0 = x0;
+    L.site_Lx = Lx_global;
+    if (cudaMemcpy((LatticeDev<double>*)c->d_lat + lattice, &L, sizeof(L), cudaMemcpyHostToDevice) != cudaSuccess)
+      return LB_ERR_CUDA;
+  }
+  return LB_OK;
+}
+
+namespace {
+int columns_impl(lb_ctx* c, int lattice, int x_first, int n_cols, void* buf, bool export_) {
+  if (!lattice_ok(c, lattice) || !buf) return LB_ERR_BAD_PARAM;
+  const lb_params& p = c->params[lattice];
+  if (n_cols < 1 || x_first < 0 || x_first > p.Lx - n_cols) return LB_ERR_BAD_PARAM;
+  cudaPointerAttributes at;
+  int dev = -1;
+  if (cudaPointerGetAttributes(&at, buf) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ERR_BAD_PARAM;
+  }
+  if (!(at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev)))
+    return LB_ERR_BAD_PARAM;
+  cudaError_t e = c->dev32 ? launch_columns<float>((float*)c->f[c->cur] + c->f_off[lattice], p.Lx, p.Lz, x_first,
+                                                   n_cols, (float*)buf, export_, c->stream)
+                           : launch_columns<double>((double*)c->f[c->cur] + c->f_off[lattice], p.Lx, p.Lz, x_first,
+                                                    n_cols, (double*)buf, export_, c->stream);
+  return cuda_err(e);
+}
+}  // namespace
+
+int lb_export_columns(lb_ctx* c, int lattice, int x_first, int n_cols, void* device_out) {
+  return columns_impl(c, lattice, x_first, n_cols, device_out, true);
+}
+
+int lb_import_columns(lb_ctx* c, int lattice, int x_first, int n_cols, const void* device_in) {
+  return columns_impl(c, lattice, x_first, n_cols, const_cast<void*>(device_in), false);
+}
+
 int lb_reset_statistics(lb_ctx* c) {
   if (!c) return LB_ERR_BAD_PARAM;
   int rc = sync_and_check(c);
@@ -1505,39 +1618,10 @@ void lb_destroy(lb_ctx* c) {
   delete c;
 }
 
-namespace {
-bool device_pointer(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-int prepare_power_spectrum_once() {
-  static std::mutex mu;
-  static bool done = false;
-  std::lock_guard<std::mutex> g(mu);
-  if (!done) {
-    if (prepare_power_spectrum() != cudaSuccess) return LB_ERR_CUDA;
-    done = true;
-  }
-  return LB_OK;
-}
-
-int power_spectrum_args_ok(const double* field, int Lx, int Lz, const double* out) {
-  if (!field || !out || !is_pow2(Lx) || !is_pow2(Lz) || Lx < 2 || Lz < 2 || Lx > 8192 || Lz > 8192)
-    return LB_ERR_BAD_PARAM;
-  if (!device_pointer(field) || !device_pointer(out)) return LB_ERR_BAD_PARAM;
-  return LB_OK;
-}
-}  // namespace
-
 int lb_power_spectrum(const double* field, int Lx, int Lz, double* out, void* stream) {
   int rc = power_spectrum_args_ok(field, Lx, Lz, out);
   if (rc) return rc;
-  rc = prepare_power_spectrum_once();
+  rc = prepare_power_spectrum_current_device();
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   void* tmp = nullptr;
@@ -1613,6 +1697,16 @@ int lb_debug_schedule(int n_lat, const int* Lx, const int* Lz, int tile_x, int r
   }
   std::copy(off.begin(), off.end(), off_out);
   std::copy(nbr.begin(), nbr.end(), nbr_out);
+  return LB_OK;
+}
+
+int lb_debug_fma_rate(int precision, double* flops_per_s) {
+  if ((precision != LB_PREC_FP64 && precision != LB_PREC_DEV32) || !flops_per_s) return LB_ERR_BAD_PARAM;
+  cudaError_t e = measure_fma_rate(precision == LB_PREC_FP64, flops_per_s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_err(e);
+  }
   return LB_OK;
 }
 

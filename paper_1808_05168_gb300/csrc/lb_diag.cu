@@ -8,6 +8,8 @@
 // transform) and one block per strip of adjacent q_x transforms the columns along z, squares,
 // scales by 1 / (Lx Lz) and adds the result to double-precision Kahan (compensated)
 // accumulators.
+#include <algorithm>
+
 #include "lb_internal.cuh"
 
 namespace lbk {
@@ -531,7 +533,81 @@ __global__ void init_rest_kernel(real* f, BgParams bp) {
   }
 }
 
+// Columns x_first .. x_first + n - 1 of every (species, link) plane, to (to_buf) or from a packed
+// buffer [18][Lz][n]; thread k handles element k of the buffer.
+template <class real>
+__global__ void columns_kernel(real* f, int Lx, int Lz, int x_first, int n, real* buf, bool to_buf) {
+  const int64_t total = (int64_t)18 * Lz * n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = k / n;  // plane * Lz + z
+    const int j = (int)(k - row * n);
+    real* g = f + row * Lx + x_first + j;
+    if (to_buf) buf[k] = *g;
+    else *g = buf[k];
+  }
+}
+
+// Fused multiply-add throughput: eight independent chains per thread x <- x a + b (|a| < 1, so the
+// values stay bounded), enough resident warps to fill every pipe; the sum keeps the chains live.
+template <class T>
+__global__ void fma_rate_kernel(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k) * (T)1e-6;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  T sum = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 }  // namespace
+
+cudaError_t measure_fma_rate(bool fp64, double* flops_per_s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int threads = 256, blocks = 8 * sms, iters = fp64 ? 2048 : 16384;
+  void* out = nullptr;
+  e = cudaMalloc(&out, (size_t)threads * blocks * sizeof(double));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto run = [&]() {
+    if (fp64) fma_rate_kernel<double><<<blocks, threads>>>((double*)out, iters, 0.9999999, 1e-9);
+    else fma_rate_kernel<float><<<blocks, threads>>>((float*)out, iters, 0.9999f, 1e-6f);
+  };
+  float best = 1e30f;
+  if ((e = cudaEventCreate(&e0)) == cudaSuccess && (e = cudaEventCreate(&e1)) == cudaSuccess) {
+    run();  // warm-up
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+      cudaEventRecord(e0);
+      run();
+      cudaEventRecord(e1);
+      e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess) best = std::min(best, ms);
+    }
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e == cudaSuccess) *flops_per_s = 2.0 * 8 * iters * (double)threads * blocks / (best * 1e-3);
+  return e;
+}
+
+template <class real>
+cudaError_t launch_columns(real* f, int Lx, int Lz, int x_first, int n, real* buf, bool to_buf, cudaStream_t s) {
+  const int64_t total = (int64_t)18 * Lz * n;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
+  columns_kernel<real><<<blocks, 256, 0, s>>>(f, Lx, Lz, x_first, n, buf, to_buf);
+  return cudaGetLastError();
+}
 
 template <class real>
 cudaError_t prepare_sf(size_t smem_rows, size_t smem_cols) {
@@ -583,18 +659,23 @@ cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Columns per block of the one-snapshot column pass (shared memory at most 160 KB).
+// Dynamic shared memory of the one-snapshot passes for transforms of up to 8192 points: the
+// points plus half as many twiddles, 16 bytes each (196,608 bytes, within the 227 KB a block may
+// opt in to).
+constexpr size_t kPsSmemMax = (8192 + 4096) * sizeof(Cplx<double>);
+
+// Columns per block of the one-snapshot column pass: up to 16, as many as fit in kPsSmemMax (one
+// column of 8192 points fills it).
 static int ps_column_strip(int Lx, int Lz) {
   int cq = 16;
-  while (cq > 1 && ((size_t)Lz * cq + Lz / 2) * sizeof(Cplx<double>) > 160 * 1024) cq >>= 1;
+  while (cq > 1 && ((size_t)Lz * cq + Lz / 2) * sizeof(Cplx<double>) > kPsSmemMax) cq >>= 1;
   return cq < Lx ? cq : Lx;
 }
 
 cudaError_t prepare_power_spectrum() {
-  cudaError_t e = cudaFuncSetAttribute(ps_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((8192 + 4096) * sizeof(Cplx<double>)));
+  cudaError_t e = cudaFuncSetAttribute(ps_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPsSmemMax);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(ps_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  return cudaFuncSetAttribute(ps_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPsSmemMax);
 }
 
 cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* out, void* tmp, cudaStream_t s) {
@@ -711,6 +792,7 @@ cudaError_t launch_corr(const CorrPlan& p, const real* fields, const void* tmp, 
   template cudaError_t launch_to_absolute<real>(const real*, const BgParams&, double*, cudaStream_t);        \
   template cudaError_t launch_from_absolute<real>(const double*, const BgParams&, real*, cudaStream_t);      \
   template cudaError_t launch_init_rest<real>(real*, const BgParams&, cudaStream_t);                         \
+  template cudaError_t launch_columns<real>(real*, int, int, int, int, real*, bool, cudaStream_t);           \
   template cudaError_t launch_profiles<real>(const DiagLattice*, const int*, int, const real*, const real*,    \
                                              double*, double*, cudaStream_t);                                \
   template cudaError_t launch_corr<real>(const CorrPlan&, const real*, const void*, double*, double*, cudaStream_t);

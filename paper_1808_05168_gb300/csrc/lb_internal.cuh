@@ -36,6 +36,9 @@ struct LatticeDev {
   int row_off;       // offset into the per-row table
   int flags;         // DF_* bits
   uint32_t key0, key1, lattice_id, pad;
+  // Philox site counter of column x, row z: z * site_Lx + (x + site_x0) mod site_Lx; the
+  // identity (0, Lx) unless the lattice is an x-slab window of a wider one (lb_set_site_map)
+  int site_x0, site_Lx;
   real lam[9];       // relaxation rate per moment (Eq. MRT)
   real omh[9];       // 1 - lambda_a / 2 (second-order forcing)
   real G;            // coupling (Eq. aNI)
@@ -214,16 +217,36 @@ __device__ __forceinline__ void sincos_ftz(float x, float& s, float& c) {
   asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
+// 1 / rho of a site's total density: the hardware reciprocal in single precision (at most 1 ulp
+// from the exact value; rho is near rho_bar = 1, never subnormal), refined by Newton steps in
+// double.
+__device__ __forceinline__ float site_reciprocal(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double site_reciprocal(double x) {
+  // two Newton steps y <- y + y (1 - x y) from the single-precision seed (relative error 2^-23
+  // -> 2^-46 -> the last bit); x is near 1
+  double y = (double)site_reciprocal((float)x);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 // Tables of the double-precision Box-Muller (the table-driven method of P. T. P. Tang for the
-// logarithm and for sine/cosine): cs[j] = (cos, sin)(2 pi j / 1024) and ln[j] = (-2 ln y_j,
-// 1 / y_j) with y_j = 3/4 + j/256, j = 0 .. 192.  The single-precision path needs none.
+// logarithm and for sine/cosine): cs[j] = (cos, sin)(2 pi j / 1024), ln[j] = (-2 ln y_j, 1 / y_j)
+// with y_j = 3/4 + j/256, j = 0 .. 192, and the exponent's share ex[k] = (-2 n ln2_hi,
+// -2 n ln2_lo) for n = k - 24, k = 0 .. 24 (ln 2 = ln2_hi + ln2_lo, ln2_hi rounded to 24 bits, so
+// the first product is exact).  The single-precision path needs none.
 template <class real>
 struct BmTables {};
 template <>
 struct BmTables<double> {
   double2 cs[1024];
   double2 ln[193];
+  double2 ex[25];
 };
+constexpr double kLn2Hi = 0.693147182464599609375, kLn2Lo = -1.904654299957768e-09;
 
 // All threads of the block fill the tables (from the correctly rounded library functions); the
 // caller synchronises the block before use.
@@ -239,6 +262,10 @@ __device__ __forceinline__ void fill_bm_tables(BmTables<real>* T) {
       const double y = 0.75 + (double)j / 256.0;
       T->ln[j] = make_double2(-2.0 * log(y), 1.0 / y);  // -2 ln y_j (an exact scaling), 1 / y_j
     }
+    for (int k = threadIdx.x; k < 25; k += blockDim.x) {
+      const double n = (double)(k - 24);
+      T->ex[k] = make_double2(n * (-2.0 * kLn2Hi), n * (-2.0 * kLn2Lo));
+    }
   }
 }
 
@@ -251,7 +278,9 @@ __device__ __forceinline__ void fill_bm_tables(BmTables<real>* T) {
 // phi = 2 pi u2 - pi.  Absolute error below 3e-6 on a normal.
 // FP64, table-driven: u = m 2^-24 with m = 2 (k mod 2^23) + 1.  ln u1 = (e - 24) ln 2 + ln y with
 // m = 2^e y, y in [3/4, 3/2); ln y = ln y_j + ln(1 + t), y_j the table point nearest y and
-// t = (y - y_j) / y_j, |t| <= 2^-9 / (3/4), from its series to t^6.  The angle 2 pi m 2^-24 is
+// t = y (1 / y_j) - 1 (one fused multiply-add; exact where y_j = 1, i.e. wherever u1 is near 1
+// and -2 ln u1 small), |t| <= 2^-9 / (3/4), from its series to t^6; (e - 24) times the two parts
+// of -2 ln 2 comes from a table.  The angle 2 pi m 2^-24 is
 // the table angle 2 pi (m >> 14) / 1024 plus d = 2 pi (m mod 2^14) 2^-24 < 6.2e-3, whose sine and
 // cosine come from their series (to d^5 and d^6) and the addition theorems.  Within a few units
 // in the last place of the library functions.
@@ -276,8 +305,6 @@ __device__ __forceinline__ void normal_pair<float>(uint32_t a, uint32_t b, float
 template <>
 __device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, double& n0, double& n1,
                                                     const BmTables<double>* T) {
-  // ln 2 split so that (e - 24) ln2_hi is exact (ln2_hi: ln 2 rounded to 24 bits)
-  const double ln2_hi = 0.693147182464599609375, ln2_lo = -1.904654299957768e-09;
   const uint32_t m1 = 2u * (a & 0x7FFFFFu) + 1u;
   const unsigned long long bits = (unsigned long long)__double_as_longlong((double)m1);
   int e = (int)(bits >> 52) - 1023;
@@ -293,14 +320,13 @@ __device__ __forceinline__ void normal_pair<double>(uint32_t a, uint32_t b, doub
     j = 64 + (int)((mant + (1ull << 43)) >> 44);
   }
   const double2 L = T->ln[j];
-  const double yj = fma((double)j, 0.00390625, 0.75);
-  const double t = (y - yj) * L.y;
+  const double t = fma(y, L.y, -1.0);
   // -2 ln u1 directly: every term and coefficient scaled by -2, a power of two, so the result is
   // bit for bit -2 times the logarithm formed term by term
   const double p2 =
       fma(t, fma(t, fma(t, fma(t, fma(t, 1.0 / 3.0, -0.4), 0.5), -2.0 / 3.0), 1.0), -2.0);  // -2 p(t)
-  const double ne = (double)(e - 24);
-  const double m2lnu = fma(ne, -2.0 * ln2_hi, L.x + fma(t, p2, ne * (-2.0 * ln2_lo)));
+  const double2 E = T->ex[e];  // e - 24 in -24 .. 0
+  const double m2lnu = E.x + (L.x + fma(t, p2, E.y));
   const double r = sqrt(m2lnu);
   // angle
   const uint32_t m2 = 2u * (b & 0x7FFFFFu) + 1u;
@@ -549,20 +575,39 @@ template <class real>
 cudaError_t launch_from_absolute(const double* in, const BgParams& bp, real* f, cudaStream_t s);
 template <class real>
 cudaError_t launch_init_rest(real* f, const BgParams& bp, cudaStream_t s);
+// Columns x_first .. x_first + n - 1 of all 18 planes of a stored state f (Lx x Lz) to or from a
+// packed buffer [18][Lz][n] (x-slab halo exchange).
+template <class real>
+cudaError_t launch_columns(real* f, int Lx, int Lz, int x_first, int n, real* buf, bool to_buf, cudaStream_t s);
 
 // Power spectrum of one real double-precision field (Lx, Lz powers of two, 2..8192), with a
-// caller-provided scratch of Lx * Lz complex doubles; prepare once before use.
+// caller-provided scratch of Lx * Lz complex doubles; prepare once per device before use.
 cudaError_t prepare_power_spectrum();
 cudaError_t launch_power_spectrum(const double* field, int Lx, int Lz, double* out, void* tmp, cudaStream_t s);
 
+// Host-side checks shared by the two spectrum entry points (lb_api.cu): LB_ERR_BAD_PARAM unless
+// Lx and Lz are powers of two in 2..8192 and field and out are device (or managed) memory of the
+// current device; LB_OK otherwise.
+int power_spectrum_args_ok(const double* field, int Lx, int Lz, const double* out);
+// prepare_power_spectrum once per device, with that device current (LB_OK or LB_ERR_CUDA).
+int prepare_power_spectrum_current_device();
+
 // One adjoint step (lb_adjoint.cu): from fbar (sensitivity to f*_k) and the forward state f_prev
-// = f*_{k-1}, write fbar_prev and add sign * (this step's gradient share) to grad[3].
-// The sensitivities (fbar, rho, fl, sb) are double precision for either state precision.
+// = f*_{k-1}, write fbar_prev and add this step's gradient share, block by block, to partials
+// (3 doubles per block of adjoint_blocks(n_sites), zeroed before the sweep); then
+// launch_adjoint_gradient sums the blocks into grad[3].  The sensitivities (fbar, rho, fl, sb) are
+// double precision for either state precision.
+constexpr int kAdjBlock = 128;
+inline int adjoint_blocks(int n_sites) { return (n_sites + kAdjBlock - 1) / kAdjBlock; }
 template <class real>
 cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* fbar_prev, const LatticeDev<real>* lat,
                                 const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
-                                double sign, double* rho, double* fl, double* sb, double* partials, double* grad,
-                                cudaStream_t s);
+                                double* rho, double* fl, double* sb, double* partials, cudaStream_t s);
+cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double* grad, cudaStream_t s);
+
+// Measured fused multiply-add rate of the current device (FP64 or FP32 scalar FMA, 2 flops each),
+// best of five timed launches after a warm-up (lb_diag.cu).
+cudaError_t measure_fma_rate(bool fp64, double* flops_per_s);
 
 template <class real>
 cudaError_t launch_debug_normals(const uint32_t* words, int64_t n_pairs, double* out, cudaStream_t s);

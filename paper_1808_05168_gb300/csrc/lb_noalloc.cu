@@ -26,16 +26,6 @@ static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxPoints];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
-bool g_prepared[kMaxDevices] = {};
-
-bool is_device_pointer(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 // Once per device, with that device current: the array's device address (the host-side name of
 // g_noalloc_scratch is only a stand-in and must never reach a kernel) and the kernels'
@@ -43,32 +33,31 @@ bool is_device_pointer(const void* p) {
 int setup_current_device(void** scratch) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LB_ERR_CUDA;
-  std::lock_guard<std::mutex> g(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return LB_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return LB_ERR_CUDA;
+      }
+      g_scratch_addr[dev] = p;
     }
-    g_scratch_addr[dev] = p;
+    *scratch = g_scratch_addr[dev];
   }
-  if (!g_prepared[dev]) {
-    if (lbk::prepare_power_spectrum() != cudaSuccess) return LB_ERR_CUDA;
-    g_prepared[dev] = true;
-  }
-  *scratch = g_scratch_addr[dev];
-  return LB_OK;
+  return lbk::prepare_power_spectrum_current_device();
 }
 
 }  // namespace
 
 extern "C" int lb_power_spectrum_noalloc(const double* field, int Lx, int Lz, double* out, void* stream) {
-  const bool pow2 = Lx > 0 && Lz > 0 && (Lx & (Lx - 1)) == 0 && (Lz & (Lz - 1)) == 0;
-  if (!field || !out || !pow2 || Lx < 2 || Lz < 2) return LB_ERR_BAD_PARAM;
+  // the checks of lb_power_spectrum (sizes 2..8192, powers of two, device memory of the current
+  // device: LB_ERR_BAD_PARAM), then the array's own limit (LB_ERR_SIZE)
+  int rc = lbk::power_spectrum_args_ok(field, Lx, Lz, out);
+  if (rc) return rc;
   if ((long long)Lx * Lz > kNoAllocMaxPoints) return LB_ERR_SIZE;
-  if (!is_device_pointer(field) || !is_device_pointer(out)) return LB_ERR_BAD_PARAM;
   void* scratch = nullptr;
-  int rc = setup_current_device(&scratch);
+  rc = setup_current_device(&scratch);
   if (rc) return rc;
   if (lbk::launch_power_spectrum(field, Lx, Lz, out, scratch, (cudaStream_t)stream) != cudaSuccess)
     return LB_ERR_CUDA;

@@ -409,7 +409,7 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
   const P sz = add2(fma2(c9, sub2(n, s), mul2(c36, sub2(add2(ne, nw), add2(se, sw)))), pr(rc.dbgA, rc.dbgB));
   const P rs = add2(pr(rc.bgA, rc.bgB), d);  // (rho^A, rho^B)
   const real rho = rs.x + rs.y;
-  const real inv = real(1) / rho;
+  const real inv = site_reciprocal(rho);
   // non-ideal forces: F^A = -G rho^A sum(rho^B), F^B = -G rho^B sum(rho^A)
   const real gA = -K.G * rs.x, gB = -K.G * rs.y;
   const real FnAx = gA * sx.y, FnAz = gA * sz.y, FnBx = gB * sx.x, FnBz = gB * sz.x;
@@ -581,6 +581,10 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   const int flags = L.flags;
   const RowConst<real>* rows = a.rows + L.row_off;
   const int z0 = it.z0, z1 = it.z1;
+  // noise counter of this thread's site: z * L.site_Lx + (x + L.site_x0) mod L.site_Lx (the
+  // lattice's own site index z Lx + x unless it is an x-slab window of a wider lattice), carried
+  // from row to row
+  uint32_t site = (uint32_t)(z0 * L.site_Lx + (x + L.site_x0) % L.site_Lx);
 
   auto stage_row = [&](int r) {
     if (r >= 0 && r < Lz && r <= z1) {
@@ -645,24 +649,25 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
       // the variants are inlined; the branches are uniform over the block (one lattice per item)
-      auto site = [&](auto unit, auto astar) {
+      auto site_at = [&](auto unit, auto astar) {
         Pr<real> v[9];
         read_generic(sb, W, tid + 1, below, above, k9, k36, v);
         Mom<real> m = moments<real>(v);
         if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
-            K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
+            K, rows[z], m, ring, bc, bu, bd, site, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags, bm);
       };
       if (flags & DF_UNIT) {
-        if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>());
-        else site(BoolC<true>(), BoolC<false>());
+        if (flags & DF_ASTAR) site_at(BoolC<true>(), BoolC<true>());
+        else site_at(BoolC<true>(), BoolC<false>());
       } else {
-        if (flags & DF_ASTAR) site(BoolC<false>(), BoolC<true>());
-        else site(BoolC<false>(), BoolC<false>());
+        if (flags & DF_ASTAR) site_at(BoolC<false>(), BoolC<true>());
+        else site_at(BoolC<false>(), BoolC<false>());
       }
     }
+    site += (uint32_t)L.site_Lx;
   }
   cp_wait<0>();  // nothing may land in shared memory after the item
   if (SAMPLE) block_partials(acc_p, acc_a, acc_b, red, a.partials + 3 * item_index);
@@ -745,6 +750,10 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   const int flags = L.flags;
   const RowConst<real>* rows = a.rows + L.row_off;
   const int z0 = it.z0, z1 = it.z1;
+  // noise counter of this thread's site: z * L.site_Lx + (x + L.site_x0) mod L.site_Lx (the
+  // lattice's own site index z Lx + x unless it is an x-slab window of a wider lattice), carried
+  // from row to row
+  uint32_t site = (uint32_t)(z0 * L.site_Lx + (x + L.site_x0) % L.site_Lx);
   const unsigned row_bytes = 18u * (unsigned)(nact + 2 * PAD) * (unsigned)sizeof(real);
 
   // copy k of row r (plane k, or run k on the tensor path; its source row, reflected at the
@@ -878,24 +887,24 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
       const int r0 = z * Lx + x;
       // the variants are inlined; the branches are uniform over the block (one lattice per item,
       // one row at a time): unit rates, a*, and interior rows (no wall within one link)
-      auto site = [&](auto unit, auto astar, auto inner) {
+      auto site_at = [&](auto unit, auto astar, auto inner) {
         constexpr bool IN = decltype(inner)::value;
         Pr<real> v[9];
         read_bulk<real, SW>(sb, tid + PAD, IN || below, IN || above, k9, k36, v);
         Mom<real> m = moments<real>(v);
         if (IN) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
         site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
-            K, rows[z], m, ring, bc, bu, bd, (uint32_t)r0, step,
+            K, rows[z], m, ring, bc, bu, bd, site, step,
             a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
             g + 9 * LzLx + r0, LzLx, flags, bm);
       };
       auto rates = [&](auto inner) {
         if (flags & DF_UNIT) {
-          if (flags & DF_ASTAR) site(BoolC<true>(), BoolC<true>(), inner);
-          else site(BoolC<true>(), BoolC<false>(), inner);
+          if (flags & DF_ASTAR) site_at(BoolC<true>(), BoolC<true>(), inner);
+          else site_at(BoolC<true>(), BoolC<false>(), inner);
         } else {
-          if (flags & DF_ASTAR) site(BoolC<false>(), BoolC<true>(), inner);
-          else site(BoolC<false>(), BoolC<false>(), inner);
+          if (flags & DF_ASTAR) site_at(BoolC<false>(), BoolC<true>(), inner);
+          else site_at(BoolC<false>(), BoolC<false>(), inner);
         }
       };
       if (below && above) rates(BoolC<true>());
@@ -904,6 +913,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     sp = sc;
     sc = sn;
     sn = sn + 1 == NSI ? 0 : sn + 1;
+    site += (uint32_t)L.site_Lx;
   }
   if (!ok) {
     // drain the input rows still in flight (bounded), then stop

@@ -1,8 +1,9 @@
 """Parity at the benchmark's full sizes and launch configuration.
 
 The ensemble (768 lattices, 66.8 M sites) runs exactly as the benchmark times it (FP32
-deviations, CUDA graphs, autotuned tile); a set of its lattices is then compared in full with
-the oracle run from the same rest state.  The 8192 x 2048 lattice is checked one step at a time
+deviations, CUDA graphs, the persistent launch of the plain steps, autotuned tile, a sample every
+100 steps, advanced one sample step and 99 plain steps at a time); a set of its lattices is then
+compared in full with the oracle run from the same rest state.  The 8192 x 2048 lattice is checked one step at a time
 on column windows: a site's update depends only on the state within two columns, so the oracle
 on a 5-column window (with the large lattice's noise counters) gives that column exactly.
 """
@@ -27,28 +28,51 @@ def background(Lx, Lz, grad_c0):
     return b
 
 
-def oracle_of(p, Lx=None):
+def oracle_of(p, Lx=None, omp=False):
     return oracle.OracleLattice(Lx or p.Lx, p.Lz, lambda_s=p.lambda_s, lambda_d=p.lambda_d, lambda_e=p.lambda_e,
                                 lambda_q=p.lambda_q, lambda_eps=p.lambda_eps, kT=p.kT, G=p.G, grad_c0=p.grad_c0,
-                                seed=p.seed, lattice_id=p.lattice_id)
+                                seed=p.seed, lattice_id=p.lattice_id, omp=omp)
 
 
 def test_ensemble_in_benchmark_configuration():
+    """201 steps as the benchmark runs them: sample steps 0, 100 and 200 (ordinary launches with
+    their diagnostics kernels), each of the two runs of 99 plain steps in between one persistent
+    launch (items of the autotuned tile handed out in order, per-item dependency waits), all in
+    CUDA graphs.  Lattices of every size and gradient and both ends of the ids against the
+    oracle: populations (1e-5 of the deviations), S_c(q_x, q_z) and the other three fields'
+    spectra over the whole q grid (the bar of the spectra tests), and the mean pressure (1e-7)."""
     lattices = workloads.c3()
-    steps = 12
-    with Simulation(lattices, precision="dev32", graph=True, autotune=True) as sim:
+    with Simulation(lattices, precision="dev32", graph=True, persistent=True, autotune=True) as sim:
         sim.set_sampling(0, 100)
-        sim.step(steps)
-        picks = [0, 1, 2, 5, 10, 11, 383, 766, 767]  # every size, every gradient, both ends of the ids
-        got = {i: sim.populations(i) for i in picks}
+        for _ in range(2):
+            sim.step(1)
+            sim.step(99)
+        sim.step(1)
+        assert sim.time == 201
+        picks = [0, 2, 5, 8, 11, 383, 766]  # every size, every gradient, both ends of the ids
+        got = {i: (sim.populations(i), {f: sim.structure_factor(f, lattice=i) for f in ("rho", "c", "ux", "uz")},
+                   sim.mean_pressure(i)) for i in picks}
     for i in picks:
         p = lattices[i]
-        o = oracle_of(p)
-        o.step(steps)
+        o = oracle_of(p, omp=True)
+        o.set_sampling(0, 100)
+        o.step(201)
         want = o.populations()
         dev = want - background(p.Lx, p.Lz, p.grad_c0)
-        err = np.max(np.abs(got[i] - want))
+        f32, S, (last, avg) = got[i]
+        err = np.max(np.abs(f32 - want))
         assert err <= 1e-5 * np.max(np.abs(dev)), (i, err, np.max(np.abs(dev)))
+        for f, (Sg, n) in S.items():
+            Sw, no = o.structure_factor(f)
+            assert n == no == 3, (i, f, n, no)
+            # absolute part: the noise-dominated modes; relative part: the q_x = 0 modes, which carry
+            # the deterministic density and concentration profiles -- the FP32 deviations behind
+            # them carry the populations' bar (1e-5), doubled in |phi(q)|^2, plus FP32 transforms
+            err = np.abs(Sg - Sw)
+            assert np.all(err <= 2e-3 * Sw.mean() + 5e-5 * np.abs(Sw)), (
+                i, f, float(np.max(err / (2e-3 * Sw.mean() + 5e-5 * np.abs(Sw)))), float(np.max(err / np.abs(Sw).max())))
+        olast, oavg, _ = o.mean_pressure()
+        assert abs(last - olast) <= 1e-7 * abs(olast) and abs(avg - oavg) <= 1e-7 * abs(oavg), (i, last, olast)
 
 
 @pytest.mark.parametrize("prec", ["dev32", "fp64"])
@@ -83,7 +107,7 @@ def test_large_lattice_column_windows(prec):
 @pytest.fixture(scope="module")
 def c2_oracle():
     (p,) = workloads.c2()
-    o = oracle_of(p)
+    o = oracle_of(p, omp=True)
     o.set_sampling(40, 10)
     o.step(60)
     return p, o

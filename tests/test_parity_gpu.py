@@ -80,16 +80,25 @@ def test_fp64_nonideal_ragged_tiles(tile):
     assert_fp64_parity(got, o.populations())
 
 
-@pytest.mark.parametrize("variant", ["no_astar", "wall_fixed", "noise_loc"])
-def test_fp64_variants(variant):
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+@pytest.mark.parametrize("variant", ["no_astar", "wall_fixed", "noise_loc", "all_three"])
+def test_variants(variant, prec):
+    """The method's variants, each a kernel instantiation of its own, in both precisions, 1000
+    steps: a* off (footnote to Eq. ne-acc), fixed wall composition of the non-ideal force's ghost
+    rows (Sec. II.A), noise variances from the local densities (loc, Sec. III.B), and all three
+    together; G > 0 and rates != 1 so that every term is exercised."""
     p = LatticeParams(40, 12, lambda_s=1.2, lambda_d=1.1, kT=1e-4, G=0.6, grad_c0=0.3 / 12, seed=3)
-    kw = {"no_astar": dict(astar=False), "wall_fixed": dict(wall_fixed=True), "noise_loc": dict(noise_loc=True)}
-    with Simulation(p, precision="fp64", **kw[variant]) as sim:
-        sim.step(200)
+    kw = {"no_astar": dict(astar=False), "wall_fixed": dict(wall_fixed=True), "noise_loc": dict(noise_loc=True),
+          "all_three": dict(astar=False, wall_fixed=True, noise_loc=True)}
+    with Simulation(p, precision=prec, **kw[variant]) as sim:
+        sim.step(1000)
         got = sim.populations()
     o = oracle_of(p, **kw[variant])
-    o.step(200)
-    assert_fp64_parity(got, o.populations())
+    o.step(1000)
+    if prec == "fp64":
+        assert_fp64_parity(got, o.populations())
+    else:
+        assert_dev32_parity(got, o.populations(), background(p.Lx, p.Lz, p.grad_c0))
 
 
 C2_SMALL = LatticeParams(64, 32, lambda_s=1.0, lambda_d=0.8, kT=1e-5, G=0.5, grad_c0=0.5 / 32, seed=2)
@@ -345,6 +354,17 @@ def test_errors_on_device():
         assert e.value.code == capi.LB_ERR_SIZE
         with pytest.raises(capi.LBError):
             sim.populations(1)
+
+
+def test_measured_fma_rates_are_plausible():
+    """lb_debug_fma_rate, the ceiling of the FP64 path: GB300's FP64 FMA rate is about 1.25
+    TFLOP/s and its FP32 one about 80 TFLOP/s (152 SMs, 128 lanes, about 2 GHz)."""
+    f64 = capi.lb_debug_fma_rate(capi.LB_PREC_FP64)
+    f32 = capi.lb_debug_fma_rate(capi.LB_PREC_DEV32)
+    assert 0.5e12 < f64 < 2.5e12, f64
+    assert 20e12 < f32 < 120e12, f32
+    with pytest.raises(capi.LBError):
+        capi.lb_debug_fma_rate(7)
 
 
 def test_box_muller_normals_of_both_precisions():

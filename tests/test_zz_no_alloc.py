@@ -16,8 +16,9 @@ def test_noalloc_spectrum_matches_allocating_one_on_consecutive_calls():
     import torch
     stream = torch.cuda.current_stream().cuda_stream
     rng = np.random.default_rng(2024)
-    # two calls in a row: a larger field first, then a smaller one that reuses part of the array
-    for Lx, Lz in [(256, 128), (64, 32)]:
+    # calls in a row: a field that fills the array, a smaller one that reuses part of it, and the
+    # longest columns (8192 points, one per block)
+    for Lx, Lz in [(256, 1024), (64, 32), (32, 8192), (2, 8192)]:
         phi = torch.from_numpy(rng.standard_normal((Lz, Lx))).cuda()
         want = torch.empty_like(phi)
         got = torch.full_like(phi, float("nan"))
@@ -29,8 +30,15 @@ def test_noalloc_spectrum_matches_allocating_one_on_consecutive_calls():
 
 
 def test_noalloc_spectrum_rejects_sizes_beyond_its_array():
+    """More points than the fixed array holds: LB_ERR_SIZE; a transform longer than 8192 points
+    (which lb_power_spectrum rejects too): LB_ERR_BAD_PARAM, before anything is launched."""
     import torch
-    buf = torch.zeros(2 * capi.LB_NOALLOC_MAX_POINTS, dtype=torch.float64, device="cuda")
+    a = torch.zeros(2 * capi.LB_NOALLOC_MAX_POINTS, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
     with pytest.raises(capi.LBError) as e:
-        capi.lb_power_spectrum_noalloc(buf.data_ptr(), 1024, 512, buf.data_ptr())
+        capi.lb_power_spectrum_noalloc(a.data_ptr(), 1024, 512, b.data_ptr())
     assert e.value.code == capi.LB_ERR_SIZE
+    for Lx, Lz in [(16384, 16), (16, 16384)]:
+        with pytest.raises(capi.LBError) as e:
+            capi.lb_power_spectrum_noalloc(a.data_ptr(), Lx, Lz, b.data_ptr())
+        assert e.value.code == capi.LB_ERR_BAD_PARAM, (Lx, Lz)
