@@ -273,6 +273,23 @@ int lb_pressure_shift_gradient(lb_ctx* ctx, int64_t steps, int64_t ckpt_every, d
 /* Clear the structure-factor and pressure accumulators (the step count is kept). */
 int lb_reset_statistics(lb_ctx* ctx);
 
+/* Checkpoint and resume (the paper's averages are taken over long stationary runs, Sec. III and
+ * Appendix A; this lets such a run stop and continue).  A checkpoint holds the context's whole
+ * dynamic state: the stored populations of every lattice (storage type), the step count (which
+ * keys the noise), the site maps, the sampling and correlation settings, and every accumulator
+ * (structure factors, profiles, correlations, pressure and mass statistics, sample counts).
+ * lb_checkpoint_bytes gives its size for the context as it is now; lb_save_checkpoint writes it to
+ * a caller-owned host buffer of exactly that many bytes (LB_ERR_SIZE otherwise), after the
+ * context's pending work; lb_load_checkpoint restores one into a context created with the same
+ * lattices (parameters, seeds, ids) and the same result-affecting flags (precision, a*, wall
+ * rule, noise) -- LB_ERR_STATE otherwise, LB_ERR_BAD_PARAM for a buffer that is not a checkpoint
+ * of this format.  The launch flags (graphs, persistent launch, tile) may differ: a resumed run
+ * then reproduces the uninterrupted one bit for bit, except that another tile groups the
+ * double-precision pressure sums differently (a few units in the last place).  Synchronous. */
+int lb_checkpoint_bytes(lb_ctx* ctx, size_t* bytes);
+int lb_save_checkpoint(lb_ctx* ctx, void* host_buf, size_t bytes);
+int lb_load_checkpoint(lb_ctx* ctx, const void* host_buf, size_t bytes);
+
 /* Number of kernels lb_step has enqueued on the device so far (every step kernel, every
  * diagnostics kernel, every step-counter update; kernels inside replayed graphs included). */
 int lb_kernel_launches(lb_ctx* ctx, int64_t* n);

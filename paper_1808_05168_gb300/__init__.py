@@ -189,6 +189,18 @@ class Simulation:
         capi.lb_get_populations(self.h, lattice, out)
         return out
 
+    # ---- checkpoint / resume
+    def save_checkpoint(self) -> np.ndarray:
+        """The context's whole dynamic state (populations, step count, settings, accumulators) as
+        bytes in host memory (a uint8 array); lb_load_checkpoint restores it."""
+        buf = np.empty(capi.lb_checkpoint_bytes(self.h), np.uint8)
+        capi.lb_save_checkpoint(self.h, buf)
+        return buf
+
+    def load_checkpoint(self, buf):
+        """Resume from save_checkpoint's bytes (same lattices and result-affecting options)."""
+        capi.lb_load_checkpoint(self.h, np.ascontiguousarray(buf, dtype=np.uint8))
+
     # ---- x-slab decomposition (one large lattice cut into windows of columns)
     def set_site_map(self, x0: int, Lx_global: int, lattice: int = 0):
         """Noise counters of column x of this lattice: those of column (x + x0) mod Lx_global of

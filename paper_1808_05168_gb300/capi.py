@@ -44,7 +44,8 @@ EXPORTS = ("lb_create", "lb_create_batch", "lb_create_batch_with_allocator", "lb
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
            "lb_debug_box_muller", "lb_debug_schedule",
            "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient", "lb_set_site_map",
-           "lb_export_columns", "lb_import_columns", "lb_debug_fma_rate")
+           "lb_export_columns", "lb_import_columns", "lb_debug_fma_rate", "lb_checkpoint_bytes",
+           "lb_save_checkpoint", "lb_load_checkpoint")
 LB_NOALLOC_MAX_POINTS = 1 << 18
 LB_CORR_MAX_MODES = 16
 
@@ -120,6 +121,9 @@ def load():
             "lb_export_columns": [vp, i, i, i, vp],
             "lb_import_columns": [vp, i, i, i, vp],
             "lb_debug_fma_rate": [i, dp],
+            "lb_checkpoint_bytes": [vp, ctypes.POINTER(sz)],
+            "lb_save_checkpoint": [vp, vp, sz],
+            "lb_load_checkpoint": [vp, vp, sz],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -318,6 +322,25 @@ def lb_error_string(code):
 def lb_destroy(h):
     if h:
         load().lb_destroy(h)
+
+
+def lb_checkpoint_bytes(h) -> int:
+    out = ctypes.c_size_t()
+    _check(load().lb_checkpoint_bytes(h, ctypes.byref(out)), "lb_checkpoint_bytes")
+    return int(out.value)
+
+
+def lb_save_checkpoint(h, buf: np.ndarray):
+    """buf: a C-contiguous uint8 array of exactly lb_checkpoint_bytes(h) bytes."""
+    if buf.dtype != np.uint8 or not buf.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous uint8 array")
+    _check(load().lb_save_checkpoint(h, ctypes.c_void_p(buf.ctypes.data), buf.size), "lb_save_checkpoint")
+
+
+def lb_load_checkpoint(h, buf: np.ndarray):
+    if buf.dtype != np.uint8 or not buf.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous uint8 array")
+    _check(load().lb_load_checkpoint(h, ctypes.c_void_p(buf.ctypes.data), buf.size), "lb_load_checkpoint")
 
 
 def lb_debug_fma_rate(precision) -> float:

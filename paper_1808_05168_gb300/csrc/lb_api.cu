@@ -2,6 +2,7 @@
 // decomposition, step scheduling (direct launches, CUDA graphs, or one cooperative
 // persistent launch per run of steps), sampling, autotuning of the tile shape.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -24,6 +25,15 @@ constexpr double kCBar0 = 0.5;  // reference concentration c_0(z = 0) (Sec. II.A
 const double kNorm[9] = {1.0, 1.0 / 3, 1.0 / 3, 4.0, 4.0 / 9, 1.0 / 9, 2.0 / 3, 2.0 / 3, 16.0};  // N_a, Table I
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// An NVTX range over a host call (profilers show where lb_step, the sampling, the autotuner and the
+// adjoint sweeps enqueue their work; without a profiler attached it costs a branch).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct GraphKey {
   int64_t nsteps;
@@ -600,6 +610,7 @@ StepArgs<real> step_args(lb_ctx* c, int cur, int t_offset) {
 
 template <class real>
 cudaError_t enqueue_sample(lb_ctx* c) {
+  NvtxRange r("lb sample step diagnostics");
   SfPlan p;
   p.lat = c->d_diag;
   p.row_tasks = c->d_row_tasks;
@@ -704,6 +715,7 @@ cudaError_t enqueue(lb_ctx* c, int cur, int64_t n, const std::vector<int64_t>& s
 
 template <class real>
 int autotune(lb_ctx* c) {
+  NvtxRange r("lb autotune");
   static std::mutex mu;
   static std::map<std::tuple<int, int64_t, int, int, int, int, int>, std::pair<int, int>> cache;
   const bool persistent = c->flags & LB_PERSISTENT;
@@ -792,6 +804,7 @@ int autotune(lb_ctx* c) {
 
 template <class real>
 int step_impl(lb_ctx* c, int64_t n) {
+  NvtxRange r("lb_step");
   if (c->flags & LB_AUTOTUNE && !c->tuned && !c->tile_fixed) {
     int rc = autotune<real>(c);
     if (rc) return rc;
@@ -849,6 +862,7 @@ int step_impl(lb_ctx* c, int64_t n) {
 
 int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn alloc_fn = nullptr,
                 lb_free_fn free_fn = nullptr, void* alloc_user = nullptr) {
+  NvtxRange r("lb_create");
   if (!out) return LB_ERR_BAD_PARAM;
   *out = nullptr;
   if (n < 1 || !ps) return LB_ERR_BAD_PARAM;
@@ -1012,6 +1026,7 @@ namespace {
 // ---- adjoint sweep for the gradient of the mean-pressure shift -----------------------------
 template <class real>
 int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* loss) {
+  NvtxRange r("lb_pressure_shift_gradient");
   const lb_params& p = c->params[0];
   const int N = p.Lx * p.Lz;
   const size_t S = (size_t)18 * N;  // reals per state (lattice 0 starts at offset 0)
@@ -1069,6 +1084,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   double L[2] = {0.0, 0.0};
   for (int run = 0; run < 2 && e == cudaSuccess; ++run) {
     const int noise = run == 0 ? c->noise_mode : NOISE_OFF;
+    NvtxRange rr(run == 0 ? "lb adjoint: noisy run" : "lb adjoint: noiseless run");
     // forward from rest: checkpoints f*_{c-1} before every C-th step, pressure of every step
     ok(launch_init_rest<real>(cur, bp, st));
     ok(cudaMemsetAsync(stats, 0, sizeof(DiagStats), st));
@@ -1555,6 +1571,151 @@ int lb_export_columns(lb_ctx* c, int lattice, int x_first, int n_cols, void* dev
 
 int lb_import_columns(lb_ctx* c, int lattice, int x_first, int n_cols, const void* device_in) {
   return columns_impl(c, lattice, x_first, n_cols, const_cast<void*>(device_in), false);
+}
+
+namespace {
+// ---- checkpoint / resume -------------------------------------------------------------------
+// Layout of a checkpoint (host memory, native byte order): the header, then per lattice its site
+// map (x0, Lx of the whole lattice), the stored state of every lattice (n_f values of the storage
+// type), the per-lattice statistics, and, when the diagnostics are allocated, the structure-factor
+// and profile accumulators (sums and compensations), then the correlation accumulators if any.
+constexpr uint64_t kCkptMagic = 0x3130545043424c4cull;  // "LLBCKPT01" without the first L
+constexpr uint32_t kCkptVersion = 1;
+constexpr int kResultFlags = LB_PREC_DEV32 | LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC;
+
+struct CkptHeader {
+  uint64_t magic;
+  uint32_t version, n_lat;
+  int32_t flags, corr_mask;
+  int64_t t, discard, every, nsamples, corr_samples;
+  int32_t n_modes, diag_ready;
+  int32_t modes[LB_CORR_MAX_MODES];
+  uint64_t params_hash;
+  uint64_t bytes;
+};
+
+// FNV-1a over the lattices' parameters (sizes, rates, kT, G, gradient, seeds, ids)
+uint64_t params_hash(const lb_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(c->params.data());
+  for (size_t i = 0; i < c->params.size() * sizeof(lb_params); ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+size_t state_bytes(const lb_ctx* c) { return (size_t)c->n_f * (c->dev32 ? sizeof(float) : sizeof(double)); }
+
+size_t ckpt_bytes(const lb_ctx* c, bool diag_ready, bool corr) {
+  size_t n = sizeof(CkptHeader) + (size_t)c->n_lat * 2 * sizeof(int32_t) + state_bytes(c) +
+             (size_t)c->n_lat * sizeof(DiagStats);
+  if (diag_ready) n += (2 * 4 * (size_t)c->n_sites + 2 * 5 * (size_t)c->n_rows) * sizeof(double);
+  if (corr) n += (c->corr_R_n + c->corr_C_n) * sizeof(double);
+  return n;
+}
+}  // namespace
+
+int lb_checkpoint_bytes(lb_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LB_ERR_BAD_PARAM;
+  *bytes = ckpt_bytes(c, c->diag_ready, c->corr_mask != 0);
+  return LB_OK;
+}
+
+int lb_save_checkpoint(lb_ctx* c, void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return LB_ERR_BAD_PARAM;
+  const bool corr = c->corr_mask != 0;
+  const size_t need = ckpt_bytes(c, c->diag_ready, corr);
+  if (bytes != need) return LB_ERR_SIZE;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kCkptMagic;
+  h.version = kCkptVersion;
+  h.n_lat = (uint32_t)c->n_lat;
+  h.flags = c->flags & kResultFlags;
+  h.corr_mask = c->corr_mask;
+  h.t = c->t;
+  h.discard = c->discard;
+  h.every = c->every;
+  h.nsamples = c->nsamples;
+  h.corr_samples = c->corr_samples;
+  h.n_modes = (int32_t)c->corr_modes.size();
+  h.diag_ready = c->diag_ready ? 1 : 0;
+  for (int m = 0; m < h.n_modes; ++m) h.modes[m] = c->corr_modes[m];
+  h.params_hash = params_hash(c);
+  h.bytes = need;
+  char* p = static_cast<char*>(host_buf);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (int i = 0; i < c->n_lat; ++i) {
+    const int32_t m[2] = {c->site_map[i].first, c->site_map[i].second};
+    std::memcpy(p, m, sizeof(m));
+    p += sizeof(m);
+  }
+  auto from_device = [&](const void* d, size_t n) {
+    if (cudaMemcpy(p, d, n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    p += n;
+    return true;
+  };
+  bool ok = from_device(c->f[c->cur], state_bytes(c)) && from_device(c->stats, (size_t)c->n_lat * sizeof(DiagStats));
+  if (ok && c->diag_ready) {
+    const size_t ns = 4 * (size_t)c->n_sites * sizeof(double), nr = 5 * (size_t)c->n_rows * sizeof(double);
+    ok = from_device(c->acc_sum, ns) && from_device(c->acc_comp, ns) && from_device(c->prof_sum, nr) &&
+         from_device(c->prof_comp, nr);
+  }
+  if (ok && corr) ok = from_device(c->corr_R, c->corr_R_n * sizeof(double)) &&
+                       (c->corr_C_n == 0 || from_device(c->corr_C, c->corr_C_n * sizeof(double)));
+  return ok ? LB_OK : LB_ERR_CUDA;
+}
+
+int lb_load_checkpoint(lb_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf || bytes < sizeof(CkptHeader)) return LB_ERR_BAD_PARAM;
+  CkptHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (h.magic != kCkptMagic || h.version != kCkptVersion || h.bytes != bytes || h.n_modes < 0 ||
+      h.n_modes > LB_CORR_MAX_MODES)
+    return LB_ERR_BAD_PARAM;
+  if ((int)h.n_lat != c->n_lat || h.flags != (c->flags & kResultFlags) || h.params_hash != params_hash(c))
+    return LB_ERR_STATE;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  // the same sampling and correlations (this allocates and clears their accumulators)
+  rc = lb_set_sampling(c, h.discard, h.every);
+  if (!rc && h.diag_ready && !c->diag_ready) rc = alloc_diag(c);
+  if (!rc) rc = lb_set_correlations(c, h.corr_mask, h.n_modes, h.modes);
+  if (rc) return rc;
+  if (ckpt_bytes(c, h.diag_ready != 0, h.corr_mask != 0) != bytes) return LB_ERR_SIZE;
+  const char* p = static_cast<const char*>(host_buf) + sizeof(h);
+  for (int i = 0; i < c->n_lat; ++i) {
+    int32_t m[2];
+    std::memcpy(m, p, sizeof(m));
+    p += sizeof(m);
+    if (m[0] != c->site_map[i].first || m[1] != c->site_map[i].second) {
+      rc = lb_set_site_map(c, i, m[0], m[1]);
+      if (rc) return rc;
+    }
+  }
+  auto to_device = [&](void* d, size_t n) {
+    if (cudaMemcpy(d, p, n, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    p += n;
+    return true;
+  };
+  c->cur = 0;
+  bool ok = to_device(c->f[0], state_bytes(c)) && to_device(c->stats, (size_t)c->n_lat * sizeof(DiagStats));
+  if (ok && h.diag_ready) {
+    const size_t ns = 4 * (size_t)c->n_sites * sizeof(double), nr = 5 * (size_t)c->n_rows * sizeof(double);
+    ok = to_device(c->acc_sum, ns) && to_device(c->acc_comp, ns) && to_device(c->prof_sum, nr) &&
+         to_device(c->prof_comp, nr);
+  }
+  if (ok && h.corr_mask) ok = to_device(c->corr_R, c->corr_R_n * sizeof(double)) &&
+                              (c->corr_C_n == 0 || to_device(c->corr_C, c->corr_C_n * sizeof(double)));
+  // the step count, on the host and in the device counter that keys the noise
+  if (ok) ok = cudaMemcpy(c->d_t, &h.t, sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) return LB_ERR_CUDA;
+  c->t = h.t;
+  c->nsamples = h.nsamples;
+  c->corr_samples = h.corr_samples;
+  drop_graphs(c);
+  return LB_OK;
 }
 
 int lb_reset_statistics(lb_ctx* c) {
