@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1808_05168_gb300 import Simulation, workloads
+from paper_1808_05168_gb300 import LatticeParams, Simulation, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -146,3 +146,42 @@ def test_c2_spectra_pressure_and_profiles(prec, c2_oracle):
         else:
             b = bg.get(f, want.mean())
             assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - b)) + 1e-12, f
+
+
+@pytest.mark.parametrize("prec,kw", [("dev32", dict(persistent=True)), ("fp64", dict())], ids=["dev32", "fp64"])
+def test_largest_lattices_in_one_batch(prec, kw):
+    """The largest lattice the interface admits (18 Lx Lz just below 2^31 values: 32768 x 3640,
+    119 M sites) twice in one batch, so that the second lattice's populations start beyond 2^31
+    values (64-bit offsets in the batch, per-lattice tensor maps) -- 34 GB of FP32 or 69 GB of FP64
+    state.  One step from rest, then one more: column windows at both x edges and in the middle of
+    both lattices against the oracle (a site's update depends only on the state within two columns,
+    so the oracle on a 5-column window with the large lattice's noise counters gives that column
+    exactly)."""
+    import torch
+    Lx, Lz = 32768, 3640
+    assert 18 * Lx * Lz < 2 ** 31
+    ps = [LatticeParams(Lx, Lz, kT=1e-5, G=0.5, grad_c0=0.5 / Lz, seed=41, lattice_id=i,
+                        lambda_s=1.0, lambda_d=0.8, lambda_e=1.0) for i in range(2)]
+    cols = [0, 1, 16383, 32766, 32767]
+    # (each lattice's populations are 17 GB in double precision on the host: keep only the windows)
+    windows = lambda f: {x: np.ascontiguousarray(f[..., [(x + d) % Lx for d in range(-2, 3)]]) for x in cols}
+    with Simulation(ps, precision=prec, **kw) as sim:
+        sim.step(1)
+        before = [windows(sim.populations(i)) for i in range(2)]
+        sim.step(1)
+        after = [{x: np.ascontiguousarray(f[..., x]) for x in cols} for f in (sim.populations(i) for i in range(2))]
+    torch.cuda.empty_cache()
+    b = background(5, Lz, ps[0].grad_c0)
+    for i, p in enumerate(ps):
+        for x in cols:
+            o = oracle_of(p, Lx=5)
+            o.set_site_map((x - 2) % Lx, Lx)
+            o.set_populations(before[i][x])
+            o.time = 1
+            o.step(1)
+            want = o.populations()[:, :, :, 2]
+            got = after[i][x]
+            if prec == "fp64":
+                assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-12, (i, x)
+            else:
+                assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(o.populations() - b)), (i, x)
