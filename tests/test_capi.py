@@ -80,3 +80,30 @@ def test_batch_rejects_reserved_field(lib):
     h = ctypes.c_void_p()
     assert lib.lb_create_batch(ctypes.byref(h), 1, (capi.lb_params * 1)(p), 0) == capi.LB_ERR_BAD_PARAM
     assert lib.lb_create_batch(ctypes.byref(h), 0, None, 0) == capi.LB_ERR_BAD_PARAM
+
+
+@pytest.mark.parametrize("fail_at", [0, 1, 3, 7])
+def test_allocation_failure_is_reported_and_cleaned_up(lib, fail_at):
+    """An allocator that refuses its (fail_at + 1)-th request (host-side fault injection, no GPU
+    needed: the context's first allocations precede any device call): lb_create_batch_with_allocator
+    returns LB_ERR_OOM, leaves *out NULL, and hands every pointer it did get back to free_fn, once."""
+    from paper_1808_05168_gb300 import capi
+    given, freed = [], []
+
+    def alloc(nbytes, user):
+        if len(given) == fail_at:
+            return None
+        given.append(0x10000 * (len(given) + 1))  # never dereferenced on the host
+        return given[-1]
+
+    def free(ptr, user):
+        freed.append(ptr)
+
+    a, f = capi.LB_ALLOC_FN(alloc), capi.LB_FREE_FN(free)
+    p = capi.lb_params(64, 16, 1.0, 0.8, 1.0, 1.0, 1.0, 1e-5, 0.5, 0.01, 1, 0, 0)
+    h = ctypes.c_void_p()
+    rc = lib.lb_create_batch_with_allocator(ctypes.byref(h), 1, (capi.lb_params * 1)(p), capi.LB_PREC_DEV32, a, f,
+                                            None)
+    assert rc == capi.LB_ERR_OOM
+    assert not h.value
+    assert len(given) == fail_at and sorted(freed) == sorted(given)
