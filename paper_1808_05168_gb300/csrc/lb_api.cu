@@ -727,7 +727,7 @@ int autotune(lb_ctx* c) {
     if (it != cache.end()) return build_items(c, it->second.first, it->second.second);
   }
   const int txs[] = {32, 64, 128, 256};
-  const int rows[] = {8, 16, 32, 64, 128, 256, 1 << 30};
+  const int rows[] = {2, 4, 8, 16, 32, 64, 128, 256, 1 << 30};
   float best = 1e30f;
   int bx = c->tile_x, br = c->rows_per_item;
   std::vector<std::tuple<float, int, int>> trials;  // (ms, tile_x, rows)
