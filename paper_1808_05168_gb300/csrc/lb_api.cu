@@ -1676,9 +1676,10 @@ int lb_load_checkpoint(lb_ctx* c, const void* host_buf, size_t bytes) {
     return LB_ERR_BAD_PARAM;
   if ((int)h.n_lat != c->n_lat || h.flags != (c->flags & kResultFlags) || h.params_hash != params_hash(c))
     return LB_ERR_STATE;
-  int rc = sync_and_check(c);
+  // start from cleared statistics (a context that sampled before keeps no stale sums), then the
+  // same sampling and correlations (this allocates what the checkpoint needs)
+  int rc = lb_reset_statistics(c);
   if (rc) return rc;
-  // the same sampling and correlations (this allocates and clears their accumulators)
   rc = lb_set_sampling(c, h.discard, h.every);
   if (!rc && h.diag_ready && !c->diag_ready) rc = alloc_diag(c);
   if (!rc) rc = lb_set_correlations(c, h.corr_mask, h.n_modes, h.modes);

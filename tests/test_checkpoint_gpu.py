@@ -87,3 +87,32 @@ def test_checkpoints_are_checked():
             with pytest.raises(capi.LBError) as e:
                 sim.load_checkpoint(ck)
             assert e.value.code == capi.LB_ERR_STATE
+
+
+def test_loading_replaces_earlier_statistics():
+    """A context that has sampled before takes the checkpoint's statistics, not its own: a checkpoint
+    saved before any sampling, loaded into a context with accumulated spectra, continues exactly as
+    the saving context does."""
+    with Simulation(PS, precision="dev32") as sim:
+        sim.step(30)
+        ck = sim.save_checkpoint()
+        sim.set_sampling(0, 5)
+        sim.step(20)
+        want = outputs_spectra(sim)
+    with Simulation(PS, precision="dev32") as sim:
+        sim.set_sampling(0, 5)
+        sim.step(20)
+        assert sim.structure_factor("c")[1] == 4
+        sim.load_checkpoint(ck)
+        assert sim.time == 30 and sim.structure_factor("c")[1] == 0
+        assert np.all(sim.structure_factor("c")[0] == 0)
+        sim.set_sampling(0, 5)
+        sim.step(20)
+        got = outputs_spectra(sim)
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
+
+
+def outputs_spectra(sim):
+    return [sim.populations(0), sim.structure_factor("c")[0], sim.structure_factor("uz", lattice=1)[0],
+            np.array(sim.mean_pressure(1)), sim.profile("p")[0]]
