@@ -1073,6 +1073,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
     StepArgs<real> a = step_args<real>(c, 0, 0);
     a.src = src;
     a.dst = dst;
+    a.tmaps = nullptr;  // the context's tensor maps describe its own state buffers, not these
     a.d_t = zero_t;
     a.t_offset = (int)k;
     a.fields = fields;

@@ -75,6 +75,23 @@ def test_fp32_gradient_follows_fp64_full_size():
     np.testing.assert_allclose(g32, g64, rtol=0, atol=2e-2 * np.max(np.abs(g64)))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_gradient_does_not_depend_on_the_tile(prec):
+    """The reverse sweep recomputes the forward states in buffers of its own; with tiles narrow
+    enough for strips away from the x edges (staged by tensor copies in the forward run) it must
+    give the default tile's states, hence its gradient, bit for bit (the loss sums per-item pressure
+    partials, so its rounding follows the tile)."""
+    p = LatticeParams(256, 16, kT=1e-4, G=0.5, grad_c0=0.02, seed=9)
+    out = []
+    for tile in (128, 64, 32):
+        with Simulation(p, precision=prec) as sim:
+            sim.set_tile(tile, 8)
+            out.append(sim.pressure_shift_gradient(30, 7))
+    for loss, g in out[1:]:
+        assert abs(loss - out[0][0]) <= 1e-12 * abs(out[0][0])
+        np.testing.assert_array_equal(g, out[0][1])
+
+
 def test_autograd_function():
     import torch
     from paper_1808_05168_gb300.autograd import MeanPressureShift
