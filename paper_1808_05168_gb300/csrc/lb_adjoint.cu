@@ -85,12 +85,12 @@ __device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int L
       const int xs = (x - kCX[l] + Lx) % Lx;
       double val;
       if (zs >= 0 && zs < Lz) {
-        val = (double)f[(s * 9 + l) * LzLx + zs * Lx + xs];
+        val = (double)f[state_index(s, l, zs, xs, Lx, LzLx)];
         const double q = (l == 0 || l == 1 || l == 3) ? 0.0 : ((l <= 4) ? k9 : k36);
         const double sh = kCZ[l] > 0 ? -q : (kCZ[l] < 0 ? q : 0.0);
         val += s == 0 ? sh : -sh;
       } else {
-        val = (double)f[(s * 9 + kOPP[l]) * LzLx + z * Lx + x];
+        val = (double)f[state_index(s, kOPP[l], z, x, Lx, LzLx)];
       }
       v[s * 9 + l] = val;
     }

@@ -450,10 +450,13 @@ EncodeTiled encode_tiled() {
   return fn;
 }
 
+// Tensor maps of the FP32 state: each (A, B) pair is one 8-byte element of a 3-d map [x][z][link]
+// (an FP64 pair, 16 bytes, has no element type; those rows go by 1-d bulk copies).
 int build_tmaps(lb_ctx* c, int tile_x) {
   c->tma = false;
-  const int es = c->dev32 ? 4 : 8, pad = 16 / es, bw = tile_x + 2 * pad;
-  if (!c->bulk_ok || (c->flags & LB_NO_TENSOR_MAPS) || !(tile_x == 32 || tile_x == 64 || tile_x == 128) || bw > 256)
+  const int es = 8, pad = 2, bw = tile_x + 2 * pad;  // bytes per pair, halo columns
+  if (!c->dev32 || !c->bulk_ok || (c->flags & LB_NO_TENSOR_MAPS) || !(tile_x == 32 || tile_x == 64 || tile_x == 128) ||
+      bw > 256)
     return LB_OK;
   EncodeTiled enc = encode_tiled();
   if (!enc) return LB_OK;
@@ -468,15 +471,14 @@ int build_tmaps(lb_ctx* c, int tile_x) {
     for (int i = 0; i < c->n_lat; ++i) {
       const lb_params& p = c->params[i];
       if (p.Lx <= 2 * tile_x) continue;  // no strip away from the x edges
-      const cuuint64_t dims[4] = {(cuuint64_t)p.Lx, (cuuint64_t)p.Lz, 9, 2};
-      const cuuint64_t strides[3] = {(cuuint64_t)p.Lx * es, (cuuint64_t)p.Lx * p.Lz * es, 9ull * p.Lx * p.Lz * es};
-      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      const cuuint64_t dims[3] = {(cuuint64_t)p.Lx, (cuuint64_t)p.Lz, 9};
+      const cuuint64_t strides[2] = {(cuuint64_t)p.Lx * es, (cuuint64_t)p.Lx * p.Lz * es};
+      const cuuint32_t estr[3] = {1, 1, 1};
       for (int run = 1; run <= 2; ++run) {
-        const cuuint32_t box[4] = {(cuuint32_t)bw, 1, (cuuint32_t)run, 2};
-        void* base = (char*)c->f[buf] + (size_t)c->f_off[i] * es;
-        CUresult r = enc(&maps[((size_t)buf * c->n_lat + i) * 2 + (run - 1)],
-                         c->dev32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims,
-                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        const cuuint32_t box[3] = {(cuuint32_t)bw, 1, (cuuint32_t)run};
+        void* base = (char*)c->f[buf] + (size_t)c->f_off[i] * sizeof(float);
+        CUresult r = enc(&maps[((size_t)buf * c->n_lat + i) * 2 + (run - 1)], CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return LB_OK;
       }
@@ -904,7 +906,7 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn
   c->n_f = foff;
   c->n_sites = soff;
   {
-    const int align = c->dev32 ? 4 : 2;  // elements in 16 bytes
+    const int align = 2;  // rows of pairs 16-byte aligned, and at least the two halo columns
     c->bulk_ok = !(flags & LB_NO_BULK);
     for (int i = 0; i < n; ++i)
       if (ps[i].Lx % align != 0) c->bulk_ok = false;
@@ -1581,7 +1583,7 @@ namespace {
 // type), the per-lattice statistics, and, when the diagnostics are allocated, the structure-factor
 // and profile accumulators (sums and compensations), then the correlation accumulators if any.
 constexpr uint64_t kCkptMagic = 0x3130545043424c4cull;  // "LLBCKPT01" without the first L
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;  // 2: the state as (A, B) pairs
 constexpr int kResultFlags = LB_PREC_DEV32 | LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC;
 
 struct CkptHeader {

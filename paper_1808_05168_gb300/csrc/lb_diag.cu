@@ -466,9 +466,8 @@ template <class real>
 __global__ void mass_kernel(const real* f, BgParams bp, double* out) {
   const int s = blockIdx.x;
   const int64_t LzLx = (int64_t)bp.Lx * bp.Lz;
-  const real* fs = f + (int64_t)s * 9 * LzLx;
-  double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < 9 * LzLx; k += blockDim.x) acc += (double)fs[k];
+  double acc = 0.0;  // over the pairs [link][z][x], species s of each
+  for (int64_t k = threadIdx.x; k < 9 * LzLx; k += blockDim.x) acc += (double)f[2 * k + s];
   __shared__ double red[1024];
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -497,13 +496,15 @@ __device__ __forceinline__ double background(const BgParams& bp, int s, int l, i
   return weight_of(l) * bp.rho_bar * (s == 0 ? c0 : 1.0 - c0);
 }
 
+// The API layout [species][link][z][x] (index k) against the stored pairs (state_index).
 template <class real>
 __global__ void to_absolute_kernel(const real* f, BgParams bp, double* out) {
   const int64_t LzLx = (int64_t)bp.Lx * bp.Lz, n = 18 * LzLx;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int sl = (int)(k / LzLx);
-    const int z = (int)((k - sl * LzLx) / bp.Lx);
-    out[k] = (double)f[k] + background(bp, sl / 9, sl % 9, z);
+    const int sl = (int)(k / LzLx), s = sl / 9, l = sl - 9 * s;
+    const int64_t r = k - sl * LzLx;
+    const int z = (int)(r / bp.Lx);
+    out[k] = (double)f[state_index(s, l, 0, 0, bp.Lx, LzLx) + 2 * r] + background(bp, s, l, z);
   }
 }
 
@@ -511,9 +512,10 @@ template <class real>
 __global__ void from_absolute_kernel(const double* in, BgParams bp, real* f) {
   const int64_t LzLx = (int64_t)bp.Lx * bp.Lz, n = 18 * LzLx;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int sl = (int)(k / LzLx);
-    const int z = (int)((k - sl * LzLx) / bp.Lx);
-    f[k] = (real)(in[k] - background(bp, sl / 9, sl % 9, z));
+    const int sl = (int)(k / LzLx), s = sl / 9, l = sl - 9 * s;
+    const int64_t r = k - sl * LzLx;
+    const int z = (int)(r / bp.Lx);
+    f[state_index(s, l, 0, 0, bp.Lx, LzLx) + 2 * r] = (real)(in[k] - background(bp, s, l, z));
   }
 }
 
@@ -524,24 +526,25 @@ __global__ void init_rest_kernel(real* f, BgParams bp) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     if (bp.dev) {
       f[k] = real(0);
-    } else {
-      const int sl = (int)(k / LzLx);
-      const int z = (int)((k - sl * LzLx) / bp.Lx);
+    } else {  // element k of the stored pairs: species k mod 2 of pair k / 2
+      const int64_t q = k >> 1;
+      const int s = (int)(k & 1), l = (int)(q / LzLx);
+      const int z = (int)((q - l * LzLx) / bp.Lx);
       const double c0 = 0.5 + (z + 0.5 - 0.5 * bp.Lz) * bp.grad_c0;
-      f[k] = (real)(weight_of(sl % 9) * bp.rho_bar * ((sl / 9) == 0 ? c0 : 1.0 - c0));
+      f[k] = (real)(weight_of(l) * bp.rho_bar * (s == 0 ? c0 : 1.0 - c0));
     }
   }
 }
 
 // Columns x_first .. x_first + n - 1 of every (species, link) plane, to (to_buf) or from a packed
-// buffer [18][Lz][n]; thread k handles element k of the buffer.
+// buffer [9 * species + link][Lz][n] (the API layout); thread k handles element k of the buffer.
 template <class real>
 __global__ void columns_kernel(real* f, int Lx, int Lz, int x_first, int n, real* buf, bool to_buf) {
-  const int64_t total = (int64_t)18 * Lz * n;
+  const int64_t total = (int64_t)18 * Lz * n, LzLx = (int64_t)Lx * Lz;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = k / n;  // plane * Lz + z
-    const int j = (int)(k - row * n);
-    real* g = f + row * Lx + x_first + j;
+    const int j = (int)(k - row * n), sl = (int)(row / Lz), z = (int)(row - (int64_t)sl * Lz), s = sl / 9;
+    real* g = f + state_index(s, sl - 9 * s, z, x_first + j, Lx, LzLx);
     if (to_buf) buf[k] = *g;
     else *g = buf[k];
   }

@@ -399,31 +399,36 @@ struct StepArgs {
                        // deviation mode (sample steps only)
   double* partials;    // per item: pressure deviation sum, mass deviation A, B
   int* err;            // set to 1 by a device-side wait that gave up
-  // bulk path: 4-d tensor maps [x][z][link][species] of the populations, per state buffer and
-  // lattice, for runs of one and of two links (index (buffer n_lat + lattice) 2 + run length - 1),
-  // or null; src_buf: the state buffer src points to
+  // bulk path (FP32 state): 3-d tensor maps [x][z][link] of the (A, B) pairs as 8-byte elements,
+  // per state buffer and lattice, for runs of one and of two links (index (buffer n_lat +
+  // lattice) 2 + run length - 1), or null; src_buf: the state buffer src points to
   const CUtensorMap* tmaps;
   int n_lat;
   int src_buf;
 };
 
-// The input row slot of the bulk path: the 18 (species, link) planes grouped in the six runs of
-// consecutive links with equal c_z, (0 1) (2) (3) (4) (5 6) (7 8).  Run j holds
-// [species][link of the run][BW columns] at a 128-byte aligned base: the layout one 4-d bulk
-// tensor copy writes (a box of BW columns, one row, the run's links, both species).
+// The stored state of a lattice: [link l][row z][column x][species s], so the populations of both
+// species of one (link, site) are adjacent and one 8-byte (FP32) or 16-byte (FP64) access moves
+// the pair.  The element index of f^s_l(x, z):
+__host__ __device__ __forceinline__ int64_t state_index(int s, int l, int z, int x, int Lx, int64_t LzLx) {
+  return ((int64_t)l * LzLx + (int64_t)z * Lx + x) * 2 + s;
+}
+
+// The input row slot of the bulk path, in (A, B) pairs: the 9 link rows grouped in the six runs of
+// consecutive links with equal c_z, (0 1) (2) (3) (4) (5 6) (7 8).  Run j holds [link of the
+// run][BW columns] at a 128-byte aligned base: the layout one tensor copy writes (a box of BW
+// columns, one row, the run's links).  PS: bytes per pair.
 __host__ __device__ constexpr int run_of(int l) { return l < 2 ? 0 : (l < 5 ? l - 1 : (l < 7 ? 4 : 5)); }
 __host__ __device__ constexpr int run_l0(int j) { return j == 0 ? 0 : (j <= 3 ? j + 1 : (j == 4 ? 5 : 7)); }
 __host__ __device__ constexpr int run_n(int j) { return (j == 0 || j >= 4) ? 2 : 1; }
-template <int BW, int ES>
+template <int BW, int PS>
 struct SlotLayout {
-  static constexpr int ALIGN = 128 / ES;  // elements per 128 bytes
-  __host__ __device__ static constexpr int run_size(int j) { return ((2 * run_n(j) * BW + ALIGN - 1) / ALIGN) * ALIGN; }
+  static constexpr int ALIGN = 128 / PS;  // pairs per 128 bytes
+  __host__ __device__ static constexpr int run_size(int j) { return ((run_n(j) * BW + ALIGN - 1) / ALIGN) * ALIGN; }
   __host__ __device__ static constexpr int base(int j) { return j == 0 ? 0 : base(j - 1) + run_size(j - 1); }
-  // element offset of plane (species s, link l) in the slot
-  __host__ __device__ static constexpr int plane(int s, int l) {
-    return base(run_of(l)) + (s * run_n(run_of(l)) + l - run_l0(run_of(l))) * BW;
-  }
-  static constexpr int slot = base(6);  // elements per slot (a multiple of 128 bytes)
+  // pair offset of link row l in the slot
+  __host__ __device__ static constexpr int plane(int l) { return base(run_of(l)) + (l - run_l0(run_of(l))) * BW; }
+  static constexpr int slot = base(6);  // pairs per slot (a multiple of 128 bytes)
   // base(j) for a run index known only at run time
   __host__ __device__ static int base_of(int j) {
     constexpr int b1 = base(1), b2 = base(2), b3 = base(3), b4 = base(4), b5 = base(5);

@@ -2,19 +2,24 @@
 // (Eq. LB with Eq. MRT), one launch per step for every lattice of a batch, or one cooperative
 // launch for a run of steps whose work items wait only for their neighbours' previous step.
 //
+// The state is stored as (A, B) pairs, [link][z][x][species] (state_index), so each population
+// pair moves as one 8-byte (FP32) or 16-byte (FP64) access.
+//
 // Work decomposition: a block of TX threads owns TX consecutive columns x of one lattice and
-// marches up rows z0..z1-1 of that lattice.  The 18 populations arriving at each site (Eq. LB;
-// mid-way bounce-back at the walls of Sec. II.A) are staged in shared memory, several rows
-// ahead of the row being collided, so that every stored value is read once per step from HBM
-// and no population is held in registers across rows.  Two staging paths compute the same
+// marches up rows z0..z1-1 of that lattice.  The 9 population pairs arriving at each site
+// (Eq. LB; mid-way bounce-back at the walls of Sec. II.A) are staged in shared memory, several
+// rows ahead of the row being collided, so that every stored value is read once per step from
+// HBM and no population is held in registers across rows.  Two staging paths compute the same
 // numbers bit for bit:
-//  - bulk (rows 16-byte aligned, TX = 32, 64, 128 or 256): for each of the 18 (species, link)
-//    planes one lane issues a bulk asynchronous copy of the row window [x0 - PAD, x0 + TX + PAD)
-//    (PAD = 16 bytes; wrapped periodically at the lattice's x edges) into a ring of NSI row
-//    slots, completion tracked by one mbarrier per slot; a one-warp block (TX = 32) marches
-//    without waiting on other warps;
-//  - generic (any Lx, any tile): every thread stages its own 18 values with per-thread
-//    asynchronous copies and stores with plain streaming stores.
+//  - bulk (rows 16-byte aligned, TX = 32, 64, 128 or 256): for each of the 9 link rows one lane
+//    issues a bulk asynchronous copy of the row window [x0 - PAD, x0 + TX + PAD) (PAD = 2
+//    columns; wrapped periodically at the lattice's x edges) into a ring of NSI row
+//    slots, or, away from the x edges, one 3-d tensor copy per run of links with equal c_z,
+//    completion tracked by one mbarrier per slot; a one-warp block (TX = 32) marches without
+//    waiting on other warps;
+//  - generic (any Lx, any tile): every thread stages its own 9 pairs with per-thread
+//    asynchronous copies.
+// Both store each post-collision pair with one streaming store.
 // The non-ideal force (Eq. aNI) needs the densities of the 8 neighbours at the same time
 // level: the densities of rows z-1, z, z+1 live in a 4-slot shared-memory ring (one barrier per
 // row); the halo columns are read by the edge threads.  The wall ghost rows follow Sec. II.A.
@@ -45,100 +50,6 @@ constexpr int NSI = LB_BULK_NSI;  // bulk path: input row slots
 constexpr int WAIT_MS = 2000;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-// ---- per-thread asynchronous copies (generic path) ---------------------------------
-template <class real>
-__device__ __forceinline__ void cp_async(real* dst_smem, const real* src);
-template <>
-__device__ __forceinline__ void cp_async<float>(float* dst_smem, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
-}
-template <>
-__device__ __forceinline__ void cp_async<double>(double* dst_smem, const double* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// ---- bulk copies and mbarriers (bulk path) ------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst_smem)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// One box of a 4-d tensor map (coordinates x, z, link, species) into shared memory (128-byte
-// aligned), completion counted on the mbarrier.
-__device__ __forceinline__ void tensor_g2s(void* dst_smem, const CUtensorMap* map, int x, int z, int l, int s,
-                                           uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];\n" ::"r"(smem_u32(dst_smem)),
-      "l"(map), "r"(x), "r"(z), "r"(l), "r"(s), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void bulk_s2g(void* dst, const void* src_smem, unsigned bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src_smem)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ int ring_slot(int z) { return (z + 4) & 3; }
-
-// Generic path: stage the 18 populations arriving at (x, z) (Eq. LB) into dst[k * W],
-// k = 9 s + l: link l comes from (x - c_lx, z - c_lz); a link whose source row lies beyond a
-// wall takes the reflected population f*_opp(l)(x, z).
-template <class real>
-__device__ __forceinline__ void stage_column(const real* __restrict__ f, int LzLx, int Lx, int Lz, int z, int x,
-                                             real* dst, int W) {
-  const int xm = (x == 0) ? Lx - 1 : x - 1;
-  const int xp = (x + 1 == Lx) ? 0 : x + 1;
-  const bool below = z > 0, above = z < Lz - 1;
-  const int r0 = z * Lx, rdn = r0 - Lx, rup = r0 + Lx;
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const real* fs = f + s * 9 * LzLx;
-    real* d = dst + s * 9 * W;
-    cp_async(d + 0 * W, fs + 0 * LzLx + r0 + x);
-    cp_async(d + 1 * W, fs + 1 * LzLx + r0 + xm);
-    cp_async(d + 3 * W, fs + 3 * LzLx + r0 + xp);
-    cp_async(d + 2 * W, below ? fs + 2 * LzLx + rdn + x : fs + 4 * LzLx + r0 + x);
-    cp_async(d + 4 * W, above ? fs + 4 * LzLx + rup + x : fs + 2 * LzLx + r0 + x);
-    cp_async(d + 5 * W, below ? fs + 5 * LzLx + rdn + xm : fs + 7 * LzLx + r0 + x);
-    cp_async(d + 6 * W, below ? fs + 6 * LzLx + rdn + xp : fs + 8 * LzLx + r0 + x);
-    cp_async(d + 7 * W, above ? fs + 7 * LzLx + rup + xp : fs + 5 * LzLx + r0 + x);
-    cp_async(d + 8 * W, above ? fs + 8 * LzLx + rup + xm : fs + 6 * LzLx + r0 + x);
-  }
-}
 
 // ---- (A, B) pairs ------------------------------------------------------------------
 // The two species go through identical arithmetic, so every per-species quantity of a site is
@@ -173,6 +84,90 @@ __device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
 
+// ---- per-thread asynchronous copies of one (A, B) pair (generic path) ---------------
+__device__ __forceinline__ void cp_async(float2* dst_smem, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double2* dst_smem, const double2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---- bulk copies and mbarriers (bulk path) ------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst_smem)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// One box of a 3-d tensor map (coordinates x, z, link) into shared memory (128-byte aligned),
+// completion counted on the mbarrier.
+__device__ __forceinline__ void tensor_g2s(void* dst_smem, const CUtensorMap* map, int x, int z, int l, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst_smem)),
+      "l"(map), "r"(x), "r"(z), "r"(l), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src_smem, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src_smem)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ring_slot(int z) { return (z + 4) & 3; }
+
+// Generic path: stage the 9 population pairs arriving at (x, z) (Eq. LB) into dst[l * W]: link l
+// comes from (x - c_lx, z - c_lz); a link whose source row lies beyond a wall takes the reflected
+// pair f*_opp(l)(x, z).  f: the lattice's state as pairs, [link][z][x].
+template <class P>
+__device__ __forceinline__ void stage_column(const P* __restrict__ f, int LzLx, int Lx, int Lz, int z, int x, P* dst,
+                                             int W) {
+  const int xm = (x == 0) ? Lx - 1 : x - 1;
+  const int xp = (x + 1 == Lx) ? 0 : x + 1;
+  const bool below = z > 0, above = z < Lz - 1;
+  const int r0 = z * Lx, rdn = r0 - Lx, rup = r0 + Lx;
+  cp_async(dst + 0 * W, f + 0 * LzLx + r0 + x);
+  cp_async(dst + 1 * W, f + 1 * LzLx + r0 + xm);
+  cp_async(dst + 3 * W, f + 3 * LzLx + r0 + xp);
+  cp_async(dst + 2 * W, below ? f + 2 * LzLx + rdn + x : f + 4 * LzLx + r0 + x);
+  cp_async(dst + 4 * W, above ? f + 4 * LzLx + rup + x : f + 2 * LzLx + r0 + x);
+  cp_async(dst + 5 * W, below ? f + 5 * LzLx + rdn + xm : f + 7 * LzLx + r0 + x);
+  cp_async(dst + 6 * W, below ? f + 6 * LzLx + rdn + xp : f + 8 * LzLx + r0 + x);
+  cp_async(dst + 7 * W, above ? f + 7 * LzLx + rup + xp : f + 5 * LzLx + r0 + x);
+  cp_async(dst + 8 * W, above ? f + 8 * LzLx + rup + xm : f + 6 * LzLx + r0 + x);
+}
+
 // The 9 populations of both species of one site as deviations from the background of its row.
 // In deviation mode the background difference b_l(z - c_lz) - b_l(z) = -w_l rho_bar c_lz
 // d_z c^S_0 belongs on every non-reflected link with c_lz != 0 (k9, k36: its size on the
@@ -203,32 +198,30 @@ __device__ __forceinline__ Pr<real> interior_m2_shift(real k9, real k36) {
   return pr(-q, q);
 }
 
-// Generic path: stage column c of a slot holds the already-shifted values of that site.
+// Generic path: stage column c of a slot holds the pairs pulled to that site.
 template <class real>
-__device__ __forceinline__ void read_generic(const real* st, int W, int c, bool below, bool above, real k9, real k36,
-                                             Pr<real> v[9]) {
-  const real* d = st + c;
+__device__ __forceinline__ void read_generic(const Pr<real>* st, int W, int c, bool below, bool above, real k9,
+                                             real k36, Pr<real> v[9]) {
+  const Pr<real>* d = st + c;
 #pragma unroll
-  for (int l = 0; l < 9; ++l) v[l] = pr(d[l * W], d[(9 + l) * W]);
+  for (int l = 0; l < 9; ++l) v[l] = d[l * W];
   deviations(v, below, above, k9, k36);
 }
 
-// Bulk path: plane (s, l) of a slot (SlotLayout) holds the source row window of link l, so link
-// l of the site at window column j sits at column j - c_lx (at j on reflected links, whose plane
+// Bulk path: link row l of a slot (SlotLayout) holds the source row window of link l, so link l
+// of the site at window column j sits at column j - c_lx (at j on reflected links, whose row
 // holds the opposite link's own row).
 template <class real, int SW>
-__device__ __forceinline__ void read_bulk(const real* st, int j, bool below, bool above, real k9, real k36,
+__device__ __forceinline__ void read_bulk(const Pr<real>* st, int j, bool below, bool above, real k9, real k36,
                                           Pr<real> v[9]) {
-  using LAY = SlotLayout<SW, (int)sizeof(real)>;
-  constexpr int oa[9] = {LAY::plane(0, 0), LAY::plane(0, 1), LAY::plane(0, 2), LAY::plane(0, 3), LAY::plane(0, 4),
-                         LAY::plane(0, 5), LAY::plane(0, 6), LAY::plane(0, 7), LAY::plane(0, 8)};
-  constexpr int ob[9] = {LAY::plane(1, 0), LAY::plane(1, 1), LAY::plane(1, 2), LAY::plane(1, 3), LAY::plane(1, 4),
-                         LAY::plane(1, 5), LAY::plane(1, 6), LAY::plane(1, 7), LAY::plane(1, 8)};
-  const real* a = st + j;
+  using LAY = SlotLayout<SW, (int)sizeof(Pr<real>)>;
+  constexpr int o[9] = {LAY::plane(0), LAY::plane(1), LAY::plane(2), LAY::plane(3), LAY::plane(4),
+                        LAY::plane(5), LAY::plane(6), LAY::plane(7), LAY::plane(8)};
+  const Pr<real>* a = st + j;
   const int j5 = below ? -1 : 0, j6 = below ? 1 : 0, j7 = above ? 1 : 0, j8 = above ? -1 : 0;
   const int dx[9] = {0, -1, 0, 1, 0, j5, j6, j7, j8};
 #pragma unroll
-  for (int l = 0; l < 9; ++l) v[l] = pr(a[oa[l] + dx[l]], a[ob[l] + dx[l]]);
+  for (int l = 0; l < 9; ++l) v[l] = a[o[l] + dx[l]];
   deviations(v, below, above, k9, k36);
 }
 
@@ -297,14 +290,6 @@ struct BoolC {
   static constexpr bool value = B;
 };
 
-// Output of one post-collision population: a streaming store to the lattice, or a store to the
-// shared output row (compile-time stride) that a bulk copy writes back.
-template <class real, bool TO_GLOBAL, int STRIDE>
-__device__ __forceinline__ void put(real* out, int stride, int l, real v) {
-  if (TO_GLOBAL) __stcs(out + l * stride, v);
-  else out[l * STRIDE] = v;
-}
-
 // Collision of both species in moment space (Eq. MRT) with second-order forcing and noise, and
 // the inverse transform f_l = w_l sum_a T_al m*_a / N_a.  Relaxation, forcing and noise factors
 // and 1/N_a are folded into the per-lattice coefficients kA..kN; moments 1-2 share theirs (both
@@ -312,10 +297,10 @@ __device__ __forceinline__ void put(real* out, int stride, int l, real v) {
 // pre-collision values drop out (kA = 0) and are never formed.  nz[1..8]: the standard normals
 // of the moments (pairs); cm, cq: their amplitude factors for moments 1-2 and 3-8 (sign and
 // local density; (1, -1) and (1, 1) for hom noise).
-template <class real, int NOISE, bool UNIT, bool TO_GLOBAL, int STRIDE>
+template <class real, int NOISE, bool UNIT>
 __device__ __forceinline__ void collide_out(const Mom<real>& m, Pr<real> d, Pr<real> rs, real Ux, real Uz,
                                             Pr<real> Fx, Pr<real> Fz, const SiteK<real>& K, const Pr<real> nz[9],
-                                            Pr<real> cm, Pr<real> cq, real* outA, real* outB, int stride) {
+                                            Pr<real> cm, Pr<real> cq, Pr<real>* out, int stride) {
   using P = Pr<real>;
   const P U_x = pr(Ux), U_z = pr(Uz);
   const real UxUx = Ux * Ux, UzUz = Uz * Uz;
@@ -378,10 +363,7 @@ __device__ __forceinline__ void collide_out(const Mom<real>& m, Pr<real> d, Pr<r
                   sub2(u57, v57),
                   add2(u68, v68)};
 #pragma unroll
-  for (int l = 0; l < 9; ++l) {
-    put<real, TO_GLOBAL, STRIDE>(outA, stride, l, f[l].x);
-    put<real, TO_GLOBAL, STRIDE>(outB, stride, l, f[l].y);
-  }
+  for (int l = 0; l < 9; ++l) __stcs(out + l * stride, f[l]);  // the pair of link l, streaming
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -393,12 +375,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Everything of one site after its moments are known and the densities of its row and the two
 // neighbouring rows sit in the ring: forces, velocity, optional sampling, noise, collision of
 // both species and the output.
-template <class real, bool SAMPLE, int NOISE, bool UNIT, bool ASTAR, bool TO_GLOBAL, int STRIDE>
+template <class real, bool SAMPLE, int NOISE, bool UNIT, bool ASTAR>
 __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst<real>& rc, const Mom<real>& m,
                                             const Pr<real>* ring, int bc, int bu, int bd, uint32_t site,
                                             uint32_t step, real* fl, real* pl, int LzLx, double& acc_p,
-                                            double& acc_a, double& acc_b, real* outA, real* outB, int ostride,
-                                            int flags, const BmTables<real>* bm) {
+                                            double& acc_a, double& acc_b, Pr<real>* out, int ostride, int flags,
+                                            const BmTables<real>* bm) {
   using P = Pr<real>;
   const P c9 = pr(real(1) / 9), c36 = pr(real(1) / 36);
   const P d = ring[bc];
@@ -469,7 +451,7 @@ __device__ __forceinline__ void site_update(const SiteK<real>& K, const RowConst
 #pragma unroll
     for (int k = 3; k < 9; ++k) nz[k] = pr(g[k - 1], g[k + 5]);
   }
-  collide_out<real, NOISE, UNIT, TO_GLOBAL, STRIDE>(m, d, rs, Ux, Uz, Fx, Fz, K, nz, cm, cq, outA, outB, ostride);
+  collide_out<real, NOISE, UNIT>(m, d, rs, Ux, Uz, Fx, Fz, K, nz, cm, cq, out, ostride);
 }
 
 __device__ __forceinline__ void block_partials(double acc_p, double acc_a, double acc_b, double* red, double* out) {
@@ -501,8 +483,8 @@ __device__ __forceinline__ void block_partials(double acc_p, double acc_a, doubl
 // ======================================================================================
 // Shared-memory layouts.
 // ======================================================================================
-// Generic: reduction scratch, lattice constants, density ring (2 x 4 rows of TX + 2), stage
-// (NS rows x 18 links x (TX + 2)).
+// Generic: reduction scratch, lattice constants, density ring (4 rows of TX + 2 pairs), stage
+// (NS rows x 9 links x (TX + 2) pairs).
 template <class real>
 struct BmBytes {
   static constexpr size_t value = sizeof(real) == 8 ? sizeof(BmTables<double>) : 0;
@@ -515,7 +497,7 @@ struct Smem {
   static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
   __host__ __device__ static size_t stage(int tx) { return ring + (size_t)8 * (tx + 2) * sizeof(real); }
   __host__ __device__ static size_t bm(int tx) {
-    return ((stage(tx) + (size_t)NS * 18 * (tx + 2) * sizeof(real) + 15) / 16) * 16;
+    return ((stage(tx) + (size_t)NS * 9 * (tx + 2) * sizeof(Pr<real>) + 15) / 16) * 16;
   }
   __host__ __device__ static size_t bytes(int tx) { return bm(tx) + BmBytes<real>::value; }
 };
@@ -525,19 +507,21 @@ struct Smem {
 // the double-precision Box-Muller tables (FP64 kernels only).
 template <class real, int TX>
 struct SmemBulk {
-  static constexpr int PAD = 16 / (int)sizeof(real);
+  // halo columns on each side: the densities of the columns next to the strip pull from two
+  // columns out (16 or 32 bytes of pairs, so every copy stays 16-byte aligned)
+  static constexpr int PAD = 2;
   static constexpr int SW = TX + 2 * PAD;
-  using LAY = SlotLayout<SW, (int)sizeof(real)>;
+  using LAY = SlotLayout<SW, (int)sizeof(Pr<real>)>;
   static constexpr size_t red = 0;
   static constexpr size_t lat = 8 * 3 * sizeof(double);
   static constexpr size_t ring = lat + ((sizeof(LatticeDev<real>) + 15) / 16) * 16;
   static constexpr size_t in = ((ring + 8 * (TX + 2) * sizeof(real) + 127) / 128) * 128;
-  static constexpr size_t bars = in + (size_t)NSI * LAY::slot * sizeof(real);
+  static constexpr size_t bars = in + (size_t)NSI * LAY::slot * sizeof(Pr<real>);
   static constexpr size_t abort_flag = bars + NSI * sizeof(uint64_t);
   static constexpr size_t tmap = abort_flag + 8;  // the item's tensor maps (pointer), or null
-  // per-plane and per-run copy descriptors (int4 each), filled once per launch by bulk_init
+  // per-link and per-run copy descriptors (int4 each), filled once per launch by bulk_init
   static constexpr size_t ptab = ((tmap + 8 + 15) / 16) * 16;
-  static constexpr size_t rtab = ptab + 18 * 16;
+  static constexpr size_t rtab = ptab + 9 * 16;
   static constexpr size_t bm = rtab + 6 * 16;  // 16-byte entries
   static constexpr size_t bytes = bm + BmBytes<real>::value;
   static_assert(in % 128 == 0 && bars % 8 == 0 && tmap % 8 == 0 && ptab % 16 == 0 && bm % 16 == 0,
@@ -556,7 +540,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + Smem<real>::lat);
   const int TX = blockDim.x, W = TX + 2;
   Pr<real>* ring = reinterpret_cast<Pr<real>*>(smem + Smem<real>::ring);
-  real* stage = reinterpret_cast<real*>(smem + Smem<real>::stage(TX));
+  Pr<real>* stage = reinterpret_cast<Pr<real>*>(smem + Smem<real>::stage(TX));
 
   const WorkItem it = a.items[item_index];
   __syncthreads();  // shared memory may still be read for the previous item
@@ -575,8 +559,8 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
   const int xl = (it.x0 == 0) ? Lx - 1 : it.x0 - 1;
   const int xr = (it.x0 + nact == Lx) ? 0 : it.x0 + nact;
   const bool do_left = tid == 0, do_right = tid == nact - 1;
-  const real* f = src + L.f_off;
-  real* g = dst + L.f_off;
+  const Pr<real>* f = reinterpret_cast<const Pr<real>*>(src + L.f_off);  // [link][z][x] pairs
+  Pr<real>* g = reinterpret_cast<Pr<real>*>(dst + L.f_off);
   const real k9 = L.k9, k36 = L.k36;
   const int flags = L.flags;
   const RowConst<real>* rows = a.rows + L.row_off;
@@ -588,7 +572,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
 
   auto stage_row = [&](int r) {
     if (r >= 0 && r < Lz && r <= z1) {
-      real* sb = stage + (r & (NS - 1)) * 18 * W;
+      Pr<real>* sb = stage + (r & (NS - 1)) * 9 * W;
       if (active) stage_column(f, LzLx, Lx, Lz, r, x, sb + tid + 1, W);
       if (do_left) stage_column(f, LzLx, Lx, Lz, r, xl, sb, W);
       if (do_right) stage_column(f, LzLx, Lx, Lz, r, xr, sb + nact + 1, W);
@@ -596,7 +580,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     cp_commit();
   };
   auto rho_at = [&](int r, int c) {
-    const real* sb = stage + (r & (NS - 1)) * 18 * W;
+    const Pr<real>* sb = stage + (r & (NS - 1)) * 9 * W;
     Pr<real> v[9];
     read_generic(sb, W, c, r > 0, r < Lz - 1, k9, k36, v);
     return sum9<real>(v);
@@ -645,7 +629,7 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real* sb = stage + (z & (NS - 1)) * 18 * W;
+      const Pr<real>* sb = stage + (z & (NS - 1)) * 9 * W;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
       // the variants are inlined; the branches are uniform over the block (one lattice per item)
@@ -654,10 +638,9 @@ __device__ __forceinline__ void process_item(const StepArgs<real>& a, const real
         read_generic(sb, W, tid + 1, below, above, k9, k36, v);
         Mom<real> m = moments<real>(v);
         if (below && above) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
-        site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
-            K, rows[z], m, ring, bc, bu, bd, site, step,
-            a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
-            g + 9 * LzLx + r0, LzLx, flags, bm);
+        site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value>(
+            K, rows[z], m, ring, bc, bu, bd, site, step, a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0,
+            LzLx, acc_p, acc_a, acc_b, g + r0, LzLx, flags, bm);
       };
       if (flags & DF_UNIT) {
         if (flags & DF_ASTAR) site_at(BoolC<true>(), BoolC<true>());
@@ -686,15 +669,15 @@ __device__ __forceinline__ void bulk_init(unsigned char* smem) {
     *reinterpret_cast<volatile int*>(smem + SM::abort_flag) = 0;
     mbar_fence_init();
   }
-  // plane k = 9 s + l: (slot offset, c_z, source plane, source plane on a reflected link);
-  // run j: (slot offset, first link, first link when reflected, run length + 4 (c_z + 1))
+  // link l: (slot offset, c_z, source link, source link on a reflected row); run j: (slot
+  // offset, first link, first link when reflected, run length + 4 (c_z + 1))
   const int t = threadIdx.x;
-  if (t < 18) {
-    const int s = t / 9, l = t - 9 * s, j = run_of(l);
+  if (t < 9) {
+    const int j = run_of(t);
     reinterpret_cast<int4*>(smem + SM::ptab)[t] =
-        make_int4(LAY::base_of(j) + (s * run_n(j) + l - run_l0(j)) * SM::SW, LB_CZ(l), t, 9 * s + LB_OPP(l));
-  } else if (t < 24) {
-    const int j = t - 18, l0 = run_l0(j);
+        make_int4(LAY::base_of(j) + (t - run_l0(j)) * SM::SW, LB_CZ(t), t, LB_OPP(t));
+  } else if (t < 15) {
+    const int j = t - 9, l0 = run_l0(j);
     reinterpret_cast<int4*>(smem + SM::rtab)[j] =
         make_int4(LAY::base_of(j), l0, LB_OPP(l0), run_n(j) + 4 * (LB_CZ(l0) + 1));
   }
@@ -714,7 +697,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   const BmTables<real>* bm = reinterpret_cast<const BmTables<real>*>(smem + SM::bm);
   LatticeDev<real>* Ls = reinterpret_cast<LatticeDev<real>*>(smem + SM::lat);
   Pr<real>* ring = reinterpret_cast<Pr<real>*>(smem + SM::ring);
-  real* instage = reinterpret_cast<real*>(smem + SM::in);
+  Pr<real>* instage = reinterpret_cast<Pr<real>*>(smem + SM::in);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SM::bars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::abort_flag);
 
@@ -744,8 +727,8 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   const bool active = tid < nact;
   const int x = x0 + (active ? tid : 0);
   const bool do_left = tid == 0, do_right = tid == nact - 1;
-  const real* f = src + L.f_off;
-  real* g = dst + L.f_off;
+  const Pr<real>* f = reinterpret_cast<const Pr<real>*>(src + L.f_off);  // [link][z][x] pairs
+  Pr<real>* g = reinterpret_cast<Pr<real>*>(dst + L.f_off);
   const real k9 = L.k9, k36 = L.k36;
   const int flags = L.flags;
   const RowConst<real>* rows = a.rows + L.row_off;
@@ -754,9 +737,9 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   // lattice's own site index z Lx + x unless it is an x-slab window of a wider lattice), carried
   // from row to row
   uint32_t site = (uint32_t)(z0 * L.site_Lx + (x + L.site_x0) % L.site_Lx);
-  const unsigned row_bytes = 18u * (unsigned)(nact + 2 * PAD) * (unsigned)sizeof(real);
+  const unsigned row_bytes = 9u * (unsigned)(nact + 2 * PAD) * (unsigned)sizeof(Pr<real>);
 
-  // copy k of row r (plane k, or run k on the tensor path; its source row, reflected at the
+  // copy k of row r (link row k, or run k on the tensor path; its source row, reflected at the
   // walls) is issued by lane k / NW of warp k % NW, so that every warp issues about the same
   // number of copies
   constexpr int NW = TX / 32;
@@ -765,10 +748,11 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
   auto stage_row = [&](int r, int slot) {
     if (r < 0 || r >= Lz || r > z1) return;
     uint64_t* bar = bars + slot;
-    real* sbase = instage + slot * LAY::slot;
+    Pr<real>* sbase = instage + slot * LAY::slot;
     if (tid == 0) mbar_expect_tx(bar, row_bytes);
-    // interior strips (no periodic wrap) with tensor maps: one 4-d tensor copy per run of links
-    // (both species); otherwise one 1-d bulk copy (or up to three at the x edges) per plane
+    const unsigned sz = (unsigned)sizeof(Pr<real>);
+    // interior strips (no periodic wrap) with tensor maps: one 3-d tensor copy per run of links;
+    // otherwise one 1-d bulk copy (or up to three at the x edges) per link row
     if (TX + 2 * PAD <= 256 && a.tmaps != nullptr && x0 > 0 && x0 + nact < Lx) {
       if (my_plane < 6) {
         const CUtensorMap* maps = *tmap_s;
@@ -779,27 +763,23 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
           sr = r;
           ls = e.z;
         }
-        real* d = sbase + e.x;
+        Pr<real>* d = sbase + e.x;
         if (maps) {
-          tensor_g2s(d, maps + (n - 1), x0 - PAD, sr, ls, 0, bar);
-        } else {  // the same box as 1-d copies, one per plane
-          for (int q = 0; q < 2 * n; ++q) {
-            const int s = q / n, l = ls + q - s * n;
-            bulk_g2s(d + q * SW, f + (size_t)(9 * s + l) * LzLx + (size_t)sr * Lx + x0 - PAD,
-                     (unsigned)SW * (unsigned)sizeof(real), bar);
-          }
+          tensor_g2s(d, maps + (n - 1), x0 - PAD, sr, ls, bar);
+        } else {  // the same box as 1-d copies, one per link row
+          for (int q = 0; q < n; ++q)
+            bulk_g2s(d + q * SW, f + (size_t)(ls + q) * LzLx + (size_t)sr * Lx + x0 - PAD, (unsigned)SW * sz, bar);
         }
       }
-    } else if (my_plane < 18) {
+    } else if (my_plane < 9) {
       const int4 e = ptab[my_plane];
       int sr = r - e.y, p = e.z;
       if (sr < 0 || sr >= Lz) {
         sr = r;
         p = e.w;
       }
-      const real* rowp = f + (size_t)p * LzLx + (size_t)sr * Lx;
-      real* d = sbase + e.x;
-      const unsigned sz = (unsigned)sizeof(real);
+      const Pr<real>* rowp = f + (size_t)p * LzLx + (size_t)sr * Lx;
+      Pr<real>* d = sbase + e.x;
       if (x0 > 0 && x0 + nact < Lx) {
         bulk_g2s(d, rowp + x0 - PAD, (unsigned)(nact + 2 * PAD) * sz, bar);
       } else {
@@ -829,7 +809,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     ph ^= 1u << slot;
   };
   auto rho_at = [&](int r, int slot, int j) {
-    const real* sb = instage + slot * LAY::slot;
+    const Pr<real>* sb = instage + slot * LAY::slot;
     Pr<real> v[9];
     read_bulk<real, SW>(sb, j, r > 0, r < Lz - 1, k9, k36, v);
     return sum9<real>(v);
@@ -882,7 +862,7 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
     if (active) {
       const int bc = ring_slot(z) * W + tid + 1, bu = ring_slot(z + 1) * W + tid + 1,
                 bd = ring_slot(z - 1) * W + tid + 1;
-      const real* sb = instage + sc * LAY::slot;
+      const Pr<real>* sb = instage + sc * LAY::slot;
       const bool below = z > 0, above = z < Lz - 1;
       const int r0 = z * Lx + x;
       // the variants are inlined; the branches are uniform over the block (one lattice per item,
@@ -893,10 +873,9 @@ __device__ __forceinline__ bool process_item_bulk(const StepArgs<real>& a, const
         read_bulk<real, SW>(sb, tid + PAD, IN || below, IN || above, k9, k36, v);
         Mom<real> m = moments<real>(v);
         if (IN) m.m2 = add2(m.m2, interior_m2_shift(k9, k36));
-        site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value, true, 0>(
-            K, rows[z], m, ring, bc, bu, bd, site, step,
-            a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0, LzLx, acc_p, acc_a, acc_b, g + r0,
-            g + 9 * LzLx + r0, LzLx, flags, bm);
+        site_update<real, SAMPLE, NOISE, decltype(unit)::value, decltype(astar)::value>(
+            K, rows[z], m, ring, bc, bu, bd, site, step, a.fields + 4 * L.site_off + r0, a.pfield + L.site_off + r0,
+            LzLx, acc_p, acc_a, acc_b, g + r0, LzLx, flags, bm);
       };
       auto rates = [&](auto inner) {
         if (flags & DF_UNIT) {
