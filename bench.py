@@ -113,16 +113,20 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ("lb_step_impl.cuh", "lb_internal.cuh")
+
+
 def kernel_code_hash():
-    """sha256 of the step kernels' source with comments and blank lines removed (a comment edit
-    does not change the kernel)."""
+    """sha256 of the step kernels' sources (the kernel and the layouts and device helpers it
+    includes) with comments and blank lines removed (a comment edit does not change the kernel)."""
     lines = []
-    with open(os.path.join(ROOT, "paper_1808_05168_gb300", "csrc", "lb_step_impl.cuh")) as f:
-        for ln in f.read().splitlines():
-            i = ln.find("//")
-            ln = (ln if i < 0 else ln[:i]).rstrip()
-            if ln:
-                lines.append(ln)
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1808_05168_gb300", "csrc", name)) as f:
+            for ln in f.read().splitlines():
+                i = ln.find("//")
+                ln = (ln if i < 0 else ln[:i]).rstrip()
+                if ln:
+                    lines.append(ln)
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
