@@ -29,7 +29,7 @@
 #include <cmath>
 #include <vector>
 
-#include "lb_internal.cuh"
+#include "lb_adjoint.cuh"
 
 namespace lbk {
 
@@ -67,9 +67,8 @@ __device__ __forceinline__ void all_moments(const real v[9], real m[9]) {
   m[8] = 2 * v[0] - 4 * e + 8 * dg;
 }
 
-__constant__ int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int kCZ[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-__constant__ int kOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+// The lattice velocities enter through LB_CX / LB_CZ / LB_OPP in fully unrolled loops: as
+// compile-time constants, the products with c = 0 and c = +-1 cost no FP64 instruction.
 
 // Deviations of the 18 populations pulled at (x, z) (Eq. LB; reflected at the walls; the
 // background streaming shift on non-reflected links), as in the forward kernel.
@@ -81,30 +80,28 @@ __device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int L
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int l = 0; l < 9; ++l) {
-      const int zs = z - kCZ[l];
-      const int xs = (x - kCX[l] + Lx) % Lx;
+      const int zs = z - LB_CZ(l);
+      const int xs = LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx;
       double val;
       if (zs >= 0 && zs < Lz) {
         val = (double)f[state_index(s, l, zs, xs, Lx, LzLx)];
-        const double q = (l == 0 || l == 1 || l == 3) ? 0.0 : ((l <= 4) ? k9 : k36);
-        const double sh = kCZ[l] > 0 ? -q : (kCZ[l] < 0 ? q : 0.0);
-        val += s == 0 ? sh : -sh;
+        if (LB_CZ(l) != 0) {  // the background shift -c_lz w_l rho_bar d_z c_0 (k9, k36: species A)
+          const double q = l <= 4 ? k9 : k36;
+          const double sh = LB_CZ(l) > 0 ? -q : q;
+          val += s == 0 ? sh : -sh;
+        }
       } else {
-        val = (double)f[state_index(s, kOPP[l], z, x, Lx, LzLx)];
+        val = (double)f[state_index(s, LB_OPP(l), z, x, Lx, LzLx)];
       }
       v[s * 9 + l] = val;
     }
 }
 
-// Absolute pre-collision densities of every site.
+// Absolute pre-collision densities of site i = z Lx + x of state f, into rho[i] and rho[N + i].
 template <class real>
-__global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real>* lat, const RowConst<real>* rows,
-                               double* __restrict__ rho) {
-  const LatticeDev<real> L = lat[0];
+__device__ __forceinline__ void site_densities(const real* __restrict__ f, const LatticeDev<real>& L,
+                                               const RowConst<real>* rows, int i, int x, int z, double* rho) {
   const int N = L.Lx * L.Lz;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int x = i % L.Lx, z = i / L.Lx;
   double v[18];
   pull18(f, L.Lx, L.Lz, x, z, (double)L.k9, (double)L.k36, v);
   double a = 0, b = 0;
@@ -115,6 +112,17 @@ __global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real
   }
   rho[i] = (double)rows[z].bgA + a;
   rho[N + i] = (double)rows[z].bgB + b;
+}
+
+// Absolute pre-collision densities of every site.
+template <class real>
+__global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real>* lat, const RowConst<real>* rows,
+                               double* __restrict__ rho) {
+  const LatticeDev<real> L = lat[0];
+  const int N = L.Lx * L.Lz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  site_densities(f, L, rows, i, i % L.Lx, i / L.Lx, rho);
 }
 
 // Density of species s at (x, z) with the copy-rule wall ghosts.
@@ -128,12 +136,6 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// d sigma / d lambda for sigma^2 = K (2 - lambda) lambda.
-template <class real>
-__device__ __forceinline__ real dsigma(real sigma, real lam) {
-  return sigma * (1 - lam) / ((2 - lam) * lam);
 }
 
 // The fourteen normals of a site.  FP32: exactly those of the forward FP32 kernel.  FP64: the
@@ -173,7 +175,7 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
 // precision throughout, since the loss is a small difference of two runs' pressures.
 template <class real, bool NOISE>
 __global__ void adj_local_kernel(const real* __restrict__ f, const double* __restrict__ fbar,
-                                 const LatticeDev<real>* lat, const RowConst<real>* rows,
+                                 const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst kc,
                                  const double* __restrict__ rho, uint32_t step, double alpha, double* __restrict__ fl,
                                  double* __restrict__ sb, double* __restrict__ partials) {
   using real_s = real;
@@ -192,17 +194,22 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     const double rho_t = rA + rB, inv = double(1) / rho_t;
     // neighbour sums (Eq. aNI) and the pressure's neighbour sums, copy-rule ghosts
     double sAx = 0, sAz = 0, sBx = 0, sBz = 0, NA = 0, NB = 0;
+#pragma unroll
     for (int l = 1; l < 9; ++l) {
-      const double w = l <= 4 ? double(1) / 9 : double(1) / 36;
-      const double c2 = (double)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
-      const double a = rho_at(rho, Lx, Lz, 0, x + kCX[l], z + kCZ[l]);
-      const double b = rho_at(rho, Lx, Lz, 1, x + kCX[l], z + kCZ[l]);
-      sAx += w * kCX[l] * a;
-      sAz += w * kCZ[l] * a;
-      sBx += w * kCX[l] * b;
-      sBz += w * kCZ[l] * b;
-      NA += w * c2 * a;
-      NB += w * c2 * b;
+      constexpr double w9 = double(1) / 9, w36 = double(1) / 36;
+      const double w = l <= 4 ? w9 : w36, wc2 = l <= 4 ? w9 : 2 * w36;  // w_l, w_l |c_l|^2
+      const double a = rho_at(rho, Lx, Lz, 0, x + LB_CX(l), z + LB_CZ(l));
+      const double b = rho_at(rho, Lx, Lz, 1, x + LB_CX(l), z + LB_CZ(l));
+      if (LB_CX(l) != 0) {
+        sAx += (LB_CX(l) * w) * a;
+        sBx += (LB_CX(l) * w) * b;
+      }
+      if (LB_CZ(l) != 0) {
+        sAz += (LB_CZ(l) * w) * a;
+        sBz += (LB_CZ(l) * w) * b;
+      }
+      NA += wc2 * a;
+      NB += wc2 * b;
     }
     const double G = L.G;
     const double FNx = -G * (rA * sBx + rB * sAx), FNz = -G * (rA * sBz + rB * sAz);
@@ -255,10 +262,10 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
       double mbar[9];
       mbar[0] = 0;
       double meqb[6], srcb[6];
-      for (int a = 1; a < 9; ++a) mbar[a] = (1 - lam[a]) * sbar[a];
+      for (int a = 1; a < 9; ++a) mbar[a] = kc.oml[a] * sbar[a];
       for (int a = 1; a < 6; ++a) {
         meqb[a] = lam[a] * sbar[a];
-        srcb[a] = (1 - double(0.5) * lam[a]) * sbar[a];
+        srcb[a] = kc.ohl[a] * sbar[a];
         const double dl = sbar[a] * (meq[a] - m[a] - double(0.5) * src[a]);
         if (a <= 2) lamb_d += dl;
         else if (a >= 4) lamb_s += dl;
@@ -310,10 +317,8 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     rhob[1] += rhob_t;
     // noise amplitudes depend on lambda_d (moments 1, 2) and lambda_s (moments 4, 5)
     if (NOISE) {
-      const double dsm = dsigma<double>((double)L.sig_mom, ld);
-      lamb_d += dsm * (n[0] * (sbarA[1] - sbarB[1]) + n[1] * (sbarA[2] - sbarB[2]));
-      const double d4 = dsigma<double>((double)L.sig[4], ls), d5 = dsigma<double>((double)L.sig[5], ls);
-      lamb_s += d4 * (sbarA[4] * n[3] + sbarB[4] * n[9]) + d5 * (sbarA[5] * n[4] + sbarB[5] * n[10]);
+      lamb_d += kc.dsm * (n[0] * (sbarA[1] - sbarB[1]) + n[1] * (sbarA[2] - sbarB[2]));
+      lamb_s += kc.d4 * (sbarA[4] * n[3] + sbarB[4] * n[9]) + kc.d5 * (sbarA[5] * n[4] + sbarB[5] * n[10]);
     }
     gS += (double)lamb_s;
     gD += (double)lamb_d;
@@ -322,11 +327,9 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
       double o[9];
       mb[s][0] = rhob[s];
       transpose_moments(mb[s], o);
+      const double k1 = alpha * double(0.5), k2 = alpha;  // alpha |c_l|^2 / 2 on the axis, diagonal links
 #pragma unroll
-      for (int l = 0; l < 9; ++l) {
-        const double c2 = (double)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
-        fl[(s * 9 + l) * N + i] = o[l] + alpha * double(0.5) * c2;
-      }
+      for (int l = 0; l < 9; ++l) fl[(s * 9 + l) * N + i] = l == 0 ? o[l] : o[l] + (l <= 4 ? k1 : k2);
     }
   }
   // block partials of the parameter gradient
@@ -355,41 +358,57 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
 }
 
 // Gather the neighbour-owed density sensitivities and push along the transposed streaming map.
+// With f_next (the state before f_prev) given, also the densities of f_next into rho_next, for the
+// next adjoint step (one launch instead of two).
 template <class real>
-__global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const double* __restrict__ rho,
-                                       const double* __restrict__ fl, const double* __restrict__ sb, double alpha,
-                                       double* __restrict__ fbar_prev) {
+__global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowConst<real>* rows,
+                                       const double* __restrict__ rho, const double* __restrict__ fl,
+                                       const double* __restrict__ sb, double alpha, double* __restrict__ fbar_prev,
+                                       const real* __restrict__ f_next, double* __restrict__ rho_next) {
   const LatticeDev<real> L = lat[0];
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int x = i % Lx, z = i / Lx;
+  if (f_next) site_densities(f_next, L, rows, i, x, z, rho_next);
   const double q = alpha * 0.25 * (double)L.G;
   double rbA = 0, rbB = 0;
-  auto add_from = [&](int xs, int zs, int l) {
-    const int j = zs * Lx + ((xs + Lx) % Lx);
-    const double w = l <= 4 ? 1.0 / 9 : 1.0 / 36;
-    const double c2 = (double)(kCX[l] * kCX[l] + kCZ[l] * kCZ[l]);
-    rbA += w * (kCX[l] * sb[0 * N + j] + kCZ[l] * sb[1 * N + j]) + w * c2 * q * rho[N + j];
-    rbB += w * (kCX[l] * sb[2 * N + j] + kCZ[l] * sb[3 * N + j]) + w * c2 * q * rho[j];
-  };
+#pragma unroll
   for (int l = 1; l < 9; ++l) {
-    const int zs = z - kCZ[l];
-    if (zs >= 0 && zs < Lz) add_from(x - kCX[l], zs, l);
+    constexpr double w9 = 1.0 / 9, w36 = 1.0 / 36;
+    const double w = l <= 4 ? w9 : w36, wc2 = l <= 4 ? w9 : 2 * w36;  // w_l, w_l |c_l|^2
+    auto add_from = [&](int zs) {
+      const int j = zs * Lx + (LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx);
+      double ta = 0, tb = 0;
+      if (LB_CX(l) != 0) {
+        ta = LB_CX(l) * sb[0 * N + j];
+        tb = LB_CX(l) * sb[2 * N + j];
+      }
+      if (LB_CZ(l) != 0) {
+        ta = LB_CX(l) != 0 ? ta + LB_CZ(l) * sb[1 * N + j] : LB_CZ(l) * sb[1 * N + j];
+        tb = LB_CX(l) != 0 ? tb + LB_CZ(l) * sb[3 * N + j] : LB_CZ(l) * sb[3 * N + j];
+      }
+      rbA += w * ta + (wc2 * q) * rho[N + j];
+      rbB += w * tb + (wc2 * q) * rho[j];
+    };
+    const int zs = z - LB_CZ(l);
+    if (zs >= 0 && zs < Lz) add_from(zs);
     // the wall ghost next to this row copies this row's density
-    if ((z == 0 && kCZ[l] == -1) || (z == Lz - 1 && kCZ[l] == 1)) add_from(x - kCX[l], z, l);
+    if ((z == 0 && LB_CZ(l) == -1) || (z == Lz - 1 && LB_CZ(l) == 1)) add_from(z);
   }
-  const int LzLx = N;
+  const int64_t LzLx = N;
+#pragma unroll
   for (int s = 0; s < 2; ++s) {
     const double rb = s == 0 ? rbA : rbB;
+#pragma unroll
     for (int l = 0; l < 9; ++l) {
       const double val = fl[(s * 9 + l) * N + i] + rb;
-      const int zs = z - kCZ[l];
+      const int zs = z - LB_CZ(l);
       if (zs >= 0 && zs < Lz) {
-        const int xs = (x - kCX[l] + Lx) % Lx;
+        const int xs = LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx;
         fbar_prev[(s * 9 + l) * LzLx + zs * Lx + xs] = val;
       } else {
-        fbar_prev[(s * 9 + kOPP[l]) * LzLx + z * Lx + x] = val;
+        fbar_prev[(s * 9 + LB_OPP(l)) * LzLx + z * Lx + x] = val;
       }
     }
   }
@@ -417,16 +436,19 @@ __global__ void adj_sum_partials(const double* partials, int n, double* grad) {
 }  // namespace
 
 template <class real>
-cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* fbar_prev, const LatticeDev<real>* lat,
-                                const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
-                                double* rho, double* fl, double* sb, double* partials, cudaStream_t s) {
+cudaError_t launch_adjoint_step(const real* f_prev, const real* f_next, const double* fbar, double* fbar_prev,
+                                const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst& kc,
+                                int n_sites, uint32_t step, bool noise, double alpha, bool rho_ready, double* rho,
+                                double* rho_next, double* fl, double* sb, double* partials, cudaStream_t s) {
   const int nb = adjoint_blocks(n_sites);
-  adj_rho_kernel<real><<<nb, kAdjBlock, 0, s>>>(f_prev, lat, rows, rho);
+  if (!rho_ready) adj_rho_kernel<real><<<nb, kAdjBlock, 0, s>>>(f_prev, lat, rows, rho);
   if (noise)
-    adj_local_kernel<real, true><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
+    adj_local_kernel<real, true><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kc, rho, step, alpha, fl, sb,
+                                                          partials);
   else
-    adj_local_kernel<real, false><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, rho, step, alpha, fl, sb, partials);
-  adj_gather_push_kernel<real><<<nb, kAdjBlock, 0, s>>>(lat, rho, fl, sb, alpha, fbar_prev);
+    adj_local_kernel<real, false><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kc, rho, step, alpha, fl, sb,
+                                                           partials);
+  adj_gather_push_kernel<real><<<nb, kAdjBlock, 0, s>>>(lat, rows, rho, fl, sb, alpha, fbar_prev, f_next, rho_next);
   return cudaGetLastError();
 }
 
@@ -435,11 +457,13 @@ cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double*
   return cudaGetLastError();
 }
 
-template cudaError_t launch_adjoint_step<float>(const float*, const double*, double*, const LatticeDev<float>*,
-                                                const RowConst<float>*, int, uint32_t, bool, double, double*, double*,
-                                                double*, double*, cudaStream_t);
-template cudaError_t launch_adjoint_step<double>(const double*, const double*, double*, const LatticeDev<double>*,
-                                                 const RowConst<double>*, int, uint32_t, bool, double, double*,
-                                                 double*, double*, double*, cudaStream_t);
+template cudaError_t launch_adjoint_step<float>(const float*, const float*, const double*, double*,
+                                                const LatticeDev<float>*, const RowConst<float>*, const AdjConst&, int,
+                                                uint32_t, bool, double, bool, double*, double*, double*, double*,
+                                                double*, cudaStream_t);
+template cudaError_t launch_adjoint_step<double>(const double*, const double*, const double*, double*,
+                                                 const LatticeDev<double>*, const RowConst<double>*, const AdjConst&,
+                                                 int, uint32_t, bool, double, bool, double*, double*, double*, double*,
+                                                 double*, cudaStream_t);
 
 }  // namespace lbk

@@ -1,0 +1,48 @@
+// lb_adjoint.cuh -- host interface of the adjoint sweep (lb_adjoint.cu): the gradient of the
+// time-averaged mean-pressure shift with respect to (G, lambda_s, lambda_d).
+#pragma once
+
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+constexpr int kAdjBlock = 128;
+inline int adjoint_blocks(int n_sites) { return (n_sites + kAdjBlock - 1) / kAdjBlock; }
+
+// Per-lattice constants of the transposed step, formed once on the host in double precision from
+// the rates and noise amplitudes the device holds.  For sigma^2 = K (2 - lambda) lambda,
+// d sigma / d lambda = sigma (1 - lambda) / ((2 - lambda) lambda).
+struct AdjConst {
+  double oml[9];  // 1 - lambda_a (relaxation, Eq. MRT)
+  double ohl[6];  // 1 - lambda_a / 2 (second-order forcing, moments 1..5)
+  double dsm;     // d sigma / d lambda_d of the momentum noise (moments 1, 2)
+  double d4, d5;  // d sigma / d lambda_s of moments 4 and 5
+};
+
+template <class real>
+inline AdjConst adjoint_constants(const LatticeDev<real>& L) {
+  AdjConst k;
+  for (int a = 0; a < 9; ++a) k.oml[a] = 1 - (double)L.lam[a];
+  for (int a = 0; a < 6; ++a) k.ohl[a] = 1 - 0.5 * (double)L.lam[a];
+  auto dsigma = [](double sigma, double lam) { return sigma * (1 - lam) / ((2 - lam) * lam); };
+  const double ld = (double)L.lam[1], ls = (double)L.lam[4];
+  k.dsm = dsigma((double)L.sig_mom, ld);
+  k.d4 = dsigma((double)L.sig[4], ls);
+  k.d5 = dsigma((double)L.sig[5], ls);
+  return k;
+}
+
+// One adjoint step: from fbar (sensitivity to f*_k) and the forward state f_prev = f*_{k-1}, write
+// fbar_prev and add this step's gradient share, block by block, to partials (3 doubles per block
+// of adjoint_blocks(n_sites), zeroed before the sweep); then launch_adjoint_gradient sums the
+// blocks into grad[3].  rho (2 n_sites doubles) holds the densities of f_prev if rho_ready, else
+// they are computed first; with f_next = f*_{k-2} given, its densities go to rho_next for the next
+// step.  The sensitivities (fbar, rho, fl, sb) are double precision for either state precision.
+template <class real>
+cudaError_t launch_adjoint_step(const real* f_prev, const real* f_next, const double* fbar, double* fbar_prev,
+                                const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst& kc,
+                                int n_sites, uint32_t step, bool noise, double alpha, bool rho_ready, double* rho,
+                                double* rho_next, double* fl, double* sb, double* partials, cudaStream_t s);
+cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double* grad, cudaStream_t s);
+
+}  // namespace lbk

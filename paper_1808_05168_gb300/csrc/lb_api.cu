@@ -14,6 +14,7 @@
 #include <tuple>
 #include <vector>
 
+#include "lb_adjoint.cuh"
 #include "lb_internal.cuh"
 
 using namespace lbk;
@@ -1051,7 +1052,7 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   double* fb = want_grad ? (double*)alloc(2 * S * sizeof(double)) : nullptr;
   real* fields = (real*)alloc(4 * (size_t)N * sizeof(real));
   real* pfield = (real*)alloc((size_t)N * sizeof(real));
-  double* rho = want_grad ? (double*)alloc(2 * (size_t)N * sizeof(double)) : nullptr;
+  double* rho = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;  // two density sets
   double* fl = want_grad ? (double*)alloc(S * sizeof(double)) : nullptr;
   double* sb = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;
   double* partials = (double*)alloc((size_t)3 * c->items.size() * sizeof(double));
@@ -1084,6 +1085,8 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
     return a;
   };
   const BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+  const AdjConst kc = adjoint_constants(
+      make_lattice<real>(p, c->flags, c->dev32, c->f_off[0], c->site_off[0], c->row_off[0]));
   double L[2] = {0.0, 0.0};
   for (int run = 0; run < 2 && e == cudaSuccess; ++run) {
     const int noise = run == 0 ? c->noise_mode : NOISE_OFF;
@@ -1120,11 +1123,18 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
       for (int64_t i = 1; i < len; ++i)
         ok(launch_step<real>(args(ring + (i - 1) * S, ring + i * S, c0 + i - 1), c->tile_x, false, noise, c->bulk_ok,
                              st));
+      // the densities of each step's state come with the previous step's gather (within a
+      // segment; at its top they are computed on their own)
+      int rcur = 0;
       for (int64_t k = c0 + len - 1; k >= c0 && e == cudaSuccess; --k) {
-        ok(launch_adjoint_step<real>(ring + (k - c0) * S, fb + fcur * S, fb + (1 - fcur) * S,
-                                     (const LatticeDev<real>*)c->d_lat, (const RowConst<real>*)c->d_rows, N,
-                                     (uint32_t)k, noise != NOISE_OFF, alpha, rho, fl, sb, gpart, st));
+        double* rho_k = rho + (size_t)rcur * 2 * N;
+        double* rho_n = rho + (size_t)(1 - rcur) * 2 * N;
+        ok(launch_adjoint_step<real>(ring + (k - c0) * S, k > c0 ? ring + (k - 1 - c0) * S : nullptr, fb + fcur * S,
+                                     fb + (1 - fcur) * S, (const LatticeDev<real>*)c->d_lat,
+                                     (const RowConst<real>*)c->d_rows, kc, N, (uint32_t)k, noise != NOISE_OFF, alpha,
+                                     k < c0 + len - 1, rho_k, rho_n, fl, sb, gpart, st));
         fcur = 1 - fcur;
+        rcur = 1 - rcur;
       }
     }
   }

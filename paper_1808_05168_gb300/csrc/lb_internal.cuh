@@ -597,19 +597,6 @@ int power_spectrum_args_ok(const double* field, int Lx, int Lz, const double* ou
 // prepare_power_spectrum once per device, with that device current (LB_OK or LB_ERR_CUDA).
 int prepare_power_spectrum_current_device();
 
-// One adjoint step (lb_adjoint.cu): from fbar (sensitivity to f*_k) and the forward state f_prev
-// = f*_{k-1}, write fbar_prev and add this step's gradient share, block by block, to partials
-// (3 doubles per block of adjoint_blocks(n_sites), zeroed before the sweep); then
-// launch_adjoint_gradient sums the blocks into grad[3].  The sensitivities (fbar, rho, fl, sb) are
-// double precision for either state precision.
-constexpr int kAdjBlock = 128;
-inline int adjoint_blocks(int n_sites) { return (n_sites + kAdjBlock - 1) / kAdjBlock; }
-template <class real>
-cudaError_t launch_adjoint_step(const real* f_prev, const double* fbar, double* fbar_prev, const LatticeDev<real>* lat,
-                                const RowConst<real>* rows, int n_sites, uint32_t step, bool noise, double alpha,
-                                double* rho, double* fl, double* sb, double* partials, cudaStream_t s);
-cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double* grad, cudaStream_t s);
-
 // Measured fused multiply-add rate of the current device (FP64 or FP32 scalar FMA, 2 flops each),
 // best of five timed launches after a warm-up (lb_diag.cu).
 cudaError_t measure_fma_rate(bool fp64, double* flops_per_s);
