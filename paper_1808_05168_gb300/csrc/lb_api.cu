@@ -428,11 +428,11 @@ int build_schedule(lb_ctx* c, const std::vector<WorkItem>& items, const std::vec
   return LB_OK;
 }
 
-// The 4-d tensor maps of the bulk staging (see the bulk path of the step kernels): for both state
-// buffers and every lattice with strips away from its x edges (Lx > 2 tile_x), the populations
-// as [species][link][z][x] with a box of tile_x + 32 bytes' worth of columns, one row, one or
-// two links and both species.  Any map the driver does not accept switches the tensor copies
-// off for the context (the 1-d copies remain).
+// The tensor maps of the bulk staging (see the bulk path of the step kernels): for both FP32 state
+// buffers and every lattice with strips away from its x edges (Lx > 2 tile_x), the (A, B) pairs
+// as [link][z][x] with a box of tile_x + 4 pairs (two halo columns per side), one row and one or
+// two links.  Any map the driver does not accept switches the tensor copies off for the context
+// (the 1-d copies remain).
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

@@ -1,9 +1,10 @@
 // lb_internal.cuh -- types and device helpers shared by the library's translation units.
 //
-// Populations of lattice i live at f + lat[i].f_off with layout [species][link][z][x]
-// (x contiguous, structure of arrays).  The stored value is the post-collision population
-// minus the background b^S_l(z) = w_l rho_bar c^S_0(z) in LB_PREC_DEV32 mode, and the plain
-// post-collision population in LB_PREC_FP64 mode (where the background is zero).
+// Populations of lattice i live at f + lat[i].f_off as (A, B) pairs, [link][z][x][species]
+// (state_index; the two species of a link and site adjacent, then x).  The stored value is the
+// post-collision population minus the background b^S_l(z) = w_l rho_bar c^S_0(z) in
+// LB_PREC_DEV32 mode, and the plain post-collision population in LB_PREC_FP64 mode (where the
+// background is zero).
 #pragma once
 
 #include <cuda.h>  // CUtensorMap
