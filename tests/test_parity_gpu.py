@@ -198,9 +198,10 @@ def test_profiles_of_a_batch(prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "dev32"])
 def test_tensor_copies_of_link_runs_match_plane_copies_and_oracle(prec):
-    """Strips away from the periodic x edges are staged by 4-d tensor copies of runs of links
-    (both species per copy); the result is bit-identical to per-plane 1-d copies, for every tile
-    width that uses them, per-step and persistent launches, and matches the oracle."""
+    """Strips away from the periodic x edges are staged by 3-d tensor copies of runs of links
+    (8-byte (A, B) pair elements, FP32 state); the result is bit-identical to 1-d copies per link
+    row, for every tile width that uses them, per-step and persistent launches, and matches the
+    oracle."""
     p = LatticeParams(512, 32, kT=1e-5, G=0.5, grad_c0=0.4 / 32, seed=13)
     o = oracle_of(p)
     o.set_sampling(0, 5)
@@ -437,11 +438,14 @@ def test_correlations_of_a_batch(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "dev32"])
-def test_degenerate_lattices_in_one_batch(prec):
+@pytest.mark.parametrize("shapes", [[(1, 2), (1, 5), (2, 2), (3, 3), (4, 2), (5, 7)],
+                                    [(2, 2), (2, 5), (4, 2), (6, 3), (8, 7)]], ids=["generic", "bulk"])
+def test_degenerate_lattices_in_one_batch(prec, shapes):
     """The smallest lattices the method allows, in one batch: one column (every link wraps onto
     the site itself), two and three columns, and two rows (both rows are wall rows, every vertical
-    link is reflected), with the bulk-copy path on a 4-column (16-byte) lattice beside them."""
-    shapes = [(1, 2), (1, 5), (2, 2), (3, 3), (4, 2), (5, 7)]
+    link is reflected).  Bulk copies need every width of the batch even, so the odd widths run the
+    per-thread staging; the even batch runs the bulk copies, down to two columns, where both
+    two-column halos are the lattice itself."""
     ps = [LatticeParams(Lx, Lz, lambda_s=1.1, lambda_d=0.9, kT=1e-4, G=0.4, grad_c0=0.3 / Lz, seed=8,
                         lattice_id=i) for i, (Lx, Lz) in enumerate(shapes)]
     with Simulation(ps, precision=prec) as sim:
@@ -454,6 +458,31 @@ def test_degenerate_lattices_in_one_batch(prec):
             assert_fp64_parity(got[i], o.populations())
         else:
             assert_dev32_parity(got[i], o.populations(), background(p.Lx, p.Lz, p.grad_c0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_bulk_strips_with_a_two_column_remainder(prec):
+    """Bulk staging where the last strip holds two columns (Lx = tile + 2 and 2 tiles + 2): its
+    right halo wraps to x = 0, 1 while the strips before it stage full windows (by tensor copies
+    where they lie away from the x edges); per-step and persistent launches."""
+    ps = [LatticeParams(130, 9, lambda_s=1.2, lambda_d=0.9, kT=1e-4, G=0.5, grad_c0=0.3 / 9, seed=31, lattice_id=0),
+          LatticeParams(258, 6, lambda_s=1.2, lambda_d=0.9, kT=1e-4, G=0.5, grad_c0=0.2 / 6, seed=31, lattice_id=1)]
+    oracles = []
+    for p in ps:
+        o = oracle_of(p)
+        o.step(12)
+        oracles.append(o.populations())
+    for tile in [(128, 4), (64, 9)]:
+        for kw in (dict(), dict(persistent=True)):
+            with Simulation(ps, precision=prec, **kw) as sim:
+                sim.set_tile(*tile)
+                sim.step(12)
+                got = [sim.populations(i) for i in range(len(ps))]
+            for i, p in enumerate(ps):
+                if prec == "fp64":
+                    assert_fp64_parity(got[i], oracles[i])
+                else:
+                    assert_dev32_parity(got[i], oracles[i], background(p.Lx, p.Lz, p.grad_c0))
 
 
 def test_device_memory_from_the_callers_allocator():
