@@ -7,8 +7,10 @@
 //
 // One step k maps the stored state f*_{k-1} to f*_k (Eq. LB with Eq. MRT).  Its adjoint maps
 // fbar*_k (the loss's sensitivity to f*_k) to fbar*_{k-1} and adds the step's share of the
-// parameter gradient, in three kernels:
-//   1. densities: rho^S of the pre-collision state at every site (needed by the neighbours);
+// parameter gradient, in three passes:
+//   1. densities: rho^S of the pre-collision state at every site (needed by the neighbours),
+//      computed by the previous adjoint step's gather/push, or on their own at the top of a
+//      checkpoint segment;
 //   2. local: at every site, the forward quantities are recomputed and the transposed Jacobian
 //      of the site update is applied to fbar*_k(r) (plus the pressure term of the loss); this
 //      gives the sensitivity to the 18 pulled populations through the site's own moments and
