@@ -223,8 +223,8 @@ def run_ours(args):
         "config": {"workload": "c3 batched ensemble: 64 seeds x Lz {32,64,128,256} (Lx=4Lz) x dc {0.1,0.3,0.5}, "
                                "G=0.5, kT=1e-5; 768 lattices, 66,846,720 sites per rank",
                    "lb_steps_per_step": P, "sample_every": P, "precision": "dev32 (f32 deviations, f64 sums)",
-                   "launch": "CUDA graph per period: one persistent launch of the 99 plain steps (items handed out "
-                             "in order, per-item dependencies), then the sample step and its kernels",
+                   "launch": "CUDA graph per period: the sample step and its kernels, then one persistent launch "
+                             "of the 99 plain steps (items handed out in order, per-item dependencies)",
                    "tile": {"tile_x": tile[0], "rows": tile[1]},
                    "l2": "state 9.6 GB >> 129 MB L2; no flush needed", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
