@@ -62,9 +62,9 @@ extern "C" {
 #define LB_AUTOTUNE 0x40   /* time the candidate tile shapes on the first lb_step          */
 #define LB_NO_BULK 0x80    /* stage populations with per-thread copies even where rows are
                               16-byte aligned (bulk copies are used by default there)     */
-#define LB_NO_TENSOR_MAPS 0x100 /* bulk staging with 1-d copies only: no 4-d tensor copies of
-                              runs of links (used by default for strips away from the
-                              periodic x edges with tiles of up to 128 columns)           */
+#define LB_NO_TENSOR_MAPS 0x100 /* bulk staging with 1-d copies only: no 3-d tensor copies of
+                              runs of links (used by default in FP32 for strips away from
+                              the periodic x edges with tiles of up to 128 columns)       */
 
 /* ---- structure-factor fields and modes (Appendix A) ---------------------------------- */
 #define LB_FIELD_RHO 0 /* delta rho = rho - rho_bar                                         */
@@ -265,8 +265,10 @@ int lb_power_spectrum_noalloc(const double* field, int Lx, int Lz, double* out, 
  * by a hand-written reverse sweep of the step that recomputes the forward states from
  * checkpoints taken every ckpt_every steps (1 <= ckpt_every <= steps); grad may be NULL to get
  * the loss alone.  The context's own state, step count and statistics are not touched.
- * Requires a single-lattice context with the default options (a* on, copy-rule wall ghosts,
- * hom noise; LB_ERR_STATE otherwise).  Device memory: about (steps/ckpt_every + ckpt_every + 5)
+ * Requires a single-lattice context (LB_ERR_STATE otherwise); every option of the step is
+ * differentiated: a* on or off (LB_NO_ASTAR), copy-rule or fixed-composition wall ghosts
+ * (LB_WALL_FIXED), hom or loc noise (LB_NOISE_LOC, whose amplitudes follow the local densities).
+ * Device memory: about (steps/ckpt_every + ckpt_every + 5)
  * states, allocated for the call and freed before it returns.  Synchronous. */
 int lb_pressure_shift_gradient(lb_ctx* ctx, int64_t steps, int64_t ckpt_every, double grad[3], double* loss);
 

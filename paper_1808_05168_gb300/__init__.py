@@ -57,8 +57,8 @@ class Simulation:
         graph: lb_step through captured CUDA graphs; persistent: one cooperative launch per run of
         plain steps (items handed out in order, each waiting only for its neighbours' previous
         step), the fastest launch for batches; autotune: time tile shapes on the first step.
-        bulk / tensor_maps: stage rows with bulk copies / with 4-d tensor copies of link runs
-        where possible (both default; results are bit-identical either way).
+        bulk / tensor_maps: stage rows with bulk copies / with 3-d tensor copies of link runs
+        (FP32) where possible (both default; results are bit-identical either way).
         allocator: None (the library allocates with cudaMalloc), "torch" (torch's caching
         allocator on the current device) or an (alloc, free) pair of capi callbacks."""
         if isinstance(lattices, LatticeParams):

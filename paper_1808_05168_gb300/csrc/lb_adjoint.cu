@@ -23,12 +23,13 @@
 // The forward states are recomputed segment by segment from checkpoints (every C steps) into a
 // ring of C states, so memory is O(T/C + C) states.
 //
-// Supported: one lattice, the a* correction on, wall ghosts copying the adjacent row, hom noise
-// (the default configuration); both precisions.
+// Supported: one lattice; the a* correction on or off, wall ghosts copying the adjacent row or
+// taking the fixed wall composition, hom or loc noise; both precisions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "lb_adjoint.cuh"
@@ -127,11 +128,17 @@ __global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real
   site_densities(f, L, rows, i, i % L.Lx, i / L.Lx, rho);
 }
 
-// Density of species s at (x, z) with the copy-rule wall ghosts.
-__device__ __forceinline__ double rho_at(const double* rho, int Lx, int Lz, int s, int x, int z) {
+// Density of species s at (x, z), beyond a wall the ghost of Sec. II.A: a copy of the adjacent
+// row, or (fixed) that row's total density split by the wall composition cw of that row.
+template <class real>
+__device__ __forceinline__ double rho_at(const double* rho, const RowConst<real>* rows, bool fixed, int Lx, int Lz,
+                                         int s, int x, int z) {
   x = (x + Lx) % Lx;
-  z = z < 0 ? 0 : (z >= Lz ? Lz - 1 : z);
-  return rho[s * Lx * Lz + z * Lx + x];
+  if (z >= 0 && z < Lz) return rho[s * Lx * Lz + z * Lx + x];
+  const int za = z < 0 ? 0 : Lz - 1;
+  if (!fixed) return rho[s * Lx * Lz + za * Lx + x];
+  const double cw = (double)rows[za].ghost_cA, t = rho[za * Lx + x] + rho[Lx * Lz + za * Lx + x];
+  return s == 0 ? cw * t : (1 - cw) * t;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -175,7 +182,7 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
 // slot of `partials` (zeroed before the sweep; one fixed summation order, step after step).
 // The state may be single precision (FP32 deviations); the transposed step is evaluated in double
 // precision throughout, since the loss is a small difference of two runs' pressures.
-template <class real, bool NOISE>
+template <class real, bool NOISE, bool OPTS>
 __global__ void adj_local_kernel(const real* __restrict__ f, const double* __restrict__ fbar,
                                  const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst kc,
                                  const double* __restrict__ rho, uint32_t step, double alpha, double* __restrict__ fl,
@@ -185,6 +192,9 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double gG = 0, gS = 0, gD = 0;
+  // the default options (a* on, copy-rule ghosts, hom noise) are compiled without the branches
+  const bool astar = !OPTS || (L.flags & DF_ASTAR), fixed = OPTS && (L.flags & DF_WALL_FIXED),
+             loc = OPTS && NOISE && (L.flags & DF_NOISE_LOC);
   if (i < N) {
     const int x = i % Lx, z = i / Lx;
     double v[18];
@@ -200,8 +210,8 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     for (int l = 1; l < 9; ++l) {
       constexpr double w9 = double(1) / 9, w36 = double(1) / 36;
       const double w = l <= 4 ? w9 : w36, wc2 = l <= 4 ? w9 : 2 * w36;  // w_l, w_l |c_l|^2
-      const double a = rho_at(rho, Lx, Lz, 0, x + LB_CX(l), z + LB_CZ(l));
-      const double b = rho_at(rho, Lx, Lz, 1, x + LB_CX(l), z + LB_CZ(l));
+      const double a = rho_at(rho, rows, fixed, Lx, Lz, 0, x + LB_CX(l), z + LB_CZ(l));
+      const double b = rho_at(rho, rows, fixed, Lx, Lz, 1, x + LB_CX(l), z + LB_CZ(l));
       if (LB_CX(l) != 0) {
         sAx += (LB_CX(l) * w) * a;
         sBx += (LB_CX(l) * w) * b;
@@ -217,8 +227,10 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     const double FNx = -G * (rA * sBx + rB * sAx), FNz = -G * (rA * sBz + rB * sAz);
     const double cA = rA * inv, cB = rB * inv;
     const double ne = rho_t * L.g3;
-    const double FA[2] = {cA * FNx, cA * FNz + ne};
-    const double FB[2] = {cB * FNx, cB * FNz - ne};
+    // the species' forces: with a*, F^S = (rho^S / rho) F_N; without, F^A = -G rho^A s^B and
+    // F^B = -G rho^B s^A; plus the gradient forcing +- (0, rho g3)
+    const double FA[2] = {astar ? cA * FNx : -G * rA * sBx, (astar ? cA * FNz : -G * rA * sBz) + ne};
+    const double FB[2] = {astar ? cB * FNx : -G * rB * sAx, (astar ? cB * FNz : -G * rB * sAz) - ne};
     const double Px = mA[1] + mB[1] + double(0.5) * FNx, Pz = mA[2] + mB[2] + double(0.5) * FNz;
     const double Ux = Px * inv, Uz = Pz * inv;
     const double ld = L.lam[1], le = L.lam[3], ls = L.lam[4], lq = L.lam[6], leps = L.lam[8];
@@ -238,6 +250,7 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     double mb[2][9];
     double lamb_d = 0, lamb_s = 0;
     double sbarA[9], sbarB[9];
+    double Fb[2][2];  // sensitivities of the species' forces (without a*)
     for (int s = 0; s < 2; ++s) {
       const double* m = s == 0 ? mA : mB;
       const double rs = s == 0 ? rA : rB;
@@ -282,13 +295,17 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
       const double Fbz = srcb[2] + 6 * srcb[3] * Uz - 2 * srcb[4] * Uz + srcb[5] * Ux;
       Ubx += 6 * srcb[3] * F[0] + 2 * srcb[4] * F[0] + srcb[5] * F[1];
       Ubz += 6 * srcb[3] * F[1] - 2 * srcb[4] * F[1] + srcb[5] * F[0];
-      // F^S = (rho^S / rho) F_N +- (0, rho g3)
-      const double cS = s == 0 ? cA : cB;
-      FNbx += cS * Fbx;
-      FNbz += cS * Fbz;
-      const double cSb = Fbx * FNx + Fbz * FNz;
-      rhob[s] += cSb * inv;
-      invb += cSb * rs;
+      if (astar) {  // F^S = (rho^S / rho) F_N +- (0, rho g3)
+        const double cS = s == 0 ? cA : cB;
+        FNbx += cS * Fbx;
+        FNbz += cS * Fbz;
+        const double cSb = Fbx * FNx + Fbz * FNz;
+        rhob[s] += cSb * inv;
+        invb += cSb * rs;
+      } else {
+        Fb[s][0] = Fbx;
+        Fb[s][1] = Fbz;
+      }
       rhob_t += (s == 0 ? 1 : -1) * L.g3 * Fbz;
       for (int a = 0; a < 9; ++a) mb[s][a] = mbar[a];
     }
@@ -305,10 +322,20 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     gG += (double)(-(FNbx * (rA * sBx + rB * sAx) + FNbz * (rA * sBz + rB * sAz)));
     rhob[0] += -G * (FNbx * sBx + FNbz * sBz);
     rhob[1] += -G * (FNbx * sAx + FNbz * sAz);
-    sb[0 * N + i] = -G * rB * FNbx;  // sensitivity of s^A (x, z)
-    sb[1 * N + i] = -G * rB * FNbz;
-    sb[2 * N + i] = -G * rA * FNbx;  // sensitivity of s^B (x, z)
-    sb[3 * N + i] = -G * rA * FNbz;
+    double eAx = 0, eAz = 0, eBx = 0, eBz = 0;  // the species' own forces (without a*)
+    if (!astar) {
+      gG += -(Fb[0][0] * rA * sBx + Fb[0][1] * rA * sBz + Fb[1][0] * rB * sAx + Fb[1][1] * rB * sAz);
+      rhob[0] += -G * (Fb[0][0] * sBx + Fb[0][1] * sBz);
+      rhob[1] += -G * (Fb[1][0] * sAx + Fb[1][1] * sAz);
+      eAx = -G * rB * Fb[1][0];
+      eAz = -G * rB * Fb[1][1];
+      eBx = -G * rA * Fb[0][0];
+      eBz = -G * rA * Fb[0][1];
+    }
+    sb[0 * N + i] = -G * rB * FNbx + eAx;  // sensitivity of s^A (x, z)
+    sb[1 * N + i] = -G * rB * FNbz + eAz;
+    sb[2 * N + i] = -G * rA * FNbx + eBx;  // sensitivity of s^B (x, z)
+    sb[3 * N + i] = -G * rA * FNbz + eBz;
     // the loss's pressure at this site: (1/2) sum |c|^2 f + (G/4) [rho^A N^B + rho^B N^A]
     rhob[0] += alpha * double(0.25) * G * NB;
     rhob[1] += alpha * double(0.25) * G * NA;
@@ -317,10 +344,30 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
     rhob_t += -invb * inv * inv;
     rhob[0] += rhob_t;
     rhob[1] += rhob_t;
-    // noise amplitudes depend on lambda_d (moments 1, 2) and lambda_s (moments 4, 5)
+    // noise amplitudes depend on lambda_d (moments 1, 2) and lambda_s (moments 4, 5); loc noise
+    // also on the site's densities: sigma_mom = p_mom sqrt(rho^A rho^B / rho), sigma^S_a = p_a
+    // sqrt(rho^S)
     if (NOISE) {
-      lamb_d += kc.dsm * (n[0] * (sbarA[1] - sbarB[1]) + n[1] * (sbarA[2] - sbarB[2]));
-      lamb_s += kc.d4 * (sbarA[4] * n[3] + sbarB[4] * n[9]) + kc.d5 * (sbarA[5] * n[4] + sbarB[5] * n[10]);
+      const double q1 = n[0] * (sbarA[1] - sbarB[1]) + n[1] * (sbarA[2] - sbarB[2]);
+      if (loc) {
+        const double sm = sqrt(rA * rB * inv), qA = sqrt(rA), qB = sqrt(rB);
+        lamb_d += kc.dpm * sm * q1;
+        lamb_s += kc.dp4 * (qA * sbarA[4] * n[3] + qB * sbarB[4] * n[9]) +
+                  kc.dp5 * (qA * sbarA[5] * n[4] + qB * sbarB[5] * n[10]);
+        // d sm / d rho^A = (rho^B / rho)^2 / (2 sm), d sm / d rho^B = (rho^A / rho)^2 / (2 sm)
+        const double hm = kc.pm * q1 * inv * inv / (2 * sm);
+        double tA = 0, tB = 0;
+#pragma unroll
+        for (int a = 3; a < 9; ++a) {
+          tA += kc.pa[a] * sbarA[a] * n[a - 1];
+          tB += kc.pa[a] * sbarB[a] * n[a + 5];
+        }
+        rhob[0] += hm * rB * rB + tA / (2 * qA);
+        rhob[1] += hm * rA * rA + tB / (2 * qB);
+      } else {
+        lamb_d += kc.dsm * q1;
+        lamb_s += kc.d4 * (sbarA[4] * n[3] + sbarB[4] * n[9]) + kc.d5 * (sbarA[5] * n[4] + sbarB[5] * n[10]);
+      }
     }
     gS += (double)lamb_s;
     gD += (double)lamb_d;
@@ -374,12 +421,14 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowCon
   const int x = i % Lx, z = i / Lx;
   if (f_next) site_densities(f_next, L, rows, i, x, z, rho_next);
   const double q = alpha * 0.25 * (double)L.G;
+  const bool fixed = L.flags & DF_WALL_FIXED;
   double rbA = 0, rbB = 0;
 #pragma unroll
   for (int l = 1; l < 9; ++l) {
     constexpr double w9 = 1.0 / 9, w36 = 1.0 / 36;
     const double w = l <= 4 ? w9 : w36, wc2 = l <= 4 ? w9 : 2 * w36;  // w_l, w_l |c_l|^2
-    auto add_from = [&](int zs) {
+    // what the site j = (x - c_lx, zs) owes the densities (A, B) its link l reaches
+    auto owed = [&](int zs, double& oa, double& ob) {
       const int j = zs * Lx + (LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx);
       double ta = 0, tb = 0;
       if (LB_CX(l) != 0) {
@@ -390,13 +439,29 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowCon
         ta = LB_CX(l) != 0 ? ta + LB_CZ(l) * sb[1 * N + j] : LB_CZ(l) * sb[1 * N + j];
         tb = LB_CX(l) != 0 ? tb + LB_CZ(l) * sb[3 * N + j] : LB_CZ(l) * sb[3 * N + j];
       }
-      rbA += w * ta + (wc2 * q) * rho[N + j];
-      rbB += w * tb + (wc2 * q) * rho[j];
+      oa = w * ta + (wc2 * q) * rho[N + j];
+      ob = w * tb + (wc2 * q) * rho[j];
     };
+    double oa, ob;
     const int zs = z - LB_CZ(l);
-    if (zs >= 0 && zs < Lz) add_from(zs);
-    // the wall ghost next to this row copies this row's density
-    if ((z == 0 && LB_CZ(l) == -1) || (z == Lz - 1 && LB_CZ(l) == 1)) add_from(z);
+    if (zs >= 0 && zs < Lz) {
+      owed(zs, oa, ob);
+      rbA += oa;
+      rbB += ob;
+    }
+    // the wall ghost next to this row: a copy of this row's densities, or (fixed) this row's total
+    // density split by the wall composition
+    if ((z == 0 && LB_CZ(l) == -1) || (z == Lz - 1 && LB_CZ(l) == 1)) {
+      owed(z, oa, ob);
+      if (fixed) {
+        const double cw = (double)rows[z].ghost_cA, t = cw * oa + (1 - cw) * ob;
+        rbA += t;
+        rbB += t;
+      } else {
+        rbA += oa;
+        rbB += ob;
+      }
+    }
   }
   const int64_t LzLx = N;
 #pragma unroll
@@ -444,12 +509,14 @@ cudaError_t launch_adjoint_step(const real* f_prev, const real* f_next, const do
                                 double* rho_next, double* fl, double* sb, double* partials, cudaStream_t s) {
   const int nb = adjoint_blocks(n_sites);
   if (!rho_ready) adj_rho_kernel<real><<<nb, kAdjBlock, 0, s>>>(f_prev, lat, rows, rho);
-  if (noise)
-    adj_local_kernel<real, true><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kc, rho, step, alpha, fl, sb,
-                                                          partials);
-  else
-    adj_local_kernel<real, false><<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kc, rho, step, alpha, fl, sb,
-                                                           partials);
+  auto local = [&](auto noise_c, auto opts_c) {
+    adj_local_kernel<real, decltype(noise_c)::value, decltype(opts_c)::value>
+        <<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kc, rho, step, alpha, fl, sb, partials);
+  };
+  using T = std::true_type;
+  using F = std::false_type;
+  if (noise) kc.options ? local(T(), T()) : local(T(), F());
+  else kc.options ? local(F(), T()) : local(F(), F());
   adj_gather_push_kernel<real><<<nb, kAdjBlock, 0, s>>>(lat, rows, rho, fl, sb, alpha, fbar_prev, f_next, rho_next);
   return cudaGetLastError();
 }

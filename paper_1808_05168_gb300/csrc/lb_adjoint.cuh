@@ -15,8 +15,12 @@ inline int adjoint_blocks(int n_sites) { return (n_sites + kAdjBlock - 1) / kAdj
 struct AdjConst {
   double oml[9];  // 1 - lambda_a (relaxation, Eq. MRT)
   double ohl[6];  // 1 - lambda_a / 2 (second-order forcing, moments 1..5)
-  double dsm;     // d sigma / d lambda_d of the momentum noise (moments 1, 2)
-  double d4, d5;  // d sigma / d lambda_s of moments 4 and 5
+  double dsm;     // d sigma / d lambda_d of the momentum noise (moments 1, 2), hom noise
+  double d4, d5;  // d sigma / d lambda_s of moments 4 and 5, hom noise
+  // loc noise: sigma_mom = pm sqrt(rho^A rho^B / rho) and sigma^S_a = pa[a] sqrt(rho^S) with the
+  // local densities; dpm = d pm / d lambda_d, dp4 and dp5 = d pa[4], pa[5] / d lambda_s
+  double pm, dpm, pa[9], dp4, dp5;
+  bool options;  // any of no a*, fixed wall composition, loc noise (the kernels that handle them)
 };
 
 template <class real>
@@ -29,6 +33,12 @@ inline AdjConst adjoint_constants(const LatticeDev<real>& L) {
   k.dsm = dsigma((double)L.sig_mom, ld);
   k.d4 = dsigma((double)L.sig[4], ls);
   k.d5 = dsigma((double)L.sig[5], ls);
+  k.pm = (double)L.pref_mom;
+  k.dpm = dsigma(k.pm, ld);
+  for (int a = 0; a < 9; ++a) k.pa[a] = a >= 3 ? (double)L.pref[a] : 0.0;
+  k.dp4 = dsigma(k.pa[4], ls);
+  k.dp5 = dsigma(k.pa[5], ls);
+  k.options = !(L.flags & DF_ASTAR) || (L.flags & (DF_WALL_FIXED | DF_NOISE_LOC));
   return k;
 }
 

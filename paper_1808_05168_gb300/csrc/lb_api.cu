@@ -1160,7 +1160,7 @@ extern "C" {
 
 int lb_pressure_shift_gradient(lb_ctx* c, int64_t steps, int64_t ckpt_every, double grad[3], double* loss) {
   if (!c || steps < 1 || ckpt_every < 1 || ckpt_every > steps) return LB_ERR_BAD_PARAM;
-  if (c->n_lat != 1 || (c->flags & (LB_NO_ASTAR | LB_WALL_FIXED | LB_NOISE_LOC))) return LB_ERR_STATE;
+  if (c->n_lat != 1) return LB_ERR_STATE;
   if (c->site_map[0] != std::make_pair(0, c->params[0].Lx)) return LB_ERR_STATE;
   if (steps >= ((int64_t)1 << 31)) return LB_ERR_BAD_PARAM;
   int rc = sync_and_check(c);

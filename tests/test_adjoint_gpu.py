@@ -106,11 +106,45 @@ def test_autograd_function():
     np.testing.assert_array_equal([G.grad.item(), ls.grad.item(), ld.grad.item()], 2.0 * g)
 
 
-def test_unsupported_configurations_are_refused():
+def test_batches_are_refused():
     with Simulation([LatticeParams(8, 4), LatticeParams(8, 4, lattice_id=1)]) as sim:
         with pytest.raises(capi.LBError) as e:
             sim.pressure_shift_gradient(10, 5)
         assert e.value.code == capi.LB_ERR_STATE
-    with Simulation(LatticeParams(8, 4, kT=1e-4), noise_loc=True) as sim:
-        with pytest.raises(capi.LBError):
-            sim.pressure_shift_gradient(10, 5)
+
+
+VARIANTS = {"no_astar": dict(astar=False), "wall_fixed": dict(wall_fixed=True), "noise_loc": dict(noise_loc=True),
+            "all_three": dict(astar=False, wall_fixed=True, noise_loc=True)}
+
+
+@pytest.mark.parametrize("prec,gtol,ltol", [("fp64", 1e-8, 1e-10), ("dev32", 3e-3, 1e-4)])
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_adjoint_of_every_step_option_matches_oracle(variant, prec, gtol, ltol):
+    """The options of the step (no a*, fixed wall composition in the ghosts of Sec. II.A, loc noise
+    whose amplitudes follow the local densities) against the oracle's dual-number gradient of the
+    same configuration."""
+    opts = VARIANTS[variant]
+    p = LatticeParams(**SMALL)
+    with Simulation(p, precision=prec, **opts) as sim:
+        loss, g = sim.pressure_shift_gradient(40, 7)
+    o_loss, o_g = oracle.pressure_shift_grad(p.Lx, p.Lz, 40, lambda_s=p.lambda_s, lambda_d=p.lambda_d,
+                                             lambda_e=p.lambda_e, kT=p.kT, G=p.G, grad_c0=p.grad_c0, seed=p.seed,
+                                             **opts)
+    assert abs(loss - o_loss) <= ltol * abs(o_loss), (loss, o_loss)
+    np.testing.assert_allclose(g, o_g, rtol=0, atol=gtol * np.max(np.abs(o_g)))
+
+
+def test_autograd_function_with_step_options():
+    import torch
+    from paper_1808_05168_gb300.autograd import MeanPressureShift
+    p = LatticeParams(**SMALL)
+    opts = VARIANTS["all_three"]
+    G = torch.tensor(p.G, dtype=torch.float64, requires_grad=True)
+    ls = torch.tensor(p.lambda_s, dtype=torch.float64, requires_grad=True)
+    ld = torch.tensor(p.lambda_d, dtype=torch.float64, requires_grad=True)
+    L = MeanPressureShift.apply(G, ls, ld, p, 25, 5, "fp64", opts)
+    L.backward()
+    with Simulation(p, precision="fp64", **opts) as sim:
+        loss, g = sim.pressure_shift_gradient(25, 5)
+    assert float(L.detach()) == loss
+    np.testing.assert_array_equal([G.grad.item(), ls.grad.item(), ld.grad.item()], g)
