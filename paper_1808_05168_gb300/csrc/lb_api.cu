@@ -110,7 +110,7 @@ struct lb_ctx {
   int* d_nbr_off = nullptr;       // persistent launch: dependency lists of the items (CSR)
   int* d_nbr = nullptr;
   int sched_items_cap = 0, sched_nbr_cap = 0;
-  CUtensorMap* d_tmaps = nullptr;  // bulk staging: 4-d tensor maps [buffer][lattice][run of 1, 2 links]
+  CUtensorMap* d_tmaps = nullptr;  // bulk staging: 3-d tensor maps [buffer][lattice][run of 1, 2 links]
   bool tma = false;                // d_tmaps holds maps for the current tile
   int* d_err = nullptr;
   double* d_scratch = nullptr;  // 18 * max_lattice_sites doubles (populations I/O)

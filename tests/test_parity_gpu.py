@@ -197,7 +197,7 @@ def test_profiles_of_a_batch(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "dev32"])
-def test_tensor_copies_of_link_runs_match_plane_copies_and_oracle(prec):
+def test_tensor_copies_of_link_runs_match_1d_copies_and_oracle(prec):
     """Strips away from the periodic x edges are staged by 3-d tensor copies of runs of links
     (8-byte (A, B) pair elements, FP32 state); the result is bit-identical to 1-d copies per link
     row, for every tile width that uses them, per-step and persistent launches, and matches the
