@@ -130,6 +130,10 @@ def kernel_code_hash():
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
+C3_WORKLOAD = ("c3 batched ensemble: 64 seeds x Lz {32,64,128,256} (Lx=4Lz) x dc {0.1,0.3,0.5}, G=0.5, "
+               "kT=1e-5; 768 lattices, 66,846,720 sites per rank")
+
+
 def kernel_traffic(kind):
     """DRAM bytes per LB step of the dominant kernel at full size from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
@@ -220,8 +224,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "c3 batched ensemble: 64 seeds x Lz {32,64,128,256} (Lx=4Lz) x dc {0.1,0.3,0.5}, "
-                               "G=0.5, kT=1e-5; 768 lattices, 66,846,720 sites per rank",
+        "config": {"workload": C3_WORKLOAD,
                    "lb_steps_per_step": P, "sample_every": P, "precision": "dev32 (f32 deviations, f64 sums)",
                    "launch": "CUDA graph per period: the sample step and its kernels, then one persistent launch "
                              "of the 99 plain steps (items handed out in order, per-item dependencies)",
@@ -438,7 +441,9 @@ def run_reference(args):
         "unit": "GLUPS", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "c3 batched ensemble (oracle on a bounded sample: its largest member)"},
+        "config": {"workload": C3_WORKLOAD, "lb_steps_per_step": LB_STEPS_PER_STEP,
+                   "sample_every": LB_STEPS_PER_STEP, "precision": "f64 (the oracle)",
+                   "sample": "a bounded sample per step: " + sample},
         "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
