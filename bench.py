@@ -298,6 +298,16 @@ def measure_adjoint(torch):
             sim.pressure_shift_gradient(2000, 100)
             t2 = time.perf_counter()
         out[prec] = {"loss_only_s": t1 - t0, "loss_and_gradient_s": t2 - t1, "ratio": (t2 - t1) / (t1 - t0)}
+    # 16 seeds of the same lattice in one sweep (each its own loss and gradient)
+    from dataclasses import replace
+    ps = [replace(p, seed=p.seed + k, lattice_id=k) for k in range(16)]
+    with Simulation(ps, precision="dev32") as sim:
+        sim.pressure_shift_gradients(100, 100)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.pressure_shift_gradients(2000, 100)
+        t1 = time.perf_counter()
+    out["dev32_batch16"] = {"lattices": 16, "loss_and_gradient_s": t1 - t0, "per_lattice_s": (t1 - t0) / 16}
     return out
 
 

@@ -272,6 +272,14 @@ int lb_power_spectrum_noalloc(const double* field, int Lx, int Lz, double* out, 
  * states, allocated for the call and freed before it returns.  Synchronous. */
 int lb_pressure_shift_gradient(lb_ctx* ctx, int64_t steps, int64_t ckpt_every, double grad[3], double* loss);
 
+/* lb_pressure_shift_gradient for every lattice of a batch in one sweep: each lattice's own loss
+ * L_i (its runs with and without noise, the spatial mean over its own sites) in losses[i] and its
+ * gradient in grads[3 i .. 3 i + 2] (host arrays of n_lat and 3 n_lat doubles; either may be
+ * NULL, grads NULL gives the losses alone).  A lattice's results equal those of a context that
+ * holds it alone, bit for bit.  Device memory: as above, for the states of the whole batch. */
+int lb_pressure_shift_gradient_batch(lb_ctx* ctx, int64_t steps, int64_t ckpt_every, double* grads,
+                                     double* losses);
+
 /* Clear the structure-factor and pressure accumulators (the step count is kept). */
 int lb_reset_statistics(lb_ctx* ctx);
 

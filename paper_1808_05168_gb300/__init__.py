@@ -183,6 +183,12 @@ class Simulation:
         the rest state over `steps` steps (reverse sweep with checkpoints every `ckpt_every`)."""
         return capi.lb_pressure_shift_gradient(self.h, steps, min(ckpt_every, steps), want_grad)
 
+    def pressure_shift_gradients(self, steps: int, ckpt_every: int = 100, want_grad: bool = True):
+        """pressure_shift_gradient of every lattice of the batch in one sweep: (losses[n],
+        grads[n, 3]); each lattice's results equal those of a context holding it alone."""
+        return capi.lb_pressure_shift_gradient_batch(self.h, steps, min(ckpt_every, steps), len(self.lattices),
+                                                     want_grad)
+
     def populations(self, lattice: int = 0) -> np.ndarray:
         Lx, Lz = self.shape(lattice)
         out = np.empty((2, 9, Lz, Lx), np.float64)

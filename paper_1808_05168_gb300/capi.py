@@ -43,7 +43,8 @@ EXPORTS = ("lb_create", "lb_create_batch", "lb_create_batch_with_allocator", "lb
            "lb_profile", "lb_set_correlations", "lb_correlation", "lb_mode_correlation", "lb_mean_pressure", "lb_mass", "lb_get_populations", "lb_set_populations", "lb_reset_statistics",
            "lb_device_bytes", "lb_kernel_launches", "lb_error_string", "lb_destroy", "lb_debug_barrier",
            "lb_debug_box_muller", "lb_debug_schedule",
-           "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient", "lb_set_site_map",
+           "lb_power_spectrum", "lb_power_spectrum_noalloc", "lb_pressure_shift_gradient",
+           "lb_pressure_shift_gradient_batch", "lb_set_site_map",
            "lb_export_columns", "lb_import_columns", "lb_debug_fma_rate", "lb_checkpoint_bytes",
            "lb_save_checkpoint", "lb_load_checkpoint")
 LB_NOALLOC_MAX_POINTS = 1 << 18
@@ -117,6 +118,7 @@ def load():
             "lb_power_spectrum": [vp, i, i, vp, vp],
             "lb_power_spectrum_noalloc": [vp, i, i, vp, vp],
             "lb_pressure_shift_gradient": [vp, i64, i64, dp, dp],
+            "lb_pressure_shift_gradient_batch": [vp, i64, i64, dp, dp],
             "lb_set_site_map": [vp, i, i, i],
             "lb_export_columns": [vp, i, i, i, vp],
             "lb_import_columns": [vp, i, i, i, vp],
@@ -386,6 +388,15 @@ def lb_pressure_shift_gradient(h, steps, ckpt_every, want_grad=True):
     _check(load().lb_pressure_shift_gradient(h, int(steps), int(ckpt_every), _dptr(grad) if want_grad else None,
                                              ctypes.byref(loss)), "lb_pressure_shift_gradient")
     return loss.value, (grad if want_grad else None)
+
+
+def lb_pressure_shift_gradient_batch(h, steps, ckpt_every, n_lattices, want_grad=True):
+    """(losses[n], grads[n, 3] or None): see include/lb.h."""
+    losses = np.zeros(int(n_lattices), np.float64)
+    grads = np.zeros((int(n_lattices), 3), np.float64)
+    _check(load().lb_pressure_shift_gradient_batch(h, int(steps), int(ckpt_every), _dptr(grads) if want_grad else None,
+                                                   _dptr(losses)), "lb_pressure_shift_gradient_batch")
+    return losses, (grads if want_grad else None)
 
 
 def lb_debug_barrier(blocks, expected, limit_ms):

@@ -23,8 +23,9 @@
 // The forward states are recomputed segment by segment from checkpoints (every C steps) into a
 // ring of C states, so memory is O(T/C + C) states.
 //
-// Supported: one lattice; the a* correction on or off, wall ghosts copying the adjacent row or
-// taking the fixed wall composition, hom or loc noise; both precisions.
+// Supported: every lattice of a batch at once, each with its own loss and gradient; the a*
+// correction on or off, wall ghosts copying the adjacent row or taking the fixed wall
+// composition, hom or loc noise; both precisions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -117,15 +118,22 @@ __device__ __forceinline__ void site_densities(const real* __restrict__ f, const
   rho[N + i] = (double)rows[z].bgB + b;
 }
 
-// Absolute pre-collision densities of every site.
+// The lattice of this block (AdjMap) and the block's first site within it.
+__device__ __forceinline__ int adj_lattice(const AdjMap& map) { return map.lat_of[blockIdx.x]; }
+__device__ __forceinline__ int adj_site(const AdjMap& map, int li) {
+  return (blockIdx.x - map.first[li]) * blockDim.x + threadIdx.x;
+}
+
+// Absolute pre-collision densities of every site of every lattice.
 template <class real>
 __global__ void adj_rho_kernel(const real* __restrict__ f, const LatticeDev<real>* lat, const RowConst<real>* rows,
-                               double* __restrict__ rho) {
-  const LatticeDev<real> L = lat[0];
+                               const AdjMap map, double* __restrict__ rho) {
+  const int li = adj_lattice(map);
+  const LatticeDev<real> L = lat[li];
   const int N = L.Lx * L.Lz;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = adj_site(map, li);
   if (i >= N) return;
-  site_densities(f, L, rows, i, i % L.Lx, i / L.Lx, rho);
+  site_densities(f + L.f_off, L, rows + L.row_off, i, i % L.Lx, i / L.Lx, rho + 2 * L.site_off);
 }
 
 // Density of species s at (x, z), beyond a wall the ghost of Sec. II.A: a copy of the adjacent
@@ -175,8 +183,9 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
   for (int p = 0; p < 7; ++p) normal_pair<float>(k[2 * p], k[2 * p + 1], n[2 * p], n[2 * p + 1], nullptr);
 }
 
-// The local part of the transposed step at every site (see the file comment).  alpha: weight of
-// the site's pressure in the loss.  Outputs: fl[18][N] (local sensitivity of the pulled
+// The local part of the transposed step at every site of every lattice (see the file comment).
+// alpha = sign w_loss: weight of the site's pressure in the loss.  Outputs, per lattice at its
+// site offset: fl[18][N] (local sensitivity of the pulled
 // populations), sb[4][N] (sensitivity of sum_l w_l c_l rho^A, rho^B (r + c_l): x, z for A then
 // B), and per block the three parameter partials (G, lambda_s, lambda_d), added to the block's own
 // slot of `partials` (zeroed before the sweep; one fixed summation order, step after step).
@@ -184,13 +193,24 @@ __device__ __forceinline__ void normals14<float>(uint32_t site, uint32_t step, c
 // precision throughout, since the loss is a small difference of two runs' pressures.
 template <class real, bool NOISE, bool OPTS>
 __global__ void adj_local_kernel(const real* __restrict__ f, const double* __restrict__ fbar,
-                                 const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst kc,
-                                 const double* __restrict__ rho, uint32_t step, double alpha, double* __restrict__ fl,
-                                 double* __restrict__ sb, double* __restrict__ partials) {
+                                 const LatticeDev<real>* lat, const RowConst<real>* rows,
+                                 const AdjConst* __restrict__ kcs, const AdjMap map, const double* __restrict__ rho,
+                                 uint32_t step, double sign, double* __restrict__ fl, double* __restrict__ sb,
+                                 double* __restrict__ partials) {
   using real_s = real;
-  const LatticeDev<real_s> L = lat[0];
+  const int li = adj_lattice(map);
+  const LatticeDev<real_s> L = lat[li];
+  const AdjConst& kc = kcs[li];
+  const double alpha = sign * kc.w_loss;  // weight of this site's pressure in the loss
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = adj_site(map, li);
+  // this lattice's part of the batch's buffers
+  f += L.f_off;
+  rows += L.row_off;
+  fbar += 18 * L.site_off;
+  rho += 2 * L.site_off;
+  fl += 18 * L.site_off;
+  sb += 4 * L.site_off;
   double gG = 0, gS = 0, gD = 0;
   // the default options (a* on, copy-rule ghosts, hom noise) are compiled without the branches
   const bool astar = !OPTS || (L.flags & DF_ASTAR), fixed = OPTS && (L.flags & DF_WALL_FIXED),
@@ -411,13 +431,23 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
 // next adjoint step (one launch instead of two).
 template <class real>
 __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowConst<real>* rows,
+                                       const AdjConst* __restrict__ kcs, const AdjMap map,
                                        const double* __restrict__ rho, const double* __restrict__ fl,
-                                       const double* __restrict__ sb, double alpha, double* __restrict__ fbar_prev,
+                                       const double* __restrict__ sb, double sign, double* __restrict__ fbar_prev,
                                        const real* __restrict__ f_next, double* __restrict__ rho_next) {
-  const LatticeDev<real> L = lat[0];
+  const int li = adj_lattice(map);
+  const LatticeDev<real> L = lat[li];
+  const double alpha = sign * kcs[li].w_loss;
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = adj_site(map, li);
   if (i >= N) return;
+  rows += L.row_off;
+  rho += 2 * L.site_off;
+  fl += 18 * L.site_off;
+  sb += 4 * L.site_off;
+  fbar_prev += 18 * L.site_off;
+  if (f_next) f_next += L.f_off;
+  rho_next += 2 * L.site_off;
   const int x = i % Lx, z = i / Lx;
   if (f_next) site_densities(f_next, L, rows, i, x, z, rho_next);
   const double q = alpha * 0.25 * (double)L.G;
@@ -481,9 +511,13 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowCon
   }
 }
 
-// grad[k] = sum over the blocks of partials[3 b + k]: one warp, lanes strided over the blocks, then
-// a fixed butterfly (deterministic).
-__global__ void adj_sum_partials(const double* partials, int n, double* grad) {
+// grads[3 i + k] = sum over the blocks b of lattice i of partials[3 b + k]: one warp per lattice
+// (block i), lanes strided over the blocks, then a fixed butterfly (deterministic).
+__global__ void adj_sum_partials(const double* partials, const AdjMap map, double* grads) {
+  const int li = blockIdx.x;
+  const int b0 = map.first[li], n = map.first[li + 1] - b0;
+  partials += 3 * (size_t)b0;
+  double* grad = grads + 3 * li;
   double a = 0, b = 0, c = 0;
   for (int k = threadIdx.x; k < n; k += 32) {
     a += partials[3 * k];
@@ -504,35 +538,37 @@ __global__ void adj_sum_partials(const double* partials, int n, double* grad) {
 
 template <class real>
 cudaError_t launch_adjoint_step(const real* f_prev, const real* f_next, const double* fbar, double* fbar_prev,
-                                const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst& kc,
-                                int n_sites, uint32_t step, bool noise, double alpha, bool rho_ready, double* rho,
-                                double* rho_next, double* fl, double* sb, double* partials, cudaStream_t s) {
-  const int nb = adjoint_blocks(n_sites);
-  if (!rho_ready) adj_rho_kernel<real><<<nb, kAdjBlock, 0, s>>>(f_prev, lat, rows, rho);
+                                const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst* kcs,
+                                bool options, const AdjMap& map, uint32_t step, bool noise, double sign,
+                                bool rho_ready, double* rho, double* rho_next, double* fl, double* sb,
+                                double* partials, cudaStream_t s) {
+  const int nb = map.n_blocks;
+  if (!rho_ready) adj_rho_kernel<real><<<nb, kAdjBlock, 0, s>>>(f_prev, lat, rows, map, rho);
   auto local = [&](auto noise_c, auto opts_c) {
     adj_local_kernel<real, decltype(noise_c)::value, decltype(opts_c)::value>
-        <<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kc, rho, step, alpha, fl, sb, partials);
+        <<<nb, kAdjBlock, 0, s>>>(f_prev, fbar, lat, rows, kcs, map, rho, step, sign, fl, sb, partials);
   };
   using T = std::true_type;
   using F = std::false_type;
-  if (noise) kc.options ? local(T(), T()) : local(T(), F());
-  else kc.options ? local(F(), T()) : local(F(), F());
-  adj_gather_push_kernel<real><<<nb, kAdjBlock, 0, s>>>(lat, rows, rho, fl, sb, alpha, fbar_prev, f_next, rho_next);
+  if (noise) options ? local(T(), T()) : local(T(), F());
+  else options ? local(F(), T()) : local(F(), F());
+  adj_gather_push_kernel<real>
+      <<<nb, kAdjBlock, 0, s>>>(lat, rows, kcs, map, rho, fl, sb, sign, fbar_prev, f_next, rho_next);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double* grad, cudaStream_t s) {
-  adj_sum_partials<<<1, 32, 0, s>>>(partials, adjoint_blocks(n_sites), grad);
+cudaError_t launch_adjoint_gradient(const double* partials, const AdjMap& map, double* grads, cudaStream_t s) {
+  adj_sum_partials<<<map.n_lat, 32, 0, s>>>(partials, map, grads);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_adjoint_step<float>(const float*, const float*, const double*, double*,
-                                                const LatticeDev<float>*, const RowConst<float>*, const AdjConst&, int,
-                                                uint32_t, bool, double, bool, double*, double*, double*, double*,
-                                                double*, cudaStream_t);
+                                                const LatticeDev<float>*, const RowConst<float>*, const AdjConst*,
+                                                bool, const AdjMap&, uint32_t, bool, double, bool, double*, double*,
+                                                double*, double*, double*, cudaStream_t);
 template cudaError_t launch_adjoint_step<double>(const double*, const double*, const double*, double*,
-                                                 const LatticeDev<double>*, const RowConst<double>*, const AdjConst&,
-                                                 int, uint32_t, bool, double, bool, double*, double*, double*, double*,
-                                                 double*, cudaStream_t);
+                                                 const LatticeDev<double>*, const RowConst<double>*, const AdjConst*,
+                                                 bool, const AdjMap&, uint32_t, bool, double, bool, double*, double*,
+                                                 double*, double*, double*, cudaStream_t);
 
 }  // namespace lbk

@@ -20,7 +20,8 @@ struct AdjConst {
   // loc noise: sigma_mom = pm sqrt(rho^A rho^B / rho) and sigma^S_a = pa[a] sqrt(rho^S) with the
   // local densities; dpm = d pm / d lambda_d, dp4 and dp5 = d pa[4], pa[5] / d lambda_s
   double pm, dpm, pa[9], dp4, dp5;
-  bool options;  // any of no a*, fixed wall composition, loc noise (the kernels that handle them)
+  bool options;   // any of no a*, fixed wall composition, loc noise (the kernels that handle them)
+  double w_loss;  // 1 / (T N): the loss's weight of one site's pressure at one step (set per call)
 };
 
 template <class real>
@@ -42,17 +43,32 @@ inline AdjConst adjoint_constants(const LatticeDev<real>& L) {
   return k;
 }
 
-// One adjoint step: from fbar (sensitivity to f*_k) and the forward state f_prev = f*_{k-1}, write
-// fbar_prev and add this step's gradient share, block by block, to partials (3 doubles per block
-// of adjoint_blocks(n_sites), zeroed before the sweep); then launch_adjoint_gradient sums the
-// blocks into grad[3].  rho (2 n_sites doubles) holds the densities of f_prev if rho_ready, else
-// they are computed first; with f_next = f*_{k-2} given, its densities go to rho_next for the next
-// step.  The sensitivities (fbar, rho, fl, sb) are double precision for either state precision.
+// The adjoint's blocks over a batch: the blocks of lattice i are first[i] .. first[i + 1] - 1
+// (adjoint_blocks of its sites each), lat_of[b] the lattice of block b; so every block belongs to
+// one lattice and a lattice's blocks and sums are those of the lattice alone.  Device arrays.
+struct AdjMap {
+  const int* lat_of;  // [n_blocks]
+  const int* first;   // [n_lat + 1]
+  int n_blocks, n_lat;
+};
+
+// One adjoint step of every lattice of the batch: from fbar (sensitivity to f*_k) and the forward
+// state f_prev = f*_{k-1}, write fbar_prev and add this step's gradient share, block by block, to
+// partials (3 doubles per block, zeroed before the sweep); then launch_adjoint_gradient sums each
+// lattice's blocks into grads[3 i ..].  The site-indexed buffers hold the lattices one after
+// another at their site offsets (LatticeDev::site_off): rho 2, fl and fbar 18, sb 4 doubles per
+// site; the states have the context's layout (LatticeDev::f_off).  rho holds the densities of
+// f_prev if rho_ready, else they are computed first; with f_next = f*_{k-2} given, its densities
+// go to rho_next for the next step.  kcs: the lattices' AdjConst (device); options: any lattice
+// uses a non-default option of the step; sign: +1 for the noisy run, -1 for the noiseless one
+// (the loss weight of a site is sign w_loss).  The sensitivities are double precision for either
+// state precision.
 template <class real>
 cudaError_t launch_adjoint_step(const real* f_prev, const real* f_next, const double* fbar, double* fbar_prev,
-                                const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst& kc,
-                                int n_sites, uint32_t step, bool noise, double alpha, bool rho_ready, double* rho,
-                                double* rho_next, double* fl, double* sb, double* partials, cudaStream_t s);
-cudaError_t launch_adjoint_gradient(const double* partials, int n_sites, double* grad, cudaStream_t s);
+                                const LatticeDev<real>* lat, const RowConst<real>* rows, const AdjConst* kcs,
+                                bool options, const AdjMap& map, uint32_t step, bool noise, double sign,
+                                bool rho_ready, double* rho, double* rho_next, double* fl, double* sb,
+                                double* partials, cudaStream_t s);
+cudaError_t launch_adjoint_gradient(const double* partials, const AdjMap& map, double* grads, cudaStream_t s);
 
 }  // namespace lbk

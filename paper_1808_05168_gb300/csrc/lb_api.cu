@@ -1027,15 +1027,31 @@ int prepare_power_spectrum_current_device() {
 namespace {
 
 // ---- adjoint sweep for the gradient of the mean-pressure shift -----------------------------
+// Every lattice of the context at once: losses[i] and grads[3 i ..] per lattice (either may be
+// null; grads null: the loss alone).
 template <class real>
-int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* loss) {
+int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grads, double* losses) {
   NvtxRange r("lb_pressure_shift_gradient");
-  const lb_params& p = c->params[0];
-  const int N = p.Lx * p.Lz;
-  const size_t S = (size_t)18 * N;  // reals per state (lattice 0 starts at offset 0)
+  const int n = c->n_lat;
+  const size_t S = c->n_f;         // reals per state: every lattice at its f_off
+  const size_t NS = c->n_sites;    // sites of the batch: every lattice at its site_off
   const int64_t nck = (T + C - 1) / C;
-  const bool want_grad = grad != nullptr;
+  const bool want_grad = grads != nullptr;
   cudaStream_t st = c->stream;
+  // the adjoint's blocks, lattice by lattice, and the lattices' constants of the transposed step
+  std::vector<int> first(n + 1, 0), lat_of;
+  std::vector<AdjConst> kcs(n);
+  bool options = false;
+  for (int i = 0; i < n; ++i) {
+    const int nb = adjoint_blocks(c->params[i].Lx * c->params[i].Lz);
+    first[i + 1] = first[i] + nb;
+    lat_of.insert(lat_of.end(), nb, i);
+    kcs[i] = adjoint_constants(
+        make_lattice<real>(c->params[i], c->flags, c->dev32, c->f_off[i], c->site_off[i], c->row_off[i]));
+    kcs[i].w_loss = 1.0 / ((double)T * (double)(c->params[i].Lx * c->params[i].Lz));
+    options = options || kcs[i].options;
+  }
+  const int nblk = first[n];
   std::vector<void*> owned;
   auto alloc = [&](size_t bytes) -> void* {
     void* q = ctx_malloc(c, bytes);
@@ -1050,18 +1066,20 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   real* ring = want_grad ? (real*)alloc(C * S * sizeof(real)) : nullptr;
   real* cur = (real*)alloc(2 * S * sizeof(real));
   double* fb = want_grad ? (double*)alloc(2 * S * sizeof(double)) : nullptr;
-  real* fields = (real*)alloc(4 * (size_t)N * sizeof(real));
-  real* pfield = (real*)alloc((size_t)N * sizeof(real));
-  double* rho = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;  // two density sets
+  real* fields = (real*)alloc(4 * NS * sizeof(real));
+  real* pfield = (real*)alloc(NS * sizeof(real));
+  double* rho = want_grad ? (double*)alloc(4 * NS * sizeof(double)) : nullptr;  // two density sets
   double* fl = want_grad ? (double*)alloc(S * sizeof(double)) : nullptr;
-  double* sb = want_grad ? (double*)alloc(4 * (size_t)N * sizeof(double)) : nullptr;
+  double* sb = want_grad ? (double*)alloc(4 * NS * sizeof(double)) : nullptr;
   double* partials = (double*)alloc((size_t)3 * c->items.size() * sizeof(double));
-  double* gpart = want_grad ? (double*)alloc((size_t)3 * adjoint_blocks(N) * sizeof(double)) : nullptr;
-  double* d_grad = (double*)alloc(3 * sizeof(double));
-  DiagStats* stats = (DiagStats*)alloc(sizeof(DiagStats));
+  double* gpart = want_grad ? (double*)alloc((size_t)3 * nblk * sizeof(double)) : nullptr;
+  double* d_grad = (double*)alloc((size_t)3 * n * sizeof(double));
+  DiagStats* stats = (DiagStats*)alloc((size_t)n * sizeof(DiagStats));
   int64_t* zero_t = (int64_t*)alloc(sizeof(int64_t));
-  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb || !gpart)) || !cur || !fields || !pfield || !partials ||
-      !d_grad || !stats || !zero_t) {
+  int* d_map = want_grad ? (int*)alloc((size_t)(nblk + n + 1) * sizeof(int)) : nullptr;
+  AdjConst* d_kcs = want_grad ? (AdjConst*)alloc((size_t)n * sizeof(AdjConst)) : nullptr;
+  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb || !gpart || !d_map || !d_kcs)) || !cur || !fields ||
+      !pfield || !partials || !d_grad || !stats || !zero_t) {
     release();
     return LB_ERR_OOM;
   }
@@ -1069,9 +1087,17 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   auto ok = [&](cudaError_t r) {
     if (e == cudaSuccess && r != cudaSuccess) e = r;
   };
+  AdjMap map{nullptr, nullptr, nblk, n};
+  if (want_grad) {
+    ok(cudaMemcpy(d_map, lat_of.data(), (size_t)nblk * sizeof(int), cudaMemcpyHostToDevice));
+    ok(cudaMemcpy(d_map + nblk, first.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    ok(cudaMemcpy(d_kcs, kcs.data(), (size_t)n * sizeof(AdjConst), cudaMemcpyHostToDevice));
+    map.lat_of = d_map;
+    map.first = d_map + nblk;
+  }
   ok(cudaMemsetAsync(zero_t, 0, sizeof(int64_t), st));
-  ok(cudaMemsetAsync(d_grad, 0, 3 * sizeof(double), st));
-  if (want_grad) ok(cudaMemsetAsync(gpart, 0, (size_t)3 * adjoint_blocks(N) * sizeof(double), st));
+  ok(cudaMemsetAsync(d_grad, 0, (size_t)3 * n * sizeof(double), st));
+  if (want_grad) ok(cudaMemsetAsync(gpart, 0, (size_t)3 * nblk * sizeof(double), st));
   auto args = [&](const real* src, real* dst, int64_t k) {
     StepArgs<real> a = step_args<real>(c, 0, 0);
     a.src = src;
@@ -1084,37 +1110,40 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
     a.partials = partials;
     return a;
   };
-  const BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
-  const AdjConst kc = adjoint_constants(
-      make_lattice<real>(p, c->flags, c->dev32, c->f_off[0], c->site_off[0], c->row_off[0]));
-  double L[2] = {0.0, 0.0};
+  std::vector<double> L0(n, 0.0), L1(n, 0.0);
+  std::vector<DiagStats> hs(n);
   for (int run = 0; run < 2 && e == cudaSuccess; ++run) {
     const int noise = run == 0 ? c->noise_mode : NOISE_OFF;
     NvtxRange rr(run == 0 ? "lb adjoint: noisy run" : "lb adjoint: noiseless run");
     // forward from rest: checkpoints f*_{c-1} before every C-th step, pressure of every step
-    ok(launch_init_rest<real>(cur, bp, st));
-    ok(cudaMemsetAsync(stats, 0, sizeof(DiagStats), st));
+    for (int i = 0; i < n; ++i) {
+      const lb_params& p = c->params[i];
+      const BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+      ok(launch_init_rest<real>(cur + c->f_off[i], bp, st));
+    }
+    ok(cudaMemsetAsync(stats, 0, (size_t)n * sizeof(DiagStats), st));
     for (int64_t k = 0; k < T && e == cudaSuccess; ++k) {
       real* src = cur + (k & 1) * S;
       real* dst = cur + ((k + 1) & 1) * S;
       if (k % C == 0) ok(cudaMemcpyAsync(ck + (k / C) * S, src, S * sizeof(real), cudaMemcpyDeviceToDevice, st));
       ok(launch_step<real>(args(src, dst, k), c->tile_x, true, noise, c->bulk_ok, st));
-      ok(launch_finalize(c->d_diag, 1, partials, stats, st));
+      ok(launch_finalize(c->d_diag, n, partials, stats, st));
     }
-    DiagStats hs;
-    ok(cudaMemcpyAsync(&hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(hs.data(), stats, (size_t)n * sizeof(DiagStats), cudaMemcpyDeviceToHost, st));
     ok(cudaStreamSynchronize(st));
     if (e != cudaSuccess) break;
-    if (hs.nonfinite) {
-      release();
-      return LB_ERR_NONFINITE;
+    for (int i = 0; i < n; ++i) {
+      if (hs[i].nonfinite) {
+        release();
+        return LB_ERR_NONFINITE;
+      }
+      (run == 0 ? L0 : L1)[i] = (hs[i].P_sum + hs[i].P_comp) / (double)T;
     }
-    L[run] = (hs.P_sum + hs.P_comp) / (double)T;
     if (!want_grad) continue;
     // reverse sweep, one checkpoint segment at a time; the run's sign (+ noisy, - noiseless)
-    // enters through the loss weight alpha, to which the whole sweep is linear
+    // enters through the loss weight alpha = sign / (T N) of each lattice, to which the whole
+    // sweep is linear
     const double sign = run == 0 ? 1.0 : -1.0;
-    const double alpha = sign / ((double)T * (double)N);
     int fcur = 0;
     ok(cudaMemsetAsync(fb, 0, S * sizeof(double), st));
     for (int64_t seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
@@ -1127,25 +1156,26 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
       // segment; at its top they are computed on their own)
       int rcur = 0;
       for (int64_t k = c0 + len - 1; k >= c0 && e == cudaSuccess; --k) {
-        double* rho_k = rho + (size_t)rcur * 2 * N;
-        double* rho_n = rho + (size_t)(1 - rcur) * 2 * N;
+        double* rho_k = rho + (size_t)rcur * 2 * NS;
+        double* rho_n = rho + (size_t)(1 - rcur) * 2 * NS;
         ok(launch_adjoint_step<real>(ring + (k - c0) * S, k > c0 ? ring + (k - 1 - c0) * S : nullptr, fb + fcur * S,
                                      fb + (1 - fcur) * S, (const LatticeDev<real>*)c->d_lat,
-                                     (const RowConst<real>*)c->d_rows, kc, N, (uint32_t)k, noise != NOISE_OFF, alpha,
-                                     k < c0 + len - 1, rho_k, rho_n, fl, sb, gpart, st));
+                                     (const RowConst<real>*)c->d_rows, d_kcs, options, map, (uint32_t)k,
+                                     noise != NOISE_OFF, sign, k < c0 + len - 1, rho_k, rho_n, fl, sb, gpart, st));
         fcur = 1 - fcur;
         rcur = 1 - rcur;
       }
     }
   }
   if (e == cudaSuccess && want_grad) {
-    ok(launch_adjoint_gradient(gpart, N, d_grad, st));
-    ok(cudaMemcpyAsync(grad, d_grad, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ok(launch_adjoint_gradient(gpart, map, d_grad, st));
+    ok(cudaMemcpyAsync(grads, d_grad, (size_t)3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
     ok(cudaStreamSynchronize(st));
   }
   release();
   if (e != cudaSuccess) return cuda_err(e);
-  if (loss) *loss = L[0] - L[1];
+  if (losses)
+    for (int i = 0; i < n; ++i) losses[i] = L0[i] - L1[i];
   int err = 0;
   if (cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && err) {
     cudaMemset(c->d_err, 0, sizeof(int));
@@ -1154,19 +1184,28 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grad, double* l
   return LB_OK;
 }
 
+int pressure_shift_checked(lb_ctx* c, int64_t steps, int64_t ckpt_every, double* grads, double* losses) {
+  if (!c || steps < 1 || ckpt_every < 1 || ckpt_every > steps) return LB_ERR_BAD_PARAM;
+  for (int i = 0; i < c->n_lat; ++i)
+    if (c->site_map[i] != std::make_pair(0, c->params[i].Lx)) return LB_ERR_STATE;
+  if (steps >= ((int64_t)1 << 31)) return LB_ERR_BAD_PARAM;
+  int rc = sync_and_check(c);
+  if (rc) return rc;
+  return c->dev32 ? pressure_shift_impl<float>(c, steps, ckpt_every, grads, losses)
+                  : pressure_shift_impl<double>(c, steps, ckpt_every, grads, losses);
+}
+
 }  // namespace
 
 extern "C" {
 
 int lb_pressure_shift_gradient(lb_ctx* c, int64_t steps, int64_t ckpt_every, double grad[3], double* loss) {
-  if (!c || steps < 1 || ckpt_every < 1 || ckpt_every > steps) return LB_ERR_BAD_PARAM;
-  if (c->n_lat != 1) return LB_ERR_STATE;
-  if (c->site_map[0] != std::make_pair(0, c->params[0].Lx)) return LB_ERR_STATE;
-  if (steps >= ((int64_t)1 << 31)) return LB_ERR_BAD_PARAM;
-  int rc = sync_and_check(c);
-  if (rc) return rc;
-  return c->dev32 ? pressure_shift_impl<float>(c, steps, ckpt_every, grad, loss)
-                  : pressure_shift_impl<double>(c, steps, ckpt_every, grad, loss);
+  if (c && c->n_lat != 1) return LB_ERR_STATE;
+  return pressure_shift_checked(c, steps, ckpt_every, grad, loss);
+}
+
+int lb_pressure_shift_gradient_batch(lb_ctx* c, int64_t steps, int64_t ckpt_every, double* grads, double* losses) {
+  return pressure_shift_checked(c, steps, ckpt_every, grads, losses);
 }
 
 int lb_create(lb_ctx** out, int Lx, int Lz, double lambda_s, double lambda_d, double lambda_e, double lambda_q,

@@ -113,6 +113,34 @@ def test_batches_are_refused():
         assert e.value.code == capi.LB_ERR_STATE
 
 
+@pytest.mark.parametrize("prec", ["fp64", "dev32"])
+def test_batch_gives_every_lattice_its_own_gradient(prec):
+    """One sweep over a batch of different lattices (sizes, parameters, seeds, ids): each lattice's
+    loss and gradient equal those of a context that holds it alone, bit for bit, and the oracle's
+    dual numbers."""
+    ps = [LatticeParams(**SMALL),
+          LatticeParams(24, 6, kT=2e-3, G=0.3, grad_c0=0.04, lambda_s=1.1, lambda_d=1.3, lambda_e=0.9, seed=7,
+                        lattice_id=1),
+          LatticeParams(130, 12, kT=1e-3, G=0.6, grad_c0=-0.02, lambda_s=0.8, lambda_d=1.0, seed=5, lattice_id=2)]
+    steps, ckpt = 30, 7
+    with Simulation(ps, precision=prec) as sim:
+        losses, grads = sim.pressure_shift_gradients(steps, ckpt)
+    for i, p in enumerate(ps):
+        with Simulation(p, precision=prec) as sim:
+            loss, g = sim.pressure_shift_gradient(steps, ckpt)
+        assert losses[i] == loss
+        np.testing.assert_array_equal(grads[i], g)
+        o_loss, o_g = oracle.pressure_shift_grad(p.Lx, p.Lz, steps, lambda_s=p.lambda_s, lambda_d=p.lambda_d,
+                                                 lambda_e=p.lambda_e, kT=p.kT, G=p.G, grad_c0=p.grad_c0,
+                                                 seed=p.seed, lattice_id=p.lattice_id)
+        gtol = 1e-8 if prec == "fp64" else 3e-3
+        np.testing.assert_allclose(g, o_g, rtol=0, atol=gtol * np.max(np.abs(o_g)))
+    with Simulation(ps, precision=prec) as sim:
+        losses2, none = sim.pressure_shift_gradients(steps, ckpt, want_grad=False)
+    assert none is None
+    np.testing.assert_array_equal(losses2, losses)
+
+
 VARIANTS = {"no_astar": dict(astar=False), "wall_fixed": dict(wall_fixed=True), "noise_loc": dict(noise_loc=True),
             "all_three": dict(astar=False, wall_fixed=True, noise_loc=True)}
 
