@@ -932,10 +932,14 @@ int create_impl(lb_ctx** out, int n, const lb_params* ps, int flags, lb_alloc_fn
               cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess))
     rc = LB_ERR_CUDA;
   if (!rc) {
-    // default tile: 128 columns; rows per item chosen so that the grid has a few waves
+    // default tile: 128 columns; rows per item chosen so that the grid has a few waves, down to
+    // 16 rows, or to 2 when a state buffer fits well inside L2 (32 MB): short items re-read two
+    // halo rows each, which then come from L2 (on 256 x 128: 16 items of 16 rows 0.149 s per
+    // 2 x 2000 steps, 128 items of 2 rows 0.132 s)
     int rows = c->max_Lz;
     const int64_t cols = [&] { int64_t s = 0; for (auto& p : c->params) s += (p.Lx + 127) / 128; return s; }();
-    while (rows > 16 && cols * ((c->max_Lz + rows - 1) / rows) < 4 * 152) rows /= 2;
+    const int min_rows = c->n_f * rs <= ((size_t)32 << 20) ? 2 : 16;
+    while (rows > min_rows && cols * ((c->max_Lz + rows - 1) / rows) < 4 * 152) rows /= 2;
     rc = build_items(c, 128, rows);
   }
   if (!rc) {
