@@ -74,31 +74,37 @@ __device__ __forceinline__ void all_moments(const real v[9], real m[9]) {
 // The lattice velocities enter through LB_CX / LB_CZ / LB_OPP in fully unrolled loops: as
 // compile-time constants, the products with c = 0 and c = +-1 cost no FP64 instruction.
 
-// Deviations of the 18 populations pulled at (x, z) (Eq. LB; reflected at the walls; the
-// background streaming shift on non-reflected links), as in the forward kernel.
+// Deviations of the 9 populations of species s pulled at (x, z) (Eq. LB; reflected at the walls;
+// the background streaming shift on non-reflected links), as in the forward kernel.
+template <class real>
+__device__ __forceinline__ void pull9(const real* __restrict__ f, int Lx, int Lz, int x, int z, double k9, double k36,
+                                      int s, double v[9]) {
+  const int LzLx = Lx * Lz;
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const int zs = z - LB_CZ(l);
+    const int xs = LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx;
+    double val;
+    if (zs >= 0 && zs < Lz) {
+      val = (double)f[state_index(s, l, zs, xs, Lx, LzLx)];
+      if (LB_CZ(l) != 0) {  // the background shift -c_lz w_l rho_bar d_z c_0 (k9, k36: species A)
+        const double q = l <= 4 ? k9 : k36;
+        const double sh = LB_CZ(l) > 0 ? -q : q;
+        val += s == 0 ? sh : -sh;
+      }
+    } else {
+      val = (double)f[state_index(s, LB_OPP(l), z, x, Lx, LzLx)];
+    }
+    v[l] = val;
+  }
+}
+
+// Both species: v[9 s + l].
 template <class real>
 __device__ __forceinline__ void pull18(const real* __restrict__ f, int Lx, int Lz, int x, int z, double k9, double k36,
                                        double v[18]) {
-  const int LzLx = Lx * Lz;
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const int zs = z - LB_CZ(l);
-      const int xs = LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx;
-      double val;
-      if (zs >= 0 && zs < Lz) {
-        val = (double)f[state_index(s, l, zs, xs, Lx, LzLx)];
-        if (LB_CZ(l) != 0) {  // the background shift -c_lz w_l rho_bar d_z c_0 (k9, k36: species A)
-          const double q = l <= 4 ? k9 : k36;
-          const double sh = LB_CZ(l) > 0 ? -q : q;
-          val += s == 0 ? sh : -sh;
-        }
-      } else {
-        val = (double)f[state_index(s, LB_OPP(l), z, x, Lx, LzLx)];
-      }
-      v[s * 9 + l] = val;
-    }
+  pull9(f, Lx, Lz, x, z, k9, k36, 0, v);
+  pull9(f, Lx, Lz, x, z, k9, k36, 1, v + 9);
 }
 
 // Absolute pre-collision densities of site i = z Lx + x of state f, into rho[i] and rho[N + i].
@@ -428,7 +434,9 @@ __global__ void adj_local_kernel(const real* __restrict__ f, const double* __res
 
 // Gather the neighbour-owed density sensitivities and push along the transposed streaming map.
 // With f_next (the state before f_prev) given, also the densities of f_next into rho_next, for the
-// next adjoint step (one launch instead of two).
+// next adjoint step (one launch instead of two).  Two threads per site, one per species (blocks of
+// 2 kAdjBlock threads over the lattice's adjoint blocks): the species' work is independent but
+// for the fixed-composition ghosts, which mix both.
 template <class real>
 __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowConst<real>* rows,
                                        const AdjConst* __restrict__ kcs, const AdjMap map,
@@ -439,7 +447,7 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowCon
   const LatticeDev<real> L = lat[li];
   const double alpha = sign * kcs[li].w_loss;
   const int Lx = L.Lx, Lz = L.Lz, N = Lx * Lz;
-  const int i = adj_site(map, li);
+  const int t = adj_site(map, li), i = t >> 1, sp = t & 1;  // site, species
   if (i >= N) return;
   rows += L.row_off;
   rho += 2 * L.site_off;
@@ -449,64 +457,56 @@ __global__ void adj_gather_push_kernel(const LatticeDev<real>* lat, const RowCon
   if (f_next) f_next += L.f_off;
   rho_next += 2 * L.site_off;
   const int x = i % Lx, z = i / Lx;
-  if (f_next) site_densities(f_next, L, rows, i, x, z, rho_next);
+  if (f_next) {  // this species' density of f_next at the site
+    double v[9];
+    pull9(f_next, Lx, Lz, x, z, (double)L.k9, (double)L.k36, sp, v);
+    double a = 0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) a += v[l];
+    rho_next[sp * N + i] = (double)(sp == 0 ? rows[z].bgA : rows[z].bgB) + a;
+  }
   const double q = alpha * 0.25 * (double)L.G;
   const bool fixed = L.flags & DF_WALL_FIXED;
-  double rbA = 0, rbB = 0;
+  double rb = 0;
 #pragma unroll
   for (int l = 1; l < 9; ++l) {
     constexpr double w9 = 1.0 / 9, w36 = 1.0 / 36;
     const double w = l <= 4 ? w9 : w36, wc2 = l <= 4 ? w9 : 2 * w36;  // w_l, w_l |c_l|^2
-    // what the site j = (x - c_lx, zs) owes the densities (A, B) its link l reaches
-    auto owed = [&](int zs, double& oa, double& ob) {
+    // what the site j = (x - c_lx, zs) owes the density of species s its link l reaches: through
+    // its neighbour sums of s (sb[2 s], sb[2 s + 1]) and its pressure, which pairs s with the
+    // other species' density there
+    auto owed = [&](int zs, int s) {
       const int j = zs * Lx + (LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx);
-      double ta = 0, tb = 0;
-      if (LB_CX(l) != 0) {
-        ta = LB_CX(l) * sb[0 * N + j];
-        tb = LB_CX(l) * sb[2 * N + j];
-      }
-      if (LB_CZ(l) != 0) {
-        ta = LB_CX(l) != 0 ? ta + LB_CZ(l) * sb[1 * N + j] : LB_CZ(l) * sb[1 * N + j];
-        tb = LB_CX(l) != 0 ? tb + LB_CZ(l) * sb[3 * N + j] : LB_CZ(l) * sb[3 * N + j];
-      }
-      oa = w * ta + (wc2 * q) * rho[N + j];
-      ob = w * tb + (wc2 * q) * rho[j];
+      const double* sx = sb + (2 * s) * N;
+      const double* sz = sb + (2 * s + 1) * N;
+      double ts = 0;
+      if (LB_CX(l) != 0) ts = LB_CX(l) * sx[j];
+      if (LB_CZ(l) != 0) ts = LB_CX(l) != 0 ? ts + LB_CZ(l) * sz[j] : LB_CZ(l) * sz[j];
+      return w * ts + (wc2 * q) * rho[(1 - s) * N + j];
     };
-    double oa, ob;
     const int zs = z - LB_CZ(l);
-    if (zs >= 0 && zs < Lz) {
-      owed(zs, oa, ob);
-      rbA += oa;
-      rbB += ob;
-    }
+    if (zs >= 0 && zs < Lz) rb += owed(zs, sp);
     // the wall ghost next to this row: a copy of this row's densities, or (fixed) this row's total
     // density split by the wall composition
     if ((z == 0 && LB_CZ(l) == -1) || (z == Lz - 1 && LB_CZ(l) == 1)) {
-      owed(z, oa, ob);
       if (fixed) {
-        const double cw = (double)rows[z].ghost_cA, t = cw * oa + (1 - cw) * ob;
-        rbA += t;
-        rbB += t;
+        const double cw = (double)rows[z].ghost_cA;
+        rb += cw * owed(z, 0) + (1 - cw) * owed(z, 1);
       } else {
-        rbA += oa;
-        rbB += ob;
+        rb += owed(z, sp);
       }
     }
   }
   const int64_t LzLx = N;
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const double rb = s == 0 ? rbA : rbB;
-#pragma unroll
-    for (int l = 0; l < 9; ++l) {
-      const double val = fl[(s * 9 + l) * N + i] + rb;
-      const int zs = z - LB_CZ(l);
-      if (zs >= 0 && zs < Lz) {
-        const int xs = LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx;
-        fbar_prev[(s * 9 + l) * LzLx + zs * Lx + xs] = val;
-      } else {
-        fbar_prev[(s * 9 + LB_OPP(l)) * LzLx + z * Lx + x] = val;
-      }
+  for (int l = 0; l < 9; ++l) {
+    const double val = fl[(sp * 9 + l) * N + i] + rb;
+    const int zs = z - LB_CZ(l);
+    if (zs >= 0 && zs < Lz) {
+      const int xs = LB_CX(l) == 0 ? x : (x - LB_CX(l) + Lx) % Lx;
+      fbar_prev[(sp * 9 + l) * LzLx + zs * Lx + xs] = val;
+    } else {
+      fbar_prev[(sp * 9 + LB_OPP(l)) * LzLx + z * Lx + x] = val;
     }
   }
 }
@@ -553,7 +553,7 @@ cudaError_t launch_adjoint_step(const real* f_prev, const real* f_next, const do
   if (noise) options ? local(T(), T()) : local(T(), F());
   else options ? local(F(), T()) : local(F(), F());
   adj_gather_push_kernel<real>
-      <<<nb, kAdjBlock, 0, s>>>(lat, rows, kcs, map, rho, fl, sb, sign, fbar_prev, f_next, rho_next);
+      <<<nb, 2 * kAdjBlock, 0, s>>>(lat, rows, kcs, map, rho, fl, sb, sign, fbar_prev, f_next, rho_next);
   return cudaGetLastError();
 }
 

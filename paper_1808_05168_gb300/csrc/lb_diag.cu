@@ -441,16 +441,29 @@ __global__ void ps_cols_kernel(const Cplx<double>* __restrict__ tmp, int Lx, int
   }
 }
 
+// One warp per lattice: lanes strided over the lattice's items, then a fixed butterfly, so the
+// order of the sums is fixed (deterministic) and a lattice of many items costs a few loads per
+// lane rather than one long chain.
+__device__ __forceinline__ double warp_total(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void finalize_kernel(const DiagLattice* lat, int n_lat, const double* partials, DiagStats* stats) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_lat) return;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n_lat) return;  // the whole warp
   const DiagLattice L = lat[i];
   double p = 0, ma = 0, mb = 0;
-  for (int k = L.item_begin; k < L.item_end; ++k) {
+  for (int k = L.item_begin + lane; k < L.item_end; k += 32) {
     p += partials[3 * k];
     ma += partials[3 * k + 1];
     mb += partials[3 * k + 2];
   }
+  p = warp_total(p);
+  ma = warp_total(ma);
+  mb = warp_total(mb);
+  if (lane != 0) return;
   DiagStats st = stats[i];
   const double P = L.P_bg_mean + p / L.n_sites;
   st.P_last = P;
@@ -634,7 +647,7 @@ cudaError_t launch_sf(const SfPlan& p, const real* fields, void* tmp, double* ac
 
 cudaError_t launch_finalize(const DiagLattice* d_lat, int n_lat, const double* partials, DiagStats* stats,
                             cudaStream_t s) {
-  finalize_kernel<<<(n_lat + 127) / 128, 128, 0, s>>>(d_lat, n_lat, partials, stats);
+  finalize_kernel<<<(n_lat + 3) / 4, 128, 0, s>>>(d_lat, n_lat, partials, stats);  // 4 lattices per block
   return cudaGetLastError();
 }
 
