@@ -1062,28 +1062,62 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grads, double* 
     if (q) owned.push_back(q);
     return q;
   };
+  // the noisy run (index 0) and the noiseless run (1) are independent until their losses and
+  // gradients are combined: each has its own buffers and its own stream, so that their small
+  // kernels overlap on the GPU
+  struct Run {
+    cudaStream_t s = nullptr;
+    real *ck = nullptr, *ring = nullptr, *cur = nullptr, *fields = nullptr, *pfield = nullptr;
+    double *fb = nullptr, *rho = nullptr, *fl = nullptr, *sb = nullptr, *partials = nullptr, *gpart = nullptr;
+    DiagStats* stats = nullptr;
+    int noise = NOISE_OFF;
+    double sign = 1.0;
+    int fcur = 0;
+  } runs[2];
+  cudaStream_t s1 = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   auto release = [&]() {
     cudaStreamSynchronize(st);
+    if (s1) cudaStreamSynchronize(s1);
     for (void* q : owned) dev_free(c, q);
+    if (s1) cudaStreamDestroy(s1);
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
   };
-  real* ck = (real*)alloc(nck * S * sizeof(real));
-  real* ring = want_grad ? (real*)alloc(C * S * sizeof(real)) : nullptr;
-  real* cur = (real*)alloc(2 * S * sizeof(real));
-  double* fb = want_grad ? (double*)alloc(2 * S * sizeof(double)) : nullptr;
-  real* fields = (real*)alloc(4 * NS * sizeof(real));
-  real* pfield = (real*)alloc(NS * sizeof(real));
-  double* rho = want_grad ? (double*)alloc(4 * NS * sizeof(double)) : nullptr;  // two density sets
-  double* fl = want_grad ? (double*)alloc(S * sizeof(double)) : nullptr;
-  double* sb = want_grad ? (double*)alloc(4 * NS * sizeof(double)) : nullptr;
-  double* partials = (double*)alloc((size_t)3 * c->items.size() * sizeof(double));
-  double* gpart = want_grad ? (double*)alloc((size_t)3 * nblk * sizeof(double)) : nullptr;
-  double* d_grad = (double*)alloc((size_t)3 * n * sizeof(double));
-  DiagStats* stats = (DiagStats*)alloc((size_t)n * sizeof(DiagStats));
+  bool got = cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess;
+  if (!got) {
+    release();
+    return LB_ERR_CUDA;
+  }
+  for (int q = 0; q < 2; ++q) {
+    Run& R = runs[q];
+    R.s = q == 0 ? st : s1;
+    R.noise = q == 0 ? c->noise_mode : NOISE_OFF;
+    R.sign = q == 0 ? 1.0 : -1.0;
+    R.ck = (real*)alloc(nck * S * sizeof(real));
+    R.cur = (real*)alloc(2 * S * sizeof(real));
+    R.fields = (real*)alloc(4 * NS * sizeof(real));
+    R.pfield = (real*)alloc(NS * sizeof(real));
+    R.partials = (double*)alloc((size_t)3 * c->items.size() * sizeof(double));
+    R.stats = (DiagStats*)alloc((size_t)n * sizeof(DiagStats));
+    got = got && R.ck && R.cur && R.fields && R.pfield && R.partials && R.stats;
+    if (want_grad) {
+      R.ring = (real*)alloc(C * S * sizeof(real));
+      R.fb = (double*)alloc(2 * S * sizeof(double));
+      R.rho = (double*)alloc(4 * NS * sizeof(double));  // two density sets
+      R.fl = (double*)alloc(S * sizeof(double));
+      R.sb = (double*)alloc(4 * NS * sizeof(double));
+      R.gpart = (double*)alloc((size_t)3 * nblk * sizeof(double));
+      got = got && R.ring && R.fb && R.rho && R.fl && R.sb && R.gpart;
+    }
+  }
+  double* d_grad = (double*)alloc((size_t)6 * n * sizeof(double));  // per run
   int64_t* zero_t = (int64_t*)alloc(sizeof(int64_t));
   int* d_map = want_grad ? (int*)alloc((size_t)(nblk + n + 1) * sizeof(int)) : nullptr;
   AdjConst* d_kcs = want_grad ? (AdjConst*)alloc((size_t)n * sizeof(AdjConst)) : nullptr;
-  if (!ck || (want_grad && (!ring || !fb || !rho || !fl || !sb || !gpart || !d_map || !d_kcs)) || !cur || !fields ||
-      !pfield || !partials || !d_grad || !stats || !zero_t) {
+  if (!got || !d_grad || !zero_t || (want_grad && (!d_map || !d_kcs))) {
     release();
     return LB_ERR_OOM;
   }
@@ -1100,86 +1134,96 @@ int pressure_shift_impl(lb_ctx* c, int64_t T, int64_t C, double* grads, double* 
     map.first = d_map + nblk;
   }
   ok(cudaMemsetAsync(zero_t, 0, sizeof(int64_t), st));
-  ok(cudaMemsetAsync(d_grad, 0, (size_t)3 * n * sizeof(double), st));
-  if (want_grad) ok(cudaMemsetAsync(gpart, 0, (size_t)3 * nblk * sizeof(double), st));
-  auto args = [&](const real* src, real* dst, int64_t k) {
+  ok(cudaMemsetAsync(d_grad, 0, (size_t)6 * n * sizeof(double), st));
+  ok(cudaEventRecord(ev[0], st));  // the second run's stream starts after the set-up
+  ok(cudaStreamWaitEvent(s1, ev[0], 0));
+  auto args = [&](const Run& R, const real* src, real* dst, int64_t k) {
     StepArgs<real> a = step_args<real>(c, 0, 0);
     a.src = src;
     a.dst = dst;
     a.tmaps = nullptr;  // the context's tensor maps describe its own state buffers, not these
     a.d_t = zero_t;
     a.t_offset = (int)k;
-    a.fields = fields;
-    a.pfield = pfield;
-    a.partials = partials;
+    a.fields = R.fields;
+    a.pfield = R.pfield;
+    a.partials = R.partials;
     return a;
   };
-  std::vector<double> L0(n, 0.0), L1(n, 0.0);
-  std::vector<DiagStats> hs(n);
-  for (int run = 0; run < 2 && e == cudaSuccess; ++run) {
-    const int noise = run == 0 ? c->noise_mode : NOISE_OFF;
-    NvtxRange rr(run == 0 ? "lb adjoint: noisy run" : "lb adjoint: noiseless run");
-    // forward from rest: checkpoints f*_{c-1} before every C-th step, pressure of every step
-    for (int i = 0; i < n; ++i) {
-      const lb_params& p = c->params[i];
-      const BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
-      ok(launch_init_rest<real>(cur + c->f_off[i], bp, st));
-    }
-    ok(cudaMemsetAsync(stats, 0, (size_t)n * sizeof(DiagStats), st));
-    for (int64_t k = 0; k < T && e == cudaSuccess; ++k) {
-      real* src = cur + (k & 1) * S;
-      real* dst = cur + ((k + 1) & 1) * S;
-      if (k % C == 0) ok(cudaMemcpyAsync(ck + (k / C) * S, src, S * sizeof(real), cudaMemcpyDeviceToDevice, st));
-      ok(launch_step<real>(args(src, dst, k), c->tile_x, true, noise, c->bulk_ok, st));
-      ok(launch_finalize(c->d_diag, n, partials, stats, st));
-    }
-    ok(cudaMemcpyAsync(hs.data(), stats, (size_t)n * sizeof(DiagStats), cudaMemcpyDeviceToHost, st));
-    ok(cudaStreamSynchronize(st));
-    if (e != cudaSuccess) break;
-    for (int i = 0; i < n; ++i) {
-      if (hs[i].nonfinite) {
-        release();
-        return LB_ERR_NONFINITE;
+  // forward runs from rest, step by step in both streams: checkpoints f*_{c-1} before every C-th
+  // step, pressure of every step
+  {
+    NvtxRange rr("lb adjoint: forward runs");
+    for (Run& R : runs) {
+      if (want_grad) ok(cudaMemsetAsync(R.gpart, 0, (size_t)3 * nblk * sizeof(double), R.s));
+      for (int i = 0; i < n; ++i) {
+        const lb_params& p = c->params[i];
+        const BgParams bp{p.Lx, p.Lz, c->dev32 ? 1 : 0, kRhoBar, p.grad_c0};
+        ok(launch_init_rest<real>(R.cur + c->f_off[i], bp, R.s));
       }
-      (run == 0 ? L0 : L1)[i] = (hs[i].P_sum + hs[i].P_comp) / (double)T;
+      ok(cudaMemsetAsync(R.stats, 0, (size_t)n * sizeof(DiagStats), R.s));
     }
-    if (!want_grad) continue;
-    // reverse sweep, one checkpoint segment at a time; the run's sign (+ noisy, - noiseless)
-    // enters through the loss weight alpha = sign / (T N) of each lattice, to which the whole
-    // sweep is linear
-    const double sign = run == 0 ? 1.0 : -1.0;
-    int fcur = 0;
-    ok(cudaMemsetAsync(fb, 0, S * sizeof(double), st));
+    for (int64_t k = 0; k < T && e == cudaSuccess; ++k)
+      for (Run& R : runs) {
+        real* src = R.cur + (k & 1) * S;
+        real* dst = R.cur + ((k + 1) & 1) * S;
+        if (k % C == 0)
+          ok(cudaMemcpyAsync(R.ck + (k / C) * S, src, S * sizeof(real), cudaMemcpyDeviceToDevice, R.s));
+        ok(launch_step<real>(args(R, src, dst, k), c->tile_x, true, R.noise, c->bulk_ok, R.s));
+        ok(launch_finalize(c->d_diag, n, R.partials, R.stats, R.s));
+      }
+  }
+  // reverse sweeps, one checkpoint segment at a time in both streams; a run's sign (+ noisy,
+  // - noiseless) enters through the loss weight alpha = sign / (T N) of each lattice, to which the
+  // whole sweep is linear
+  if (want_grad && e == cudaSuccess) {
+    NvtxRange rr("lb adjoint: reverse sweeps");
+    for (Run& R : runs) ok(cudaMemsetAsync(R.fb, 0, S * sizeof(double), R.s));
     for (int64_t seg = nck - 1; seg >= 0 && e == cudaSuccess; --seg) {
       const int64_t c0 = seg * C, len = std::min<int64_t>(C, T - c0);
-      ok(cudaMemcpyAsync(ring, ck + seg * S, S * sizeof(real), cudaMemcpyDeviceToDevice, st));
-      for (int64_t i = 1; i < len; ++i)
-        ok(launch_step<real>(args(ring + (i - 1) * S, ring + i * S, c0 + i - 1), c->tile_x, false, noise, c->bulk_ok,
-                             st));
+      for (Run& R : runs) {
+        ok(cudaMemcpyAsync(R.ring, R.ck + seg * S, S * sizeof(real), cudaMemcpyDeviceToDevice, R.s));
+        for (int64_t i = 1; i < len; ++i)
+          ok(launch_step<real>(args(R, R.ring + (i - 1) * S, R.ring + i * S, c0 + i - 1), c->tile_x, false, R.noise,
+                               c->bulk_ok, R.s));
+      }
       // the densities of each step's state come with the previous step's gather (within a
       // segment; at its top they are computed on their own)
       int rcur = 0;
       for (int64_t k = c0 + len - 1; k >= c0 && e == cudaSuccess; --k) {
-        double* rho_k = rho + (size_t)rcur * 2 * NS;
-        double* rho_n = rho + (size_t)(1 - rcur) * 2 * NS;
-        ok(launch_adjoint_step<real>(ring + (k - c0) * S, k > c0 ? ring + (k - 1 - c0) * S : nullptr, fb + fcur * S,
-                                     fb + (1 - fcur) * S, (const LatticeDev<real>*)c->d_lat,
-                                     (const RowConst<real>*)c->d_rows, d_kcs, options, map, (uint32_t)k,
-                                     noise != NOISE_OFF, sign, k < c0 + len - 1, rho_k, rho_n, fl, sb, gpart, st));
-        fcur = 1 - fcur;
+        for (Run& R : runs) {
+          double* rho_k = R.rho + (size_t)rcur * 2 * NS;
+          double* rho_n = R.rho + (size_t)(1 - rcur) * 2 * NS;
+          ok(launch_adjoint_step<real>(R.ring + (k - c0) * S, k > c0 ? R.ring + (k - 1 - c0) * S : nullptr,
+                                       R.fb + R.fcur * S, R.fb + (1 - R.fcur) * S, (const LatticeDev<real>*)c->d_lat,
+                                       (const RowConst<real>*)c->d_rows, d_kcs, options, map, (uint32_t)k,
+                                       R.noise != NOISE_OFF, R.sign, k < c0 + len - 1, rho_k, rho_n, R.fl, R.sb,
+                                       R.gpart, R.s));
+          R.fcur = 1 - R.fcur;
+        }
         rcur = 1 - rcur;
       }
     }
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+      ok(launch_adjoint_gradient(runs[q].gpart, map, d_grad + (size_t)3 * n * q, runs[q].s));
   }
-  if (e == cudaSuccess && want_grad) {
-    ok(launch_adjoint_gradient(gpart, map, d_grad, st));
-    ok(cudaMemcpyAsync(grads, d_grad, (size_t)3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    ok(cudaStreamSynchronize(st));
-  }
+  // join the second stream, then read the results
+  ok(cudaEventRecord(ev[1], s1));
+  ok(cudaStreamWaitEvent(st, ev[1], 0));
+  std::vector<DiagStats> hs(2 * (size_t)n);
+  std::vector<double> hg(6 * (size_t)n, 0.0);
+  ok(cudaMemcpyAsync(hs.data(), runs[0].stats, (size_t)n * sizeof(DiagStats), cudaMemcpyDeviceToHost, st));
+  ok(cudaMemcpyAsync(hs.data() + n, runs[1].stats, (size_t)n * sizeof(DiagStats), cudaMemcpyDeviceToHost, st));
+  if (want_grad) ok(cudaMemcpyAsync(hg.data(), d_grad, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ok(cudaStreamSynchronize(st));
   release();
   if (e != cudaSuccess) return cuda_err(e);
-  if (losses)
-    for (int i = 0; i < n; ++i) losses[i] = L0[i] - L1[i];
+  for (const DiagStats& x : hs)
+    if (x.nonfinite) return LB_ERR_NONFINITE;
+  for (int i = 0; i < n; ++i) {
+    if (losses) losses[i] = (hs[i].P_sum + hs[i].P_comp) / (double)T - (hs[n + i].P_sum + hs[n + i].P_comp) / (double)T;
+    if (want_grad)
+      for (int k = 0; k < 3; ++k) grads[3 * i + k] = hg[3 * i + k] + hg[(size_t)3 * n + 3 * i + k];
+  }
   int err = 0;
   if (cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && err) {
     cudaMemset(c->d_err, 0, sizeof(int));
