@@ -268,8 +268,10 @@ int lb_power_spectrum_noalloc(const double* field, int Lx, int Lz, double* out, 
  * Requires a single-lattice context (LB_ERR_STATE otherwise); every option of the step is
  * differentiated: a* on or off (LB_NO_ASTAR), copy-rule or fixed-composition wall ghosts
  * (LB_WALL_FIXED), hom or loc noise (LB_NOISE_LOC, whose amplitudes follow the local densities).
- * Device memory: about (steps/ckpt_every + ckpt_every + 5)
- * states, allocated for the call and freed before it returns.  Synchronous. */
+ * The runs with and without noise are independent until they are combined and run on two
+ * streams (the context's and one of the call's own), each with its own buffers.  Device memory:
+ * about 2 (steps/ckpt_every + ckpt_every + 5) states, allocated for the call and freed before it
+ * returns.  Synchronous. */
 int lb_pressure_shift_gradient(lb_ctx* ctx, int64_t steps, int64_t ckpt_every, double grad[3], double* loss);
 
 /* lb_pressure_shift_gradient for every lattice of a batch in one sweep: each lattice's own loss
